@@ -1,0 +1,271 @@
+"""CPU oracle for the adaptive SIS permanent estimator (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``pm_oracle.c`` (plain C, no
+code shared with the CUDA library) through ctypes.  Matrices are passed as any
+object with ``n``, ``row_ptr`` (int64), ``col_idx`` (int32) and ``values``
+(float32 or None).
+
+Parity status of each function (what pins it lives in tests/test_oracle_*.py):
+  philox4x32_10        pinned: published known-answer vectors
+  ryser / ryser_real   pinned: brute force over S_n, closed forms
+  run / stats          pinned: exhaustive trajectory enumeration (sum of
+                       P(path) X(path) equals per), all-ones closed form,
+                       hand-worked steps, statistics closed forms
+  dm_mask              pinned: brute-force support test per edge
+  sk_full              pinned: k-regular closed form, doubly-stochastic limit
+  local repair         pinned: hand-computed Eq. 5 example
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pm_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+VR_MIN_DEGREE_2SIDED, VR_ROW_ORDER = 0, 1
+SK_NONE, SK_FIXED, SK_ADAPTIVE, SK_LOCAL = 0, 1, 2, 3
+DM_NONE, DM_ALL, DM_THRS, DM_TRCK = 0, 1, 2, 3
+PREC_FP32, PREC_FP64 = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile pm_oracle.c into _build/liboracle.so (gcc, no fast-math, no
+    FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Schedule(C.Structure):
+    _fields_ = [("vertex_rule", C.c_int32), ("initial_dm", C.c_int32), ("K0", C.c_int32),
+                ("K", C.c_int32), ("sk", C.c_int32), ("dm", C.c_int32),
+                ("precision", C.c_int32), ("pad", C.c_int32), ("theta", C.c_double)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("log_estimate", C.c_double), ("p_match", C.c_double),
+                ("rel_spread", C.c_double), ("rse", C.c_double), ("ess", C.c_double),
+                ("log_sum_x", C.c_double), ("log_sum_x2", C.c_double), ("n_alive", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.c_void_p
+        L.or_philox4x32_10.argtypes = [P, P, P]
+        L.or_draw_u64.restype = C.c_uint64
+        L.or_draw_u64.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
+        L.or_uniform_below.restype = C.c_int64
+        L.or_uniform_below.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32]
+        L.or_ryser_int.argtypes = [C.c_int, P, P, P]
+        L.or_ryser_real_d.restype = C.c_double
+        L.or_ryser_real_d.argtypes = [C.c_int, P]
+        L.or_prepare.restype = P
+        L.or_prepare.argtypes = [C.c_int, C.c_int64, P, P, P, C.POINTER(_Schedule)]
+        L.or_prep_free.argtypes = [P]
+        L.or_prep_ok.restype = C.c_int
+        L.or_prep_ok.argtypes = [P]
+        L.or_prep_scaling.argtypes = [P, P, P]
+        L.or_prep_mask.argtypes = [P, P]
+        L.or_forced_run.restype = C.c_int
+        L.or_forced_run.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P]
+        L.or_run.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
+                             P, P, P, P, P]
+        L.or_dm_mask.restype = C.c_int
+        L.or_dm_mask.argtypes = [P, P]
+        L.or_sk_full.argtypes = [P, C.c_int, P, P]
+        L.or_statistics.argtypes = [P, C.c_int64, C.POINTER(_Stats)]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------------------
+# random numbers and exact permanents
+# ---------------------------------------------------------------------------
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return [int(x) for x in o]
+
+
+def draw_u64(seed, traj, matrix, step, attempt) -> int:
+    return int(lib().or_draw_u64(seed, traj, matrix, step, attempt))
+
+
+def uniform_below(W, seed, traj, matrix, step) -> int:
+    return int(lib().or_uniform_below(W, seed, traj, matrix, step))
+
+
+def ryser(dense) -> int:
+    """Exact permanent of an integer matrix (n <= 30), Ryser's formula."""
+    a = np.ascontiguousarray(np.asarray(dense).round().astype(np.int64))
+    n = a.shape[0]
+    hi, lo = C.c_uint64(), C.c_uint64()
+    lib().or_ryser_int(n, _ptr(a), C.byref(hi), C.byref(lo))
+    v = (hi.value << 64) | lo.value
+    if v >= 1 << 127:
+        v -= 1 << 128
+    return v
+
+
+def ryser_real(dense) -> float:
+    a = np.ascontiguousarray(np.asarray(dense, dtype=np.float64))
+    return float(lib().or_ryser_real_d(a.shape[0], _ptr(a)))
+
+
+# ---------------------------------------------------------------------------
+# the estimator
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Schedule:
+    vertex_rule: int = VR_MIN_DEGREE_2SIDED
+    initial_dm: int = 0
+    K0: int = 0
+    K: int = 0
+    sk: int = SK_NONE
+    dm: int = DM_NONE
+    precision: int = PREC_FP64
+    theta: float = 0.33
+
+    def c(self) -> _Schedule:
+        return _Schedule(self.vertex_rule, self.initial_dm, self.K0, self.K, self.sk, self.dm,
+                         self.precision, 0, self.theta)
+
+
+PRESETS = {
+    # the five variants of Sec. 4: two-sided MD, K0=100, K=10, initial DM
+    "fixed_all": dict(sk=SK_FIXED, dm=DM_ALL),
+    "adaptive_threshold": dict(sk=SK_ADAPTIVE, dm=DM_THRS),
+    "local_threshold": dict(sk=SK_LOCAL, dm=DM_THRS),
+    "adaptive_tracked": dict(sk=SK_ADAPTIVE, dm=DM_TRCK),
+    "local_tracked": dict(sk=SK_LOCAL, dm=DM_TRCK),
+}
+
+
+def preset(name: str, precision: int = PREC_FP64) -> Schedule:
+    return Schedule(initial_dm=1, K0=100, K=10, theta=0.33, precision=precision, **PRESETS[name])
+
+
+class Prepared:
+    """Preprocessing of Algorithm 2 for one matrix (InitialDM + K0 SK)."""
+
+    def __init__(self, csr, sched: Schedule):
+        self.n = int(csr.n)
+        self.rp = np.ascontiguousarray(csr.row_ptr, dtype=np.int64)
+        self.ci = np.ascontiguousarray(csr.col_idx, dtype=np.int32)
+        self.val = None if csr.values is None else np.ascontiguousarray(csr.values, dtype=np.float32)
+        self.m = int(self.rp[-1])
+        self.sched = sched
+        self._s = sched.c()
+        self.h = lib().or_prepare(self.n, self.m, _ptr(self.rp), _ptr(self.ci), _ptr(self.val),
+                                  C.byref(self._s))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_prep_free(self.h)
+            self.h = None
+
+    @property
+    def ok(self) -> bool:
+        return bool(lib().or_prep_ok(self.h))
+
+    def scaling(self):
+        r = np.zeros(self.n)
+        c = np.zeros(self.n)
+        lib().or_prep_scaling(self.h, _ptr(r), _ptr(c))
+        return r, c
+
+    def mask(self):
+        m = np.zeros(self.m, dtype=np.uint8)
+        lib().or_prep_mask(self.h, _ptr(m))
+        return m
+
+    def run(self, seed: int, count: int, first_traj: int = 0, matrix: int = 0,
+            threads: int = 1, trace: bool = False):
+        """Run trajectories first_traj .. first_traj+count-1.  Returns a dict
+        with log_x, dead_step, op counts and (trace) chosen [count, n, 2]
+        unified ids (v, u) and deg_v [count, n]."""
+        lx = np.zeros(count)
+        ds = np.zeros(count, dtype=np.int32)
+        ch = np.zeros((count, self.n, 2), dtype=np.int32) if trace else None
+        dv = np.zeros((count, self.n), dtype=np.int32) if trace else None
+        oc = np.zeros(3, dtype=np.int64)
+        lib().or_run(self.h, seed, matrix, first_traj, count, threads, _ptr(lx), _ptr(ds),
+                     _ptr(ch), _ptr(dv), _ptr(oc))
+        out = dict(log_x=lx, dead_step=ds, n_dm=int(oc[0]), n_full_sk=int(oc[1]),
+                   n_local_sk=int(oc[2]))
+        if trace:
+            out["chosen"] = ch
+            out["deg_v"] = dv
+        return out
+
+    def forced(self, choices):
+        """Replay with forced candidate indices.  Returns ("need", w[], W,
+        log_x_prefix, info) when the choices run out before the trajectory
+        ends, else ("done", log_x, dead_step, info); info holds the chosen
+        (v, u) pairs so far and the DM / full-SK / local-SK counts."""
+        ch = np.ascontiguousarray(choices, dtype=np.int32)
+        w = np.zeros(max(1, self.n), dtype=np.uint64)
+        W = C.c_uint64()
+        nc = C.c_int32()
+        lx = C.c_double()
+        ds = C.c_int32()
+        chosen = np.zeros((max(1, self.n), 2), dtype=np.int32)
+        counts = np.zeros(3, dtype=np.int32)
+        need = lib().or_forced_run(self.h, _ptr(ch), len(ch), _ptr(w), C.byref(W), C.byref(nc),
+                                   C.byref(lx), C.byref(ds), _ptr(chosen), _ptr(counts))
+        info = dict(chosen=chosen[: self.n], n_dm=int(counts[0]), n_full_sk=int(counts[1]),
+                    n_local_sk=int(counts[2]))
+        if need:
+            return ("need", [int(x) for x in w[: nc.value]], int(W.value), lx.value, info)
+        return ("done", lx.value, ds.value, info)
+
+
+def dm_mask(csr):
+    """Supported-edge mask of a whole matrix (Sec. 2 DM); None if the matrix
+    has no perfect matching."""
+    P = Prepared(csr, Schedule())
+    m = np.zeros(P.m, dtype=np.uint8)
+    ok = lib().or_dm_mask(P.h, _ptr(m))
+    return m if ok else None
+
+
+def sk_full(csr, iters: int, precision: int = PREC_FP64):
+    P = Prepared(csr, Schedule(precision=precision))
+    r = np.zeros(P.n)
+    c = np.zeros(P.n)
+    lib().or_sk_full(P.h, iters, _ptr(r), _ptr(c))
+    return r, c
+
+
+def stats(log_x) -> dict:
+    a = np.ascontiguousarray(log_x, dtype=np.float64)
+    s = _Stats()
+    lib().or_statistics(_ptr(a), a.size, C.byref(s))
+    return dict(log_estimate=s.log_estimate, p_match=s.p_match, rel_spread=s.rel_spread,
+                rse=s.rse, ess=s.ess, log_sum_x=s.log_sum_x, log_sum_x2=s.log_sum_x2,
+                n_alive=int(s.n_alive), n_traj=int(a.size))

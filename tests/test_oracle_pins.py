@@ -1,0 +1,434 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, the definition of the permanent (Eq. 1) by brute force,
+closed forms, exhaustive enumeration of every trajectory (unbiasedness,
+Sec. 2: E[X] = per(A)), hand-worked fixtures under tests/golden/, and the
+brute-force definition of a supported edge (Sec. 2, DM).
+"""
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_15390_b300 import inputs as G
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# brute-force helpers written from the definitions (no oracle code)
+# ---------------------------------------------------------------------------
+
+def per_bruteforce(d):
+    """Eq. 1: sum over permutations of the product of entries."""
+    n = d.shape[0]
+    tot = 0.0
+    for p in itertools.permutations(range(n)):
+        prod = 1.0
+        for i in range(n):
+            prod *= d[i, p[i]]
+            if prod == 0:
+                break
+        tot += prod
+    return tot
+
+
+def perfect_matchings(d):
+    n = d.shape[0]
+    return [p for p in itertools.permutations(range(n)) if all(d[i, p[i]] != 0 for i in range(n))]
+
+
+def random_small(n, p, seed, weighted=False, planted=True):
+    rng = np.random.default_rng(seed)
+    dense = rng.random((n, n)) < p
+    if planted:
+        dense[np.arange(n), rng.permutation(n)] = True
+    if weighted:
+        w = rng.uniform(1.0, 1.5, size=(n, n)).astype(np.float32)
+        r, c = np.nonzero(dense)
+        return G.csr_from_coo(n, r, c, w[r, c])
+    return G.csr_from_dense(dense)
+
+
+# ---------------------------------------------------------------------------
+# Philox and the bounded draw
+# ---------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        vals = [int(x, 16) for x in r]
+        assert O.philox4x32_10(vals[:4], vals[4:6]) == vals[6:10]
+
+
+def test_draw_word_layout():
+    # the draw layout is a reading of this build (the paper fixes no RNG):
+    # attempt 2a -> words 0,1 and 2a+1 -> words 2,3 of block a
+    seed, traj, mat, step = 0x1234_5678_9ABC_DEF0, (7 << 32) | 99, 3, 11
+    blk = O.philox4x32_10([99, 7 | (3 << 16), 11, 2], [0x9ABCDEF0, 0x12345678])
+    assert O.draw_u64(seed, traj, mat, step, 4) == (blk[0] << 32) | blk[1]
+    assert O.draw_u64(seed, traj, mat, step, 5) == (blk[2] << 32) | blk[3]
+
+
+def test_uniform_below_power_of_two_is_top_bits():
+    # W = 2^k never rejects; the result is the top k bits of the first draw
+    for k in (1, 5, 39):
+        u = O.draw_u64(5, 17, 0, 3, 0)
+        assert O.uniform_below(1 << k, 5, 17, 0, 3) == u >> (64 - k)
+
+
+def test_uniform_below_is_uniform():
+    W = 7
+    counts = np.zeros(W)
+    N = 70000
+    for t in range(N):
+        x = O.uniform_below(W, 1, t, 0, 0)
+        assert 0 <= x < W
+        counts[x] += 1
+    chi2 = ((counts - N / W) ** 2 / (N / W)).sum()
+    assert chi2 < 22.5  # 6 dof, p ~ 0.001
+
+
+# ---------------------------------------------------------------------------
+# exact permanents (Eq. 1, Ryser)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_ryser_matches_definition(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 8))
+    d = (rng.random((n, n)) < 0.6).astype(np.int64)
+    assert O.ryser(d) == round(per_bruteforce(d.astype(float)))
+    w = rng.uniform(0.5, 2.0, size=(n, n)) * (rng.random((n, n)) < 0.7)
+    assert O.ryser_real(w) == pytest.approx(per_bruteforce(w), rel=1e-12)
+
+
+def test_ryser_closed_forms():
+    for n in range(1, 13):
+        assert O.ryser(np.ones((n, n))) == math.factorial(n)           # per(J_n) = n!
+    fib = [0, 1, 1]
+    for _ in range(30):
+        fib.append(fib[-1] + fib[-2])
+    for n in range(1, 20):
+        assert O.ryser(G.tridiagonal(n).to_dense()) == fib[n + 1]      # F_{n+1}
+        assert O.ryser(G.upper_triangular(n).to_dense()) == 1
+        assert O.ryser(G.permutation(n, n).to_dense()) == 1
+
+
+def test_block_diagonal_product():
+    m = G.block_diagonal(40, 0.5, seed=3)
+    prod = 1
+    for b in m.blocks:
+        prod *= O.ryser(b)
+    assert len(m.blocks) == 2 and prod > 0
+    # the permuted full matrix must have the same permanent (n = 40 is too big
+    # for Ryser; check a 2x20-block instance through the per-block identity)
+    small = G.block_diagonal(45, 0.6, seed=4)
+    assert sorted(b.shape[0] for b in small.blocks) == [20, 25]
+
+
+# ---------------------------------------------------------------------------
+# exhaustive trajectory enumeration: E[X] = per(A) (Sec. 2), for every schedule
+# ---------------------------------------------------------------------------
+
+def enumerate_paths(P):
+    leaves = []
+    stack = [([], Fraction(1))]
+    while stack:
+        prefix, prob = stack.pop()
+        r = P.forced(prefix)
+        if r[0] == "need":
+            _, w, W, _, _ = r
+            assert sum(w) == W and all(x >= 1 for x in w)
+            for k, wk in enumerate(w):
+                stack.append((prefix + [k], prob * Fraction(wk, W)))
+        else:
+            _, lx, ds, info = r
+            leaves.append((prob, lx, ds, info["chosen"].copy()))
+    return leaves
+
+
+SCHEDULES = {
+    "plain_md": O.Schedule(),
+    "plain_row_order": O.Schedule(vertex_rule=O.VR_ROW_ORDER),
+    "md_outer_sk": O.Schedule(K0=20),
+    "md_initial_dm": O.Schedule(initial_dm=1),
+    "fixed_all": O.preset("fixed_all"),
+    "adaptive_threshold": O.preset("adaptive_threshold"),
+    "local_threshold": O.preset("local_threshold"),
+    "adaptive_tracked": O.preset("adaptive_tracked"),
+    "local_tracked": O.preset("local_tracked"),
+    "local_threshold_fp32": O.preset("local_threshold", precision=O.PREC_FP32),
+    "adaptive_threshold_fp32": O.preset("adaptive_threshold", precision=O.PREC_FP32),
+    "fixed_none_fp32": O.Schedule(K0=5, K=3, sk=O.SK_FIXED, precision=O.PREC_FP32),
+}
+
+
+@pytest.mark.parametrize("name", list(SCHEDULES))
+@pytest.mark.parametrize("case", [(5, 0.5, 1, False), (6, 0.45, 2, False), (5, 0.6, 3, True),
+                                  (6, 0.35, 4, True)])
+def test_enumeration_is_unbiased(name, case):
+    n, p, seed, weighted = case
+    A = random_small(n, p, seed, weighted)
+    d = A.to_dense()
+    P = O.Prepared(A, SCHEDULES[name])
+    leaves = enumerate_paths(P)
+    assert sum(l[0] for l in leaves) == 1
+    per = per_bruteforce(d)
+    est = 0.0
+    done = []
+    for prob, lx, ds, chosen in leaves:
+        if ds >= 0:
+            assert lx == -math.inf
+            continue
+        # each completed leaf is a perfect matching; P(path) * X(path) is the
+        # product of its entries (the importance correction cancels q exactly)
+        rows = np.where(chosen[:, 0] < n, chosen[:, 0], chosen[:, 1])
+        cols = np.where(chosen[:, 0] < n, chosen[:, 1], chosen[:, 0]) - n
+        perm = [0] * n
+        for r_, c_ in zip(rows, cols):
+            perm[r_] = c_
+        prodB = np.prod([d[i, perm[i]] for i in range(n)])
+        assert float(prob) * math.exp(lx) == pytest.approx(prodB, rel=1e-12)
+        done.append(tuple(perm))
+        est += float(prob) * math.exp(lx)
+    # every perfect matching is reached by exactly one completed path
+    assert sorted(done) == sorted(perfect_matchings(d))
+    assert est == pytest.approx(per, rel=1e-12)
+    if SCHEDULES[name].dm == O.DM_ALL:
+        assert all(ds < 0 for _, _, ds, _ in leaves)  # DM on every child: p_match = 1
+
+
+def test_enumeration_zero_permanent():
+    d = np.zeros((4, 4))
+    d[0, :] = 1
+    d[1, 0] = d[2, 0] = d[3, 0] = 1        # rows 1..3 share one column: per = 0
+    A = G.csr_from_dense(d)
+    leaves = enumerate_paths(O.Prepared(A, O.Schedule()))
+    assert all(ds >= 0 for _, _, ds, _ in leaves)
+    P = O.Prepared(A, O.Schedule(initial_dm=1))
+    assert not P.ok
+    res = P.run(1, 10)
+    assert np.all(res["log_x"] == -np.inf)
+
+
+# ---------------------------------------------------------------------------
+# hand-worked fixtures
+# ---------------------------------------------------------------------------
+
+def _read_md_paths():
+    cases, cur = [], None
+    for line in open(os.path.join(GOLD, "md_paths.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        tok = line.split()
+        if tok[0] == "matrix":
+            cur = dict(n=int(tok[2]), rows=[], steps=[])
+            cases.append(cur)
+        elif tok[0] == "row":
+            cur["rows"].append([int(x) for x in tok[1:]])
+        elif tok[0] == "forced":
+            cur["forced"] = [int(x) for x in tok[1:]]
+        elif tok[0] == "step":
+            cur["steps"].append([int(x) for x in tok[1:]])
+        elif tok[0] == "logx":
+            cur["logx"] = float(tok[1])
+    return cases
+
+
+def test_md_pick_hand_worked():
+    for case in _read_md_paths():
+        n = case["n"]
+        rows = np.repeat(np.arange(n), [len(r) for r in case["rows"]])
+        A = G.csr_from_coo(n, rows, np.concatenate(case["rows"]))
+        P = O.Prepared(A, O.Schedule())
+        kind, lx, ds, info = P.forced(case["forced"])
+        assert kind == "done" and ds == -1
+        for t, v, u, dv in case["steps"]:
+            assert tuple(info["chosen"][t]) == (v, u)
+        assert lx == pytest.approx(case["logx"], rel=1e-15)
+        # the deg_v trace of a Philox-driven run follows the same rule
+        res = P.run(seed=3, count=50, trace=True)
+        assert np.all(res["deg_v"][:, 0] == case["steps"][0][3])
+
+
+def test_local_repair_hand_worked():
+    lines = [l.split() for l in open(os.path.join(GOLD, "local_repair.txt"))
+             if l.strip() and not l.startswith("#")]
+    forced = [int(x) for x in lines[0][1:]]
+    want = {l[0]: [int(x) for x in l[1:]] for l in lines[1:]}
+    A = G.csr_from_coo(4, [0, 0, 0, 1, 1, 2, 2, 2, 3, 3], [0, 1, 2, 0, 1, 1, 2, 3, 2, 3])
+    for prec, key in ((O.PREC_FP64, "w_fp64"), (O.PREC_FP32, "w_fp32")):
+        P = O.Prepared(A, O.Schedule(sk=O.SK_LOCAL, precision=prec))
+        kind, w, W, _, info = P.forced(forced)
+        assert kind == "need"
+        assert tuple(info["chosen"][0]) == (1, 4)
+        assert w == want[key] and W == sum(want[key])
+        assert info["n_local_sk"] == 1
+
+
+def test_adaptive_sweep_count_regular():
+    # circulant 3-regular: one outer SK sweep gives c = 1/3, r = 1, so the
+    # first step has z = 1/3 and Adaptive runs ceil((1 - 1/3) * 10) = 7 sweeps
+    A = G.circulant(7, 3)
+    for prec in (O.PREC_FP64, O.PREC_FP32):
+        P = O.Prepared(A, O.Schedule(K0=1, K=10, sk=O.SK_ADAPTIVE, precision=prec))
+        kind, *_, info = P.forced([0])
+        assert kind == "need" and info["n_full_sk"] == 7
+        # Thrs at 0.33 does not fire for z = 1/3; for a 4-regular matrix it does
+        P = O.Prepared(A, O.Schedule(K0=1, K=10, sk=O.SK_NONE, dm=O.DM_THRS, precision=prec))
+        assert P.forced([0])[-1]["n_dm"] == 0
+        P = O.Prepared(G.circulant(7, 4),
+                       O.Schedule(K0=1, sk=O.SK_NONE, dm=O.DM_THRS, precision=prec))
+        assert P.forced([0])[-1]["n_dm"] == 1
+        # Trck: track = (1/3)(...) drops below 0.33 on the second step
+        P = O.Prepared(A, O.Schedule(K0=1, sk=O.SK_NONE, dm=O.DM_TRCK, precision=prec))
+        assert P.forced([0])[-1]["n_dm"] == 0
+        assert P.forced([0, 0])[-1]["n_dm"] == 1
+
+
+# ---------------------------------------------------------------------------
+# closed forms of whole runs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [O.PREC_FP64, O.PREC_FP32])
+def test_all_ones_every_trajectory_is_n_factorial(prec):
+    n = 9
+    for sched in (O.Schedule(precision=prec), O.preset("local_threshold", prec),
+                  O.preset("adaptive_tracked", prec)):
+        P = O.Prepared(G.all_ones(n), sched)
+        res = P.run(seed=7, count=200, trace=True)
+        assert np.allclose(res["log_x"], math.log(math.factorial(n)), rtol=1e-13, atol=0)
+        assert np.all(res["dead_step"] == -1)
+        st = O.stats(res["log_x"])
+        assert st["rel_spread"] == pytest.approx(0.0, abs=1e-12)
+        assert st["ess"] == pytest.approx(200, rel=1e-12)
+        assert st["p_match"] == 1.0
+
+
+def test_estimate_converges_to_ryser():
+    A = G.planted_bernoulli(20, 0.3, seed=1)
+    per = O.ryser(A.to_dense())
+    P = O.Prepared(A, O.Schedule())
+    res = P.run(seed=1, count=40000, threads=os.cpu_count() or 1)
+    st = O.stats(res["log_x"])
+    rel = abs(math.exp(st["log_estimate"]) / per - 1)
+    assert rel < 5 * st["rse"]
+    assert st["ess"] <= st["n_traj"] * st["p_match"] + 1e-9   # Cauchy-Schwarz (Sec. 2)
+
+
+def test_run_is_thread_count_invariant():
+    A = G.er_planted(60, 4.0, seed=5)
+    P = O.Prepared(A, O.preset("local_threshold", O.PREC_FP32))
+    a = P.run(seed=9, count=64, threads=1, trace=True)
+    b = P.run(seed=9, count=64, threads=4, trace=True)
+    assert np.array_equal(a["chosen"], b["chosen"])
+    assert np.array_equal(a["log_x"], b["log_x"])
+
+
+# ---------------------------------------------------------------------------
+# statistics (Sec. 2 ESS / p_match, Sec. 4 metrics)
+# ---------------------------------------------------------------------------
+
+def test_statistics_closed_form():
+    x = np.array([1.0, 3.0, 0.0, 2.0])
+    lx = np.where(x > 0, np.log(np.where(x > 0, x, 1)), -np.inf)
+    for shift in (0.0, 700.0, -700.0):
+        st = O.stats(lx + shift)
+        assert st["log_estimate"] == pytest.approx(math.log(1.5) + shift, rel=1e-14, abs=1e-13)
+        assert st["p_match"] == 0.75
+        assert st["rel_spread"] == pytest.approx(math.sqrt(5 / 3) / 1.5, rel=1e-13)
+        assert st["rse"] == pytest.approx(math.sqrt(5 / 3) / 1.5 / 2, rel=1e-13)
+        assert st["ess"] == pytest.approx(36 / 14, rel=1e-13)
+        assert st["n_alive"] == 3
+
+
+def test_statistics_cauchy_schwarz_random():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        lx = rng.normal(size=500) * 3
+        lx[rng.random(500) < 0.3] = -np.inf
+        st = O.stats(lx)
+        assert st["ess"] <= 500 * st["p_match"] * (1 + 1e-12)
+
+
+def test_statistics_all_dead():
+    st = O.stats(np.full(10, -np.inf))
+    assert st["log_estimate"] == -np.inf and st["p_match"] == 0 and st["ess"] == 0
+
+
+# ---------------------------------------------------------------------------
+# DM (Sec. 2) against the brute-force definition of a supported edge
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(8))
+def test_dm_mask_matches_bruteforce(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(3, 8))
+    A = random_small(n, float(rng.uniform(0.2, 0.5)), seed, planted=bool(seed % 4))
+    d = A.to_dense()
+    pm = perfect_matchings(d)
+    mask = O.dm_mask(A)
+    if not pm:
+        assert mask is None
+        return
+    supported = {(i, p[i]) for p in pm for i in range(n)}
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    for e in range(A.nnz):
+        assert bool(mask[e]) == ((rows[e], A.col_idx[e]) in supported)
+
+
+def test_dm_upper_triangular_keeps_diagonal():
+    A = G.upper_triangular(12)
+    mask = O.dm_mask(A)
+    rows = np.repeat(np.arange(12), np.diff(A.row_ptr))
+    assert np.array_equal(mask.astype(bool), rows == A.col_idx)
+
+
+# ---------------------------------------------------------------------------
+# SK (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [(O.PREC_FP64, 1e-15), (O.PREC_FP32, 1e-7)])
+def test_sk_regular_closed_form(prec, tol):
+    for k in (2, 3, 5):
+        r, c = O.sk_full(G.circulant(11, k), 1, prec)
+        cast = (lambda v: float(np.float32(v))) if prec == O.PREC_FP32 else float
+        assert np.all(c == cast(1.0 / k))
+        assert np.allclose(r, 1.0, rtol=0, atol=tol * k)
+
+
+def test_sk_converges_to_doubly_stochastic():
+    A = G.planted_bernoulli(30, 0.15, seed=2)
+    mask = O.dm_mask(A)
+    rows = np.repeat(np.arange(30), np.diff(A.row_ptr))
+    B = G.csr_from_coo(30, rows[mask == 1], A.col_idx[mask == 1])  # total support
+    r, c = O.sk_full(B, 2000)
+    S = B.to_dense() * r[:, None] * c[None, :]
+    assert np.allclose(S.sum(0), 1, atol=1e-9) and np.allclose(S.sum(1), 1, atol=1e-9)
+
+
+def test_sk_proxy_tracks_minor_ratios():
+    # Sec. 3.1 / Fig. 1: after 10 SK iterations r_v c_u tracks the exact
+    # probability per(A\{v,u})/per(A) of (v,u) in a uniform perfect matching
+    A = G.planted_bernoulli(12, 0.25, seed=6)
+    mask = O.dm_mask(A)
+    rows = np.repeat(np.arange(12), np.diff(A.row_ptr))
+    B = G.csr_from_coo(12, rows[mask == 1], A.col_idx[mask == 1])
+    d = B.to_dense()
+    per = O.ryser(d)
+    r, c = O.sk_full(B, 10)
+    xs, ys = [], []
+    rr = np.repeat(np.arange(12), np.diff(B.row_ptr))
+    for i, j in zip(rr, B.col_idx):
+        minor = np.delete(np.delete(d, i, 0), j, 1)
+        xs.append(O.ryser(minor) / per)
+        ys.append(r[i] * c[j])
+    assert np.corrcoef(xs, ys)[0, 1] > 0.9
