@@ -1,0 +1,182 @@
+/*
+ * pm.h -- C ABI of the B300 (sm_103a) sparse-matrix permanent estimator.
+ *
+ * The library estimates per(A) = sum_{pi in S_n} prod_v A_{v,pi(v)} (Eq. 1)
+ * of a sparse nonnegative n x n matrix with the adaptive sequential
+ * importance sampler of "The Quick and the Dead" (Algorithm 2): many
+ * independent trajectories, each picking the active row or column of minimum
+ * live degree (Sec. 3.2), drawing a partner from the scaled proposal of
+ * Eq. 3, multiplying its weight by the correction B_vu / q(u|v), eliminating
+ * the pair with degree updates, and running the scheduled SK / Local scaling
+ * (Sec. 3.3, Eq. 5) and DM support filtering (Sec. 2, Sec. 3.3) between steps.
+ *
+ * Conventions for every function:
+ *  - returns pm_status; PM_OK (0) on success.  No function aborts the process
+ *    or traps the device; device-side failures come back through a status
+ *    word read after the stream synchronises (PM_EDEVICE).
+ *  - outputs are written only when the call returns PM_OK.
+ *  - all pointers are caller-owned and not retained after the call returns,
+ *    except the handles the library allocates (pm_context, pm_matrix).
+ *  - a context serialises its work on one CUDA stream; calls on one context
+ *    must not overlap in time from several host threads.
+ *  - per(A) = 0 is not an error: PM_OK with log_estimate = -INFINITY,
+ *    estimate = 0 and p_match = 0.
+ */
+#ifndef PM_H_
+#define PM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PM_OK = 0,
+    PM_EINVAL = 1,         /* malformed matrix, size mismatch, bad schedule, NULL argument */
+    PM_ENOMEM = 2,         /* device or pinned-host allocation failed */
+    PM_ECUDA = 3,          /* a CUDA runtime call failed (the message is kept, see pm_last_error) */
+    PM_ETIMEOUT = 4,       /* a bounded device-side wait ran out */
+    PM_ECANCELLED = 5,
+    PM_EUNSUPPORTED = 6,   /* size or option outside what this build supports */
+    PM_EDEVICE = 7         /* a kernel reported an internal error through the status word */
+} pm_status;
+
+/* Sparse matrix in CSR form.  row_ptr[0] = 0, row_ptr nondecreasing,
+ * row_ptr[n] = nnz; col_idx strictly increasing inside each row, in [0, n);
+ * values > 0 (float32) or NULL for a 0/1 matrix.  on_device = 1: the three
+ * arrays are device pointers of the context's device; 0: host pointers. */
+typedef struct {
+    int32_t n;
+    int32_t on_device;
+    int64_t nnz;
+    const int64_t* row_ptr;   /* [n + 1] */
+    const int32_t* col_idx;   /* [nnz] */
+    const float* values;      /* [nnz] or NULL */
+} pm_csr;
+
+/* Vertex rule R_V (Alg. 2): two-sided minimum degree over active rows and
+ * columns, ties to the lowest unified id (row i -> i, column j -> n + j); or
+ * the fixed row order of Alg. 1. */
+typedef enum { PM_VR_MIN_DEGREE_2SIDED = 0, PM_VR_ROW_ORDER = 1 } pm_vertex_rule;
+/* SK policy P_SK (Sec. 3.3); NONE keeps the outer scaling for the whole trajectory. */
+typedef enum { PM_SK_NONE = 0, PM_SK_FIXED = 1, PM_SK_ADAPTIVE = 2, PM_SK_LOCAL = 3 } pm_sk_policy;
+/* DM policy P_DM (Sec. 3.3). */
+typedef enum { PM_DM_NONE = 0, PM_DM_ALL = 1, PM_DM_THRS = 2, PM_DM_TRCK = 3 } pm_dm_policy;
+/* FP32_PROPOSAL: scaling vectors and proposal scores in binary32, log-weights
+ * and statistics in binary64.  FP64: everything in binary64. */
+typedef enum { PM_PREC_FP32_PROPOSAL = 0, PM_PREC_FP64 = 1 } pm_precision;
+
+/* Inputs of Algorithm 2.  Presets of Sec. 4: two-sided MD, initial_dm = 1,
+ * K0 = 100, K = 10, theta = 0.33 with (sk, dm) = fixed_all (FIXED, ALL),
+ * adaptive_threshold (ADAPTIVE, THRS), local_threshold (LOCAL, THRS),
+ * adaptive_tracked (ADAPTIVE, TRCK), local_tracked (LOCAL, TRCK). */
+typedef struct {
+    int32_t vertex_rule;   /* pm_vertex_rule */
+    int32_t initial_dm;    /* 1: InitialDM before the outer SK (Alg. 2 preprocessing) */
+    int32_t K0;            /* outer SK iterations, >= 0 */
+    int32_t K;             /* inner SK iteration cap, >= 0 */
+    int32_t sk;            /* pm_sk_policy */
+    int32_t dm;            /* pm_dm_policy */
+    int32_t precision;     /* pm_precision */
+    int32_t reserved;      /* must be 0 */
+    double theta;          /* Thrs / Trck threshold theta_th = theta_tr */
+} pm_schedule;
+
+typedef struct {
+    double log_estimate;   /* ln(mean X); -INFINITY if every X = 0 */
+    double estimate;       /* exp(log_estimate); +INFINITY if it overflows binary64 */
+    double ess;            /* (sum X)^2 / sum X^2 (Sec. 2) */
+    double p_match;        /* #{X > 0} / M */
+    double rel_spread;     /* s_X / |mean X|, s_X with M - 1 (Sec. 3.2) */
+    double rse;            /* rel_spread / sqrt(M) (Sec. 4 "Metrics") */
+    double log_sum_x;      /* ln sum X    (for merging runs on the host) */
+    double log_sum_x2;     /* ln sum X^2 */
+    uint64_t n_traj;       /* M */
+    uint64_t n_alive;
+    uint64_t n_dm_calls;   /* inner DM calls over all trajectories */
+    uint64_t n_full_sk;    /* full SK iterations over all trajectories */
+    uint64_t n_local_sk;   /* Local repairs over all trajectories */
+    double seconds;        /* wall time of the call on the host clock */
+    uint64_t alg_bytes;    /* algorithmic bytes the trajectories of this matrix touched:
+                              8 B per adjacency entry of each picked vertex and partner,
+                              16 B per live edge per full SK iteration, 16 B per vertex
+                              of each Local repair, 8 B per vertex at initialisation */
+    double kernel_ms;      /* device time of the trajectory kernel of the call (CUDA events
+                              on the context's stream; shared by all matrices of a batch) */
+} pm_result;
+
+/* Bookkeeping of the most recent estimate / trace call of a context. */
+typedef struct {
+    uint64_t h2d_bytes;       /* host -> device bytes the call copied */
+    uint64_t d2h_bytes;       /* device -> host bytes the call copied */
+    double traj_kernel_ms;    /* device time of the trajectory kernel */
+    double prep_kernel_ms;    /* device time of the preprocessing kernel */
+    int32_t grid;             /* CTAs of the trajectory launch */
+    int32_t warps_per_cta;    /* warps (trajectory slots) per CTA */
+} pm_call_info;
+
+typedef struct pm_context pm_context;
+
+/* Create a context on CUDA device `device` that issues all work on
+ * `cuda_stream` (a cudaStream_t; NULL = a new non-blocking stream owned by
+ * the context).  Device workspaces are allocated lazily and grown as needed. */
+pm_status pm_context_create(pm_context** ctx, int device, void* cuda_stream);
+pm_status pm_context_destroy(pm_context* ctx);
+
+/* Estimate per(csr) from n_traj trajectories with Philox4x32-10 seed `seed`;
+ * trajectory k draws from counter (k, matrix index 0, step, attempt), so any
+ * trajectory can be replayed on its own.  n must equal csr->n. */
+pm_status estimate_permanent(pm_context* ctx, const pm_csr* csr, int32_t n, uint64_t n_traj,
+                             uint64_t seed, const pm_schedule* schedule, pm_result* out);
+
+/* The same for `count` matrices in one persistent launch (matrix k uses
+ * matrix index k in the Philox counter, n_traj[k] trajectories); outs[count]. */
+pm_status estimate_permanent_batch(pm_context* ctx, const pm_csr* mats, int32_t count,
+                                   const uint64_t* n_traj, uint64_t seed,
+                                   const pm_schedule* schedule, pm_result* outs);
+
+/* estimate_permanent_batch with two extras: trajectories of matrix k are
+ * first_traj .. first_traj + n_traj[k] - 1, and, when log_x is not NULL, the
+ * per-trajectory ln X (host buffer of sum_k n_traj[k] doubles, matrix-major,
+ * -INFINITY for dead trajectories) is copied out.  Same launch as
+ * estimate_permanent_batch. */
+pm_status pm_estimate_batch_ex(pm_context* ctx, const pm_csr* mats, int32_t count,
+                               const uint64_t* n_traj, uint64_t first_traj, uint64_t seed,
+                               const pm_schedule* schedule, pm_result* outs, double* log_x);
+
+/* Replay trajectories first_traj .. first_traj + count - 1 of matrix index
+ * `matrix_index` and return their paths (host buffers, any may be NULL):
+ *   chosen[count][n][2]  unified ids (v, u) of step t, -1 after death
+ *   deg_v[count][n]      live degree of v when it was picked, -1 after death
+ *   dead_step[count]     step at which the trajectory died, -1 if it completed
+ *   log_x[count]         ln X, -INFINITY for a dead trajectory. */
+pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index,
+                   uint64_t first_traj, uint32_t count, uint64_t seed,
+                   const pm_schedule* schedule, int32_t* chosen, int32_t* deg_v,
+                   int32_t* dead_step, double* log_x);
+
+/* Preprocessing only (InitialDM + K0 outer SK): host outputs, any may be NULL:
+ * ok (1 if a perfect matching exists), keep[nnz] (1 = edge survives the
+ * initial DM, CSR order of the input), r[n], c[n] (outer scaling, binary64
+ * copies of the mode's values). */
+pm_status pm_preprocess(pm_context* ctx, const pm_csr* csr, const pm_schedule* schedule,
+                        int32_t* ok, uint8_t* keep, double* r, double* c);
+
+/* Philox4x32-10 blocks for `count` consecutive counters starting at ctr
+ * (ctr[0] incremented per block), computed on the device (host output
+ * out[count][4]); for checking the generator against published vectors. */
+pm_status pm_philox_blocks(pm_context* ctx, const uint32_t ctr[4], const uint32_t key[2],
+                           uint32_t count, uint32_t* out);
+
+/* Copy the bookkeeping of the context's most recent call into *info. */
+pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info);
+
+/* Human-readable name of a status, and the last error message of a context. */
+const char* pm_status_string(pm_status s);
+const char* pm_last_error(const pm_context* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_H_ */

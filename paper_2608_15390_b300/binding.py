@@ -1,0 +1,266 @@
+"""ctypes binding of the C ABI in include/pm.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libpm_b300.so``; when it is
+missing or cannot load, importing the binding raises, and there is no other
+code path.  Function names follow the header: ``estimate_permanent``,
+``estimate_permanent_batch``, ``pm_trace``, ``pm_preprocess``,
+``pm_philox_blocks``.
+
+Matrices are any object with ``n``, ``row_ptr`` (int64), ``col_idx`` (int32)
+and ``values`` (float32 or None) as numpy arrays (host) or torch tensors
+(host or CUDA; CUDA tensors are passed as device pointers).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpm_b300.so")
+
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_ECANCELLED, PM_EUNSUPPORTED, PM_EDEVICE = range(8)
+VR_MIN_DEGREE_2SIDED, VR_ROW_ORDER = 0, 1
+SK_NONE, SK_FIXED, SK_ADAPTIVE, SK_LOCAL = 0, 1, 2, 3
+DM_NONE, DM_ALL, DM_THRS, DM_TRCK = 0, 1, 2, 3
+PREC_FP32_PROPOSAL, PREC_FP64 = 0, 1
+
+
+class PmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class pm_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("on_device", C.c_int32), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("values", C.c_void_p)]
+
+
+class pm_schedule(C.Structure):
+    _fields_ = [("vertex_rule", C.c_int32), ("initial_dm", C.c_int32), ("K0", C.c_int32),
+                ("K", C.c_int32), ("sk", C.c_int32), ("dm", C.c_int32), ("precision", C.c_int32),
+                ("reserved", C.c_int32), ("theta", C.c_double)]
+
+
+class pm_result(C.Structure):
+    _fields_ = [("log_estimate", C.c_double), ("estimate", C.c_double), ("ess", C.c_double),
+                ("p_match", C.c_double), ("rel_spread", C.c_double), ("rse", C.c_double),
+                ("log_sum_x", C.c_double), ("log_sum_x2", C.c_double), ("n_traj", C.c_uint64),
+                ("n_alive", C.c_uint64), ("n_dm_calls", C.c_uint64), ("n_full_sk", C.c_uint64),
+                ("n_local_sk", C.c_uint64), ("seconds", C.c_double), ("alg_bytes", C.c_uint64),
+                ("kernel_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class pm_call_info(C.Structure):
+    _fields_ = [("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64), ("traj_kernel_ms", C.c_double),
+                ("prep_kernel_ms", C.c_double), ("grid", C.c_int32), ("warps_per_cta", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run python -m paper_2608_15390_b300.build)")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    L.pm_context_create.argtypes = [C.POINTER(P), C.c_int, P]
+    L.pm_context_destroy.argtypes = [P]
+    L.estimate_permanent.argtypes = [P, C.POINTER(pm_csr), C.c_int32, C.c_uint64, C.c_uint64,
+                                     C.POINTER(pm_schedule), C.POINTER(pm_result)]
+    L.estimate_permanent_batch.argtypes = [P, C.POINTER(pm_csr), C.c_int32, P, C.c_uint64,
+                                           C.POINTER(pm_schedule), C.POINTER(pm_result)]
+    L.pm_estimate_batch_ex.argtypes = [P, C.POINTER(pm_csr), C.c_int32, P, C.c_uint64, C.c_uint64,
+                                       C.POINTER(pm_schedule), C.POINTER(pm_result), P]
+    L.pm_trace.argtypes = [P, C.POINTER(pm_csr), C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64,
+                           C.POINTER(pm_schedule), P, P, P, P]
+    L.pm_preprocess.argtypes = [P, C.POINTER(pm_csr), C.POINTER(pm_schedule), P, P, P, P]
+    L.pm_philox_blocks.argtypes = [P, P, P, C.c_uint32, P]
+    L.pm_last_call_info.argtypes = [P, C.POINTER(pm_call_info)]
+    L.pm_last_call_info.restype = C.c_int
+    L.pm_status_string.restype = C.c_char_p
+    L.pm_status_string.argtypes = [C.c_int]
+    L.pm_last_error.restype = C.c_char_p
+    L.pm_last_error.argtypes = [P]
+    for name in ("pm_context_create", "pm_context_destroy", "estimate_permanent",
+                 "estimate_permanent_batch", "pm_estimate_batch_ex", "pm_trace", "pm_preprocess", "pm_philox_blocks"):
+        getattr(L, name).restype = C.c_int
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    return _lib.pm_status_string(s).decode()
+
+
+EXPORTED = ["pm_context_create", "pm_context_destroy", "estimate_permanent",
+            "estimate_permanent_batch", "pm_estimate_batch_ex", "pm_trace", "pm_preprocess", "pm_philox_blocks",
+            "pm_last_call_info", "pm_status_string", "pm_last_error"]
+
+
+@dataclass
+class Schedule:
+    vertex_rule: int = VR_MIN_DEGREE_2SIDED
+    initial_dm: int = 0
+    K0: int = 0
+    K: int = 0
+    sk: int = SK_NONE
+    dm: int = DM_NONE
+    precision: int = PREC_FP64
+    theta: float = 0.33
+
+    def c(self) -> pm_schedule:
+        return pm_schedule(self.vertex_rule, self.initial_dm, self.K0, self.K, self.sk, self.dm,
+                           self.precision, 0, self.theta)
+
+
+def preset(name: str, precision: int = PREC_FP32_PROPOSAL) -> Schedule:
+    """The five variants of Sec. 4 (two-sided MD, K0=100, K=10, theta=0.33,
+    initial DM)."""
+    sk, dm = {"fixed_all": (SK_FIXED, DM_ALL), "adaptive_threshold": (SK_ADAPTIVE, DM_THRS),
+              "local_threshold": (SK_LOCAL, DM_THRS), "adaptive_tracked": (SK_ADAPTIVE, DM_TRCK),
+              "local_tracked": (SK_LOCAL, DM_TRCK)}[name]
+    return Schedule(initial_dm=1, K0=100, K=10, sk=sk, dm=dm, precision=precision, theta=0.33)
+
+
+def _arr_ptr(a):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, 0, None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return a.data_ptr(), 1 if a.is_cuda else 0, a
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, 0, a
+
+
+def make_csr(m) -> tuple:
+    rp, d0, k0 = _arr_ptr(m.row_ptr)
+    ci, d1, k1 = _arr_ptr(m.col_idx)
+    vals = getattr(m, "values", None)
+    vp, d2, k2 = _arr_ptr(vals)
+    dev = d0
+    if d1 != dev or (vals is not None and d2 != dev):
+        raise ValueError("row_ptr, col_idx and values must all be on the host or all on the device")
+    nnz = int(m.row_ptr[-1]) if not dev else int(m.col_idx.numel())
+    c = pm_csr(int(m.n), dev, nnz, rp, ci, vp)
+    return c, (k0, k1, k2)
+
+
+class Context:
+    """Owns a pm_context (device arena + stream).  ``stream`` is a raw
+    cudaStream_t value (e.g. ``torch.cuda.current_stream().cuda_stream``)."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self.h = C.c_void_p()
+        self._check(_lib.pm_context_create(C.byref(self.h), device, stream), ctx=False)
+
+    def close(self):
+        if self.h:
+            _lib.pm_context_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, ctx: bool = True):
+        if st != PM_OK:
+            msg = _lib.pm_last_error(self.h).decode() if ctx and self.h else ""
+            raise PmError(st, msg)
+
+    # ---- entry points ----
+    def estimate_permanent(self, m, n_traj: int, seed: int, schedule: Schedule) -> dict:
+        c, keep = make_csr(m)
+        out = pm_result()
+        s = schedule.c()
+        self._check(_lib.estimate_permanent(self.h, C.byref(c), c.n, n_traj, seed, C.byref(s),
+                                            C.byref(out)))
+        return out.as_dict()
+
+    def estimate_permanent_batch(self, mats: Sequence, n_traj: Sequence[int], seed: int,
+                                 schedule: Schedule) -> List[dict]:
+        cs, keeps = [], []
+        for m in mats:
+            c, k = make_csr(m)
+            cs.append(c)
+            keeps.append(k)
+        arr = (pm_csr * len(cs))(*cs)
+        nt = np.ascontiguousarray(n_traj, dtype=np.uint64)
+        outs = (pm_result * len(cs))()
+        s = schedule.c()
+        self._check(_lib.estimate_permanent_batch(self.h, arr, len(cs), nt.ctypes.data, seed,
+                                                  C.byref(s), outs))
+        return [o.as_dict() for o in outs]
+
+    def estimate_batch_ex(self, mats: Sequence, n_traj: Sequence[int], seed: int,
+                          schedule: Schedule, first_traj: int = 0, want_log_x: bool = False):
+        """Batch estimate; returns (results, log_x or None)."""
+        cs, keeps = [], []
+        for m in mats:
+            c, k = make_csr(m)
+            cs.append(c)
+            keeps.append(k)
+        arr = (pm_csr * len(cs))(*cs)
+        nt = np.ascontiguousarray(n_traj, dtype=np.uint64)
+        outs = (pm_result * len(cs))()
+        lx = np.zeros(int(nt.sum()), dtype=np.float64) if want_log_x else None
+        s = schedule.c()
+        self._check(_lib.pm_estimate_batch_ex(self.h, arr, len(cs), nt.ctypes.data, first_traj, seed,
+                                              C.byref(s), outs,
+                                              None if lx is None else lx.ctypes.data))
+        return [o.as_dict() for o in outs], lx
+
+    def trace(self, m, count: int, seed: int, schedule: Schedule, first_traj: int = 0,
+              matrix_index: int = 0) -> dict:
+        c, keep = make_csr(m)
+        n = c.n
+        chosen = np.zeros((count, n, 2), dtype=np.int32)
+        degv = np.zeros((count, n), dtype=np.int32)
+        dead = np.zeros(count, dtype=np.int32)
+        lx = np.zeros(count, dtype=np.float64)
+        s = schedule.c()
+        self._check(_lib.pm_trace(self.h, C.byref(c), matrix_index, first_traj, count, seed,
+                                  C.byref(s), chosen.ctypes.data, degv.ctypes.data,
+                                  dead.ctypes.data, lx.ctypes.data))
+        return dict(chosen=chosen, deg_v=degv, dead_step=dead, log_x=lx)
+
+    def preprocess(self, m, schedule: Schedule) -> dict:
+        c, keep = make_csr(m)
+        ok = C.c_int32()
+        kp = np.zeros(max(1, c.nnz), dtype=np.uint8)
+        r = np.zeros(c.n)
+        cc = np.zeros(c.n)
+        s = schedule.c()
+        self._check(_lib.pm_preprocess(self.h, C.byref(c), C.byref(s), C.byref(ok), kp.ctypes.data,
+                                       r.ctypes.data, cc.ctypes.data))
+        return dict(ok=bool(ok.value), keep=kp[: c.nnz], r=r, c=cc)
+
+    def last_call_info(self) -> dict:
+        info = pm_call_info()
+        self._check(_lib.pm_last_call_info(self.h, C.byref(info)))
+        return info.as_dict()
+
+    def philox_blocks(self, ctr, key, count: int) -> np.ndarray:
+        ct = np.ascontiguousarray(ctr, dtype=np.uint32)
+        ky = np.ascontiguousarray(key, dtype=np.uint32)
+        out = np.zeros((count, 4), dtype=np.uint32)
+        self._check(_lib.pm_philox_blocks(self.h, ct.ctypes.data, ky.ctypes.data, count,
+                                          out.ctypes.data))
+        return out

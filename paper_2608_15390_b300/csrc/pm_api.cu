@@ -1,0 +1,588 @@
+// pm_api.cu -- host implementation of the C ABI declared in include/pm.h:
+// argument checks, the context's device arena, launch sequencing on the
+// context's stream, and result read-back.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pm.h"
+#include "pm_internal.h"
+
+using namespace pm;
+
+struct pm_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    std::string last_error;
+    uint8_t* arena = nullptr;
+    size_t arena_cap = 0;
+    uint8_t* slots = nullptr;
+    size_t slots_cap = 0;
+    uint8_t* pinned = nullptr;
+    size_t pinned_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the trajectory kernel
+    cudaEvent_t ev2 = nullptr;
+    double last_traj_ms = 0, last_prep_ms = 0;
+    uint64_t last_h2d = 0, last_d2h = 0;
+    int last_grid = 0, last_wpc = 0;
+};
+
+namespace {
+
+pm_status fail(pm_context* ctx, pm_status st, const std::string& msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+#define PM_CUDA(call)                                                                         \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+pm_status grow(pm_context* ctx, uint8_t** buf, size_t* cap, size_t need)
+{
+    if (need <= *cap) return PM_OK;
+    if (*buf) {
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+        PM_CUDA(cudaFree(*buf));
+        *buf = nullptr;
+        *cap = 0;
+    }
+    size_t c = need + need / 4;
+    PM_CUDA(cudaMalloc(buf, c));
+    *cap = c;
+    return PM_OK;
+}
+
+pm_status grow_pinned(pm_context* ctx, size_t need)
+{
+    if (need <= ctx->pinned_cap) return PM_OK;
+    if (ctx->pinned) {
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+        PM_CUDA(cudaFreeHost(ctx->pinned));
+        ctx->pinned = nullptr;
+        ctx->pinned_cap = 0;
+    }
+    PM_CUDA(cudaMallocHost(&ctx->pinned, need));
+    ctx->pinned_cap = need;
+    return PM_OK;
+}
+
+// bump layout over the arena (256-byte aligned pieces)
+struct Layout {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t p = off;
+        off = align_up(off + (bytes ? bytes : 1), 256);
+        return p;
+    }
+};
+
+pm_status check_schedule(pm_context* ctx, const pm_schedule* s)
+{
+    if (!s) return fail(ctx, PM_EINVAL, "schedule is NULL");
+    if (s->vertex_rule < 0 || s->vertex_rule > 1) return fail(ctx, PM_EINVAL, "bad vertex_rule");
+    if (s->sk < 0 || s->sk > 3) return fail(ctx, PM_EINVAL, "bad sk policy");
+    if (s->dm < 0 || s->dm > 3) return fail(ctx, PM_EINVAL, "bad dm policy");
+    if (s->precision < 0 || s->precision > 1) return fail(ctx, PM_EINVAL, "bad precision");
+    if (s->K0 < 0 || s->K < 0 || s->reserved != 0) return fail(ctx, PM_EINVAL, "bad K0/K/reserved");
+    if (!(s->theta == s->theta)) return fail(ctx, PM_EINVAL, "theta is NaN");
+    return PM_OK;
+}
+
+pm_status check_csr(pm_context* ctx, const pm_csr* c)
+{
+    if (!c) return fail(ctx, PM_EINVAL, "csr is NULL");
+    if (c->n < 1) return fail(ctx, PM_EINVAL, "n must be >= 1");
+    if (c->n > kSmemMaxN) return fail(ctx, PM_EUNSUPPORTED, "n above the supported maximum (16383)");
+    if (c->nnz < 0 || c->nnz >= ((int64_t)1 << 31)) return fail(ctx, PM_EINVAL, "bad nnz");
+    if (!c->row_ptr || (c->nnz > 0 && !c->col_idx)) return fail(ctx, PM_EINVAL, "NULL csr array");
+    if (c->on_device != 0 && c->on_device != 1) return fail(ctx, PM_EINVAL, "bad on_device");
+    if (!c->on_device) {  // cheap host-side checks; the device re-validates everything
+        if (c->row_ptr[0] != 0 || c->row_ptr[c->n] != c->nnz) return fail(ctx, PM_EINVAL, "row_ptr ends");
+    }
+    return PM_OK;
+}
+
+struct Run {
+    // inputs
+    const pm_csr* mats = nullptr;
+    int count = 0;
+    std::vector<uint64_t> ntraj;
+    uint64_t first_traj = 0;
+    uint32_t matrix_index0 = 0;  // matrix index of mats[0] (others: +k)
+    uint64_t seed = 0;
+    Sched s{};
+    bool trace = false;
+    bool prep_only = false;
+    // host outputs
+    pm_result* outs = nullptr;
+    int32_t *chosen = nullptr, *deg_v = nullptr, *dead_step = nullptr;
+    double* log_x = nullptr;
+    int32_t* ok_out = nullptr;
+    uint8_t* keep_out = nullptr;
+    double *r_out = nullptr, *c_out = nullptr;
+};
+
+pm_status execute(pm_context* ctx, Run& R)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    PM_CUDA(cudaSetDevice(ctx->device));
+    const int count = R.count;
+    const bool fp64 = R.s.precision == 1;
+    const size_t rb = fp64 ? 8 : 4;
+    int n_max = 1;
+    int64_t m_max = 1;
+    for (int k = 0; k < count; ++k) {
+        n_max = std::max(n_max, R.mats[k].n);
+        m_max = std::max<int64_t>(m_max, R.mats[k].nnz);
+    }
+    std::vector<uint64_t> prefix(count + 1, 0);
+    for (int k = 0; k < count; ++k) prefix[k + 1] = prefix[k] + R.ntraj[k];
+    const uint64_t total = prefix[count];
+
+    // ---- arena layout ----
+    Layout L;
+    struct MatOff {
+        size_t rp64, ci_in, val_in, a_rp, a_ci, a_val, a_cp, a_ri, a_ce, keep, rp, ci, rv, cp, ri, cv, ce, r0,
+            c0, deg0, tree0, dmws;
+    };
+    std::vector<MatOff> mo(count);
+    for (int k = 0; k < count; ++k) {
+        const pm_csr& c = R.mats[k];
+        const int n = c.n;
+        const size_t m = (size_t)c.nnz;
+        const bool w = c.values != nullptr;
+        MatOff& o = mo[k];
+        o.rp64 = c.on_device ? 0 : L.take((n + 1) * 8);
+        o.ci_in = c.on_device ? 0 : L.take(m * 4);
+        o.val_in = (c.on_device || !w) ? 0 : L.take(m * 4);
+        o.a_rp = L.take((n + 1) * 4);
+        o.a_ci = L.take(m * 4);
+        o.a_val = w ? L.take(m * 4) : 0;
+        o.a_cp = L.take((n + 1) * 4);
+        o.a_ri = L.take(m * 4);
+        o.a_ce = L.take(m * 4);
+        o.keep = L.take(m);
+        o.rp = L.take((n + 1) * 4);
+        o.ci = L.take(m * 4);
+        o.rv = w ? L.take(m * 4) : 0;
+        o.cp = L.take((n + 1) * 4);
+        o.ri = L.take(m * 4);
+        o.cv = w ? L.take(m * 4) : 0;
+        o.ce = L.take(m * 4);
+        o.r0 = L.take(n * rb);
+        o.c0 = L.take(n * rb);
+        o.deg0 = L.take((size_t)((2 * n + 7) & ~7) * 2);
+        o.tree0 = L.take((size_t)std::max(1, tree_geom(n).total) * 4);
+        o.dmws = L.take((size_t)dm_ws_ints(n) * 4);
+    }
+    const size_t o_mats = L.take(sizeof(DevMatrix) * count);
+    const size_t o_inputs = L.take(sizeof(DevInput) * count);
+    const size_t o_prefix = L.take(8 * (count + 1));
+    const size_t o_logx = L.take(8 * std::max<uint64_t>(total, 1));
+    const size_t o_counters = L.take(8 * 4 * count);
+    const size_t o_work = L.take(8);
+    const size_t o_status = L.take(4);
+    uint64_t max_t = 1;
+    for (int k = 0; k < count; ++k) max_t = std::max(max_t, R.ntraj[k]);
+    const int chunks = (int)std::min<uint64_t>(1024, std::max<uint64_t>(1, max_t / 16384));
+    const size_t o_parts = L.take(sizeof(StatsPartial) * (size_t)count * chunks);
+    const size_t o_sout = L.take(sizeof(StatsOut) * count);
+    size_t o_chosen = 0, o_degv = 0, o_dead = 0;
+    if (R.trace) {
+        o_chosen = L.take(4 * total * 2 * (size_t)n_max);
+        o_degv = L.take(4 * total * (size_t)n_max);
+        o_dead = L.take(4 * std::max<uint64_t>(total, 1));
+    }
+    pm_status st = grow(ctx, &ctx->arena, &ctx->arena_cap, L.off);
+    if (st != PM_OK) return st;
+    uint8_t* A = ctx->arena;
+    auto P = [&](size_t off) { return (void*)(A + off); };
+
+    // ---- inputs and matrix descriptors ----
+    uint64_t h2d = 0, d2h = 0;
+    ctx->last_traj_ms = ctx->last_prep_ms = 0;
+    ctx->last_grid = ctx->last_wpc = 0;
+    std::vector<DevMatrix> hm(count);
+    std::vector<DevInput> hi(count);
+    for (int k = 0; k < count; ++k) {
+        const pm_csr& c = R.mats[k];
+        const MatOff& o = mo[k];
+        const int n = c.n;
+        const size_t m = (size_t)c.nnz;
+        DevInput& I = hi[k];
+        I.n = n;
+        I.m = (int)m;
+        if (!c.on_device) h2d += (n + 1) * 8 + m * 4 + (c.values ? m * 4 : 0);
+        if (c.on_device) {
+            I.rp64 = c.row_ptr;
+            I.ci_in = c.col_idx;
+            I.val_in = c.values;
+        } else {
+            PM_CUDA(cudaMemcpyAsync(P(o.rp64), c.row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, ctx->stream));
+            if (m) PM_CUDA(cudaMemcpyAsync(P(o.ci_in), c.col_idx, m * 4, cudaMemcpyHostToDevice, ctx->stream));
+            if (c.values && m)
+                PM_CUDA(cudaMemcpyAsync(P(o.val_in), c.values, m * 4, cudaMemcpyHostToDevice, ctx->stream));
+            I.rp64 = (const int64_t*)P(o.rp64);
+            I.ci_in = (const int32_t*)P(o.ci_in);
+            I.val_in = c.values ? (const float*)P(o.val_in) : nullptr;
+        }
+        DevMatrix& M = hm[k];
+        std::memset(&M, 0, sizeof(M));
+        M.n = n;
+        M.m_a = (int)m;
+        M.idx = (int)(R.matrix_index0 + (uint32_t)k);
+        const bool w = c.values != nullptr;
+        M.a_rp = (int*)P(o.a_rp); M.a_ci = (int*)P(o.a_ci); M.a_val = w ? (float*)P(o.a_val) : nullptr;
+        M.a_cp = (int*)P(o.a_cp); M.a_ri = (int*)P(o.a_ri); M.a_ce = (int*)P(o.a_ce);
+        M.keep = (uint8_t*)P(o.keep);
+        M.rp = (int*)P(o.rp); M.ci = (int*)P(o.ci); M.rv = w ? (float*)P(o.rv) : nullptr;
+        M.cp = (int*)P(o.cp); M.ri = (int*)P(o.ri); M.cv = w ? (float*)P(o.cv) : nullptr; M.ce = (int*)P(o.ce);
+        M.r0 = P(o.r0); M.c0 = P(o.c0);
+        M.deg0 = (uint16_t*)P(o.deg0);
+        M.tree0 = (uint32_t*)P(o.tree0);
+        M.dm_ws = (int*)P(o.dmws);
+    }
+    DevMatrix* d_mats = (DevMatrix*)P(o_mats);
+    PM_CUDA(cudaMemcpyAsync(d_mats, hm.data(), sizeof(DevMatrix) * count, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(P(o_inputs), hi.data(), sizeof(DevInput) * count, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(P(o_prefix), prefix.data(), 8 * (count + 1), cudaMemcpyHostToDevice, ctx->stream));
+    h2d += sizeof(DevMatrix) * count + sizeof(DevInput) * count + 8 * (count + 1);
+    PM_CUDA(cudaMemsetAsync(P(o_counters), 0, 8 * 4 * count, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(P(o_work), 0, 8, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(P(o_status), 0, 4, ctx->stream));
+    uint32_t* d_status = (uint32_t*)P(o_status);
+
+    if (!ctx->ev0) {
+        PM_CUDA(cudaEventCreate(&ctx->ev0));
+        PM_CUDA(cudaEventCreate(&ctx->ev1));
+        PM_CUDA(cudaEventCreate(&ctx->ev2));
+    }
+    PM_CUDA(cudaEventRecord(ctx->ev2, ctx->stream));
+    PM_CUDA(launch_prepare(d_mats, (const DevInput*)P(o_inputs), count, R.s, n_max, d_status, ctx->stream));
+    PM_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
+    bool launched = false;
+
+    // ---- trajectories ----
+    if (!R.prep_only && total > 0) {
+        const bool scales = R.s.sk != 0;
+        const bool local = R.s.sk == 3;
+        const bool dm = R.s.dm != 0;
+        const SlotLayout sl = slot_layout(n_max, (int)m_max, (int)rb, scales, local, dm);
+        const int wpc = traj_kernel_max_warps_per_cta();
+        const int smem_warp = traj_smem_per_warp(n_max);
+        int ctas_per_sm = 0;
+        PM_CUDA(pm::traj_occupancy(fp64, R.trace, wpc, smem_warp * wpc, &ctas_per_sm));
+        if (ctas_per_sm < 1) return fail(ctx, PM_EUNSUPPORTED, "trajectory state does not fit in shared memory");
+        uint64_t grid = (uint64_t)ctx->sm_count * ctas_per_sm;
+        grid = std::min<uint64_t>(grid, (total + wpc - 1) / wpc);
+        const size_t need_slots = sl.bytes * (size_t)grid * wpc;
+        st = grow(ctx, &ctx->slots, &ctx->slots_cap, need_slots);
+        if (st != PM_OK) return st;
+        TrajParams tp{};
+        tp.mats = d_mats;
+        tp.count = count;
+        tp.n_max = n_max;
+        tp.prefix = (const uint64_t*)P(o_prefix);
+        tp.first_traj = R.first_traj;
+        tp.seed = R.seed;
+        tp.s = R.s;
+        tp.log_x = (double*)P(o_logx);
+        tp.counters = (unsigned long long*)P(o_counters);
+        tp.work = (unsigned long long*)P(o_work);
+        tp.status = d_status;
+        tp.slots = ctx->slots;
+        tp.slot = sl;
+        tp.smem_per_warp = smem_warp;
+        tp.warps_per_cta = wpc;
+        if (R.trace) {
+            tp.chosen = (int32_t*)P(o_chosen);
+            tp.deg_v = (int32_t*)P(o_degv);
+            tp.dead_step = (int32_t*)P(o_dead);
+        }
+        PM_CUDA(launch_trajectories(tp, (int)grid, R.trace, ctx->stream));
+        PM_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
+        launched = true;
+        ctx->last_grid = (int)grid;
+        ctx->last_wpc = wpc;
+        PM_CUDA(launch_stats((const double*)P(o_logx), prefix.data(), (const uint64_t*)P(o_prefix), count,
+                             (StatsPartial*)P(o_parts), chunks, (StatsOut*)P(o_sout), ctx->stream));
+    }
+
+    // ---- read back ----
+    const size_t pin_need = sizeof(StatsOut) * count + 8 * 4 * count + 8 + sizeof(DevMatrix) * count + 64;
+    st = grow_pinned(ctx, pin_need);
+    if (st != PM_OK) return st;
+    StatsOut* h_sout = (StatsOut*)ctx->pinned;
+    unsigned long long* h_cnt = (unsigned long long*)(h_sout + count);
+    uint32_t* h_status = (uint32_t*)(h_cnt + 4 * count);
+    DevMatrix* h_mats = (DevMatrix*)(ctx->pinned + align_up(sizeof(StatsOut) * count + 8 * 4 * count + 8, 64));
+    if (!R.prep_only && total > 0) {
+        PM_CUDA(cudaMemcpyAsync(h_sout, P(o_sout), sizeof(StatsOut) * count, cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(cudaMemcpyAsync(h_cnt, P(o_counters), 8 * 4 * count, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    PM_CUDA(cudaMemcpyAsync(h_status, d_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(h_mats, d_mats, sizeof(DevMatrix) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    d2h += 4 + sizeof(DevMatrix) * count;
+    if (!R.prep_only && total > 0) d2h += sizeof(StatsOut) * count + 8 * 4 * count;
+    {
+        float ms = 0;
+        PM_CUDA(cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev0));
+        ctx->last_prep_ms = ms;
+        if (launched) {
+            PM_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+            ctx->last_traj_ms = ms;
+        }
+    }
+    if (*h_status & ST_BAD_INPUT) return fail(ctx, PM_EINVAL, "malformed CSR (device validation)");
+    if (*h_status) return fail(ctx, PM_EDEVICE, "device status " + std::to_string(*h_status));
+
+    if (R.trace) {
+        const size_t T = total, n = R.mats[0].n;
+        if (R.chosen) PM_CUDA(cudaMemcpy(R.chosen, P(o_chosen), 4 * T * 2 * n, cudaMemcpyDeviceToHost));
+        if (R.deg_v) PM_CUDA(cudaMemcpy(R.deg_v, P(o_degv), 4 * T * n, cudaMemcpyDeviceToHost));
+        if (R.dead_step) PM_CUDA(cudaMemcpy(R.dead_step, P(o_dead), 4 * T, cudaMemcpyDeviceToHost));
+    }
+    if (R.log_x && total) {
+        PM_CUDA(cudaMemcpy(R.log_x, P(o_logx), 8 * total, cudaMemcpyDeviceToHost));
+        d2h += 8 * total;
+    }
+    if (R.prep_only) {
+        const pm_csr& c = R.mats[0];
+        if (R.ok_out) *R.ok_out = h_mats[0].ok;
+        if (R.keep_out && c.nnz) PM_CUDA(cudaMemcpy(R.keep_out, P(mo[0].keep), c.nnz, cudaMemcpyDeviceToHost));
+        if (R.r_out || R.c_out) {
+            std::vector<uint8_t> tmp((size_t)c.n * rb * 2);
+            PM_CUDA(cudaMemcpy(tmp.data(), P(mo[0].r0), c.n * rb, cudaMemcpyDeviceToHost));
+            PM_CUDA(cudaMemcpy(tmp.data() + c.n * rb, P(mo[0].c0), c.n * rb, cudaMemcpyDeviceToHost));
+            for (int q = 0; q < c.n; ++q) {
+                const double rv = fp64 ? ((double*)tmp.data())[q] : (double)((float*)tmp.data())[q];
+                const double cv = fp64 ? ((double*)(tmp.data() + c.n * rb))[q]
+                                       : (double)((float*)(tmp.data() + c.n * rb))[q];
+                if (R.r_out) R.r_out[q] = rv;
+                if (R.c_out) R.c_out[q] = cv;
+            }
+        }
+    }
+    ctx->last_h2d = h2d;
+    ctx->last_d2h = d2h;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (R.outs) {
+        for (int k = 0; k < count; ++k) {
+            pm_result& o = R.outs[k];
+            std::memset(&o, 0, sizeof(o));
+            const StatsOut& so = h_sout[k];
+            o.log_estimate = so.log_estimate;
+            o.estimate = std::exp(so.log_estimate);
+            o.ess = so.ess;
+            o.p_match = so.p_match;
+            o.rel_spread = so.rel_spread;
+            o.rse = so.rse;
+            o.log_sum_x = so.log_sum_x;
+            o.log_sum_x2 = so.log_sum_x2;
+            o.n_traj = so.n;
+            o.n_alive = so.alive;
+            o.n_dm_calls = h_cnt[4 * k + 0];
+            o.n_full_sk = h_cnt[4 * k + 1];
+            o.n_local_sk = h_cnt[4 * k + 2];
+            o.alg_bytes = h_cnt[4 * k + 3];
+            o.kernel_ms = ctx->last_traj_ms;
+            o.seconds = secs;
+        }
+    }
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_context_create(pm_context** out, int device, void* cuda_stream)
+{
+    if (!out) return PM_EINVAL;
+    *out = nullptr;
+    pm_context* ctx = new (std::nothrow) pm_context();
+    if (!ctx) return PM_ENOMEM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            ctx->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e != cudaSuccess) {
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
+    }
+    *out = ctx;
+    return PM_OK;
+}
+
+pm_status pm_context_destroy(pm_context* ctx)
+{
+    if (!ctx) return PM_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->slots) cudaFree(ctx->slots);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->ev0) { cudaEventDestroy(ctx->ev0); cudaEventDestroy(ctx->ev1); cudaEventDestroy(ctx->ev2); }
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return PM_OK;
+}
+
+static Sched to_sched(const pm_schedule* s)
+{
+    Sched o;
+    o.vertex_rule = s->vertex_rule; o.initial_dm = s->initial_dm; o.K0 = s->K0; o.K = s->K;
+    o.sk = s->sk; o.dm = s->dm; o.precision = s->precision; o.reserved = 0; o.theta = s->theta;
+    return o;
+}
+
+pm_status pm_estimate_batch_ex(pm_context* ctx, const pm_csr* mats, int32_t count, const uint64_t* n_traj,
+                               uint64_t first_traj, uint64_t seed, const pm_schedule* schedule, pm_result* outs,
+                               double* log_x)
+{
+    if (!ctx) return PM_EINVAL;
+    if (!mats || count < 1 || count > 65535 || !n_traj || !outs) return fail(ctx, PM_EINVAL, "bad batch arguments");
+    pm_status st = check_schedule(ctx, schedule);
+    if (st != PM_OK) return st;
+    for (int k = 0; k < count; ++k) {
+        st = check_csr(ctx, &mats[k]);
+        if (st != PM_OK) return st;
+        if (n_traj[k] >= ((uint64_t)1 << 48)) return fail(ctx, PM_EINVAL, "n_traj above 2^48");
+    }
+    if (first_traj >= ((uint64_t)1 << 48)) return fail(ctx, PM_EINVAL, "first_traj above 2^48");
+    Run R;
+    R.mats = mats;
+    R.count = count;
+    R.ntraj.assign(n_traj, n_traj + count);
+    R.first_traj = first_traj;
+    R.seed = seed;
+    R.s = to_sched(schedule);
+    R.outs = outs;
+    R.log_x = log_x;
+    return execute(ctx, R);
+}
+
+pm_status estimate_permanent_batch(pm_context* ctx, const pm_csr* mats, int32_t count, const uint64_t* n_traj,
+                                   uint64_t seed, const pm_schedule* schedule, pm_result* outs)
+{
+    return pm_estimate_batch_ex(ctx, mats, count, n_traj, 0, seed, schedule, outs, nullptr);
+}
+
+pm_status estimate_permanent(pm_context* ctx, const pm_csr* csr, int32_t n, uint64_t n_traj, uint64_t seed,
+                             const pm_schedule* schedule, pm_result* out)
+{
+    if (!ctx) return PM_EINVAL;
+    if (!csr || csr->n != n) return fail(ctx, PM_EINVAL, "n does not match csr->n");
+    return pm_estimate_batch_ex(ctx, csr, 1, &n_traj, 0, seed, schedule, out, nullptr);
+}
+
+pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index, uint64_t first_traj, uint32_t count,
+                   uint64_t seed, const pm_schedule* schedule, int32_t* chosen, int32_t* deg_v, int32_t* dead_step,
+                   double* log_x)
+{
+    if (!ctx) return PM_EINVAL;
+    pm_status st = check_schedule(ctx, schedule);
+    if (st != PM_OK) return st;
+    st = check_csr(ctx, csr);
+    if (st != PM_OK) return st;
+    if (count < 1 || matrix_index > 0xFFFF || first_traj + count > ((uint64_t)1 << 48))
+        return fail(ctx, PM_EINVAL, "bad trace range");
+    Run R;
+    R.mats = csr;
+    R.count = 1;
+    R.ntraj.assign(1, count);
+    R.first_traj = first_traj;
+    R.matrix_index0 = matrix_index;
+    R.seed = seed;
+    R.s = to_sched(schedule);
+    R.trace = true;
+    R.chosen = chosen;
+    R.deg_v = deg_v;
+    R.dead_step = dead_step;
+    R.log_x = log_x;
+    return execute(ctx, R);
+}
+
+pm_status pm_preprocess(pm_context* ctx, const pm_csr* csr, const pm_schedule* schedule, int32_t* ok,
+                        uint8_t* keep, double* r, double* c)
+{
+    if (!ctx) return PM_EINVAL;
+    pm_status st = check_schedule(ctx, schedule);
+    if (st != PM_OK) return st;
+    st = check_csr(ctx, csr);
+    if (st != PM_OK) return st;
+    Run R;
+    R.mats = csr;
+    R.count = 1;
+    R.ntraj.assign(1, 0);
+    R.s = to_sched(schedule);
+    R.prep_only = true;
+    R.ok_out = ok;
+    R.keep_out = keep;
+    R.r_out = r;
+    R.c_out = c;
+    return execute(ctx, R);
+}
+
+pm_status pm_philox_blocks(pm_context* ctx, const uint32_t ctr[4], const uint32_t key[2], uint32_t count,
+                           uint32_t* out)
+{
+    if (!ctx || !ctr || !key || !out || count == 0) return PM_EINVAL;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    pm_status st = grow(ctx, &ctx->arena, &ctx->arena_cap, (size_t)count * 16);
+    if (st != PM_OK) return st;
+    PM_CUDA(launch_philox(ctr, key, count, (uint32_t*)ctx->arena, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(out, ctx->arena, (size_t)count * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return PM_OK;
+}
+
+pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info)
+{
+    if (!ctx || !info) return PM_EINVAL;
+    info->h2d_bytes = ctx->last_h2d;
+    info->d2h_bytes = ctx->last_d2h;
+    info->traj_kernel_ms = ctx->last_traj_ms;
+    info->prep_kernel_ms = ctx->last_prep_ms;
+    info->grid = ctx->last_grid;
+    info->warps_per_cta = ctx->last_wpc;
+    return PM_OK;
+}
+
+const char* pm_status_string(pm_status s)
+{
+    switch (s) {
+        case PM_OK: return "PM_OK";
+        case PM_EINVAL: return "PM_EINVAL";
+        case PM_ENOMEM: return "PM_ENOMEM";
+        case PM_ECUDA: return "PM_ECUDA";
+        case PM_ETIMEOUT: return "PM_ETIMEOUT";
+        case PM_ECANCELLED: return "PM_ECANCELLED";
+        case PM_EUNSUPPORTED: return "PM_EUNSUPPORTED";
+        case PM_EDEVICE: return "PM_EDEVICE";
+    }
+    return "PM_UNKNOWN";
+}
+
+const char* pm_last_error(const pm_context* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+}  // extern "C"

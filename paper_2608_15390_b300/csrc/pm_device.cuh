@@ -1,0 +1,137 @@
+// pm_device.cuh -- device helpers: Philox4x32-10, exact bounded draws, warp
+// reductions, and binary32/binary64 arithmetic with explicit rounding (no
+// contraction into FMA, so results are fixed by IEEE 754 alone).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "pm_internal.h"
+
+namespace pm {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint16_t kInact = 0xFFFFu;
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
+// multiply-xor bijection, key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ void philox10(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                         uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        const uint32_t a_hi = __umulhi(0xD2511F53u, x0), a_lo = 0xD2511F53u * x0;
+        const uint32_t b_hi = __umulhi(0xCD9E8D57u, x2), b_lo = 0xCD9E8D57u * x2;
+        const uint32_t n0 = b_hi ^ x1 ^ k0;
+        const uint32_t n2 = a_hi ^ x3 ^ k1;
+        x0 = n0; x1 = b_lo; x2 = n2; x3 = a_lo;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// 64-bit draw number `a` of (trajectory, matrix, step).  Counter words:
+// (traj bits 0..31, traj bits 32..47 | matrix << 16, step, a >> 1); key: the
+// two halves of the seed; even a -> words (0,1), odd a -> words (2,3).
+__device__ __forceinline__ uint64_t draw_u64(uint64_t seed, uint64_t traj, uint32_t matrix,
+                                             uint32_t step, uint32_t a)
+{
+    uint32_t x0 = (uint32_t)traj, x1 = (uint32_t)((traj >> 32) & 0xFFFFu) | (matrix << 16);
+    uint32_t x2 = step, x3 = a >> 1;
+    philox10(x0, x1, x2, x3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return (a & 1u) ? (((uint64_t)x2 << 32) | x3) : (((uint64_t)x0 << 32) | x1);
+}
+
+// Exact uniform integer in [0, W): keep the high word of u*W unless the low
+// word falls below 2^64 mod W (Lemire 2019).  Returns ~0 when every allowed
+// attempt was rejected.
+__device__ __forceinline__ uint64_t uniform_below(uint64_t W, uint64_t seed, uint64_t traj,
+                                                  uint32_t matrix, uint32_t step)
+{
+    const uint64_t reject_below = (0ull - W) % W;
+    for (uint32_t a = 0; a < (uint32_t)kMaxRngAttempts; ++a) {
+        const uint64_t u = draw_u64(seed, traj, matrix, step, a);
+        if (u * W >= reject_below) return __umul64hi(u, W);
+    }
+    return ~0ull;
+}
+
+// ---- warp collectives ----
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// maximum of non-negative values (their IEEE bit patterns order as integers)
+__device__ __forceinline__ float warp_max_nonneg(float v)
+{
+    return __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(v)));
+}
+__device__ __forceinline__ double warp_max_nonneg(double v)
+{
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const long long t = __shfl_xor_sync(kFull, b, o);
+        b = t > b ? t : b;
+    }
+    return __longlong_as_double(b);
+}
+
+// ---- arithmetic of the proposal / scaling precision ----
+template <typename Real> struct RA;
+template <> struct RA<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    static __device__ __forceinline__ float pow2(int k) { return __int_as_float((127 + k) << 23); }
+    static __device__ __forceinline__ unsigned long long to_u64(float x) { return __float2ull_rz(x); }
+    static __device__ __forceinline__ float ceil_(float x) { return ceilf(x); }
+};
+template <> struct RA<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+    static __device__ __forceinline__ double pow2(int k) { return __longlong_as_double((1023ll + k) << 52); }
+    static __device__ __forceinline__ unsigned long long to_u64(double x) { return __double2ull_rz(x); }
+    static __device__ __forceinline__ double ceil_(double x) { return ceil(x); }
+};
+
+// Integer proposal weight of a candidate with score s when the largest score
+// is smax: max(1, floor((s / smax) * 2^k)); a NaN ratio gives 1.
+template <typename Real>
+__device__ __forceinline__ uint64_t quant_weight(Real s, Real smax, int k)
+{
+    const Real x = RA<Real>::mul(RA<Real>::div(s, smax), RA<Real>::pow2(k));
+    return (x >= (Real)1) ? (uint64_t)RA<Real>::to_u64(x) : 1ull;
+}
+
+// bit length of a positive 32-bit value
+__device__ __forceinline__ int bitlen(uint32_t x) { return 32 - __clz(x); }
+
+// split a positive normal x into mant * 2^e with mant in [1, 2): x becomes
+// mant and e is returned
+__device__ __forceinline__ int renorm(double& x)
+{
+    long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    b = (b & ~(0x7FFll << 52)) | (1023ll << 52);
+    x = __longlong_as_double(b);
+    return e;
+}
+
+}  // namespace pm

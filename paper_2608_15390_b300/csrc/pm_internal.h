@@ -1,0 +1,173 @@
+// pm_internal.h -- structures shared by the library's kernels and its host
+// code (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pm {
+
+constexpr int kWarp = 32;
+// degrees above this never occur in the shared-memory trajectory kernel
+// (n <= kSmemMaxN), so uint16 holds every live degree plus the inactive mark
+constexpr int kSmemMaxN = 16383;
+constexpr int kMaxTreeLevels = 4;
+constexpr int kMaxRngAttempts = 256;
+
+// device status word bits
+enum : uint32_t {
+    ST_RNG_EXHAUSTED = 1u << 0,
+    ST_BAD_INPUT = 1u << 1,
+    ST_INTERNAL = 1u << 2,
+    ST_CAPACITY = 1u << 3,
+};
+
+// Original input matrix A on the device (int32 offsets, validated).
+struct DevInput {
+    int n, m;
+    const int64_t* rp64;    // caller's row pointer
+    const int32_t* ci_in;   // caller's column indices
+    const float* val_in;    // caller's values or nullptr
+};
+
+// A prepared matrix: B0 = A after the initial DM, its CSC view, the outer
+// scaling and the initial minimum-degree state.  Everything a trajectory
+// reads; lives in the context's arena.
+struct DevMatrix {
+    int n, m;            // order, nnz of B0
+    int ok;              // initial DM found a perfect matching
+    int unit_scale;      // binary and r0 = c0 = 1: every proposal is uniform
+    int idx;             // matrix index in the Philox counter
+    int pad;
+    // A (validated copy with int32 offsets) and its CSC view
+    int* a_rp; int* a_ci; float* a_val; int* a_cp; int* a_ri; int* a_ce;
+    uint8_t* keep;       // [m_A] edge survives the initial DM
+    int m_a;
+    int pad2;
+    // B0
+    int* rp; int* ci; float* rv;          // CSR
+    int* cp; int* ri; float* cv; int* ce; // CSC; ce = CSR edge id of a CSC entry
+    void* r0; void* c0;                   // outer scaling (float or double)
+    uint16_t* deg0;                       // [2n] initial live degrees
+    uint32_t* tree0;                      // initial min-degree tree levels
+    int* dm_ws;                           // [dm_ws_ints] initial-DM workspace
+};
+
+struct Sched {
+    int vertex_rule, initial_dm, K0, K, sk, dm, precision, reserved;
+    double theta;
+};
+
+// min-degree tree geometry for 2n leaves: level l (1..nlev) holds the
+// minimum packed key of 32 entries of level l-1 (level 0 = leaves).
+struct TreeGeom {
+    int n2, nlev, idb;
+    uint32_t dcap;
+    int off[kMaxTreeLevels + 1];
+    int size[kMaxTreeLevels + 1];
+    int total;           // words of levels 1..nlev
+};
+
+__host__ __device__ inline TreeGeom tree_geom(int n)
+{
+    TreeGeom g{};
+    g.n2 = 2 * n;
+    int idb = 0;
+    while ((1 << idb) < g.n2) ++idb;
+    g.idb = idb < 1 ? 1 : idb;
+    g.dcap = (1u << (32 - g.idb)) - 2u;
+    int sz = g.n2, off = 0, l = 0;
+    g.size[0] = sz;
+    while (sz > kWarp && l < kMaxTreeLevels) {
+        sz = (sz + kWarp - 1) / kWarp;
+        ++l;
+        g.off[l] = off;
+        g.size[l] = sz;
+        off += sz;
+    }
+    g.nlev = l;
+    g.total = off;
+    return g;
+}
+
+// per-warp global scratch layout for one trajectory slot
+struct SlotLayout {
+    size_t r, c;          // Real[n_max] each
+    size_t stamp;         // int[n_max]
+    size_t tmp_id;        // int[n_max]
+    size_t tmp_val;       // Real[n_max]
+    size_t list_r, list_c;// int[n_max] each
+    size_t mask;          // uint8[m_max]
+    size_t dm;            // int[dm ints]
+    size_t bytes;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline int dm_ws_ints(int n) { return 19 * n + 8; }
+
+inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales, bool local, bool dm)
+{
+    SlotLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t p = o; o = align_up(o + bytes, 256); return p; };
+    L.r = scales ? take((size_t)n_max * real_bytes) : 0;
+    L.c = scales ? take((size_t)n_max * real_bytes) : 0;
+    L.stamp = local ? take((size_t)n_max * 4) : 0;
+    L.tmp_id = local ? take((size_t)n_max * 4) : 0;
+    L.tmp_val = local ? take((size_t)n_max * real_bytes) : 0;
+    L.list_r = local ? take((size_t)n_max * 4) : 0;
+    L.list_c = local ? take((size_t)n_max * 4) : 0;
+    L.mask = dm ? take((size_t)m_max) : 0;
+    L.dm = dm ? take((size_t)dm_ws_ints(n_max) * 4) : 0;
+    L.bytes = align_up(o, 256);
+    if (L.bytes == 0) L.bytes = 256;
+    return L;
+}
+
+struct TrajParams {
+    const DevMatrix* mats;
+    int count;
+    int n_max;
+    const uint64_t* prefix;   // [count + 1] exclusive prefix of trajectories per matrix
+    uint64_t first_traj;
+    uint64_t seed;
+    Sched s;
+    double* log_x;            // [prefix[count]]
+    unsigned long long* counters;  // [count][4]: DM calls, full SK, local SK, algorithmic bytes
+    unsigned long long* work;      // work counter
+    uint32_t* status;
+    uint8_t* slots;           // per-warp scratch
+    SlotLayout slot;
+    int smem_per_warp;        // bytes
+    int warps_per_cta;
+    // trace outputs (nullptr when not tracing)
+    int32_t* chosen;
+    int32_t* deg_v;
+    int32_t* dead_step;
+};
+
+struct StatsPartial {
+    double c;          // max log x of the chunk (-inf if none alive)
+    double s1, s2, m2; // sum y, sum y^2, sum (y - mean)^2 with y = exp(lx - c)
+    unsigned long long cnt, alive;
+};
+
+struct StatsOut {
+    double log_estimate, ess, p_match, rel_spread, rse, log_sum_x, log_sum_x2;
+    unsigned long long n, alive;
+};
+
+// ---- launchers (pm_kernels.cu) ----
+cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, Sched s,
+                           int n_max, uint32_t* status, cudaStream_t st);
+cudaError_t launch_trajectories(const TrajParams& p, int grid, bool trace, cudaStream_t st);
+cudaError_t launch_stats(const double* log_x, const uint64_t* h_prefix, const uint64_t* d_prefix,
+                         int count, StatsPartial* partials, int chunks_per_matrix, StatsOut* out,
+                         cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t count, uint32_t* out,
+                          cudaStream_t st);
+int traj_smem_per_warp(int n_max);
+cudaError_t traj_occupancy(bool fp64, bool trace, int warps_per_cta, int smem, int* ctas_per_sm);
+int traj_kernel_max_warps_per_cta();
+
+}  // namespace pm
