@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--traj", type=int, default=64, help="trajectories per matrix per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--mats", type=int, default=N_MATS,
+                   help="use the first K matrices (profiling of a smaller case)")
+    p.add_argument("--nmax", type=int, default=N_HI,
+                   help="draw n from U{100..nmax} instead (profiling of a smaller case)")
     return p.parse_args()
 
 
@@ -234,7 +238,7 @@ def main():
         dist.init_process_group("nccl")
     from paper_2608_15390_b300 import binding as B
 
-    mats = G.batch_er(N_MATS, N_LO, N_HI, D_LO, D_HI, seed=GEN_SEED)
+    mats = G.batch_er(N_MATS, N_LO, args.nmax, D_LO, D_HI, seed=GEN_SEED)[: args.mats]
     dev = [G.Csr(m.n, torch.from_numpy(m.row_ptr).cuda(), torch.from_numpy(m.col_idx).cuda())
            for m in mats]
     pinned = [G.Csr(m.n, torch.from_numpy(m.row_ptr).pin_memory(), torch.from_numpy(m.col_idx).pin_memory())
@@ -243,7 +247,7 @@ def main():
     ctx = B.Context(local, stream.cuda_stream)
     sched = B.Schedule(**schedule_fields())
     T = args.traj
-    nt = [T] * N_MATS
+    nt = [T] * len(mats)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step(i, host=False):
@@ -314,13 +318,17 @@ def main():
     achieved = (alg_bytes / args.steps) / (kern_ms / args.steps / 1e3) / 1e9
     tpb = ncu_traffic_per_byte()
     traffic = None if tpb is None else tpb * alg_bytes / args.steps
+    if args.mats != N_MATS or args.nmax != N_HI:
+        line_cfg_note = f"reduced case: first {args.mats} matrices, n<={args.nmax} (not a bench value)"
+    else:
+        line_cfg_note = None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "traj_per_matrix_per_step": T,
                    "l2": "flushed between timed steps (256 MB write outside the step events)",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}", "note": line_cfg_note},
         "traj_per_s": tot_traj / t_dev,
         "ess_per_traj": ess_per_traj,
         "median_rse_per_step": statistics.median(rse) if rse else None,

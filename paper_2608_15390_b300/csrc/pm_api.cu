@@ -1,6 +1,7 @@
 // pm_api.cu -- host implementation of the C ABI declared in include/pm.h:
 // argument checks, the context's device arena, launch sequencing on the
 // context's stream, and result read-back.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -113,6 +114,55 @@ pm_status check_csr(pm_context* ctx, const pm_csr* c)
     return PM_OK;
 }
 
+// Execution plan of one matrix (see Plan in pm_internal.h).  Preference
+// order: matrix and scaling vectors in shared memory, then scaling vectors
+// only, then neither; full-SK schedules spread a trajectory over the fewest
+// warps that still keep all 16 warps of the CTA busy.
+Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max)
+{
+    const bool full = s.sk == 1 || s.sk == 2;
+    const bool need_rc = s.sk != 0;
+    const bool dm = s.dm != 0;
+    const int avail = smem_max - kCtaMiscBytes;
+    Plan best{};
+    int best_score = -1;
+    const int combos[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
+    for (const auto& cb : combos) {
+        const bool staged = cb[0] != 0, rc = cb[1] != 0;
+        if (rc && !need_rc) continue;
+        if (staged && n > 65535) continue;
+        const int mb = staged ? staged_matrix_bytes(n, m, dm) : 0;
+        if (mb >= avail) continue;
+        const int sb = group_state_bytes(n, rb, rc);
+        const int fit = (avail - mb) / sb;
+        if (fit < 1) continue;
+        Plan p{};
+        p.staged = staged;
+        p.rc_smem = rc;
+        p.state_bytes = sb;
+        p.mat_bytes = mb;
+        if (full) {
+            for (int g = 1; g <= kCtaWarps; g *= 2) {
+                p.g = g;
+                p.groups = std::min(fit, kCtaWarps / g);
+                if (p.groups * g == kCtaWarps) break;
+            }
+        } else {
+            p.g = 1;
+            p.groups = std::min(fit, kCtaWarps);
+        }
+        const int busy = p.g * p.groups;
+        // full SK: accept the first layout that keeps >= 8 warps busy
+        const int score = busy >= (full ? 8 : 12) ? 1000 : busy;
+        if (score > best_score) {
+            best = p;
+            best_score = score;
+            if (score >= 1000) break;
+        }
+    }
+    return best;
+}
+
 struct Run {
     // inputs
     const pm_csr* mats = nullptr;
@@ -195,8 +245,8 @@ pm_status execute(pm_context* ctx, Run& R)
     const size_t o_status = L.take(4);
     uint64_t max_t = 1;
     for (int k = 0; k < count; ++k) max_t = std::max(max_t, R.ntraj[k]);
-    const int chunks = (int)std::min<uint64_t>(1024, std::max<uint64_t>(1, max_t / 16384));
-    const size_t o_parts = L.take(sizeof(StatsPartial) * (size_t)count * chunks);
+    const int chunks_stats = (int)std::min<uint64_t>(1024, std::max<uint64_t>(1, max_t / 16384));
+    const size_t o_parts = L.take(sizeof(StatsPartial) * (size_t)count * chunks_stats);
     const size_t o_sout = L.take(sizeof(StatsOut) * count);
     size_t o_chosen = 0, o_degv = 0, o_dead = 0;
     if (R.trace) {
@@ -204,7 +254,9 @@ pm_status execute(pm_context* ctx, Run& R)
         o_degv = L.take(4 * total * (size_t)n_max);
         o_dead = L.take(4 * std::max<uint64_t>(total, 1));
     }
-    pm_status st = grow(ctx, &ctx->arena, &ctx->arena_cap, L.off);
+    // room for the plans and the chunk list (at most one chunk per trajectory)
+    const size_t extra = align_up(sizeof(Plan) * count, 256) + align_up(sizeof(Chunk) * (total + count), 256) + 512;
+    pm_status st = grow(ctx, &ctx->arena, &ctx->arena_cap, L.off + extra);
     if (st != PM_OK) return st;
     uint8_t* A = ctx->arena;
     auto P = [&](size_t off) { return (void*)(A + off); };
@@ -279,18 +331,55 @@ pm_status execute(pm_context* ctx, Run& R)
         const bool local = R.s.sk == 3;
         const bool dm = R.s.dm != 0;
         const SlotLayout sl = slot_layout(n_max, (int)m_max, (int)rb, scales, local, dm);
-        const int wpc = traj_kernel_max_warps_per_cta();
-        const int smem_warp = traj_smem_per_warp(n_max);
-        int ctas_per_sm = 0;
-        PM_CUDA(pm::traj_occupancy(fp64, R.trace, wpc, smem_warp * wpc, &ctas_per_sm));
-        if (ctas_per_sm < 1) return fail(ctx, PM_EUNSUPPORTED, "trajectory state does not fit in shared memory");
-        uint64_t grid = (uint64_t)ctx->sm_count * ctas_per_sm;
-        grid = std::min<uint64_t>(grid, (total + wpc - 1) / wpc);
-        const size_t need_slots = sl.bytes * (size_t)grid * wpc;
+        const int smem_max = traj_max_smem_bytes();
+        if (smem_max <= 0) return fail(ctx, PM_ECUDA, "cannot query the shared-memory limit");
+        std::vector<Plan> plans(count);
+        int smem_need = kCtaMiscBytes;
+        for (int k = 0; k < count; ++k) {
+            plans[k] = make_plan(R.mats[k].n, R.mats[k].nnz, (int)rb, R.s, smem_max);
+            if (plans[k].groups < 1)
+                return fail(ctx, PM_EUNSUPPORTED, "trajectory state does not fit in shared memory");
+            smem_need = std::max(smem_need, kCtaMiscBytes + plans[k].mat_bytes + plans[k].groups * plans[k].state_bytes);
+        }
+        // chunks: most expensive matrices first, a few trajectories per group
+        std::vector<int> order(count);
+        for (int k = 0; k < count; ++k) order[k] = k;
+        const bool full_sk = R.s.sk == 1 || R.s.sk == 2;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const double ca = (double)R.mats[a].nnz * (full_sk ? R.mats[a].n : 1);
+            const double cb = (double)R.mats[b].nnz * (full_sk ? R.mats[b].n : 1);
+            return ca > cb;
+        });
+        std::vector<Chunk> chunks;
+        for (int k : order) {
+            const uint64_t csz = (uint64_t)plans[k].groups * 2;
+            for (uint64_t f = 0; f < R.ntraj[k]; f += csz) {
+                Chunk c;
+                c.k = k;
+                c.first = f;
+                c.count = (uint32_t)std::min<uint64_t>(csz, R.ntraj[k] - f);
+                chunks.push_back(c);
+            }
+        }
+        const int grid = ctx->sm_count;
+        Layout L2 = L;
+        const size_t o_plans = L2.take(sizeof(Plan) * count);
+        const size_t o_chunks = L2.take(sizeof(Chunk) * chunks.size());
+        const size_t o_cctr = L2.take(8);
+        if (L2.off > ctx->arena_cap) return fail(ctx, PM_EINVAL, "internal: arena layout");
+        PM_CUDA(cudaMemcpyAsync(P(o_plans), plans.data(), sizeof(Plan) * count, cudaMemcpyHostToDevice, ctx->stream));
+        PM_CUDA(cudaMemcpyAsync(P(o_chunks), chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        PM_CUDA(cudaMemsetAsync(P(o_cctr), 0, 8, ctx->stream));
+        h2d += sizeof(Plan) * count + sizeof(Chunk) * chunks.size();
+        const size_t need_slots = sl.bytes * (size_t)grid * kCtaWarps;
         st = grow(ctx, &ctx->slots, &ctx->slots_cap, need_slots);
         if (st != PM_OK) return st;
         TrajParams tp{};
         tp.mats = d_mats;
+        tp.plans = (const Plan*)P(o_plans);
+        tp.chunks = (const Chunk*)P(o_chunks);
+        tp.n_chunks = (int)chunks.size();
         tp.count = count;
         tp.n_max = n_max;
         tp.prefix = (const uint64_t*)P(o_prefix);
@@ -299,24 +388,22 @@ pm_status execute(pm_context* ctx, Run& R)
         tp.s = R.s;
         tp.log_x = (double*)P(o_logx);
         tp.counters = (unsigned long long*)P(o_counters);
-        tp.work = (unsigned long long*)P(o_work);
+        tp.chunk_counter = (int*)P(o_cctr);
         tp.status = d_status;
         tp.slots = ctx->slots;
         tp.slot = sl;
-        tp.smem_per_warp = smem_warp;
-        tp.warps_per_cta = wpc;
         if (R.trace) {
             tp.chosen = (int32_t*)P(o_chosen);
             tp.deg_v = (int32_t*)P(o_degv);
             tp.dead_step = (int32_t*)P(o_dead);
         }
-        PM_CUDA(launch_trajectories(tp, (int)grid, R.trace, ctx->stream));
+        PM_CUDA(launch_trajectories(tp, grid, smem_need, R.trace, ctx->stream));
         PM_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
         launched = true;
-        ctx->last_grid = (int)grid;
-        ctx->last_wpc = wpc;
+        ctx->last_grid = grid;
+        ctx->last_wpc = kCtaWarps;
         PM_CUDA(launch_stats((const double*)P(o_logx), prefix.data(), (const uint64_t*)P(o_prefix), count,
-                             (StatsPartial*)P(o_parts), chunks, (StatsOut*)P(o_sout), ctx->stream));
+                             (StatsPartial*)P(o_parts), chunks_stats, (StatsOut*)P(o_sout), ctx->stream));
     }
 
     // ---- read back ----

@@ -120,6 +120,15 @@ __device__ __forceinline__ uint64_t quant_weight(Real s, Real smax, int k)
     return (x >= (Real)1) ? (uint64_t)RA<Real>::to_u64(x) : 1ull;
 }
 
+// packed (degree, unified id) key of leaf x of the minimum-degree tree;
+// inactive vertices get the largest key
+__device__ __forceinline__ uint32_t leaf_key(const uint16_t* deg, int x, const TreeGeom& G)
+{
+    const uint32_t d = deg[x];
+    if (d == kInact) return 0xFFFFFFFFu;
+    return ((d < G.dcap ? d : G.dcap) << G.idb) | (uint32_t)x;
+}
+
 // bit length of a positive 32-bit value
 __device__ __forceinline__ int bitlen(uint32_t x) { return 32 - __clz(x); }
 

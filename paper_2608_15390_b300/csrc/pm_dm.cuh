@@ -15,8 +15,8 @@ namespace pm {
 __host__ __device__ inline int dm_serial_ints(int n) { return 19 * n + 3; }
 
 // Live must provide: bool row(int i), bool col(int j), bool edge(int e, int i, int j)
-template <class Live>
-__device__ bool dm_serial(int n, const int* rp, const int* ci, const int* cp, const int* ri,
+template <class Live, typename Idx>
+__device__ bool dm_serial(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri,
                           const int* ce, const Live& live, uint8_t* mask, int* ws)
 {
     int* mr = ws;

@@ -124,8 +124,33 @@ inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales,
     return L;
 }
 
+// Execution plan of one matrix, chosen on the host: a trajectory is run by a
+// group of g warps (the leader warp does the sequential step, the whole group
+// the SK sweeps); `groups` groups share a CTA; the CTA optionally stages the
+// matrix indices (uint16) in shared memory; the scaling vectors live in
+// shared memory (rc_smem) or in the group's global slot.
+struct Plan {
+    int g, groups, staged, rc_smem;
+    int state_bytes;   // shared bytes of one group
+    int mat_bytes;     // shared bytes of the staged matrix (0 if not staged)
+};
+
+// a run of trajectories first .. first + count - 1 (indices inside matrix k)
+struct Chunk {
+    int k;
+    uint32_t count;
+    uint64_t first;
+};
+
+constexpr int kCtaWarps = 16;            // 512 threads, one CTA per SM
+constexpr int kCtaMiscBytes = 64;
+constexpr int kGroupMiscInts = 32;
+
 struct TrajParams {
     const DevMatrix* mats;
+    const Plan* plans;        // [count]
+    const Chunk* chunks;      // [n_chunks]
+    int n_chunks;
     int count;
     int n_max;
     const uint64_t* prefix;   // [count + 1] exclusive prefix of trajectories per matrix
@@ -134,17 +159,32 @@ struct TrajParams {
     Sched s;
     double* log_x;            // [prefix[count]]
     unsigned long long* counters;  // [count][4]: DM calls, full SK, local SK, algorithmic bytes
-    unsigned long long* work;      // work counter
+    int* chunk_counter;
     uint32_t* status;
-    uint8_t* slots;           // per-warp scratch
+    uint8_t* slots;           // per-group global scratch, kCtaWarps slots per CTA
     SlotLayout slot;
-    int smem_per_warp;        // bytes
-    int warps_per_cta;
     // trace outputs (nullptr when not tracing)
     int32_t* chosen;
     int32_t* deg_v;
     int32_t* dead_step;
 };
+
+// shared-memory sizes used by the plan
+inline int group_state_bytes(int n, int real_bytes, bool rc_smem)
+{
+    const TreeGeom G = tree_geom(n);
+    size_t b = align_up((size_t)((2 * n + 7) & ~7) * 2, 16) + align_up((size_t)G.total * 4, 16);
+    if (rc_smem) b += 2 * align_up((size_t)n * real_bytes, 16);
+    b += kGroupMiscInts * 4;
+    return (int)b;
+}
+
+inline int staged_matrix_bytes(int n, int64_t m, bool with_ce)
+{
+    size_t b = 2 * align_up((size_t)(n + 1) * 4, 16) + 2 * align_up((size_t)m * 2, 16);
+    if (with_ce) b += align_up((size_t)m * 4, 16);
+    return (int)b;
+}
 
 struct StatsPartial {
     double c;          // max log x of the chunk (-inf if none alive)
@@ -160,14 +200,12 @@ struct StatsOut {
 // ---- launchers (pm_kernels.cu) ----
 cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, Sched s,
                            int n_max, uint32_t* status, cudaStream_t st);
-cudaError_t launch_trajectories(const TrajParams& p, int grid, bool trace, cudaStream_t st);
+cudaError_t launch_trajectories(const TrajParams& p, int grid, int smem_bytes, bool trace, cudaStream_t st);
 cudaError_t launch_stats(const double* log_x, const uint64_t* h_prefix, const uint64_t* d_prefix,
                          int count, StatsPartial* partials, int chunks_per_matrix, StatsOut* out,
                          cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t count, uint32_t* out,
                           cudaStream_t st);
-int traj_smem_per_warp(int n_max);
-cudaError_t traj_occupancy(bool fp64, bool trace, int warps_per_cta, int smem, int* ctas_per_sm);
-int traj_kernel_max_warps_per_cta();
+int traj_max_smem_bytes();
 
 }  // namespace pm

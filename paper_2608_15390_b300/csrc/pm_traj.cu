@@ -1,0 +1,802 @@
+// pm_traj.cu -- the trajectory kernel (Algorithm 2, one trajectory per group
+// of g warps).
+//
+// Per step the group's leader warp
+//   - picks the active row or column of least (live degree, unified id)
+//     from a 32-ary tree of packed keys (two-sided minimum degree, Sec. 3.2),
+//   - scans the picked vertex's adjacency (one lane per entry), forms the
+//     integer proposal weights of Eq. 3 and draws the partner with Philox,
+//   - multiplies X by B_vu / q(u|v) (kept as mantissa/exponent pairs),
+//   - eliminates the pair: decrements the live degrees of both neighbour
+//     lists and lowers / repairs the tree entries above them,
+//   - decides the DM policy (All / Thrs / Trck) and the number of full SK
+//     iterations (Fixed / Adaptive), or runs the Local repair of Eq. 5;
+// then the whole group runs the InnerDM degree rebuild and the full SK
+// iterations (one thread per column, then per row; every sum is taken in
+// adjacency order so the result is fixed by IEEE arithmetic alone).
+//
+// A persistent CTA takes chunks of trajectories of one matrix at a time and,
+// when the plan says so, stages that matrix's adjacency (uint16 indices) in
+// shared memory for all its groups.
+#include <cmath>
+#include "pm_device.cuh"
+#include "pm_dm.cuh"
+
+namespace pm {
+
+namespace {
+
+enum { VR_ROW = 1 };
+enum { SKP_NONE = 0, SKP_FIXED = 1, SKP_ADAPTIVE = 2, SKP_LOCAL = 3 };
+enum { DMP_NONE = 0, DMP_ALL = 1, DMP_THRS = 2, DMP_TRCK = 3 };
+
+template <typename Idx>
+struct MV {
+    int n;
+    const int* rp;    // row pointers
+    const int* cp;    // column pointers
+    const Idx* ci;    // column index of each row entry
+    const Idx* ri;    // row index of each column entry
+    const int* ce;    // row-entry id of each column entry (DM masks)
+    const float* rv;  // values in row order or nullptr
+    const float* cv;  // values in column order or nullptr
+};
+
+__device__ __forceinline__ size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct Grp {
+    int g, nthr, tid, wig, lane, bar;
+    int* misc;
+};
+
+__device__ __forceinline__ void gsync(const Grp& G)
+{
+    if (G.g == 1) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(G.bar), "r"(G.nthr) : "memory");
+}
+
+struct LiveTraj {
+    const uint16_t* deg;
+    const uint8_t* mask;
+    int n;
+    __device__ bool row(int i) const { return deg[i] != kInact; }
+    __device__ bool col(int j) const { return deg[n + j] != kInact; }
+    __device__ bool edge(int e, int i, int j) const
+    {
+        return mask[e] && deg[i] != kInact && deg[n + j] != kInact;
+    }
+};
+
+// ---- minimum-degree tree ----
+__device__ __forceinline__ void tree_lower(uint32_t* tree, const TreeGeom& T, int x, uint32_t d)
+{
+    const uint32_t key = ((d < T.dcap ? d : T.dcap) << T.idb) | (uint32_t)x;
+    for (int l = 1; l <= T.nlev; ++l) atomicMin(&tree[T.off[l] + (x >> (5 * l))], key);
+}
+
+__device__ void tree_fix2(const uint16_t* deg, uint32_t* tree, const TreeGeom& T, int x, int y, int lane)
+{
+    for (int l = 1; l <= T.nlev; ++l) {
+        const int gx = x >> (5 * l), gy = y >> (5 * l);
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            const int gi = w ? gy : gx;
+            if (w && gy == gx) break;
+            const int c = gi * 32 + lane;
+            uint32_t key = 0xFFFFFFFFu;
+            if (c < T.size[l - 1]) key = (l == 1) ? leaf_key(deg, c, T) : tree[T.off[l - 1] + c];
+            key = __reduce_min_sync(kFull, key);
+            if (lane == 0) tree[T.off[l] + gi] = key;
+        }
+        __syncwarp();
+    }
+}
+
+__device__ void tree_build(const uint16_t* deg, uint32_t* tree, const TreeGeom& T, int lane)
+{
+    for (int l = 1; l <= T.nlev; ++l) {
+        for (int gi = lane; gi < T.size[l]; gi += 32) {
+            uint32_t best = 0xFFFFFFFFu;
+            for (int q = 0; q < 32; ++q) {
+                const int c = gi * 32 + q;
+                if (c >= T.size[l - 1]) break;
+                const uint32_t key = (l == 1) ? leaf_key(deg, c, T) : tree[T.off[l - 1] + c];
+                best = key < best ? key : best;
+            }
+            tree[T.off[l] + gi] = best;
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ int md_pick(const uint16_t* deg, const uint32_t* tree, const TreeGeom& T, int lane)
+{
+    uint32_t key = 0xFFFFFFFFu;
+    if (T.nlev == 0) {
+        if (lane < T.n2) key = leaf_key(deg, lane, T);
+    } else if (lane < T.size[T.nlev]) {
+        key = tree[T.off[T.nlev] + lane];
+    }
+    key = __reduce_min_sync(kFull, key);
+    if ((key >> T.idb) < T.dcap) return (int)(key & ((1u << T.idb) - 1u));
+    unsigned long long best = ~0ull;  // saturated degree field: exact scan
+    for (int x = lane; x < T.n2; x += 32) {
+        const uint32_t d = deg[x];
+        if (d == kInact) continue;
+        const unsigned long long k64 = ((unsigned long long)d << 32) | (unsigned)x;
+        best = k64 < best ? k64 : best;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(kFull, best, o);
+        best = t < best ? t : best;
+    }
+    return (int)(best & 0xFFFFFFFFu);
+}
+
+template <typename Idx>
+__device__ __forceinline__ bool entry_live(const uint16_t* deg, const uint8_t* mask, const MV<Idx>& V, bool row_list,
+                                           int e, int pid)
+{
+    if (deg[pid] == kInact) return false;
+    if (!mask) return true;
+    return mask[row_list ? e : V.ce[e]] != 0;
+}
+
+// ---- SK sums in adjacency order (unrolled by four; a dead entry adds +0,
+// which leaves the sum unchanged because every partial sum is >= +0) ----
+template <typename Real, typename Idx>
+__device__ __forceinline__ Real col_sum(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, const Real* r,
+                                        int j)
+{
+    const int b = V.cp[j], e = V.cp[j + 1];
+    Real sum = 0;
+    int k = b;
+    for (; k + 4 <= e; k += 4) {
+        const int i0 = V.ri[k], i1 = V.ri[k + 1], i2 = V.ri[k + 2], i3 = V.ri[k + 3];
+        bool l0 = deg[i0] != kInact, l1 = deg[i1] != kInact, l2 = deg[i2] != kInact, l3 = deg[i3] != kInact;
+        if (mask) {
+            l0 = l0 && mask[V.ce[k]];
+            l1 = l1 && mask[V.ce[k + 1]];
+            l2 = l2 && mask[V.ce[k + 2]];
+            l3 = l3 && mask[V.ce[k + 3]];
+        }
+        Real t0 = r[i0], t1 = r[i1], t2 = r[i2], t3 = r[i3];
+        if (V.cv) {
+            t0 = RA<Real>::mul((Real)__ldg(V.cv + k), t0);
+            t1 = RA<Real>::mul((Real)__ldg(V.cv + k + 1), t1);
+            t2 = RA<Real>::mul((Real)__ldg(V.cv + k + 2), t2);
+            t3 = RA<Real>::mul((Real)__ldg(V.cv + k + 3), t3);
+        }
+        sum = RA<Real>::add(sum, l0 ? t0 : (Real)0);
+        sum = RA<Real>::add(sum, l1 ? t1 : (Real)0);
+        sum = RA<Real>::add(sum, l2 ? t2 : (Real)0);
+        sum = RA<Real>::add(sum, l3 ? t3 : (Real)0);
+    }
+    for (; k < e; ++k) {
+        const int i = V.ri[k];
+        if (deg[i] == kInact || (mask && !mask[V.ce[k]])) continue;
+        const Real t = V.cv ? RA<Real>::mul((Real)__ldg(V.cv + k), r[i]) : r[i];
+        sum = RA<Real>::add(sum, t);
+    }
+    return sum;
+}
+
+template <typename Real, typename Idx>
+__device__ __forceinline__ Real row_sum(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, const Real* c,
+                                        int i)
+{
+    const int n = V.n;
+    const int b = V.rp[i], e = V.rp[i + 1];
+    Real sum = 0;
+    int k = b;
+    for (; k + 4 <= e; k += 4) {
+        const int j0 = V.ci[k], j1 = V.ci[k + 1], j2 = V.ci[k + 2], j3 = V.ci[k + 3];
+        bool l0 = deg[n + j0] != kInact, l1 = deg[n + j1] != kInact, l2 = deg[n + j2] != kInact,
+             l3 = deg[n + j3] != kInact;
+        if (mask) {
+            l0 = l0 && mask[k];
+            l1 = l1 && mask[k + 1];
+            l2 = l2 && mask[k + 2];
+            l3 = l3 && mask[k + 3];
+        }
+        Real t0 = c[j0], t1 = c[j1], t2 = c[j2], t3 = c[j3];
+        if (V.rv) {
+            t0 = RA<Real>::mul((Real)__ldg(V.rv + k), t0);
+            t1 = RA<Real>::mul((Real)__ldg(V.rv + k + 1), t1);
+            t2 = RA<Real>::mul((Real)__ldg(V.rv + k + 2), t2);
+            t3 = RA<Real>::mul((Real)__ldg(V.rv + k + 3), t3);
+        }
+        sum = RA<Real>::add(sum, l0 ? t0 : (Real)0);
+        sum = RA<Real>::add(sum, l1 ? t1 : (Real)0);
+        sum = RA<Real>::add(sum, l2 ? t2 : (Real)0);
+        sum = RA<Real>::add(sum, l3 ? t3 : (Real)0);
+    }
+    for (; k < e; ++k) {
+        const int j = V.ci[k];
+        if (deg[n + j] == kInact || (mask && !mask[k])) continue;
+        const Real t = V.rv ? RA<Real>::mul((Real)__ldg(V.rv + k), c[j]) : c[j];
+        sum = RA<Real>::add(sum, t);
+    }
+    return sum;
+}
+
+// one full SK iteration on the residual by the whole group (Sec. 3.3):
+// columns from r, then rows from the new c; no live edge -> old scale kept
+template <typename Real, typename Idx>
+__device__ void sk_iteration(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, Real* r, Real* c,
+                             const Grp& G)
+{
+    const int n = V.n;
+    for (int j = G.tid; j < n; j += G.nthr) {
+        const uint16_t dj = deg[n + j];
+        if (dj == kInact || dj == 0) continue;
+        c[j] = RA<Real>::rcp(col_sum<Real, Idx>(V, deg, mask, r, j));
+    }
+    gsync(G);
+    for (int i = G.tid; i < n; i += G.nthr) {
+        const uint16_t di = deg[i];
+        if (di == kInact || di == 0) continue;
+        r[i] = RA<Real>::rcp(row_sum<Real, Idx>(V, deg, mask, c, i));
+    }
+    gsync(G);
+}
+
+// Local repair (Eq. 5) by the leader warp.  lr: N_t(C)\{R} (rows), lc:
+// N_t(R)\{C} (columns).  R_loc = lr U N_{t+1}(lc), C_loc = lc U N_{t+1}(lr).
+// New row scales read the old c and are staged (deduplicated by stamp);
+// column scales read the old r and are written in place; staged rows commit
+// last.  Returns the number of staged rows.
+template <typename Real, typename Idx>
+__device__ int local_repair(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, Real* r, Real* c,
+                            const int* lr, int nr, const int* lc, int nc, int* stamp, int st, int* tmp_id,
+                            Real* tmp_val, int* tmp_cnt, int lane)
+{
+    const int n = V.n;
+    if (lane == 0) *tmp_cnt = 0;
+    __syncwarp();
+    auto stage_row = [&](int i) {
+        if (atomicExch(&stamp[i], st) == st) return;
+        const Real v = (deg[i] == 0) ? r[i] : RA<Real>::rcp(row_sum<Real, Idx>(V, deg, mask, c, i));
+        const int q = atomicAdd(tmp_cnt, 1);
+        tmp_id[q] = i;
+        tmp_val[q] = v;
+    };
+    for (int q = lane; q < nr; q += 32) stage_row(lr[q]);
+    for (int q = lane; q < nc; q += 32) {
+        const int j = lc[q];
+        for (int k = V.cp[j]; k < V.cp[j + 1]; ++k) {
+            const int i = V.ri[k];
+            if (deg[i] == kInact || (mask && !mask[V.ce[k]])) continue;
+            stage_row(i);
+        }
+    }
+    __syncwarp();
+    auto col_new = [&](int j) {
+        c[j] = (deg[n + j] == 0) ? c[j] : RA<Real>::rcp(col_sum<Real, Idx>(V, deg, mask, r, j));
+    };
+    for (int q = lane; q < nc; q += 32) col_new(lc[q]);
+    for (int q = lane; q < nr; q += 32) {
+        const int i = lr[q];
+        for (int k = V.rp[i]; k < V.rp[i + 1]; ++k) {
+            const int j = V.ci[k];
+            if (deg[n + j] == kInact || (mask && !mask[k])) continue;
+            col_new(j);
+        }
+    }
+    __syncwarp();
+    const int cnt = *tmp_cnt;
+    for (int q = lane; q < cnt; q += 32) r[tmp_id[q]] = tmp_val[q];
+    __syncwarp();
+    return cnt;
+}
+
+template <typename Real, typename Idx>
+__device__ __forceinline__ Real cand_score(const MV<Idx>& V, bool vrow, int e, int p, const Real* r, const Real* c)
+{
+    const float* vals = vrow ? V.rv : V.cv;
+    const Real sc = vrow ? c[p] : r[p];
+    Real s = vals ? RA<Real>::mul((Real)__ldg(vals + e), sc) : sc;
+    if (!(s >= (Real)0)) s = 0;
+    return s;
+}
+
+// misc slots of a group (two step buffers so a fast leader never overwrites
+// values a slower warp of its group is still reading)
+enum { M_DEAD = 0, M_NIT = 1, M_DM = 2, M_CNTR = 3, M_CNTC = 4, M_STRIDE = 8, M_TMP = 16, M_TRAJ = 17, M_DMOK = 18 };
+
+template <typename Real, typename Idx, bool TRACE>
+__device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>& V, int k, uint64_t gq,
+                          uint64_t local, uint16_t* deg, uint32_t* tree, Real* r_sm, uint8_t* slot, const Grp& G)
+{
+    const int n = V.n;
+    const int lane = G.lane;
+    const bool leader = G.wig == 0;
+    const uint64_t traj = P.first_traj + local;
+    const uint32_t midx = (uint32_t)Mp->idx;
+    const Sched& S = P.s;
+    const TreeGeom T = tree_geom(n);
+    if (TRACE && leader) {
+        for (int q = lane; q < 2 * n; q += 32) P.chosen[gq * 2 * n + q] = -1;
+        for (int q = lane; q < n; q += 32) P.deg_v[gq * n + q] = -1;
+    }
+    if (!Mp->ok) {
+        if (leader && lane == 0) {
+            P.log_x[gq] = -INFINITY;
+            if (TRACE) P.dead_step[gq] = 0;
+        }
+        gsync(G);
+        return;
+    }
+    const bool inner_sk = S.sk != SKP_NONE;
+    const bool use_dm = S.dm != DMP_NONE;
+    const bool use_local = S.sk == SKP_LOCAL;
+
+    // trajectory state from the shared initial state
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(Mp->deg0);
+        uint4* dst = reinterpret_cast<uint4*>(deg);
+        const int nv = (2 * n + 7) / 8;
+        for (int q = G.tid; q < nv; q += G.nthr) dst[q] = __ldg(src + q);
+        for (int q = G.tid; q < T.total; q += G.nthr) tree[q] = __ldg(Mp->tree0 + q);
+    }
+    Real* r;
+    Real* c;
+    if (inner_sk) {
+        if (r_sm) {
+            r = r_sm;
+            c = reinterpret_cast<Real*>(reinterpret_cast<uint8_t*>(r_sm) + a16((size_t)n * sizeof(Real)));
+        } else {
+            r = reinterpret_cast<Real*>(slot + P.slot.r);
+            c = reinterpret_cast<Real*>(slot + P.slot.c);
+        }
+        const Real* r0 = reinterpret_cast<const Real*>(Mp->r0);
+        const Real* c0 = reinterpret_cast<const Real*>(Mp->c0);
+        for (int q = G.tid; q < n; q += G.nthr) { r[q] = __ldg(r0 + q); c[q] = __ldg(c0 + q); }
+    } else {
+        r = reinterpret_cast<Real*>(Mp->r0);
+        c = reinterpret_cast<Real*>(Mp->c0);
+    }
+    uint8_t* mask = nullptr;
+    int* dmws = nullptr;
+    if (use_dm) {
+        mask = slot + P.slot.mask;
+        dmws = reinterpret_cast<int*>(slot + P.slot.dm);
+        const int m = Mp->m;
+        for (int q = G.tid; q < m; q += G.nthr) mask[q] = 1;
+    }
+    int *stamp = nullptr, *tmp_id = nullptr, *list_r = nullptr, *list_c = nullptr;
+    Real* tmp_val = nullptr;
+    if (use_local) {
+        stamp = reinterpret_cast<int*>(slot + P.slot.stamp);
+        tmp_id = reinterpret_cast<int*>(slot + P.slot.tmp_id);
+        tmp_val = reinterpret_cast<Real*>(slot + P.slot.tmp_val);
+        list_r = reinterpret_cast<int*>(slot + P.slot.list_r);
+        list_c = reinterpret_cast<int*>(slot + P.slot.list_c);
+        for (int q = G.tid; q < n; q += G.nthr) stamp[q] = 0;
+    }
+    gsync(G);
+
+    const bool uniform = Mp->unit_scale && !inner_sk;
+    const Real theta = (Real)S.theta;
+    // leader-lane state: X = num / den * 2^ex
+    double num = 1.0, den = 1.0;
+    int ex = 0;
+    Real track = 1;
+    unsigned n_dm = 0, n_full = 0, n_loc = 0;
+    int dead_step = -1;
+    uint64_t alg_bytes = (uint64_t)2 * n * 4;
+    int m_live = Mp->m;
+
+    for (int t = 0; t < n; ++t) {
+        int* mb = G.misc + (t & 1) * M_STRIDE;
+        if (leader) {
+            int dead = 0, nit = 0, run_dm = 0, cnt_r = 0, cnt_c = 0;
+            do {  // the sequential part of step t (breaks out on death)
+                const int v = (S.vertex_rule == VR_ROW) ? t : md_pick(deg, tree, T, lane);
+                const int dv = deg[v];
+                if (TRACE && lane == 0) P.deg_v[gq * n + t] = dv;
+                if (dv == 0) { dead = 1; break; }
+                const bool vrow = v < n;
+                const int vi = vrow ? v : v - n;
+                const int beg = (vrow ? V.rp : V.cp)[vi];
+                const int end = (vrow ? V.rp : V.cp)[vi + 1];
+                const Idx* adj = vrow ? V.ci : V.ri;
+                const int poff = vrow ? n : 0;
+                const int kq = 40 - bitlen((uint32_t)dv);
+                const int len = end - beg;
+
+                uint64_t W = 0, w_sel = 0;
+                int sel_e = -1, sel_p = -1;
+                bool keep_live = false;
+                int keep_pid = 0;
+                uint64_t rr;
+                if (len <= 32) {
+                    const int e = beg + lane;
+                    const bool in = lane < len;
+                    const int pp = in ? (int)adj[e] : 0;
+                    const bool live = in && entry_live(deg, mask, V, vrow, e, pp + poff);
+                    const unsigned lm = __ballot_sync(kFull, live);
+                    uint64_t w;
+                    if (uniform) {
+                        w = live ? (1ull << kq) : 0ull;
+                        W = (uint64_t)dv << kq;
+                    } else {
+                        const Real sv = live ? cand_score<Real, Idx>(V, vrow, e, pp, r, c) : (Real)0;
+                        const Real smax = warp_max_nonneg(sv);
+                        w = live ? quant_weight<Real>(sv, smax, kq) : 0ull;
+                        W = warp_sum_u64(w);
+                    }
+                    rr = uniform_below(W, P.seed, traj, midx, (uint32_t)t);
+                    if (rr == ~0ull) {
+                        if (lane == 0) atomicOr(P.status, ST_RNG_EXHAUSTED);
+                        dead = 1;
+                        break;
+                    }
+                    int sl;
+                    if (uniform) {
+                        unsigned mm = lm;  // drop the first (rr >> kq) live lanes
+                        for (int q = (int)(rr >> kq); q > 0; --q) mm &= mm - 1u;
+                        sl = __ffs(mm) - 1;
+                    } else {
+                        const uint64_t pre = warp_incl_scan_u64(w, lane);
+                        const unsigned hit = __ballot_sync(kFull, live && pre > rr);
+                        sl = __ffs(hit) - 1;
+                    }
+                    if (sl >= 0) {
+                        sel_e = __shfl_sync(kFull, e, sl);
+                        sel_p = __shfl_sync(kFull, pp, sl);
+                        w_sel = __shfl_sync(kFull, w, sl);
+                    }
+                    keep_live = live && pp != sel_p;
+                    keep_pid = pp + poff;
+                } else {
+                    Real smax = 0;
+                    if (!uniform) {
+                        for (int base = beg; base < end; base += 32) {
+                            const int e = base + lane;
+                            Real sv = 0;
+                            if (e < end) {
+                                const int pp = adj[e];
+                                if (entry_live(deg, mask, V, vrow, e, pp + poff))
+                                    sv = cand_score<Real, Idx>(V, vrow, e, pp, r, c);
+                            }
+                            const Real cm = warp_max_nonneg(sv);
+                            smax = cm > smax ? cm : smax;
+                        }
+                        for (int base = beg; base < end; base += 32) {
+                            const int e = base + lane;
+                            uint64_t w = 0;
+                            if (e < end) {
+                                const int pp = adj[e];
+                                if (entry_live(deg, mask, V, vrow, e, pp + poff))
+                                    w = quant_weight<Real>(cand_score<Real, Idx>(V, vrow, e, pp, r, c), smax, kq);
+                            }
+                            W += warp_sum_u64(w);
+                        }
+                    } else {
+                        W = (uint64_t)dv << kq;
+                    }
+                    rr = uniform_below(W, P.seed, traj, midx, (uint32_t)t);
+                    if (rr == ~0ull) {
+                        if (lane == 0) atomicOr(P.status, ST_RNG_EXHAUSTED);
+                        dead = 1;
+                        break;
+                    }
+                    uint64_t carry = 0;
+                    for (int base = beg; base < end; base += 32) {
+                        const int e = base + lane;
+                        int pp = 0;
+                        bool live = false;
+                        uint64_t w = 0;
+                        if (e < end) {
+                            pp = adj[e];
+                            live = entry_live(deg, mask, V, vrow, e, pp + poff);
+                            if (live)
+                                w = uniform ? (1ull << kq)
+                                            : quant_weight<Real>(cand_score<Real, Idx>(V, vrow, e, pp, r, c), smax, kq);
+                        }
+                        const uint64_t pre = warp_incl_scan_u64(w, lane) + carry;
+                        const unsigned hit = __ballot_sync(kFull, live && pre > rr);
+                        if (hit) {
+                            const int sl = __ffs(hit) - 1;
+                            sel_e = __shfl_sync(kFull, e, sl);
+                            sel_p = __shfl_sync(kFull, pp, sl);
+                            w_sel = __shfl_sync(kFull, w, sl);
+                            break;
+                        }
+                        carry = __shfl_sync(kFull, pre, 31);
+                    }
+                }
+                if (sel_p < 0 || sel_e < beg || sel_e >= end) {  // only with corrupt degrees
+                    if (lane == 0) atomicOr(P.status, ST_INTERNAL);
+                    dead = 1;
+                    break;
+                }
+                const int R = vrow ? vi : sel_p;  // matched row
+                const int C = vrow ? sel_p : vi;  // matched column
+                if (TRACE && lane == 0) {
+                    P.chosen[(gq * n + t) * 2 + 0] = v;
+                    P.chosen[(gq * n + t) * 2 + 1] = sel_p + poff;
+                }
+                if (lane == 0) {  // X <- X * B_vu * W / w_u
+                    num = num * (double)W;
+                    const float* vals = vrow ? V.rv : V.cv;
+                    if (vals) num = num * (double)__ldg(vals + sel_e);
+                    den = den * (double)w_sel;
+                    ex += renorm(num);
+                    ex -= renorm(den);
+                }
+                const Real z = RA<Real>::mul(r[R], c[C]);
+
+                // eliminate R and C
+                __syncwarp();
+                if (lane == 0) { deg[R] = kInact; deg[n + C] = kInact; }
+                __syncwarp();
+                int* list_v = vrow ? list_c : list_r;
+                int* list_u = vrow ? list_r : list_c;
+                int cnt_v = 0, cnt_u = 0;
+                if (len <= 32) {
+                    if (keep_live) {
+                        const uint32_t d = deg[keep_pid] - 1u;
+                        deg[keep_pid] = (uint16_t)d;
+                        tree_lower(tree, T, keep_pid, d);
+                    }
+                    const unsigned km = __ballot_sync(kFull, keep_live);
+                    if (use_local && keep_live) list_v[__popc(km & ((1u << lane) - 1u))] = keep_pid - poff;
+                    cnt_v = __popc(km);
+                } else {
+                    for (int base = beg; base < end; base += 32) {
+                        const int e = base + lane;
+                        bool live = false;
+                        int pid = 0;
+                        if (e < end) {
+                            pid = (int)adj[e] + poff;
+                            live = entry_live(deg, mask, V, vrow, e, pid);
+                        }
+                        if (live) {
+                            const uint32_t d = deg[pid] - 1u;
+                            deg[pid] = (uint16_t)d;
+                            tree_lower(tree, T, pid, d);
+                        }
+                        const unsigned km = __ballot_sync(kFull, live);
+                        if (use_local && live) list_v[cnt_v + __popc(km & ((1u << lane) - 1u))] = pid - poff;
+                        cnt_v += __popc(km);
+                    }
+                }
+                int ulen = 0;
+                {  // the partner's list
+                    const bool urow = !vrow;
+                    const int ub = (urow ? V.rp : V.cp)[sel_p];
+                    const int ue = (urow ? V.rp : V.cp)[sel_p + 1];
+                    const Idx* uadj = urow ? V.ci : V.ri;
+                    const int uoff = urow ? n : 0;
+                    ulen = ue - ub;
+                    for (int base = ub; base < ue; base += 32) {
+                        const int e = base + lane;
+                        bool live = false;
+                        int pid = 0;
+                        if (e < ue) {
+                            pid = (int)uadj[e] + uoff;
+                            live = entry_live(deg, mask, V, urow, e, pid);
+                        }
+                        if (live) {
+                            const uint32_t d = deg[pid] - 1u;
+                            deg[pid] = (uint16_t)d;
+                            tree_lower(tree, T, pid, d);
+                        }
+                        const unsigned km = __ballot_sync(kFull, live);
+                        if (use_local && live) list_u[cnt_u + __popc(km & ((1u << lane) - 1u))] = pid - uoff;
+                        cnt_u += __popc(km);
+                    }
+                }
+                cnt_r = vrow ? cnt_u : cnt_v;
+                cnt_c = vrow ? cnt_v : cnt_u;
+                m_live -= dv + cnt_u;
+                alg_bytes += (uint64_t)8 * (uint64_t)(len + ulen);
+                __syncwarp();
+                if (S.vertex_rule != VR_ROW) tree_fix2(deg, tree, T, R, n + C, lane);
+                track = RA<Real>::mul(track, z);
+                if (t + 1 < n) {
+                    run_dm = (S.dm == DMP_ALL) || (S.dm == DMP_THRS && z < theta) ||
+                             (S.dm == DMP_TRCK && track < theta);
+                    if (S.sk == SKP_FIXED) {
+                        nit = S.K;
+                    } else if (S.sk == SKP_ADAPTIVE) {
+                        const Real b = RA<Real>::mul(RA<Real>::sub((Real)1, z), (Real)S.K);
+                        nit = (b > (Real)0) ? (int)RA<Real>::ceil_(b) : 0;
+                    }
+                }
+            } while (0);
+            if (dead) dead_step = t;
+            if (lane == 0) {
+                mb[M_DEAD] = dead;
+                mb[M_NIT] = nit;
+                mb[M_DM] = run_dm;
+                mb[M_CNTR] = cnt_r;
+                mb[M_CNTC] = cnt_c;
+            }
+        }
+        gsync(G);
+        if (mb[M_DEAD]) break;
+        if (t + 1 >= n) continue;
+        if (mb[M_DM]) {
+            if (leader) ++n_dm;
+            if (leader && lane == 0)
+                G.misc[M_DMOK] = dm_serial(n, V.rp, V.ci, V.cp, V.ri, V.ce, LiveTraj{deg, mask, n}, mask, dmws) ? 1 : 0;
+            gsync(G);
+            if (!G.misc[M_DMOK]) {
+                if (leader) dead_step = t;
+                break;
+            }
+            // live degrees of the filtered child
+            for (int x = G.tid; x < 2 * n; x += G.nthr) {
+                if (deg[x] == kInact) continue;
+                int d = 0;
+                if (x < n) {
+                    for (int e = V.rp[x]; e < V.rp[x + 1]; ++e) d += (mask[e] && deg[n + V.ci[e]] != kInact);
+                } else {
+                    const int j = x - n;
+                    for (int kk = V.cp[j]; kk < V.cp[j + 1]; ++kk) d += (mask[V.ce[kk]] && deg[V.ri[kk]] != kInact);
+                }
+                deg[x] = (uint16_t)d;
+            }
+            gsync(G);
+            if (leader) {
+                tree_build(deg, tree, T, lane);
+                track = 1;
+                int ml = 0;  // live edges of the child = sum of row degrees
+                for (int x = lane; x < n; x += 32) ml += (deg[x] != kInact) ? deg[x] : 0;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) ml += __shfl_xor_sync(kFull, ml, o);
+                m_live = ml;
+            }
+            gsync(G);
+        }
+        const int nit = mb[M_NIT];
+        if (nit > 0) {
+            for (int q = 0; q < nit; ++q) sk_iteration<Real, Idx>(V, deg, mask, r, c, G);
+            if (leader) {
+                n_full += nit;
+                alg_bytes += (uint64_t)16 * (uint64_t)m_live * (uint64_t)nit;
+            }
+        } else if (use_local) {
+            if (leader) {
+                const int cr = mb[M_CNTR], cc = mb[M_CNTC];
+                const int staged = local_repair<Real, Idx>(V, deg, mask, r, c, list_r, cr, list_c, cc, stamp, t + 1,
+                                                           tmp_id, tmp_val, G.misc + M_TMP, lane);
+                ++n_loc;
+                alg_bytes += (uint64_t)16 * (uint64_t)(staged + cr + cc);
+            }
+            gsync(G);
+        }
+    }
+    if (leader && lane == 0) {
+        P.log_x[gq] = (dead_step >= 0) ? -INFINITY : (log(num) - log(den)) + (double)ex * 0.6931471805599453;
+        if (TRACE) P.dead_step[gq] = dead_step;
+        if (n_dm) atomicAdd(P.counters + 4 * k + 0, (unsigned long long)n_dm);
+        if (n_full) atomicAdd(P.counters + 4 * k + 1, (unsigned long long)n_full);
+        if (n_loc) atomicAdd(P.counters + 4 * k + 2, (unsigned long long)n_loc);
+        atomicAdd(P.counters + 4 * k + 3, (unsigned long long)alg_bytes);
+    }
+    gsync(G);
+}
+
+template <typename Real, typename Idx, bool TRACE>
+__device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, const MV<Idx>& V, uint8_t* gstate,
+                          int* ctr_traj)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gidx = warp / pl.g;
+    if (gidx >= pl.groups) return;
+    const int k = ch.k;
+    const DevMatrix* Mp = P.mats + k;
+    const int n = V.n;
+    Grp G;
+    G.g = pl.g;
+    G.nthr = pl.g * 32;
+    G.tid = tid - gidx * G.nthr;
+    G.wig = G.tid >> 5;
+    G.lane = lane;
+    G.bar = 1 + gidx;
+    uint8_t* base = gstate + (size_t)gidx * pl.state_bytes;
+    const TreeGeom T = tree_geom(n);
+    uint16_t* deg = reinterpret_cast<uint16_t*>(base);
+    size_t off = a16((size_t)((2 * n + 7) & ~7) * 2);
+    uint32_t* tree = reinterpret_cast<uint32_t*>(base + off);
+    off += a16((size_t)T.total * 4);
+    Real* r_sm = nullptr;
+    if (pl.rc_smem) {
+        r_sm = reinterpret_cast<Real*>(base + off);
+        off += 2 * a16((size_t)n * sizeof(Real));
+    }
+    G.misc = reinterpret_cast<int*>(base + off);
+    uint8_t* slot = P.slots + ((size_t)blockIdx.x * kCtaWarps + gidx) * P.slot.bytes;
+    for (;;) {
+        if (G.wig == 0 && lane == 0) G.misc[M_TRAJ] = atomicAdd(ctr_traj, 1);
+        gsync(G);
+        const int q = G.misc[M_TRAJ];
+        gsync(G);
+        if (q >= (int)ch.count) break;
+        const uint64_t local = ch.first + (uint64_t)q;
+        run_group<Real, Idx, TRACE>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm, slot, G);
+    }
+}
+
+template <typename Real, bool TRACE>
+__global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    int* cmisc = reinterpret_cast<int*>(smem);  // [0] chunk, [1] trajectory counter, [2] staged matrix
+    const int tid = threadIdx.x;
+    if (tid == 0) cmisc[2] = -1;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            cmisc[0] = atomicAdd(P.chunk_counter, 1);
+            cmisc[1] = 0;
+        }
+        __syncthreads();
+        const int ci = cmisc[0];
+        if (ci >= P.n_chunks) break;
+        const Chunk ch = P.chunks[ci];
+        const Plan pl = P.plans[ch.k];
+        const DevMatrix* Mp = P.mats + ch.k;
+        const int n = Mp->n;
+        uint8_t* mat = smem + kCtaMiscBytes;
+        uint8_t* gstate = mat + pl.mat_bytes;
+        if (pl.staged) {
+            const int staged_k = cmisc[2];
+            __syncthreads();
+            const int m = Mp->m;
+            int* s_rp = reinterpret_cast<int*>(mat);
+            int* s_cp = reinterpret_cast<int*>(mat + a16((size_t)(n + 1) * 4));
+            uint16_t* s_ci = reinterpret_cast<uint16_t*>(mat + 2 * a16((size_t)(n + 1) * 4));
+            uint16_t* s_ri = reinterpret_cast<uint16_t*>(mat + 2 * a16((size_t)(n + 1) * 4) + a16((size_t)m * 2));
+            int* s_ce = reinterpret_cast<int*>(mat + 2 * a16((size_t)(n + 1) * 4) + 2 * a16((size_t)m * 2));
+            if (staged_k != ch.k) {
+                for (int q = tid; q <= n; q += blockDim.x) { s_rp[q] = __ldg(Mp->rp + q); s_cp[q] = __ldg(Mp->cp + q); }
+                for (int q = tid; q < m; q += blockDim.x) {
+                    s_ci[q] = (uint16_t)__ldg(Mp->ci + q);
+                    s_ri[q] = (uint16_t)__ldg(Mp->ri + q);
+                }
+                if (P.s.dm != DMP_NONE)
+                    for (int q = tid; q < m; q += blockDim.x) s_ce[q] = __ldg(Mp->ce + q);
+                if (tid == 0) cmisc[2] = ch.k;
+            }
+            __syncthreads();
+            MV<uint16_t> V{n, s_rp, s_cp, s_ci, s_ri, s_ce, Mp->rv, Mp->cv};
+            run_chunk<Real, uint16_t, TRACE>(P, ch, pl, V, gstate, cmisc + 1);
+        } else {
+            MV<int> V{n, Mp->rp, Mp->cp, Mp->ci, Mp->ri, Mp->ce, Mp->rv, Mp->cv};
+            run_chunk<Real, int, TRACE>(P, ch, pl, V, gstate, cmisc + 1);
+        }
+    }
+}
+
+template <typename Real, bool TRACE>
+cudaError_t launch_t(const TrajParams& p, int grid, int smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(traj_kernel<Real, TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    traj_kernel<Real, TRACE><<<grid, kCtaWarps * 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int traj_max_smem_bytes()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+cudaError_t launch_trajectories(const TrajParams& p, int grid, int smem, bool trace, cudaStream_t st)
+{
+    if (p.s.precision == 1) return trace ? launch_t<double, true>(p, grid, smem, st) : launch_t<double, false>(p, grid, smem, st);
+    return trace ? launch_t<float, true>(p, grid, smem, st) : launch_t<float, false>(p, grid, smem, st);
+}
+
+}  // namespace pm
