@@ -172,6 +172,34 @@ pm_status pm_philox_blocks(pm_context* ctx, const uint32_t ctr[4], const uint32_
 /* Copy the bookkeeping of the context's most recent call into *info. */
 pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info);
 
+/* Statistics of a set of log-weights; fields as in pm_result. */
+typedef struct {
+    double log_estimate, ess, p_match, rel_spread, rse, log_sum_x, log_sum_x2;
+    uint64_t n_traj, n_alive;
+} pm_weight_stats;
+
+/* Allocation-free statistics of M log-weights (no counterpart in the paper;
+ * a library service).  Some callers cannot allocate device memory when they
+ * call in: hosts whose own allocator has reserved the device's memory, and
+ * latency-bound loops that cannot take the device-wide synchronisation that
+ * cudaMalloc / cudaFree may cause.  This function allocates nothing: its
+ * scratch (partial sums, about 50 KB) is a fixed device array that every GPU
+ * loading the library holds until the process exits.
+ *   log_x  device pointer (current device) to M binary64 ln X values,
+ *          -INFINITY for dead trajectories
+ *   M      1 .. 2^26; larger M returns PM_EUNSUPPORTED (the scratch holds the
+ *          partial sums of at most 2^26 values)
+ *   out    device pointer (current device) receiving one pm_weight_stats
+ *   cuda_stream  stream the two kernels run on; the call does not
+ *          synchronise, out is valid once the stream has reached this point.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call shares the same scratch: calls whose kernels overlap on the GPU
+ * (other streams, other host threads) race; serialise them.  Errors:
+ * PM_EINVAL for NULL pointers or M = 0, PM_ECUDA if a launch fails. */
+pm_status pm_log_weight_stats_noalloc(const double* log_x, uint64_t M, pm_weight_stats* out,
+                                      void* cuda_stream);
+
 /* Human-readable name of a status, and the last error message of a context. */
 const char* pm_status_string(pm_status s);
 const char* pm_last_error(const pm_context* ctx);

@@ -85,6 +85,8 @@ def _load():
     L.pm_philox_blocks.argtypes = [P, P, P, C.c_uint32, P]
     L.pm_last_call_info.argtypes = [P, C.POINTER(pm_call_info)]
     L.pm_last_call_info.restype = C.c_int
+    L.pm_log_weight_stats_noalloc.argtypes = [P, C.c_uint64, P, P]
+    L.pm_log_weight_stats_noalloc.restype = C.c_int
     L.pm_status_string.restype = C.c_char_p
     L.pm_status_string.argtypes = [C.c_int]
     L.pm_last_error.restype = C.c_char_p
@@ -108,7 +110,7 @@ def _status_name(s: int) -> str:
 
 EXPORTED = ["pm_context_create", "pm_context_destroy", "estimate_permanent",
             "estimate_permanent_batch", "pm_estimate_batch_ex", "pm_trace", "pm_preprocess", "pm_philox_blocks",
-            "pm_last_call_info", "pm_status_string", "pm_last_error"]
+            "pm_last_call_info", "pm_log_weight_stats_noalloc", "pm_status_string", "pm_last_error"]
 
 
 @dataclass
@@ -159,6 +161,15 @@ def make_csr(m) -> tuple:
     nnz = int(m.row_ptr[-1]) if not dev else int(m.col_idx.numel())
     c = pm_csr(int(m.n), dev, nnz, rp, ci, vp)
     return c, (k0, k1, k2)
+
+
+WEIGHT_STATS_FIELDS = ["log_estimate", "ess", "p_match", "rel_spread", "rse", "log_sum_x",
+                       "log_sum_x2", "n_traj", "n_alive"]
+
+
+def log_weight_stats_noalloc(log_x_ptr: int, M: int, out_ptr: int, stream: int = 0) -> int:
+    """pm_log_weight_stats_noalloc on device pointers (returns the status)."""
+    return _lib.pm_log_weight_stats_noalloc(log_x_ptr, M, out_ptr, stream or None)
 
 
 class Context:
