@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--traj", type=int, default=64, help="trajectories per matrix per step")
+    p.add_argument("--traj", type=int, default=256, help="trajectories per matrix per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--mats", type=int, default=N_MATS,
