@@ -133,12 +133,13 @@ Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max)
         if (staged && n > 65535) continue;
         const int mb = staged ? staged_matrix_bytes(n, m, dm) : 0;
         if (mb >= avail) continue;
-        const int sb = group_state_bytes(n, rb, rc);
+        const int sb = group_state_bytes(n, rb, rc, full);
         const int fit = (avail - mb) / sb;
         if (fit < 1) continue;
         Plan p{};
         p.staged = staged;
         p.rc_smem = rc;
+        p.lists = full;
         p.state_bytes = sb;
         p.mat_bytes = mb;
         if (full) {

@@ -130,9 +130,10 @@ inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales,
 // matrix indices (uint16) in shared memory; the scaling vectors live in
 // shared memory (rc_smem) or in the group's global slot.
 struct Plan {
-    int g, groups, staged, rc_smem;
+    int g, groups, staged, rc_smem, lists;
     int state_bytes;   // shared bytes of one group
     int mat_bytes;     // shared bytes of the staged matrix (0 if not staged)
+    int pad;
 };
 
 // a run of trajectories first .. first + count - 1 (indices inside matrix k)
@@ -170,11 +171,12 @@ struct TrajParams {
 };
 
 // shared-memory sizes used by the plan
-inline int group_state_bytes(int n, int real_bytes, bool rc_smem)
+inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists)
 {
     const TreeGeom G = tree_geom(n);
     size_t b = align_up((size_t)((2 * n + 7) & ~7) * 2, 16) + align_up((size_t)G.total * 4, 16);
     if (rc_smem) b += 2 * align_up((size_t)n * real_bytes, 16);
+    if (lists) b += 2 * align_up((size_t)n * 2, 16);
     b += kGroupMiscInts * 4;
     return (int)b;
 }

@@ -143,101 +143,114 @@ __device__ __forceinline__ bool entry_live(const uint16_t* deg, const uint8_t* m
     return mask[row_list ? e : V.ce[e]] != 0;
 }
 
-// ---- SK sums in adjacency order (unrolled by four; a dead entry adds +0,
-// which leaves the sum unchanged because every partial sum is >= +0) ----
+// ---- SK sums in adjacency order.  Eliminated rows and columns carry a zero
+// scale in the per-trajectory vectors, so an entry to an inactive vertex
+// adds B * 0 = +0, which leaves the sum bit-identical to skipping it (every
+// partial sum is >= +0); only DM-removed edges need a test.  Unrolled by four
+// so the gathers of one vertex are in flight together. ----
 template <typename Real, typename Idx>
-__device__ __forceinline__ Real col_sum(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, const Real* r,
-                                        int j)
+__device__ __forceinline__ Real col_sum(const MV<Idx>& V, const uint8_t* mask, const Real* r, int j)
 {
     const int b = V.cp[j], e = V.cp[j + 1];
     Real sum = 0;
     int k = b;
     for (; k + 4 <= e; k += 4) {
-        const int i0 = V.ri[k], i1 = V.ri[k + 1], i2 = V.ri[k + 2], i3 = V.ri[k + 3];
-        bool l0 = deg[i0] != kInact, l1 = deg[i1] != kInact, l2 = deg[i2] != kInact, l3 = deg[i3] != kInact;
-        if (mask) {
-            l0 = l0 && mask[V.ce[k]];
-            l1 = l1 && mask[V.ce[k + 1]];
-            l2 = l2 && mask[V.ce[k + 2]];
-            l3 = l3 && mask[V.ce[k + 3]];
-        }
-        Real t0 = r[i0], t1 = r[i1], t2 = r[i2], t3 = r[i3];
+        Real t0 = r[V.ri[k]], t1 = r[V.ri[k + 1]], t2 = r[V.ri[k + 2]], t3 = r[V.ri[k + 3]];
         if (V.cv) {
             t0 = RA<Real>::mul((Real)__ldg(V.cv + k), t0);
             t1 = RA<Real>::mul((Real)__ldg(V.cv + k + 1), t1);
             t2 = RA<Real>::mul((Real)__ldg(V.cv + k + 2), t2);
             t3 = RA<Real>::mul((Real)__ldg(V.cv + k + 3), t3);
         }
-        sum = RA<Real>::add(sum, l0 ? t0 : (Real)0);
-        sum = RA<Real>::add(sum, l1 ? t1 : (Real)0);
-        sum = RA<Real>::add(sum, l2 ? t2 : (Real)0);
-        sum = RA<Real>::add(sum, l3 ? t3 : (Real)0);
+        if (mask) {
+            if (!mask[V.ce[k]]) t0 = 0;
+            if (!mask[V.ce[k + 1]]) t1 = 0;
+            if (!mask[V.ce[k + 2]]) t2 = 0;
+            if (!mask[V.ce[k + 3]]) t3 = 0;
+        }
+        sum = RA<Real>::add(sum, t0);
+        sum = RA<Real>::add(sum, t1);
+        sum = RA<Real>::add(sum, t2);
+        sum = RA<Real>::add(sum, t3);
     }
     for (; k < e; ++k) {
-        const int i = V.ri[k];
-        if (deg[i] == kInact || (mask && !mask[V.ce[k]])) continue;
-        const Real t = V.cv ? RA<Real>::mul((Real)__ldg(V.cv + k), r[i]) : r[i];
+        Real t = r[V.ri[k]];
+        if (V.cv) t = RA<Real>::mul((Real)__ldg(V.cv + k), t);
+        if (mask && !mask[V.ce[k]]) t = 0;
         sum = RA<Real>::add(sum, t);
     }
     return sum;
 }
 
 template <typename Real, typename Idx>
-__device__ __forceinline__ Real row_sum(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, const Real* c,
-                                        int i)
+__device__ __forceinline__ Real row_sum(const MV<Idx>& V, const uint8_t* mask, const Real* c, int i)
 {
-    const int n = V.n;
     const int b = V.rp[i], e = V.rp[i + 1];
     Real sum = 0;
     int k = b;
     for (; k + 4 <= e; k += 4) {
-        const int j0 = V.ci[k], j1 = V.ci[k + 1], j2 = V.ci[k + 2], j3 = V.ci[k + 3];
-        bool l0 = deg[n + j0] != kInact, l1 = deg[n + j1] != kInact, l2 = deg[n + j2] != kInact,
-             l3 = deg[n + j3] != kInact;
-        if (mask) {
-            l0 = l0 && mask[k];
-            l1 = l1 && mask[k + 1];
-            l2 = l2 && mask[k + 2];
-            l3 = l3 && mask[k + 3];
-        }
-        Real t0 = c[j0], t1 = c[j1], t2 = c[j2], t3 = c[j3];
+        Real t0 = c[V.ci[k]], t1 = c[V.ci[k + 1]], t2 = c[V.ci[k + 2]], t3 = c[V.ci[k + 3]];
         if (V.rv) {
             t0 = RA<Real>::mul((Real)__ldg(V.rv + k), t0);
             t1 = RA<Real>::mul((Real)__ldg(V.rv + k + 1), t1);
             t2 = RA<Real>::mul((Real)__ldg(V.rv + k + 2), t2);
             t3 = RA<Real>::mul((Real)__ldg(V.rv + k + 3), t3);
         }
-        sum = RA<Real>::add(sum, l0 ? t0 : (Real)0);
-        sum = RA<Real>::add(sum, l1 ? t1 : (Real)0);
-        sum = RA<Real>::add(sum, l2 ? t2 : (Real)0);
-        sum = RA<Real>::add(sum, l3 ? t3 : (Real)0);
+        if (mask) {
+            if (!mask[k]) t0 = 0;
+            if (!mask[k + 1]) t1 = 0;
+            if (!mask[k + 2]) t2 = 0;
+            if (!mask[k + 3]) t3 = 0;
+        }
+        sum = RA<Real>::add(sum, t0);
+        sum = RA<Real>::add(sum, t1);
+        sum = RA<Real>::add(sum, t2);
+        sum = RA<Real>::add(sum, t3);
     }
     for (; k < e; ++k) {
-        const int j = V.ci[k];
-        if (deg[n + j] == kInact || (mask && !mask[k])) continue;
-        const Real t = V.rv ? RA<Real>::mul((Real)__ldg(V.rv + k), c[j]) : c[j];
+        Real t = c[V.ci[k]];
+        if (V.rv) t = RA<Real>::mul((Real)__ldg(V.rv + k), t);
+        if (mask && !mask[k]) t = 0;
         sum = RA<Real>::add(sum, t);
     }
     return sum;
 }
 
-// one full SK iteration on the residual by the whole group (Sec. 3.3):
-// columns from r, then rows from the new c; no live edge -> old scale kept
-template <typename Real, typename Idx>
-__device__ void sk_iteration(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, Real* r, Real* c,
-                             const Grp& G)
+// Compact the vertices this warp owns (a contiguous id range) that an SK
+// iteration updates: active with at least one live edge.  Degrees do not
+// change during the iterations of a step, so the lists serve all of them.
+__device__ __forceinline__ int compact_owned(const uint16_t* deg, int first, int last, int base_id,
+                                             uint16_t* out, int lane)
 {
-    const int n = V.n;
-    for (int j = G.tid; j < n; j += G.nthr) {
-        const uint16_t dj = deg[n + j];
-        if (dj == kInact || dj == 0) continue;
-        c[j] = RA<Real>::rcp(col_sum<Real, Idx>(V, deg, mask, r, j));
+    int cnt = 0;
+    for (int x0 = first; x0 < last; x0 += 32) {
+        const int x = x0 + lane;
+        bool keep = false;
+        if (x < last) {
+            const uint16_t d = deg[base_id + x];
+            keep = d != kInact && d != 0;
+        }
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (keep) out[cnt + __popc(km & ((1u << lane) - 1u))] = (uint16_t)x;
+        cnt += __popc(km);
+    }
+    return cnt;
+}
+
+// one full SK iteration on the residual by the whole group (Sec. 3.3):
+// columns from r, then rows from the new c, each warp over its own list
+template <typename Real, typename Idx>
+__device__ void sk_iteration(const MV<Idx>& V, const uint8_t* mask, Real* r, Real* c, const uint16_t* lc,
+                             int nc, const uint16_t* lr, int nr, const Grp& G)
+{
+    for (int q = G.lane; q < nc; q += 32) {
+        const int j = lc[q];
+        c[j] = RA<Real>::rcp(col_sum<Real, Idx>(V, mask, r, j));
     }
     gsync(G);
-    for (int i = G.tid; i < n; i += G.nthr) {
-        const uint16_t di = deg[i];
-        if (di == kInact || di == 0) continue;
-        r[i] = RA<Real>::rcp(row_sum<Real, Idx>(V, deg, mask, c, i));
+    for (int q = G.lane; q < nr; q += 32) {
+        const int i = lr[q];
+        r[i] = RA<Real>::rcp(row_sum<Real, Idx>(V, mask, c, i));
     }
     gsync(G);
 }
@@ -257,7 +270,7 @@ __device__ int local_repair(const MV<Idx>& V, const uint16_t* deg, const uint8_t
     __syncwarp();
     auto stage_row = [&](int i) {
         if (atomicExch(&stamp[i], st) == st) return;
-        const Real v = (deg[i] == 0) ? r[i] : RA<Real>::rcp(row_sum<Real, Idx>(V, deg, mask, c, i));
+        const Real v = (deg[i] == 0) ? r[i] : RA<Real>::rcp(row_sum<Real, Idx>(V, mask, c, i));
         const int q = atomicAdd(tmp_cnt, 1);
         tmp_id[q] = i;
         tmp_val[q] = v;
@@ -273,7 +286,7 @@ __device__ int local_repair(const MV<Idx>& V, const uint16_t* deg, const uint8_t
     }
     __syncwarp();
     auto col_new = [&](int j) {
-        c[j] = (deg[n + j] == 0) ? c[j] : RA<Real>::rcp(col_sum<Real, Idx>(V, deg, mask, r, j));
+        c[j] = (deg[n + j] == 0) ? c[j] : RA<Real>::rcp(col_sum<Real, Idx>(V, mask, r, j));
     };
     for (int q = lane; q < nc; q += 32) col_new(lc[q]);
     for (int q = lane; q < nr; q += 32) {
@@ -307,7 +320,8 @@ enum { M_DEAD = 0, M_NIT = 1, M_DM = 2, M_CNTR = 3, M_CNTC = 4, M_STRIDE = 8, M_
 
 template <typename Real, typename Idx, bool TRACE>
 __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>& V, int k, uint64_t gq,
-                          uint64_t local, uint16_t* deg, uint32_t* tree, Real* r_sm, uint8_t* slot, const Grp& G)
+                          uint64_t local, uint16_t* deg, uint32_t* tree, Real* r_sm, uint16_t* lists, uint8_t* slot,
+                          const Grp& G)
 {
     const int n = V.n;
     const int lane = G.lane;
@@ -529,9 +543,13 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 }
                 const Real z = RA<Real>::mul(r[R], c[C]);
 
-                // eliminate R and C
+                // eliminate R and C (their per-trajectory scales become 0)
                 __syncwarp();
-                if (lane == 0) { deg[R] = kInact; deg[n + C] = kInact; }
+                if (lane == 0) {
+                    deg[R] = kInact;
+                    deg[n + C] = kInact;
+                    if (inner_sk) { r[R] = 0; c[C] = 0; }
+                }
                 __syncwarp();
                 int* list_v = vrow ? list_c : list_r;
                 int* list_u = vrow ? list_r : list_c;
@@ -655,7 +673,13 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         }
         const int nit = mb[M_NIT];
         if (nit > 0) {
-            for (int q = 0; q < nit; ++q) sk_iteration<Real, Idx>(V, deg, mask, r, c, G);
+            // this warp's share of the vertex ids, compacted to the ones updated
+            const int per = (n + G.g - 1) / G.g;
+            const int lo = min(n, G.wig * per), hi = min(n, lo + per);
+            const int nc = compact_owned(deg, lo, hi, n, lists + lo, lane);
+            const int nr = compact_owned(deg, lo, hi, 0, lists + n + lo, lane);
+            __syncwarp();
+            for (int q = 0; q < nit; ++q) sk_iteration<Real, Idx>(V, mask, r, c, lists + lo, nc, lists + n + lo, nr, G);
             if (leader) {
                 n_full += nit;
                 alg_bytes += (uint64_t)16 * (uint64_t)m_live * (uint64_t)nit;
@@ -710,6 +734,11 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         r_sm = reinterpret_cast<Real*>(base + off);
         off += 2 * a16((size_t)n * sizeof(Real));
     }
+    uint16_t* lists = nullptr;  // [0, n): columns, [n, 2n): rows
+    if (pl.lists) {
+        lists = reinterpret_cast<uint16_t*>(base + off);
+        off += 2 * a16((size_t)n * 2);
+    }
     G.misc = reinterpret_cast<int*>(base + off);
     uint8_t* slot = P.slots + ((size_t)blockIdx.x * kCtaWarps + gidx) * P.slot.bytes;
     for (;;) {
@@ -719,7 +748,7 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         gsync(G);
         if (q >= (int)ch.count) break;
         const uint64_t local = ch.first + (uint64_t)q;
-        run_group<Real, Idx, TRACE>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm, slot, G);
+        run_group<Real, Idx, TRACE>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm, lists, slot, G);
     }
 }
 
