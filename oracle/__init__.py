@@ -15,6 +15,10 @@ Parity status of each function (what pins it lives in tests/test_oracle_*.py):
   dm_mask              pinned: brute-force support test per edge
   sk_full              pinned: k-regular closed form, doubly-stochastic limit
   local repair         pinned: hand-computed Eq. 5 example
+  exp_score            pinned: libm exp within a few ulp, exact at 0
+  mlp_forward / grad   pinned: central finite differences of the FP64 loss
+  record (features)    pinned: hand-computed features of a 4x4 example
+  run_ext              pinned: constant logits reproduce the unscaled estimator
 """
 from __future__ import annotations
 
@@ -84,13 +88,22 @@ def lib():
         L.or_prep_scaling.argtypes = [P, P, P]
         L.or_prep_mask.argtypes = [P, P]
         L.or_forced_run.restype = C.c_int
-        L.or_forced_run.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P]
+        L.or_forced_run.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P]
         L.or_run.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
                              P, P, P, P, P]
         L.or_dm_mask.restype = C.c_int
         L.or_dm_mask.argtypes = [P, P]
         L.or_sk_full.argtypes = [P, C.c_int, P, P]
         L.or_statistics.argtypes = [P, C.c_int64, C.POINTER(_Stats)]
+        L.or_exp_score.restype = C.c_float
+        L.or_exp_score.argtypes = [C.c_float]
+        L.or_mlp_forward.argtypes = [P, P, C.c_int64, C.c_int, P]
+        L.or_mlp_grad.restype = C.c_double
+        L.or_mlp_grad.argtypes = [P, P, P, C.c_int64, P]
+        L.or_record.restype = C.c_int64
+        L.or_record.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int64, P, P, P]
+        L.or_run_ext.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
+                                 P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -223,7 +236,31 @@ class Prepared:
             out["deg_v"] = dv
         return out
 
-    def forced(self, choices):
+    def run_ext(self, seed: int, count: int, logits, first_traj: int = 0, matrix: int = 0,
+                threads: int = 1):
+        """Trajectories with the learned proposal's logits supplied:
+        logits[count, n, 32] (candidate q of step t in adjacency order)."""
+        lg = np.ascontiguousarray(logits, dtype=np.float32)
+        assert lg.shape == (count, self.n, 32)
+        lx = np.zeros(count)
+        ds = np.zeros(count, dtype=np.int32)
+        ch = np.zeros((count, self.n, 2), dtype=np.int32)
+        dv = np.zeros((count, self.n), dtype=np.int32)
+        oc = np.zeros(3, dtype=np.int64)
+        lib().or_run_ext(self.h, seed, matrix, first_traj, count, threads, _ptr(lx), _ptr(ds),
+                         _ptr(ch), _ptr(dv), _ptr(oc), _ptr(lg))
+        return dict(log_x=lx, dead_step=ds, chosen=ch, deg_v=dv)
+
+    def record(self, seed: int, count: int, cap: int, first_traj: int = 0, matrix: int = 0):
+        """(features[8], target, key) pairs along trajectories of this
+        schedule; key = traj << 28 | step << 14 | candidate index."""
+        f = np.zeros((cap, 8), dtype=np.float32)
+        t = np.zeros(cap, dtype=np.float32)
+        k = np.zeros(cap, dtype=np.uint64)
+        m = lib().or_record(self.h, seed, matrix, first_traj, count, cap, _ptr(f), _ptr(t), _ptr(k))
+        return f[:m], t[:m], k[:m]
+
+    def forced(self, choices, logits=None):
         """Replay with forced candidate indices.  Returns ("need", w[], W,
         log_x_prefix, info) when the choices run out before the trajectory
         ends, else ("done", log_x, dead_step, info); info holds the chosen
@@ -236,8 +273,9 @@ class Prepared:
         ds = C.c_int32()
         chosen = np.zeros((max(1, self.n), 2), dtype=np.int32)
         counts = np.zeros(3, dtype=np.int32)
+        lg = None if logits is None else np.ascontiguousarray(logits, dtype=np.float32)
         need = lib().or_forced_run(self.h, _ptr(ch), len(ch), _ptr(w), C.byref(W), C.byref(nc),
-                                   C.byref(lx), C.byref(ds), _ptr(chosen), _ptr(counts))
+                                   C.byref(lx), C.byref(ds), _ptr(chosen), _ptr(counts), _ptr(lg))
         info = dict(chosen=chosen[: self.n], n_dm=int(counts[0]), n_full_sk=int(counts[1]),
                     n_local_sk=int(counts[2]))
         if need:
@@ -269,3 +307,33 @@ def stats(log_x) -> dict:
     return dict(log_estimate=s.log_estimate, p_match=s.p_match, rel_spread=s.rel_spread,
                 rse=s.rse, ess=s.ess, log_sum_x=s.log_sum_x, log_sum_x2=s.log_sum_x2,
                 n_alive=int(s.n_alive), n_traj=int(a.size))
+
+
+# ---------------------------------------------------------------------------
+# learned proposal (spec extension; the paper has no learned part)
+# ---------------------------------------------------------------------------
+
+N_PARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def exp_score(x: float) -> float:
+    """e^x of the learned proposal's score (own binary32 polynomial)."""
+    return float(lib().or_exp_score(float(x)))
+
+
+def mlp_forward(params, X, round_act: bool = False):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros(x.shape[0])
+    lib().or_mlp_forward(_ptr(p), _ptr(x), x.shape[0], int(round_act), _ptr(out))
+    return out
+
+
+def mlp_grad(params, X, T):
+    """(loss, gradient) of the mean squared error of the MLP on (X, T)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(X, dtype=np.float64)
+    t = np.ascontiguousarray(T, dtype=np.float64)
+    g = np.zeros(N_PARAM)
+    loss = lib().or_mlp_grad(_ptr(p), _ptr(x), _ptr(t), x.shape[0], _ptr(g))
+    return loss, g

@@ -532,6 +532,17 @@ typedef struct {
 /* forced-choice interface for exhaustive enumeration: when forced != NULL the
  * t-th step takes candidate forced[t] instead of a Philox draw; when t reaches
  * n_forced the function stops and reports the candidate weights (need_choice). */
+/* learned-proposal hooks (spec extension; the paper has no learned
+ * proposal): ext_logits[t * 32 + q] is the logit of the q-th live candidate
+ * at step t; record_* collect (features, target) pairs of the SK estimator. */
+typedef struct {
+    const float* ext_logits;   /* [n][32] or NULL */
+    float* rec_feat;           /* [cap][8] or NULL */
+    float* rec_target;         /* [cap] */
+    uint64_t* rec_key;         /* [cap]: traj << 28 | t << 14 | q */
+    int64_t rec_cap, rec_n;
+} or_learn;
+
 typedef struct {
     const int32_t* forced;
     int32_t n_forced;
@@ -544,9 +555,155 @@ typedef struct {
 
 static int bitlen32(uint32_t x) { return x ? 32 - __builtin_clz(x) : 0; }
 
+/* Score of the learned proposal: e^x for x clamped to [-20, 20] (NaN -> -20),
+ * computed as 2^(x log2 e) with a degree-7 Taylor polynomial of
+ * 2^f = e^(f ln 2) on |f| <= 1/2.  Every step is a correctly rounded binary32
+ * operation (no contraction); the coefficients are (ln 2)^k / k! rounded to
+ * binary32, and log2 e rounded to binary32. */
+float or_exp_score(float x)
+{
+    static const float C[8] = { 1.0f, 0x1.62e430p-1f, 0x1.ebfbe0p-3f, 0x1.c6b08ep-5f,
+                                0x1.3b2ab6p-7f, 0x1.5d87fep-10f, 0x1.430912p-13f, 0x1.ffcbfcp-17f };
+    if (!(x >= -20.0f)) x = -20.0f;
+    if (x > 20.0f) x = 20.0f;
+    const float y = x * 0x1.715476p+0f;
+    const float nn = nearbyintf(y);
+    const float f = y - nn;
+    float p = C[7];
+    for (int k = 6; k >= 0; --k) p = p * f + C[k];
+    return ldexpf(p, (int)nn);
+}
+
+#define OR_NF 8
+#define OR_NH 64
+#define OR_NPARAM (OR_NH * OR_NF + OR_NH + OR_NH * OR_NH + OR_NH + OR_NH + 1)
+
+/* Per-edge features of candidate (v, l) at step t (reading of the north
+ * star's list): log1p deg(v), log1p deg(l), log1p of the degree sum over v's
+ * live candidates, log1p of the degree sum over l's live neighbours, t / n,
+ * ln of the outer scale of v and of l (r for rows, c for columns), ln B_vl. */
+static void edge_features(const or_traj* T, int t, int v, int l_unified, int64_t e, double sum_v, float* f)
+{
+    const or_prep* P = T->P;
+    const int n = P->n;
+    double sum_l = 0;
+    if (l_unified < n) {
+        for (int64_t k = P->rp[l_unified]; k < P->rp[l_unified + 1]; ++k)
+            if (edge_live(T, k, l_unified, P->ci[k])) sum_l += T->deg[n + P->ci[k]];
+    } else {
+        const int j = l_unified - n;
+        for (int64_t k = P->cp[j]; k < P->cp[j + 1]; ++k)
+            if (edge_live(T, P->ce[k], P->ri[k], j)) sum_l += T->deg[P->ri[k]];
+    }
+    const double sv = v < n ? P->r0[v] : P->c0[v - n];
+    const double sl = l_unified < n ? P->r0[l_unified] : P->c0[l_unified - n];
+    f[0] = (float)log1p((double)T->deg[v]);
+    f[1] = (float)log1p((double)T->deg[l_unified]);
+    f[2] = (float)log1p(sum_v);
+    f[3] = (float)log1p(sum_l);
+    f[4] = (float)((double)t / (double)n);
+    f[5] = (float)log(sv);
+    f[6] = (float)log(sl);
+    f[7] = (float)log(entry(P, e));
+}
+
+/* MLP 8 -> 64 -> 64 -> 1 with GELU (erf form), parameters laid out as
+ * W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3.  round_act rounds the
+ * hidden activations to bfloat16 (round to nearest even) as tensor-core
+ * inference does. */
+static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+static double gelu_d(double x)
+{
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * 3.14159265358979323846);
+}
+static double bf16_round(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+void or_mlp_forward(const double* Pm, const double* X, int64_t B, int round_act, double* out)
+{
+    const double *W1 = Pm, *b1 = W1 + OR_NH * OR_NF, *W2 = b1 + OR_NH, *b2 = W2 + OR_NH * OR_NH,
+                 *W3 = b2 + OR_NH, *b3 = W3 + OR_NH;
+    double h1[OR_NH], h2[OR_NH];
+    for (int64_t r = 0; r < B; ++r) {
+        const double* x = X + r * OR_NF;
+        for (int o = 0; o < OR_NH; ++o) {
+            double z = b1[o];
+            for (int i = 0; i < OR_NF; ++i) z += W1[o * OR_NF + i] * x[i];
+            h1[o] = round_act ? bf16_round(gelu(z)) : gelu(z);
+        }
+        for (int o = 0; o < OR_NH; ++o) {
+            double z = b2[o];
+            for (int i = 0; i < OR_NH; ++i) z += W2[o * OR_NH + i] * h1[i];
+            h2[o] = round_act ? bf16_round(gelu(z)) : gelu(z);
+        }
+        double y = b3[0];
+        for (int i = 0; i < OR_NH; ++i) y += W3[i] * h2[i];
+        out[r] = y;
+    }
+}
+
+/* Loss L = mean over rows of (y - target)^2 and its gradient dL/dparams by
+ * the chain rule (back-propagation through the three layers). */
+double or_mlp_grad(const double* Pm, const double* X, const double* Tg, int64_t B, double* G)
+{
+    const double *W1 = Pm, *b1 = W1 + OR_NH * OR_NF, *W2 = b1 + OR_NH, *b2 = W2 + OR_NH * OR_NH,
+                 *W3 = b2 + OR_NH, *b3 = W3 + OR_NH;
+    double *gW1 = G, *gb1 = gW1 + OR_NH * OR_NF, *gW2 = gb1 + OR_NH, *gb2 = gW2 + OR_NH * OR_NH,
+           *gW3 = gb2 + OR_NH, *gb3 = gW3 + OR_NH;
+    memset(G, 0, sizeof(double) * OR_NPARAM);
+    double z1[OR_NH], h1[OR_NH], z2[OR_NH], h2[OR_NH], d2[OR_NH], d1[OR_NH];
+    double loss = 0;
+    for (int64_t r = 0; r < B; ++r) {
+        const double* x = X + r * OR_NF;
+        for (int o = 0; o < OR_NH; ++o) {
+            double z = b1[o];
+            for (int i = 0; i < OR_NF; ++i) z += W1[o * OR_NF + i] * x[i];
+            z1[o] = z;
+            h1[o] = gelu(z);
+        }
+        for (int o = 0; o < OR_NH; ++o) {
+            double z = b2[o];
+            for (int i = 0; i < OR_NH; ++i) z += W2[o * OR_NH + i] * h1[i];
+            z2[o] = z;
+            h2[o] = gelu(z);
+        }
+        double y = b3[0];
+        for (int i = 0; i < OR_NH; ++i) y += W3[i] * h2[i];
+        const double err = y - Tg[r];
+        loss += err * err / (double)B;
+        const double dy = 2.0 * err / (double)B;
+        gb3[0] += dy;
+        for (int i = 0; i < OR_NH; ++i) {
+            gW3[i] += dy * h2[i];
+            d2[i] = dy * W3[i] * gelu_d(z2[i]);
+        }
+        for (int o = 0; o < OR_NH; ++o) {
+            gb2[o] += d2[o];
+            for (int i = 0; i < OR_NH; ++i) gW2[o * OR_NH + i] += d2[o] * h1[i];
+        }
+        for (int i = 0; i < OR_NH; ++i) {
+            double s = 0;
+            for (int o = 0; o < OR_NH; ++o) s += W2[o * OR_NH + i] * d2[o];
+            d1[i] = s * gelu_d(z1[i]);
+        }
+        for (int o = 0; o < OR_NH; ++o) {
+            gb1[o] += d1[o];
+            for (int i = 0; i < OR_NF; ++i) gW1[o * OR_NF + i] += d1[o] * x[i];
+        }
+    }
+    return loss;
+}
+
 static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t matrix,
                            int32_t* chosen /* [n][2] or NULL */, int32_t* degv /* [n] or NULL */,
-                           or_forced* F, or_traj_result* res)
+                           or_forced* F, or_learn* Ln, or_traj_result* res)
 {
     const or_prep* P = T->P;
     const int n = P->n;
@@ -595,9 +752,31 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
         /* nc == deg[v] by construction of deg[] */
         double smax = 0.0;
         double* sc = T->newr;  /* scratch of size n */
+        if (Ln && Ln->rec_feat) {  /* (features, SK target) pairs of this step */
+            double sum_v = 0;
+            for (int q = 0; q < nc; ++q) sum_v += T->deg[v_is_row ? n + T->cand_p[q] : T->cand_p[q]];
+            for (int q = 0; q < nc && Ln->rec_n < Ln->rec_cap; ++q) {
+                const int l = v_is_row ? n + T->cand_p[q] : T->cand_p[q];
+                edge_features(T, t, v, l, T->cand_e[q], sum_v, Ln->rec_feat + Ln->rec_n * OR_NF);
+                const double sv_ = v_is_row ? T->r[v] : T->c[v - n];
+                const double sl_ = v_is_row ? T->c[T->cand_p[q]] : T->r[T->cand_p[q]];
+                Ln->rec_target[Ln->rec_n] = (float)log(sv_ * sl_);
+                Ln->rec_key[Ln->rec_n] = (traj << 28) | ((uint64_t)t << 14) | (uint64_t)q;
+                Ln->rec_n++;
+            }
+        }
+        if (Ln && Ln->ext_logits && nc > 32) {  /* replay supports up to 32 candidates */
+            res->log_x = -INFINITY; res->dead_step = t; res->dead_reason = 4; return;
+        }
         for (int q = 0; q < nc; ++q) {
-            double scale = v_is_row ? T->c[T->cand_p[q]] : T->r[T->cand_p[q]];
-            double sv = rnd(fp32, entry(P, T->cand_e[q]) * scale);
+            double sv;
+            if (Ln && Ln->ext_logits) {
+                const float ex = or_exp_score(Ln->ext_logits[(int64_t)t * 32 + q]);
+                sv = P->val ? (double)((float)entry(P, T->cand_e[q]) * ex) : (double)ex;
+            } else {
+                double scale = v_is_row ? T->c[T->cand_p[q]] : T->r[T->cand_p[q]];
+                sv = rnd(fp32, entry(P, T->cand_e[q]) * scale);
+            }
             if (!(sv >= 0)) sv = 0;           /* NaN guard */
             sc[q] = sv;
             if (sv > smax) smax = sv;
@@ -691,7 +870,8 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
 /* Forced-choice replay for exhaustive enumeration (single trajectory). */
 int or_forced_run(const or_prep* P, const int32_t* forced, int32_t n_forced, uint64_t* w_out,
                   uint64_t* W_out, int32_t* n_cand, double* log_x, int32_t* dead_step,
-                  int32_t* chosen /* [n][2] or NULL */, int32_t* counts /* [3] or NULL */)
+                  int32_t* chosen /* [n][2] or NULL */, int32_t* counts /* [3] or NULL */,
+                  const float* ext_logits /* [n][32] or NULL */)
 {
     or_traj* T = traj_alloc(P);
     or_forced F;
@@ -700,7 +880,10 @@ int or_forced_run(const or_prep* P, const int32_t* forced, int32_t n_forced, uin
     F.n_forced = n_forced;
     F.w_out = w_out;
     or_traj_result res;
-    run_trajectory(T, 0, 0, 0, chosen, NULL, &F, &res);
+    or_learn L;
+    memset(&L, 0, sizeof(L));
+    L.ext_logits = ext_logits;
+    run_trajectory(T, 0, 0, 0, chosen, NULL, &F, ext_logits ? &L : NULL, &res);
     traj_free(T);
     *W_out = F.W_out;
     *n_cand = F.n_cand;
@@ -723,6 +906,7 @@ typedef struct {
     int32_t* dead_step;
     int32_t* chosen;  /* [count][n][2] or NULL */
     int32_t* degv;    /* [count][n] or NULL */
+    const float* ext_logits;  /* [count][n][32] or NULL */
     int64_t counts[3];
 } or_job;
 
@@ -733,9 +917,12 @@ static void* job_main(void* arg)
     or_traj* T = traj_alloc(J->P);
     for (int64_t q = J->lo; q < J->hi; ++q) {
         or_traj_result res;
+        or_learn L;
+        memset(&L, 0, sizeof(L));
+        if (J->ext_logits) L.ext_logits = J->ext_logits + q * (int64_t)n * 32;
         run_trajectory(T, J->seed, J->first + (uint64_t)q, J->matrix,
                        J->chosen ? J->chosen + q * 2 * n : NULL,
-                       J->degv ? J->degv + q * n : NULL, NULL, &res);
+                       J->degv ? J->degv + q * n : NULL, NULL, J->ext_logits ? &L : NULL, &res);
         J->log_x[q] = res.log_x;
         if (J->dead_step) J->dead_step[q] = res.dead_step;
         J->counts[0] += res.n_dm;
@@ -746,9 +933,22 @@ static void* job_main(void* arg)
     return NULL;
 }
 
+void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
+                int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
+                int64_t* op_counts, const float* ext_logits);
+
 void or_run(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
             int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
             int64_t* op_counts /* [3]: DM calls, full SK sweeps, local repairs */)
+{
+    or_run_ext(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, op_counts, NULL);
+}
+
+/* or_run with the learned proposal's logits supplied per trajectory and step
+ * (ext_logits[count][n][32], candidate q of step t in adjacency order). */
+void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
+                int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
+                int64_t* op_counts, const float* ext_logits)
 {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > count) nthreads = count > 0 ? (int)count : 1;
@@ -759,6 +959,7 @@ void or_run(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_tra
         jobs[t].lo = count * t / nthreads; jobs[t].hi = count * (t + 1) / nthreads;
         jobs[t].log_x = log_x; jobs[t].dead_step = dead_step; jobs[t].chosen = chosen;
         jobs[t].degv = degv;
+        jobs[t].ext_logits = ext_logits;
     }
     for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, job_main, &jobs[t]);
     job_main(&jobs[0]);
@@ -770,6 +971,26 @@ void or_run(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_tra
     }
     free(jobs);
     free(th);
+}
+
+/* (features, target) pairs of trajectories first..first+count-1 of the
+ * prepared schedule (one thread, trajectory order); returns the pair count. */
+int64_t or_record(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first, int64_t count,
+                  int64_t cap, float* feat, float* target, uint64_t* key)
+{
+    or_traj* T = traj_alloc(P);
+    or_learn L;
+    memset(&L, 0, sizeof(L));
+    L.rec_feat = feat;
+    L.rec_target = target;
+    L.rec_key = key;
+    L.rec_cap = cap;
+    for (int64_t q = 0; q < count && L.rec_n < cap; ++q) {
+        or_traj_result res;
+        run_trajectory(T, seed, first + (uint64_t)q, matrix, NULL, NULL, NULL, &L, &res);
+    }
+    traj_free(T);
+    return L.rec_n;
 }
 
 /* DM of a whole matrix with an explicit edge mask (for pins): returns 0 if no

@@ -1,0 +1,112 @@
+"""Pins of the oracle's learned-proposal parts (a spec extension: the
+paper has no learned proposal, so these pin the pieces against mathematics
+and against the paper's own unscaled estimator)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_15390_b300 import inputs as G
+
+
+def test_exp_score_accuracy_and_special_values():
+    # error budget: rounding y = x log2(e) to binary32 costs |y| ln2 2^-24
+    # relative, the polynomial and its eight roundings a few 2^-24
+    xs = np.linspace(-20, 20, 4001).astype(np.float32)
+    u = 2.0 ** -24
+    for x in xs:
+        got = O.exp_score(float(x))
+        want = math.exp(float(x))
+        bound = abs(float(x)) * u + 10 * u
+        assert abs(got / want - 1) < bound, x
+    assert O.exp_score(0.0) == 1.0
+    assert O.exp_score(100.0) == O.exp_score(20.0)
+    assert O.exp_score(-100.0) == O.exp_score(-20.0)
+    assert O.exp_score(float("nan")) == O.exp_score(-20.0)
+
+
+def _rand_params(rng, scale=0.3):
+    return rng.normal(size=O.N_PARAM) * scale
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    P = _rand_params(rng)
+    X = rng.normal(size=(37, 8))
+    T = rng.normal(size=37)
+    loss, g = O.mlp_grad(P, X, T)
+    yhat = O.mlp_forward(P, X)
+    assert loss == pytest.approx(np.mean((yhat - T) ** 2), rel=1e-13)
+    idx = rng.choice(O.N_PARAM, size=60, replace=False)
+    idx = np.concatenate([idx, [0, 511, 512, 575, 576, 4671, 4672, 4735, 4736, 4799, 4800]])
+    for i in idx:
+        h = 1e-6
+        Pp = P.copy(); Pp[i] += h
+        Pm = P.copy(); Pm[i] -= h
+        fd = (O.mlp_grad(Pp, X, T)[0] - O.mlp_grad(Pm, X, T)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-9), i
+
+
+def test_mlp_forward_closed_form():
+    # with W1 = W2 = 0 every hidden unit is GELU(b): y = b3 + W3 . GELU(b2)
+    P = np.zeros(O.N_PARAM)
+    P[4672:4736] = 0.5          # b2
+    P[4736:4800] = 2.0          # W3
+    P[4800] = -1.0              # b3
+    g05 = 0.5 * 0.5 * (1 + math.erf(0.5 / math.sqrt(2)))
+    y = O.mlp_forward(P, np.ones((3, 8)))
+    assert np.allclose(y, -1.0 + 64 * 2.0 * g05, rtol=1e-14)
+
+
+def test_features_hand_worked():
+    # matrix A of tests/golden/md_paths.txt; step 0 picks row 1 (degree 2)
+    # with candidates col 0 (degree 2, neighbours row0 (3) row1 (2)) and
+    # col 1 (degree 3, neighbours row0 (3) row1 (2) row2 (3)); no scaling
+    A = G.csr_from_coo(4, [0, 0, 0, 1, 1, 2, 2, 2, 3, 3], [0, 1, 2, 0, 1, 1, 2, 3, 2, 3])
+    P = O.Prepared(A, O.Schedule(precision=O.PREC_FP32))
+    f, t, k = P.record(seed=1, count=1, cap=64)
+    l1p = lambda x: np.float32(math.log1p(x))
+    want0 = [l1p(2), l1p(2), l1p(5), l1p(5), 0, 0, 0, 0]
+    want1 = [l1p(2), l1p(3), l1p(5), l1p(8), 0, 0, 0, 0]
+    assert k[0] == 0 and k[1] == 1          # trajectory 0, step 0, candidates 0 and 1
+    assert np.array_equal(f[0], np.float32(want0)) and np.array_equal(f[1], np.float32(want1))
+    assert t[0] == 0 and t[1] == 0          # log(r_v c_l) with r = c = 1
+    # the depth feature of step t is t / n
+    steps = (k >> 14) & 0x3FFF
+    assert np.allclose(f[:, 4], steps / 4.0)
+
+
+def test_constant_logits_reproduce_the_unscaled_estimator():
+    # equal scores give equal integer weights, i.e. the unscaled proposal
+    for m in (G.planted_bernoulli(20, 0.3, seed=1), G.er_planted(60, 4.0, seed=2)):
+        P = O.Prepared(m, O.Schedule(precision=O.PREC_FP32))
+        a = P.run(seed=3, count=64, trace=True)
+        lg = np.full((64, m.n, 32), 0.7, dtype=np.float32)
+        b = P.run_ext(seed=3, count=64, logits=lg)
+        assert np.array_equal(a["chosen"], b["chosen"])
+        assert np.array_equal(a["log_x"], b["log_x"])
+
+
+def test_logit_replay_is_unbiased_by_enumeration():
+    # any positive scores keep E[X] = per(A): enumerate every path of the
+    # replay with arbitrary logits and sum P(path) X(path) exactly
+    from fractions import Fraction
+    rng = np.random.default_rng(1)
+    for seed, weighted in ((5, False), (6, True), (7, False)):
+        m = G.random_weighted(6, 0.45, seed) if weighted else G.planted_bernoulli(6, 0.45, seed)
+        d = m.to_dense()
+        per = O.ryser_real(d)
+        P = O.Prepared(m, O.Schedule(precision=O.PREC_FP32))
+        lg = (rng.normal(size=(m.n, 32)) * 3).astype(np.float32)
+        total, stack = 0.0, [([], Fraction(1))]
+        while stack:
+            prefix, prob = stack.pop()
+            r = P.forced(prefix, logits=lg)
+            if r[0] == "need":
+                _, w, W, _, _ = r
+                for k, wk in enumerate(w):
+                    stack.append((prefix + [k], prob * Fraction(wk, W)))
+            elif r[2] < 0:
+                total += float(prob) * math.exp(r[1])
+        assert total == pytest.approx(per, rel=1e-12)
