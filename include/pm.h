@@ -81,6 +81,13 @@ typedef struct {
     int32_t precision;     /* pm_precision */
     int32_t reserved;      /* must be 0 */
     double theta;          /* Thrs / Trck threshold theta_th = theta_tr */
+    const struct pm_model* learned;  /* NULL: the scaled proposal of Eq. 3.  Otherwise the
+                              learned proposal (no counterpart in the paper): candidate l
+                              of v gets score B_vl * e^{f(x_vl)} where f is the model and
+                              x_vl the edge features; requires sk = PM_SK_NONE and
+                              precision = PM_PREC_FP32_PROPOSAL.  The correction still
+                              uses the realised probability, so the estimate stays
+                              unbiased. */
 } pm_schedule;
 
 typedef struct {
@@ -150,11 +157,13 @@ pm_status pm_estimate_batch_ex(pm_context* ctx, const pm_csr* mats, int32_t coun
  *   chosen[count][n][2]  unified ids (v, u) of step t, -1 after death
  *   deg_v[count][n]      live degree of v when it was picked, -1 after death
  *   dead_step[count]     step at which the trajectory died, -1 if it completed
- *   log_x[count]         ln X, -INFINITY for a dead trajectory. */
+ *   log_x[count]         ln X, -INFINITY for a dead trajectory
+ *   logits[count][n][32] learned proposal only: network output of the q-th live
+ *                        candidate (adjacency order) of step t, q < 32. */
 pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index,
                    uint64_t first_traj, uint32_t count, uint64_t seed,
                    const pm_schedule* schedule, int32_t* chosen, int32_t* deg_v,
-                   int32_t* dead_step, double* log_x);
+                   int32_t* dead_step, double* log_x, float* logits);
 
 /* Preprocessing only (InitialDM + K0 outer SK): host outputs, any may be NULL:
  * ok (1 if a perfect matching exists), keep[nnz] (1 = edge survives the
@@ -171,6 +180,64 @@ pm_status pm_philox_blocks(pm_context* ctx, const uint32_t ctr[4], const uint32_
 
 /* Copy the bookkeeping of the context's most recent call into *info. */
 pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info);
+
+/* ---- learned proposal (no counterpart in the paper) ----------------------
+ * A small network f: 8 edge features -> 64 -> 64 (GELU) -> 1 predicts
+ * ln(r_v c_l), the scale product an SK-scheduled run would use for edge
+ * (v, l).  Features of candidate l of the picked vertex v at step t:
+ * log1p deg(v), log1p deg(l), log1p of the degree sum over v's live
+ * candidates, log1p of the degree sum over l's live neighbours, t / n, ln of
+ * the outer scales of v and l, ln B_vl.  Weights are BF16 on the device
+ * (FP32 master copy for training); parameter vector layout: W1[64][8], b1[64],
+ * W2[64][64], b2[64], W3[64], b3 (4801 floats). */
+typedef struct pm_model pm_model;
+
+typedef struct {
+    uint64_t n_pairs;        /* (features, target) pairs to record from the teacher */
+    uint64_t seed;           /* Philox seed of the teacher trajectories and of the shuffle */
+    int32_t epochs;          /* passes over the recorded pairs */
+    int32_t batch;           /* rows per Adam step */
+    float lr, beta1, beta2, eps;   /* Adam */
+    pm_schedule teacher;     /* SK-scheduled estimator producing the targets (sk FIXED or
+                                ADAPTIVE, FP32 proposal); its current scales at each step
+                                are the targets */
+} pm_train_cfg;
+
+typedef struct {
+    double loss_first;       /* mean squared error of the first step */
+    double loss_last;        /* mean squared error over the last epoch */
+    uint64_t n_pairs;        /* pairs recorded */
+    int32_t steps;           /* Adam steps taken */
+    int32_t reserved;
+    double seconds_record, seconds_train;
+} pm_train_report;
+
+/* Create a model on the context's device: params (host, 4801 floats) or NULL
+ * for a seeded random initialisation. */
+pm_status pm_model_create(pm_context* ctx, const float* params, uint64_t seed, pm_model** out);
+pm_status pm_model_destroy(pm_model* model);
+/* FP32 master parameters (host out, 4801 floats) / replace them. */
+pm_status pm_model_get_params(pm_context* ctx, const pm_model* model, float* params);
+pm_status pm_model_set_params(pm_context* ctx, pm_model* model, const float* params);
+/* Train on pairs recorded from cfg->teacher running on mats[count] (matrix k
+ * uses matrix index k): record, shuffle, then epochs of Adam on the mean
+ * squared error, gradients from the tensor-core backward kernel. */
+pm_status pm_model_train(pm_context* ctx, pm_model* model, const pm_csr* mats, int32_t count,
+                         const pm_train_cfg* cfg, pm_train_report* report);
+/* Network outputs for B feature rows (host X[B][8] -> host out[B]). */
+pm_status pm_mlp_forward(pm_context* ctx, const pm_model* model, const float* X, uint64_t B,
+                         float* out);
+/* Gradient of the mean squared error over (X[B][8], T[B]) w.r.t. the
+ * parameters (host grad[4801]) and the loss, from the training kernel. */
+pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* model, const float* X, const float* T,
+                          uint64_t B, float* grad, double* loss);
+/* Record (features, target) pairs along trajectories first_traj ..
+ * first_traj + count - 1 of `teacher` on one matrix; key = traj << 28 |
+ * step << 14 | candidate.  Host outputs of capacity cap; *n_out = pairs kept. */
+pm_status pm_record_pairs(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index,
+                          uint64_t first_traj, uint32_t count, uint64_t seed,
+                          const pm_schedule* teacher, uint64_t cap, float* feat, float* target,
+                          uint64_t* key, uint64_t* n_out);
 
 /* Statistics of a set of log-weights; fields as in pm_result. */
 typedef struct {

@@ -43,7 +43,22 @@ class pm_csr(C.Structure):
 class pm_schedule(C.Structure):
     _fields_ = [("vertex_rule", C.c_int32), ("initial_dm", C.c_int32), ("K0", C.c_int32),
                 ("K", C.c_int32), ("sk", C.c_int32), ("dm", C.c_int32), ("precision", C.c_int32),
-                ("reserved", C.c_int32), ("theta", C.c_double)]
+                ("reserved", C.c_int32), ("theta", C.c_double), ("learned", C.c_void_p)]
+
+
+class pm_train_cfg(C.Structure):
+    _fields_ = [("n_pairs", C.c_uint64), ("seed", C.c_uint64), ("epochs", C.c_int32),
+                ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("teacher", pm_schedule)]
+
+
+class pm_train_report(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double), ("n_pairs", C.c_uint64),
+                ("steps", C.c_int32), ("reserved", C.c_int32), ("seconds_record", C.c_double),
+                ("seconds_train", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class pm_result(C.Structure):
@@ -80,7 +95,20 @@ def _load():
     L.pm_estimate_batch_ex.argtypes = [P, C.POINTER(pm_csr), C.c_int32, P, C.c_uint64, C.c_uint64,
                                        C.POINTER(pm_schedule), C.POINTER(pm_result), P]
     L.pm_trace.argtypes = [P, C.POINTER(pm_csr), C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64,
-                           C.POINTER(pm_schedule), P, P, P, P]
+                           C.POINTER(pm_schedule), P, P, P, P, P]
+    L.pm_model_create.argtypes = [P, P, C.c_uint64, C.POINTER(P)]
+    L.pm_model_destroy.argtypes = [P]
+    L.pm_model_get_params.argtypes = [P, P, P]
+    L.pm_model_set_params.argtypes = [P, P, P]
+    L.pm_model_train.argtypes = [P, P, C.POINTER(pm_csr), C.c_int32, C.POINTER(pm_train_cfg),
+                                 C.POINTER(pm_train_report)]
+    L.pm_mlp_forward.argtypes = [P, P, P, C.c_uint64, P]
+    L.pm_mlp_gradient.argtypes = [P, P, P, P, C.c_uint64, P, P]
+    L.pm_record_pairs.argtypes = [P, C.POINTER(pm_csr), C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64,
+                                  C.POINTER(pm_schedule), C.c_uint64, P, P, P, P]
+    for name in ("pm_model_create", "pm_model_destroy", "pm_model_get_params", "pm_model_set_params",
+                 "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs"):
+        getattr(L, name).restype = C.c_int
     L.pm_preprocess.argtypes = [P, C.POINTER(pm_csr), C.POINTER(pm_schedule), P, P, P, P]
     L.pm_philox_blocks.argtypes = [P, P, P, C.c_uint32, P]
     L.pm_last_call_info.argtypes = [P, C.POINTER(pm_call_info)]
@@ -110,7 +138,9 @@ def _status_name(s: int) -> str:
 
 EXPORTED = ["pm_context_create", "pm_context_destroy", "estimate_permanent",
             "estimate_permanent_batch", "pm_estimate_batch_ex", "pm_trace", "pm_preprocess", "pm_philox_blocks",
-            "pm_last_call_info", "pm_log_weight_stats_noalloc", "pm_status_string", "pm_last_error"]
+            "pm_last_call_info", "pm_log_weight_stats_noalloc", "pm_status_string", "pm_last_error",
+            "pm_model_create", "pm_model_destroy", "pm_model_get_params", "pm_model_set_params",
+            "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs"]
 
 
 @dataclass
@@ -123,10 +153,12 @@ class Schedule:
     dm: int = DM_NONE
     precision: int = PREC_FP64
     theta: float = 0.33
+    learned: Optional["Model"] = None
 
     def c(self) -> pm_schedule:
         return pm_schedule(self.vertex_rule, self.initial_dm, self.K0, self.K, self.sk, self.dm,
-                           self.precision, 0, self.theta)
+                           self.precision, 0, self.theta,
+                           None if self.learned is None else self.learned.h.value)
 
 
 def preset(name: str, precision: int = PREC_FP32_PROPOSAL) -> Schedule:
@@ -246,11 +278,33 @@ class Context:
         degv = np.zeros((count, n), dtype=np.int32)
         dead = np.zeros(count, dtype=np.int32)
         lx = np.zeros(count, dtype=np.float64)
+        lg = np.zeros((count, n, 32), dtype=np.float32) if schedule.learned is not None else None
         s = schedule.c()
         self._check(_lib.pm_trace(self.h, C.byref(c), matrix_index, first_traj, count, seed,
                                   C.byref(s), chosen.ctypes.data, degv.ctypes.data,
-                                  dead.ctypes.data, lx.ctypes.data))
-        return dict(chosen=chosen, deg_v=degv, dead_step=dead, log_x=lx)
+                                  dead.ctypes.data, lx.ctypes.data,
+                                  None if lg is None else lg.ctypes.data))
+        out = dict(chosen=chosen, deg_v=degv, dead_step=dead, log_x=lx)
+        if lg is not None:
+            out["logits"] = lg
+        return out
+
+    def record_pairs(self, m, count: int, seed: int, teacher: Schedule, cap: int,
+                     first_traj: int = 0, matrix_index: int = 0):
+        c, keep = make_csr(m)
+        f = np.zeros((cap, 8), dtype=np.float32)
+        t = np.zeros(cap, dtype=np.float32)
+        k = np.zeros(cap, dtype=np.uint64)
+        n_out = C.c_uint64()
+        s = teacher.c()
+        self._check(_lib.pm_record_pairs(self.h, C.byref(c), matrix_index, first_traj, count, seed,
+                                         C.byref(s), cap, f.ctypes.data, t.ctypes.data,
+                                         k.ctypes.data, C.byref(n_out)))
+        n = n_out.value
+        return f[:n], t[:n], k[:n]
+
+    def model(self, params=None, seed: int = 0) -> "Model":
+        return Model(self, params, seed)
 
     def preprocess(self, m, schedule: Schedule) -> dict:
         c, keep = make_csr(m)
@@ -275,3 +329,65 @@ class Context:
         self._check(_lib.pm_philox_blocks(self.h, ct.ctypes.data, ky.ctypes.data, count,
                                           out.ctypes.data))
         return out
+
+
+N_PARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+class Model:
+    """The learned proposal's network (pm_model)."""
+
+    def __init__(self, ctx: Context, params=None, seed: int = 0):
+        self.ctx = ctx
+        self.h = C.c_void_p()
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        ctx._check(_lib.pm_model_create(ctx.h, None if p is None else p.ctypes.data, seed,
+                                        C.byref(self.h)))
+
+    def close(self):
+        if self.h:
+            _lib.pm_model_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(N_PARAM, dtype=np.float32)
+        self.ctx._check(_lib.pm_model_get_params(self.ctx.h, self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self.ctx._check(_lib.pm_model_set_params(self.ctx.h, self.h, p.ctypes.data))
+
+    def forward(self, X) -> np.ndarray:
+        x = np.ascontiguousarray(X, dtype=np.float32)
+        out = np.zeros(x.shape[0], dtype=np.float32)
+        self.ctx._check(_lib.pm_mlp_forward(self.ctx.h, self.h, x.ctypes.data, x.shape[0], out.ctypes.data))
+        return out
+
+    def gradient(self, X, T):
+        x = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.zeros(N_PARAM, dtype=np.float32)
+        loss = C.c_double()
+        self.ctx._check(_lib.pm_mlp_gradient(self.ctx.h, self.h, x.ctypes.data, t.ctypes.data,
+                                             x.shape[0], g.ctypes.data, C.byref(loss)))
+        return loss.value, g
+
+    def train(self, mats, teacher: Schedule, n_pairs: int, epochs: int = 2, batch: int = 4096,
+              lr: float = 2e-3, seed: int = 1) -> dict:
+        cs, keeps = [], []
+        for m in mats:
+            c, k = make_csr(m)
+            cs.append(c)
+            keeps.append(k)
+        arr = (pm_csr * len(cs))(*cs)
+        cfg = pm_train_cfg(n_pairs, seed, epochs, batch, lr, 0.9, 0.999, 1e-8, teacher.c())
+        rep = pm_train_report()
+        self.ctx._check(_lib.pm_model_train(self.ctx.h, self.h, arr, len(cs), C.byref(cfg), C.byref(rep)))
+        return rep.as_dict()

@@ -3,6 +3,7 @@
 // context's stream, and result read-back.
 #include <algorithm>
 #include <chrono>
+#include <random>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -97,6 +98,8 @@ pm_status check_schedule(pm_context* ctx, const pm_schedule* s)
     if (s->precision < 0 || s->precision > 1) return fail(ctx, PM_EINVAL, "bad precision");
     if (s->K0 < 0 || s->K < 0 || s->reserved != 0) return fail(ctx, PM_EINVAL, "bad K0/K/reserved");
     if (!(s->theta == s->theta)) return fail(ctx, PM_EINVAL, "theta is NaN");
+    if (s->learned && (s->sk != 0 || s->precision != 0))
+        return fail(ctx, PM_EINVAL, "the learned proposal needs sk = NONE and the FP32 proposal");
     return PM_OK;
 }
 
@@ -114,16 +117,30 @@ pm_status check_csr(pm_context* ctx, const pm_csr* c)
     return PM_OK;
 }
 
+}  // namespace
+
+struct pm_model {
+    int device = 0;
+    float* master = nullptr;  // FP32 parameters [4801]
+    float* m1 = nullptr;      // Adam first moment
+    float* m2 = nullptr;      // Adam second moment
+    float* grad = nullptr;
+    void* img = nullptr;      // BF16 device image (DevModel)
+    int step = 0;
+};
+
+namespace {
+
 // Execution plan of one matrix (see Plan in pm_internal.h).  Preference
 // order: matrix and scaling vectors in shared memory, then scaling vectors
 // only, then neither; full-SK schedules spread a trajectory over the fewest
 // warps that still keep all 16 warps of the CTA busy.
-Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max)
+Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learned)
 {
     const bool full = s.sk == 1 || s.sk == 2;
     const bool need_rc = s.sk != 0;
     const bool dm = s.dm != 0;
-    const int avail = smem_max - kCtaMiscBytes;
+    const int avail = smem_max - kCtaMiscBytes - (learned ? (model_infer_bytes() + 15) / 16 * 16 : 0);
     Plan best{};
     int best_score = -1;
     const int combos[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
@@ -133,7 +150,7 @@ Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max)
         if (staged && n > 65535) continue;
         const int mb = staged ? staged_matrix_bytes(n, m, dm) : 0;
         if (mb >= avail) continue;
-        const int sb = group_state_bytes(n, rb, rc, full);
+        const int sb = group_state_bytes(n, rb, rc, full, learned);
         const int fit = (avail - mb) / sb;
         if (fit < 1) continue;
         Plan p{};
@@ -179,6 +196,14 @@ struct Run {
     pm_result* outs = nullptr;
     int32_t *chosen = nullptr, *deg_v = nullptr, *dead_step = nullptr;
     double* log_x = nullptr;
+    float* logits = nullptr;        // trace: [T][n][32]
+    const void* model = nullptr;    // learned proposal device image
+    // recording (device buffers)
+    float* rec_feat = nullptr;
+    float* rec_target = nullptr;
+    unsigned long long* rec_key = nullptr;
+    unsigned long long* rec_count = nullptr;
+    unsigned long long rec_cap = 0;
     int32_t* ok_out = nullptr;
     uint8_t* keep_out = nullptr;
     double *r_out = nullptr, *c_out = nullptr;
@@ -249,11 +274,12 @@ pm_status execute(pm_context* ctx, Run& R)
     const int chunks_stats = (int)std::min<uint64_t>(1024, std::max<uint64_t>(1, max_t / 16384));
     const size_t o_parts = L.take(sizeof(StatsPartial) * (size_t)count * chunks_stats);
     const size_t o_sout = L.take(sizeof(StatsOut) * count);
-    size_t o_chosen = 0, o_degv = 0, o_dead = 0;
+    size_t o_chosen = 0, o_degv = 0, o_dead = 0, o_logits = 0;
     if (R.trace) {
         o_chosen = L.take(4 * total * 2 * (size_t)n_max);
         o_degv = L.take(4 * total * (size_t)n_max);
         o_dead = L.take(4 * std::max<uint64_t>(total, 1));
+        if (R.model) o_logits = L.take(4 * total * (size_t)n_max * 32);
     }
     // room for the plans and the chunk list (at most one chunk per trajectory)
     const size_t extra = align_up(sizeof(Plan) * count, 256) + align_up(sizeof(Chunk) * (total + count), 256) + 512;
@@ -337,10 +363,11 @@ pm_status execute(pm_context* ctx, Run& R)
         std::vector<Plan> plans(count);
         int smem_need = kCtaMiscBytes;
         for (int k = 0; k < count; ++k) {
-            plans[k] = make_plan(R.mats[k].n, R.mats[k].nnz, (int)rb, R.s, smem_max);
+            plans[k] = make_plan(R.mats[k].n, R.mats[k].nnz, (int)rb, R.s, smem_max, R.model != nullptr);
             if (plans[k].groups < 1)
                 return fail(ctx, PM_EUNSUPPORTED, "trajectory state does not fit in shared memory");
-            smem_need = std::max(smem_need, kCtaMiscBytes + plans[k].mat_bytes + plans[k].groups * plans[k].state_bytes);
+            smem_need = std::max(smem_need, kCtaMiscBytes + (R.model ? (model_infer_bytes() + 15) / 16 * 16 : 0) +
+                                                plans[k].mat_bytes + plans[k].groups * plans[k].state_bytes);
         }
         // chunks: most expensive matrices first, a few trajectories per group
         std::vector<int> order(count);
@@ -397,7 +424,17 @@ pm_status execute(pm_context* ctx, Run& R)
             tp.chosen = (int32_t*)P(o_chosen);
             tp.deg_v = (int32_t*)P(o_degv);
             tp.dead_step = (int32_t*)P(o_dead);
+            if (R.model) {
+                tp.trace_logits = (float*)P(o_logits);
+                PM_CUDA(cudaMemsetAsync(tp.trace_logits, 0, 4 * total * (size_t)n_max * 32, ctx->stream));
+            }
         }
+        tp.model = R.model;
+        tp.rec_feat = R.rec_feat;
+        tp.rec_target = R.rec_target;
+        tp.rec_key = R.rec_key;
+        tp.rec_count = R.rec_count;
+        tp.rec_cap = R.rec_cap;
         PM_CUDA(launch_trajectories(tp, grid, smem_need, R.trace, ctx->stream));
         PM_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
         launched = true;
@@ -441,6 +478,7 @@ pm_status execute(pm_context* ctx, Run& R)
         if (R.chosen) PM_CUDA(cudaMemcpy(R.chosen, P(o_chosen), 4 * T * 2 * n, cudaMemcpyDeviceToHost));
         if (R.deg_v) PM_CUDA(cudaMemcpy(R.deg_v, P(o_degv), 4 * T * n, cudaMemcpyDeviceToHost));
         if (R.dead_step) PM_CUDA(cudaMemcpy(R.dead_step, P(o_dead), 4 * T, cudaMemcpyDeviceToHost));
+        if (R.logits && R.model) PM_CUDA(cudaMemcpy(R.logits, P(o_logits), 4 * T * n * 32, cudaMemcpyDeviceToHost));
     }
     if (R.log_x && total) {
         PM_CUDA(cudaMemcpy(R.log_x, P(o_logx), 8 * total, cudaMemcpyDeviceToHost));
@@ -566,6 +604,7 @@ pm_status pm_estimate_batch_ex(pm_context* ctx, const pm_csr* mats, int32_t coun
     R.s = to_sched(schedule);
     R.outs = outs;
     R.log_x = log_x;
+    R.model = schedule->learned ? schedule->learned->img : nullptr;
     return execute(ctx, R);
 }
 
@@ -585,7 +624,7 @@ pm_status estimate_permanent(pm_context* ctx, const pm_csr* csr, int32_t n, uint
 
 pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index, uint64_t first_traj, uint32_t count,
                    uint64_t seed, const pm_schedule* schedule, int32_t* chosen, int32_t* deg_v, int32_t* dead_step,
-                   double* log_x)
+                   double* log_x, float* logits)
 {
     if (!ctx) return PM_EINVAL;
     pm_status st = check_schedule(ctx, schedule);
@@ -607,6 +646,8 @@ pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index, ui
     R.deg_v = deg_v;
     R.dead_step = dead_step;
     R.log_x = log_x;
+    R.logits = logits;
+    R.model = schedule->learned ? schedule->learned->img : nullptr;
     return execute(ctx, R);
 }
 
@@ -672,5 +713,283 @@ const char* pm_status_string(pm_status s)
 }
 
 const char* pm_last_error(const pm_context* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+// ---------------------------------------------------------------------------
+// learned proposal: model, training, parity entry points
+// ---------------------------------------------------------------------------
+
+pm_status pm_model_destroy(pm_model* m)
+{
+    if (!m) return PM_EINVAL;
+    cudaSetDevice(m->device);
+    cudaFree(m->master);
+    cudaFree(m->m1);
+    cudaFree(m->m2);
+    cudaFree(m->grad);
+    cudaFree(m->img);
+    delete m;
+    return PM_OK;
+}
+
+pm_status pm_model_create(pm_context* ctx, const float* params, uint64_t seed, pm_model** out)
+{
+    if (!ctx || !out) return PM_EINVAL;
+    *out = nullptr;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    const int np = model_param_count();
+    std::vector<float> h(np, 0.0f);
+    if (params) {
+        std::copy(params, params + np, h.begin());
+    } else {  // He-style normal initialisation, zero biases
+        std::mt19937_64 rng(seed);
+        std::normal_distribution<float> nd(0.0f, 1.0f);
+        for (int i = 0; i < 64 * 8; ++i) h[i] = nd(rng) * std::sqrt(2.0f / 8.0f);
+        for (int i = 0; i < 64 * 64; ++i) h[576 + i] = nd(rng) * std::sqrt(2.0f / 64.0f);
+        for (int i = 0; i < 64; ++i) h[4736 + i] = nd(rng) * std::sqrt(1.0f / 64.0f);
+    }
+    pm_model* m = new (std::nothrow) pm_model();
+    if (!m) return PM_ENOMEM;
+    m->device = ctx->device;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&m->master, 4 * np);
+    if (e == cudaSuccess) e = cudaMalloc(&m->m1, 4 * np);
+    if (e == cudaSuccess) e = cudaMalloc(&m->m2, 4 * np);
+    if (e == cudaSuccess) e = cudaMalloc(&m->grad, 4 * np);
+    if (e == cudaSuccess) e = cudaMalloc(&m->img, model_image_bytes());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->master, h.data(), 4 * np, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->m1, 0, 4 * np, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->m2, 0, 4 * np, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->img, 0, model_image_bytes(), ctx->stream);
+    if (e == cudaSuccess) e = launch_model_image(m->master, m->img, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        pm_model_destroy(m);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA, cudaGetErrorString(e));
+    }
+    *out = m;
+    return PM_OK;
+}
+
+pm_status pm_model_get_params(pm_context* ctx, const pm_model* m, float* params)
+{
+    if (!ctx || !m || !params) return PM_EINVAL;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    PM_CUDA(cudaMemcpyAsync(params, m->master, 4 * model_param_count(), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return PM_OK;
+}
+
+pm_status pm_model_set_params(pm_context* ctx, pm_model* m, const float* params)
+{
+    if (!ctx || !m || !params) return PM_EINVAL;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    PM_CUDA(cudaMemcpyAsync(m->master, params, 4 * model_param_count(), cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(launch_model_image(m->master, m->img, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return PM_OK;
+}
+
+// small device buffers for the parity entry points (freed on return)
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+pm_status pm_mlp_forward(pm_context* ctx, const pm_model* m, const float* X, uint64_t B, float* out)
+{
+    if (!ctx || !m || !X || !out || B == 0 || B > (1ull << 30)) return PM_EINVAL;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    DevBuf bx, bo;
+    PM_CUDA(cudaMalloc(&bx.p, 32 * B));
+    PM_CUDA(cudaMalloc(&bo.p, 4 * B));
+    PM_CUDA(cudaMemcpyAsync(bx.p, X, 32 * B, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(launch_mlp_forward(m->img, (const float*)bx.p, (int)B, (float*)bo.p, ctx->sm_count, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(out, bo.p, 4 * B, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return PM_OK;
+}
+
+pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, const float* T, uint64_t B, float* grad,
+                          double* loss)
+{
+    if (!ctx || !m || !X || !T || !grad || B == 0 || B > (1ull << 30)) return PM_EINVAL;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    DevBuf bx, bt, bp, bl;
+    PM_CUDA(cudaMalloc(&bx.p, 32 * B));
+    PM_CUDA(cudaMalloc(&bt.p, 4 * B));
+    PM_CUDA(cudaMalloc(&bp.p, 4 * B));
+    PM_CUDA(cudaMalloc(&bl.p, 8));
+    std::vector<int> perm(B);
+    for (uint64_t i = 0; i < B; ++i) perm[i] = (int)i;
+    PM_CUDA(cudaMemcpyAsync(bx.p, X, 32 * B, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(bt.p, T, 4 * B, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(bp.p, perm.data(), 4 * B, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(m->grad, 0, 4 * model_param_count(), ctx->stream));
+    PM_CUDA(cudaMemsetAsync(bl.p, 0, 8, ctx->stream));
+    PM_CUDA(launch_mlp_grad(m->img, (const float*)bx.p, (const float*)bt.p, (const int*)bp.p, 0, (int)B, m->grad,
+                            (double*)bl.p, ctx->sm_count, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(grad, m->grad, 4 * model_param_count(), cudaMemcpyDeviceToHost, ctx->stream));
+    double l = 0;
+    PM_CUDA(cudaMemcpyAsync(&l, bl.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (loss) *loss = l;
+    return PM_OK;
+}
+
+// record pairs of one or more matrices into device buffers (trajectory kernel in record mode)
+static pm_status record_into(pm_context* ctx, const pm_csr* mats, int32_t count, const uint64_t* ntraj,
+                             uint64_t first, uint32_t matrix_index0, uint64_t seed, const pm_schedule* teacher,
+                             float* dfeat, float* dtarget, unsigned long long* dkey, unsigned long long* dcount,
+                             unsigned long long cap)
+{
+    Run R;
+    R.mats = mats;
+    R.count = count;
+    R.ntraj.assign(ntraj, ntraj + count);
+    R.first_traj = first;
+    R.matrix_index0 = matrix_index0;
+    R.seed = seed;
+    R.s = to_sched(teacher);
+    R.rec_feat = dfeat;
+    R.rec_target = dtarget;
+    R.rec_key = dkey;
+    R.rec_count = dcount;
+    R.rec_cap = cap;
+    std::vector<pm_result> outs(count);
+    R.outs = outs.data();
+    return execute(ctx, R);
+}
+
+static pm_status check_teacher(pm_context* ctx, const pm_schedule* t)
+{
+    pm_status st = check_schedule(ctx, t);
+    if (st != PM_OK) return st;
+    if (t->learned || t->precision != 0 || (t->sk != 1 && t->sk != 2))
+        return fail(ctx, PM_EINVAL, "the teacher must be an FP32 Fixed/Adaptive SK schedule");
+    return PM_OK;
+}
+
+pm_status pm_record_pairs(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index, uint64_t first_traj, uint32_t count,
+                          uint64_t seed, const pm_schedule* teacher, uint64_t cap, float* feat, float* target,
+                          uint64_t* key, uint64_t* n_out)
+{
+    if (!ctx || !csr || !feat || !target || !key || !n_out || cap == 0 || count == 0 || matrix_index > 0xFFFF)
+        return PM_EINVAL;
+    pm_status st = check_teacher(ctx, teacher);
+    if (st != PM_OK) return st;
+    st = check_csr(ctx, csr);
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    DevBuf bf, bt, bk, bc;
+    PM_CUDA(cudaMalloc(&bf.p, 32 * cap));
+    PM_CUDA(cudaMalloc(&bt.p, 4 * cap));
+    PM_CUDA(cudaMalloc(&bk.p, 8 * cap));
+    PM_CUDA(cudaMalloc(&bc.p, 8));
+    PM_CUDA(cudaMemsetAsync(bc.p, 0, 8, ctx->stream));
+    const uint64_t nt = count;
+    st = record_into(ctx, csr, 1, &nt, first_traj, matrix_index, seed, teacher, (float*)bf.p, (float*)bt.p,
+                     (unsigned long long*)bk.p, (unsigned long long*)bc.p, cap);
+    if (st != PM_OK) return st;
+    unsigned long long c = 0;
+    PM_CUDA(cudaMemcpy(&c, bc.p, 8, cudaMemcpyDeviceToHost));
+    const uint64_t kept = std::min<uint64_t>(c, cap);
+    PM_CUDA(cudaMemcpy(feat, bf.p, 32 * kept, cudaMemcpyDeviceToHost));
+    PM_CUDA(cudaMemcpy(target, bt.p, 4 * kept, cudaMemcpyDeviceToHost));
+    PM_CUDA(cudaMemcpy(key, bk.p, 8 * kept, cudaMemcpyDeviceToHost));
+    *n_out = kept;
+    return PM_OK;
+}
+
+pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32_t count, const pm_train_cfg* cfg,
+                         pm_train_report* report)
+{
+    if (!ctx || !m || !mats || count < 1 || count > 65535 || !cfg || cfg->n_pairs == 0 || cfg->epochs < 1 ||
+        cfg->batch < 16 || cfg->n_pairs > (1ull << 31))
+        return fail(ctx, PM_EINVAL, "bad training arguments");
+    pm_status st = check_teacher(ctx, &cfg->teacher);
+    if (st != PM_OK) return st;
+    for (int k = 0; k < count; ++k) {
+        st = check_csr(ctx, &mats[k]);
+        if (st != PM_OK) return st;
+    }
+    PM_CUDA(cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    const uint64_t cap = cfg->n_pairs;
+    DevBuf bf, bt, bk, bc, bp, bl;
+    PM_CUDA(cudaMalloc(&bf.p, 32 * cap));
+    PM_CUDA(cudaMalloc(&bt.p, 4 * cap));
+    PM_CUDA(cudaMalloc(&bk.p, 8 * cap));
+    PM_CUDA(cudaMalloc(&bc.p, 8));
+    PM_CUDA(cudaMemsetAsync(bc.p, 0, 8, ctx->stream));
+    // record until the buffer is full: about 2 pairs per step and trajectory
+    uint64_t first = 0;
+    unsigned long long have = 0;
+    for (int round = 0; round < 64 && have < cap; ++round) {
+        std::vector<uint64_t> nt(count);
+        for (int k = 0; k < count; ++k) {
+            const uint64_t per_traj = 2ull * (uint64_t)mats[k].n;
+            nt[k] = std::max<uint64_t>(1, (cap - have) / ((uint64_t)count * per_traj) + 1);
+        }
+        st = record_into(ctx, mats, count, nt.data(), first, 0, cfg->seed, &cfg->teacher, (float*)bf.p, (float*)bt.p,
+                         (unsigned long long*)bk.p, (unsigned long long*)bc.p, cap);
+        if (st != PM_OK) return st;
+        PM_CUDA(cudaMemcpy(&have, bc.p, 8, cudaMemcpyDeviceToHost));
+        first += *std::max_element(nt.begin(), nt.end());
+    }
+    const uint64_t N = std::min<uint64_t>(have, cap);
+    const auto t1 = std::chrono::steady_clock::now();
+    if (N < 16) return fail(ctx, PM_EINVAL, "the teacher produced too few pairs");
+    // start the output bias at the mean target
+    std::vector<float> tg(N);
+    PM_CUDA(cudaMemcpy(tg.data(), bt.p, 4 * N, cudaMemcpyDeviceToHost));
+    double mean = 0;
+    for (float v : tg) mean += v;
+    mean /= (double)N;
+    if (m->step == 0) {
+        const float b3 = (float)mean;
+        PM_CUDA(cudaMemcpy(m->master + 4800, &b3, 4, cudaMemcpyHostToDevice));
+        PM_CUDA(launch_model_image(m->master, m->img, ctx->stream));
+    }
+    // shuffled order
+    std::vector<int> perm(N);
+    for (uint64_t i = 0; i < N; ++i) perm[i] = (int)i;
+    std::mt19937_64 rng(cfg->seed ^ 0x9E3779B97F4A7C15ull);
+    std::shuffle(perm.begin(), perm.end(), rng);
+    PM_CUDA(cudaMalloc(&bp.p, 4 * N));
+    PM_CUDA(cudaMemcpy(bp.p, perm.data(), 4 * N, cudaMemcpyHostToDevice));
+    const uint64_t steps_per_epoch = (N + cfg->batch - 1) / cfg->batch;
+    const uint64_t total_steps = steps_per_epoch * (uint64_t)cfg->epochs;
+    PM_CUDA(cudaMalloc(&bl.p, 8 * total_steps));
+    PM_CUDA(cudaMemsetAsync(bl.p, 0, 8 * total_steps, ctx->stream));
+    uint64_t sidx = 0;
+    for (int ep = 0; ep < cfg->epochs; ++ep) {
+        for (uint64_t b = 0; b < steps_per_epoch; ++b, ++sidx) {
+            const uint64_t row0 = b * (uint64_t)cfg->batch;
+            const int B = (int)std::min<uint64_t>((uint64_t)cfg->batch, N - row0);
+            PM_CUDA(cudaMemsetAsync(m->grad, 0, 4 * model_param_count(), ctx->stream));
+            PM_CUDA(launch_mlp_grad(m->img, (const float*)bf.p, (const float*)bt.p, (const int*)bp.p, (int64_t)row0, B,
+                                    m->grad, (double*)bl.p + sidx, ctx->sm_count, ctx->stream));
+            ++m->step;
+            PM_CUDA(launch_adam(m->master, m->m1, m->m2, m->grad, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, m->step,
+                                m->img, ctx->stream));
+        }
+    }
+    std::vector<double> losses(total_steps);
+    PM_CUDA(cudaMemcpyAsync(losses.data(), bl.p, 8 * total_steps, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    const auto t2 = std::chrono::steady_clock::now();
+    if (report) {
+        std::memset(report, 0, sizeof(*report));
+        report->loss_first = losses.front();
+        double s = 0;
+        for (uint64_t q = total_steps - steps_per_epoch; q < total_steps; ++q) s += losses[q];
+        report->loss_last = s / (double)steps_per_epoch;
+        report->n_pairs = N;
+        report->steps = (int32_t)total_steps;
+        report->seconds_record = std::chrono::duration<double>(t1 - t0).count();
+        report->seconds_train = std::chrono::duration<double>(t2 - t1).count();
+    }
+    return PM_OK;
+}
 
 }  // extern "C"

@@ -168,15 +168,25 @@ struct TrajParams {
     int32_t* chosen;
     int32_t* deg_v;
     int32_t* dead_step;
+    float* trace_logits;      // [T][n][32] logits of the live candidates (learned proposal)
+    // learned proposal: BF16 device image of the network, or nullptr
+    const void* model;
+    // recording of (features, SK target) pairs, or rec_feat == nullptr
+    float* rec_feat;          // [cap][8]
+    float* rec_target;        // [cap]
+    unsigned long long* rec_key;   // [cap]: traj << 28 | step << 14 | candidate
+    unsigned long long* rec_count;
+    unsigned long long rec_cap;
 };
 
 // shared-memory sizes used by the plan
-inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists)
+inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists, bool learned)
 {
     const TreeGeom G = tree_geom(n);
     size_t b = align_up((size_t)((2 * n + 7) & ~7) * 2, 16) + align_up((size_t)G.total * 4, 16);
     if (rc_smem) b += 2 * align_up((size_t)n * real_bytes, 16);
     if (lists) b += 2 * align_up((size_t)n * 2, 16);
+    if (learned) b += 32 * 16 * 2;
     b += kGroupMiscInts * 4;
     return (int)b;
 }
@@ -209,5 +219,15 @@ cudaError_t launch_stats(const double* log_x, const uint64_t* h_prefix, const ui
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t count, uint32_t* out,
                           cudaStream_t st);
 int traj_max_smem_bytes();
+// learned proposal (pm_learn.cu)
+int model_image_bytes();
+int model_infer_bytes();
+int model_param_count();
+cudaError_t launch_model_image(const float* master, void* img, cudaStream_t st);
+cudaError_t launch_mlp_grad(const void* img, const float* feat, const float* target, const int* perm, int64_t row0,
+                            int B, float* grad, double* loss, int sm_count, cudaStream_t st);
+cudaError_t launch_mlp_forward(const void* img, const float* feat, int B, float* out, int sm_count, cudaStream_t st);
+cudaError_t launch_adam(float* master, float* m1, float* m2, const float* grad, float lr, float b1, float b2, float eps,
+                        int step, void* img, cudaStream_t st);
 
 }  // namespace pm

@@ -1,0 +1,175 @@
+// pm_mlp.cuh -- the learned proposal's network (8 -> 64 -> 64 -> 1, GELU) on
+// BF16 tensor cores with FP32 accumulation, and its binary32 score exponent.
+//
+// A 16-row tile goes through the three layers as mma.sync.m16n8k16 operations;
+// the FP32 accumulator fragments of one layer become the BF16 A fragments of
+// the next without leaving registers (the accumulator of n-tiles 2k, 2k+1 is
+// exactly the A fragment of k-tile k).  Weights sit in shared memory in the
+// [out][in] row-major layout, so every B fragment is one 32-bit load.
+#pragma once
+#include <cuda_bf16.h>
+#include "pm_device.cuh"
+
+namespace pm {
+
+constexpr int kNF = 8, kNH = 64;
+constexpr int kNParam = kNH * kNF + kNH + kNH * kNH + kNH + kNH + 1;  // 4801
+
+// device image of a model; the first kModelInferBytes are what inference needs
+struct DevModel {
+    uint16_t w1p[kNH * 16];   // W1 [out][in], in padded 8 -> 16 with zeros
+    uint16_t w2[kNH * kNH];   // W2 [out][in]
+    uint16_t w3p[8 * kNH];    // row 0 = W3, rows 1..7 zero (an 8-wide n-tile)
+    float b1[kNH];
+    float b2[kNH];
+    float b3[4];
+    uint16_t w2t[kNH * kNH];  // W2 transposed [in][out] (training only)
+};
+constexpr int kModelInferBytes = (int)(sizeof(uint16_t) * (kNH * 16 + kNH * kNH + 8 * kNH) + sizeof(float) * (2 * kNH + 4));
+
+__device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// e^x of the learned proposal's score: x clamped to [-20, 20] (NaN -> -20),
+// 2^(x log2 e) with a degree-7 Taylor polynomial of 2^f = e^(f ln 2) on
+// |f| <= 1/2; coefficients (ln 2)^k / k! and log2 e rounded to binary32, every
+// operation correctly rounded (the CPU oracle computes the same bits).
+__device__ __forceinline__ float exp_score(float x)
+{
+    if (!(x >= -20.0f)) x = -20.0f;
+    if (x > 20.0f) x = 20.0f;
+    const float y = __fmul_rn(x, 0x1.715476p+0f);
+    const float nn = rintf(y);
+    const float f = __fsub_rn(y, nn);
+    float p = 0x1.ffcbfcp-17f;
+    p = __fadd_rn(__fmul_rn(p, f), 0x1.430912p-13f);
+    p = __fadd_rn(__fmul_rn(p, f), 0x1.5d87fep-10f);
+    p = __fadd_rn(__fmul_rn(p, f), 0x1.3b2ab6p-7f);
+    p = __fadd_rn(__fmul_rn(p, f), 0x1.c6b08ep-5f);
+    p = __fadd_rn(__fmul_rn(p, f), 0x1.ebfbe0p-3f);
+    p = __fadd_rn(__fmul_rn(p, f), 0x1.62e430p-1f);
+    p = __fadd_rn(__fmul_rn(p, f), 1.0f);
+    return __fmul_rn(p, __int_as_float((127 + (int)nn) << 23));
+}
+
+// Forward of one 16-row tile whose features are A fragment `a` (bf16, K = 16
+// with features 8..15 zero).  Returns the outputs of rows g and g + 8 in lanes
+// with (lane & 3) == 0 (g = lane >> 2).  If z1 / z2 are given, the FP32
+// pre-activations of both hidden layers are kept (accumulator layout,
+// [n-tile][4]) for the backward pass, and h1 the BF16 A fragments of layer 2.
+struct FwdKeep {
+    float z1[8][4];
+    float z2[8][4];
+    uint32_t h1[4][4];
+    uint32_t h2[4][4];
+};
+
+template <bool KEEP>
+__device__ __forceinline__ void mlp_fwd_tile(const DevModel* M, const uint32_t (&a)[4], int lane, float& y_lo,
+                                             float& y_hi, FwdKeep* keep)
+{
+    const int g = lane >> 2, t = lane & 3;
+    uint32_t h[4][4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        float acc[2][4];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int j = 2 * kk + jj;
+            const float c0 = M->b1[8 * j + 2 * t], c1 = M->b1[8 * j + 2 * t + 1];
+            acc[jj][0] = c0; acc[jj][1] = c1; acc[jj][2] = c0; acc[jj][3] = c1;
+            mma16816(acc[jj], a, ld32(M->w1p + (8 * j + g) * 16 + 2 * t), ld32(M->w1p + (8 * j + g) * 16 + 2 * t + 8));
+            if (KEEP) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) keep->z1[j][q] = acc[jj][q];
+            }
+        }
+        h[kk][0] = pack_bf16(gelu_f(acc[0][0]), gelu_f(acc[0][1]));
+        h[kk][1] = pack_bf16(gelu_f(acc[0][2]), gelu_f(acc[0][3]));
+        h[kk][2] = pack_bf16(gelu_f(acc[1][0]), gelu_f(acc[1][1]));
+        h[kk][3] = pack_bf16(gelu_f(acc[1][2]), gelu_f(acc[1][3]));
+        if (KEEP) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) keep->h1[kk][q] = h[kk][q];
+        }
+    }
+    uint32_t h2[4][4];
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+        float acc[2][4];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int j = 2 * k2 + jj;
+            const float c0 = M->b2[8 * j + 2 * t], c1 = M->b2[8 * j + 2 * t + 1];
+            acc[jj][0] = c0; acc[jj][1] = c1; acc[jj][2] = c0; acc[jj][3] = c1;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma16816(acc[jj], h[kk], ld32(M->w2 + (8 * j + g) * kNH + 16 * kk + 2 * t),
+                         ld32(M->w2 + (8 * j + g) * kNH + 16 * kk + 2 * t + 8));
+            if (KEEP) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) keep->z2[j][q] = acc[jj][q];
+            }
+        }
+        h2[k2][0] = pack_bf16(gelu_f(acc[0][0]), gelu_f(acc[0][1]));
+        h2[k2][1] = pack_bf16(gelu_f(acc[0][2]), gelu_f(acc[0][3]));
+        h2[k2][2] = pack_bf16(gelu_f(acc[1][0]), gelu_f(acc[1][1]));
+        h2[k2][3] = pack_bf16(gelu_f(acc[1][2]), gelu_f(acc[1][3]));
+        if (KEEP) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) keep->h2[k2][q] = h2[k2][q];
+        }
+    }
+    float acc3[4];
+    acc3[0] = (t == 0) ? M->b3[0] : 0.0f;
+    acc3[1] = 0.0f;
+    acc3[2] = acc3[0];
+    acc3[3] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+        mma16816(acc3, h2[kk], ld32(M->w3p + g * kNH + 16 * kk + 2 * t), ld32(M->w3p + g * kNH + 16 * kk + 2 * t + 8));
+    y_lo = acc3[0];
+    y_hi = acc3[2];
+}
+
+// Inference for 32 rows of features (bf16 [32][16] in shared memory, features
+// 8..15 zero): returns the output of row `lane` in lane `lane`.
+__device__ __forceinline__ float mlp_infer32(const DevModel* M, const uint16_t* feat, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+    float lo[2], hi[2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const uint16_t* F = feat + mt * 16 * 16;
+        uint32_t a[4] = {ld32(F + g * 16 + 2 * t), ld32(F + (g + 8) * 16 + 2 * t), ld32(F + g * 16 + 2 * t + 8),
+                         ld32(F + (g + 8) * 16 + 2 * t + 8)};
+        mlp_fwd_tile<false>(M, a, lane, lo[mt], hi[mt], nullptr);
+    }
+    const int rr = lane & 15, src = (rr & 7) * 4;
+    const float l0 = __shfl_sync(kFull, lo[0], src), h0 = __shfl_sync(kFull, hi[0], src);
+    const float l1 = __shfl_sync(kFull, lo[1], src), h1 = __shfl_sync(kFull, hi[1], src);
+    const float r0 = rr < 8 ? l0 : h0, r1 = rr < 8 ? l1 : h1;
+    return lane < 16 ? r0 : r1;
+}
+
+}  // namespace pm

@@ -21,6 +21,7 @@
 #include <cmath>
 #include "pm_device.cuh"
 #include "pm_dm.cuh"
+#include "pm_mlp.cuh"
 
 namespace pm {
 
@@ -314,15 +315,55 @@ __device__ __forceinline__ Real cand_score(const MV<Idx>& V, bool vrow, int e, i
     return s;
 }
 
+// Per-edge features of candidate p of the picked vertex v at step t (the
+// learned proposal's inputs): log1p deg(v), log1p deg(p),
+// log1p of the degree sum over v's live candidates, log1p of the degree sum
+// over p's live neighbours, t / n, ln of the outer scales of v and p, ln B_vp.
+template <typename Idx>
+__device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask,
+                                              const DevMatrix* Mp, int t, int v, bool vrow, int e, int p,
+                                              float sum_v, float dv, float (&f)[8])
+{
+    const int n = V.n;
+    int sum_l = 0;
+    if (vrow) {  // p is a column: its live rows
+        for (int k = V.cp[p]; k < V.cp[p + 1]; ++k) {
+            const int i = V.ri[k];
+            if (deg[i] != kInact && (!mask || mask[V.ce[k]])) sum_l += deg[i];
+        }
+    } else {     // p is a row: its live columns
+        for (int k = V.rp[p]; k < V.rp[p + 1]; ++k) {
+            const int j = V.ci[k];
+            if (deg[n + j] != kInact && (!mask || mask[k])) sum_l += deg[n + j];
+        }
+    }
+    const float* r0 = reinterpret_cast<const float*>(Mp->r0);
+    const float* c0 = reinterpret_cast<const float*>(Mp->c0);
+    const float sv = vrow ? __ldg(r0 + v) : __ldg(c0 + (v - n));
+    const float sl = vrow ? __ldg(c0 + p) : __ldg(r0 + p);
+    const float* vals = vrow ? V.rv : V.cv;
+    f[0] = log1pf(dv);
+    f[1] = log1pf((float)deg[p + (vrow ? n : 0)]);
+    f[2] = log1pf(sum_v);
+    f[3] = log1pf((float)sum_l);
+    f[4] = __fdiv_rn((float)t, (float)n);
+    f[5] = logf(sv);
+    f[6] = logf(sl);
+    f[7] = vals ? logf(__ldg(vals + e)) : 0.0f;
+}
+
 // misc slots of a group (two step buffers so a fast leader never overwrites
 // values a slower warp of its group is still reading)
 enum { M_DEAD = 0, M_NIT = 1, M_DM = 2, M_CNTR = 3, M_CNTC = 4, M_STRIDE = 8, M_TMP = 16, M_TRAJ = 17, M_DMOK = 18 };
 
-template <typename Real, typename Idx, bool TRACE>
+// MODE: 0 scaled proposal, 1 learned proposal, 2 recording of (features, SK target) pairs
+template <typename Real, typename Idx, bool TRACE, int MODE>
 __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>& V, int k, uint64_t gq,
-                          uint64_t local, uint16_t* deg, uint32_t* tree, Real* r_sm, uint16_t* lists, uint8_t* slot,
-                          const Grp& G)
+                          uint64_t local, uint16_t* deg, uint32_t* tree, Real* r_sm, uint16_t* lists, uint16_t* feat,
+                          const DevModel* Ms, uint8_t* slot, const Grp& G)
 {
+    constexpr bool model = MODE == 1;
+    constexpr bool rec = MODE == 2;
     const int n = V.n;
     const int lane = G.lane;
     const bool leader = G.wig == 0;
@@ -425,18 +466,83 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 bool keep_live = false;
                 int keep_pid = 0;
                 uint64_t rr;
+                // learned proposal: logits of the live candidates from their features
+                float sum_v = 0.f;  // degree sum over v's live candidates (feature)
+                if (model || rec) {
+                    int sv_i = 0;
+                    for (int base = beg; base < end; base += 32) {
+                        const int e = base + lane;
+                        if (e < end) {
+                            const int pid = (int)adj[e] + poff;
+                            if (entry_live(deg, mask, V, vrow, e, pid)) sv_i += deg[pid];
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) sv_i += __shfl_xor_sync(kFull, sv_i, o);
+                    sum_v = (float)sv_i;
+                }
+                auto cand_logit = [&](int e, int pp, bool live) -> float {
+                    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    if (live) cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
+                    uint4 lo;
+                    lo.x = pack_bf16(f[0], f[1]);
+                    lo.y = pack_bf16(f[2], f[3]);
+                    lo.z = pack_bf16(f[4], f[5]);
+                    lo.w = pack_bf16(f[6], f[7]);
+                    uint4* row = reinterpret_cast<uint4*>(feat + lane * 16);
+                    row[0] = lo;
+                    row[1] = make_uint4(0u, 0u, 0u, 0u);
+                    __syncwarp();
+                    const float lg = mlp_infer32(Ms, feat, lane);
+                    __syncwarp();
+                    return lg;
+                };
+                // score of a live candidate: B * c (scaled) or B * e^logit (learned)
+                auto score = [&](int e, int pp, float lg) -> Real {
+                    if (!model) return cand_score<Real, Idx>(V, vrow, e, pp, r, c);
+                    const float* vals = vrow ? V.rv : V.cv;
+                    const float ex = exp_score(lg);
+                    Real sv = vals ? (Real)__fmul_rn(__ldg(vals + e), ex) : (Real)ex;
+                    if (!(sv >= (Real)0)) sv = 0;
+                    return sv;
+                };
+                // recording of (features, SK target) pairs and of trace logits
+                auto side_outputs = [&](int e, int pp, bool live, float lg, int live_base) {
+                    const unsigned lmk = __ballot_sync(kFull, live);
+                    const int li = live_base + __popc(lmk & ((1u << lane) - 1u));
+                    if (TRACE && model && live && li < 32) P.trace_logits[(gq * n + t) * 32 + li] = lg;
+                    if (rec) {
+                        unsigned long long base0 = 0;
+                        if (lane == 0 && lmk) base0 = atomicAdd(P.rec_count, (unsigned long long)__popc(lmk));
+                        base0 = __shfl_sync(kFull, base0, 0);
+                        const unsigned long long pos = base0 + __popc(lmk & ((1u << lane) - 1u));
+                        if (live && pos < P.rec_cap) {
+                            float f[8];
+                            cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) P.rec_feat[pos * 8 + q] = f[q];
+                            const double sv_cur = vrow ? (double)r[vi] : (double)c[vi];
+                            const double sl_cur = vrow ? (double)c[pp] : (double)r[pp];
+                            P.rec_target[pos] = (float)log(sv_cur * sl_cur);
+                            P.rec_key[pos] = (traj << 28) | ((unsigned long long)t << 14) | (unsigned long long)li;
+                        }
+                    }
+                    return __popc(lmk);
+                };
                 if (len <= 32) {
                     const int e = beg + lane;
                     const bool in = lane < len;
                     const int pp = in ? (int)adj[e] : 0;
                     const bool live = in && entry_live(deg, mask, V, vrow, e, pp + poff);
                     const unsigned lm = __ballot_sync(kFull, live);
+                    const float lg = model ? cand_logit(e, pp, live) : 0.f;
+                    if ((TRACE && model) || rec) side_outputs(e, pp, live, lg, 0);
                     uint64_t w;
                     if (uniform) {
                         w = live ? (1ull << kq) : 0ull;
                         W = (uint64_t)dv << kq;
                     } else {
-                        const Real sv = live ? cand_score<Real, Idx>(V, vrow, e, pp, r, c) : (Real)0;
+                        const Real sv = live ? score(e, pp, lg) : (Real)0;
                         const Real smax = warp_max_nonneg(sv);
                         w = live ? quant_weight<Real>(sv, smax, kq) : 0ull;
                         W = warp_sum_u64(w);
@@ -467,25 +573,33 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 } else {
                     Real smax = 0;
                     if (!uniform) {
+                        int live_base = 0;
                         for (int base = beg; base < end; base += 32) {
                             const int e = base + lane;
                             Real sv = 0;
+                            int pp = 0;
+                            bool live = false;
                             if (e < end) {
-                                const int pp = adj[e];
-                                if (entry_live(deg, mask, V, vrow, e, pp + poff))
-                                    sv = cand_score<Real, Idx>(V, vrow, e, pp, r, c);
+                                pp = adj[e];
+                                live = entry_live(deg, mask, V, vrow, e, pp + poff);
                             }
+                            const float lg = model ? cand_logit(e, pp, live) : 0.f;
+                            if ((TRACE && model) || rec) live_base += side_outputs(e, pp, live, lg, live_base);
+                            if (live) sv = score(e, pp, lg);
                             const Real cm = warp_max_nonneg(sv);
                             smax = cm > smax ? cm : smax;
                         }
                         for (int base = beg; base < end; base += 32) {
                             const int e = base + lane;
                             uint64_t w = 0;
+                            int pp = 0;
+                            bool live = false;
                             if (e < end) {
-                                const int pp = adj[e];
-                                if (entry_live(deg, mask, V, vrow, e, pp + poff))
-                                    w = quant_weight<Real>(cand_score<Real, Idx>(V, vrow, e, pp, r, c), smax, kq);
+                                pp = adj[e];
+                                live = entry_live(deg, mask, V, vrow, e, pp + poff);
                             }
+                            const float lg = model ? cand_logit(e, pp, live) : 0.f;
+                            if (live) w = quant_weight<Real>(score(e, pp, lg), smax, kq);
                             W += warp_sum_u64(w);
                         }
                     } else {
@@ -506,10 +620,9 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                         if (e < end) {
                             pp = adj[e];
                             live = entry_live(deg, mask, V, vrow, e, pp + poff);
-                            if (live)
-                                w = uniform ? (1ull << kq)
-                                            : quant_weight<Real>(cand_score<Real, Idx>(V, vrow, e, pp, r, c), smax, kq);
                         }
+                        const float lg = model ? cand_logit(e, pp, live) : 0.f;
+                        if (live) w = uniform ? (1ull << kq) : quant_weight<Real>(score(e, pp, lg), smax, kq);
                         const uint64_t pre = warp_incl_scan_u64(w, lane) + carry;
                         const unsigned hit = __ballot_sync(kFull, live && pre > rr);
                         if (hit) {
@@ -706,9 +819,9 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     gsync(G);
 }
 
-template <typename Real, typename Idx, bool TRACE>
+template <typename Real, typename Idx, bool TRACE, int MODE>
 __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, const MV<Idx>& V, uint8_t* gstate,
-                          int* ctr_traj)
+                          int* ctr_traj, const DevModel* Ms)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gidx = warp / pl.g;
@@ -739,6 +852,11 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         lists = reinterpret_cast<uint16_t*>(base + off);
         off += 2 * a16((size_t)n * 2);
     }
+    uint16_t* feat = nullptr;   // [32][16] bf16 feature tile of the learned proposal
+    if (Ms) {
+        feat = reinterpret_cast<uint16_t*>(base + off);
+        off += 32 * 16 * 2;
+    }
     G.misc = reinterpret_cast<int*>(base + off);
     uint8_t* slot = P.slots + ((size_t)blockIdx.x * kCtaWarps + gidx) * P.slot.bytes;
     for (;;) {
@@ -748,17 +866,28 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         gsync(G);
         if (q >= (int)ch.count) break;
         const uint64_t local = ch.first + (uint64_t)q;
-        run_group<Real, Idx, TRACE>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm, lists, slot, G);
+        run_group<Real, Idx, TRACE, MODE>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm, lists, feat, Ms, slot,
+                                          G);
     }
 }
 
-template <typename Real, bool TRACE>
+template <typename Real, bool TRACE, int MODE>
 __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     int* cmisc = reinterpret_cast<int*>(smem);  // [0] chunk, [1] trajectory counter, [2] staged matrix
     const int tid = threadIdx.x;
     if (tid == 0) cmisc[2] = -1;
+    // the learned proposal's weights, staged once per CTA
+    const DevModel* Ms = nullptr;
+    int model_bytes = 0;
+    if (MODE == 1) {
+        model_bytes = (kModelInferBytes + 15) & ~15;
+        const uint4* src = reinterpret_cast<const uint4*>(P.model);
+        uint4* dst = reinterpret_cast<uint4*>(smem + kCtaMiscBytes);
+        for (int q = tid; q < model_bytes / 16; q += blockDim.x) dst[q] = __ldg(src + q);
+        Ms = reinterpret_cast<const DevModel*>(smem + kCtaMiscBytes);
+    }
     for (;;) {
         __syncthreads();
         if (tid == 0) {
@@ -772,7 +901,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
         const Plan pl = P.plans[ch.k];
         const DevMatrix* Mp = P.mats + ch.k;
         const int n = Mp->n;
-        uint8_t* mat = smem + kCtaMiscBytes;
+        uint8_t* mat = smem + kCtaMiscBytes + model_bytes;
         uint8_t* gstate = mat + pl.mat_bytes;
         if (pl.staged) {
             const int staged_k = cmisc[2];
@@ -795,20 +924,21 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
             }
             __syncthreads();
             MV<uint16_t> V{n, s_rp, s_cp, s_ci, s_ri, s_ce, Mp->rv, Mp->cv};
-            run_chunk<Real, uint16_t, TRACE>(P, ch, pl, V, gstate, cmisc + 1);
+            run_chunk<Real, uint16_t, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
         } else {
             MV<int> V{n, Mp->rp, Mp->cp, Mp->ci, Mp->ri, Mp->ce, Mp->rv, Mp->cv};
-            run_chunk<Real, int, TRACE>(P, ch, pl, V, gstate, cmisc + 1);
+            run_chunk<Real, int, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
         }
     }
 }
 
-template <typename Real, bool TRACE>
+template <typename Real, bool TRACE, int MODE>
 cudaError_t launch_t(const TrajParams& p, int grid, int smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(traj_kernel<Real, TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(traj_kernel<Real, TRACE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    traj_kernel<Real, TRACE><<<grid, kCtaWarps * 32, smem, st>>>(p);
+    traj_kernel<Real, TRACE, MODE><<<grid, kCtaWarps * 32, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -824,8 +954,13 @@ int traj_max_smem_bytes()
 
 cudaError_t launch_trajectories(const TrajParams& p, int grid, int smem, bool trace, cudaStream_t st)
 {
-    if (p.s.precision == 1) return trace ? launch_t<double, true>(p, grid, smem, st) : launch_t<double, false>(p, grid, smem, st);
-    return trace ? launch_t<float, true>(p, grid, smem, st) : launch_t<float, false>(p, grid, smem, st);
+    if (p.s.precision == 1) {
+        if (p.model || p.rec_feat) return cudaErrorInvalidValue;  // learned / record are FP32-only
+        return trace ? launch_t<double, true, 0>(p, grid, smem, st) : launch_t<double, false, 0>(p, grid, smem, st);
+    }
+    if (p.model) return trace ? launch_t<float, true, 1>(p, grid, smem, st) : launch_t<float, false, 1>(p, grid, smem, st);
+    if (p.rec_feat) return launch_t<float, false, 2>(p, grid, smem, st);
+    return trace ? launch_t<float, true, 0>(p, grid, smem, st) : launch_t<float, false, 0>(p, grid, smem, st);
 }
 
 }  // namespace pm

@@ -1,0 +1,147 @@
+"""GPU parity of the learned proposal (a spec extension; the paper has
+no learned part) against the CPU oracle, and what training gains.
+
+Bars:
+  forward    BF16 weights/inputs and BF16 hidden activations on tensor cores
+             vs an FP64 network with the same rounding of weights, inputs and
+             activations: |dy| <= 2e-2 * max(1, |y|) (FP32 accumulation order
+             can flip a BF16 rounding of a hidden unit: one BF16 ulp, 2^-8)
+  gradient   cosine > 0.999 per parameter block, relative norm error < 5e-2
+  features   recorded pairs: same keys, features and targets within 1e-5
+  replay     with the GPU's logits supplied, the oracle's paths are
+             bit-exact and ln X agrees within 1e-12
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_15390_b300 import inputs as G
+from tests._gpu_common import binding, ctx, logx_close
+
+pytestmark = pytest.mark.gpu
+
+BLOCKS = {"W1": (0, 512), "b1": (512, 576), "W2": (576, 4672), "b2": (4672, 4736), "W3": (4736, 4800),
+          "b3": (4800, 4801)}
+
+
+def bf16(x):
+    a = np.asarray(x, dtype=np.float32).copy()
+    u = a.view(np.uint32)
+    u[:] = ((u.astype(np.uint64) + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return a
+
+
+def oracle_params(p):
+    """The GPU keeps weights in BF16 and biases in FP32."""
+    q = np.asarray(p, dtype=np.float32).astype(np.float64)
+    for name in ("W1", "W2", "W3"):
+        a, b = BLOCKS[name]
+        q[a:b] = bf16(p[a:b])
+    return q
+
+
+def rand_params(rng, scale=0.4):
+    return (rng.normal(size=O.N_PARAM) * scale).astype(np.float32)
+
+
+def test_mlp_forward_matches_oracle():
+    rng = np.random.default_rng(3)
+    for trial in range(3):
+        p = rand_params(rng)
+        m = ctx().model(p)
+        X = rng.normal(size=(1003, 8)).astype(np.float32)
+        y = m.forward(X)
+        ref = O.mlp_forward(oracle_params(p), bf16(X).astype(np.float64), round_act=True)
+        err = np.abs(y - ref) / np.maximum(1.0, np.abs(ref))
+        assert err.max() < 2e-2, err.max()
+        assert np.median(err) < 2e-3
+        m.close()
+
+
+def test_mlp_gradient_matches_oracle():
+    rng = np.random.default_rng(4)
+    p = rand_params(rng, 0.3)
+    m = ctx().model(p)
+    X = rng.normal(size=(4099, 8)).astype(np.float32)
+    T = rng.normal(size=4099).astype(np.float32)
+    loss, g = m.gradient(X, T)
+    ref_loss, ref = O.mlp_grad(oracle_params(p), bf16(X).astype(np.float64), T.astype(np.float64))
+    assert loss == pytest.approx(ref_loss, rel=2e-2)
+    for name, (a, b) in BLOCKS.items():
+        u, v = g[a:b].astype(np.float64), ref[a:b]
+        if name == "b3":
+            assert u[0] == pytest.approx(v[0], rel=2e-2, abs=1e-4)
+            continue
+        cos = float(u @ v / (np.linalg.norm(u) * np.linalg.norm(v)))
+        rel = float(np.linalg.norm(u - v) / np.linalg.norm(v))
+        assert cos > 0.999 and rel < 5e-2, (name, cos, rel)
+    m.close()
+
+
+def test_recorded_pairs_match_oracle():
+    B = binding()
+    m = G.er_planted(80, 5.0, seed=21)
+    teacher = O.Schedule(initial_dm=1, K0=20, K=3, sk=O.SK_FIXED, precision=O.PREC_FP32)
+    gt = B.Schedule(initial_dm=1, K0=20, K=3, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
+    f, t, k = ctx().record_pairs(m, 8, 7, gt, cap=100000)
+    of, ot, ok = O.Prepared(m, teacher).record(seed=7, count=8, cap=100000)
+    assert len(k) == len(ok) and len(k) > 100
+    order = np.argsort(k)
+    assert np.array_equal(k[order], ok)
+    assert np.allclose(f[order], of, rtol=1e-5, atol=1e-6)
+    assert np.allclose(t[order], ot, rtol=1e-5, atol=1e-6)
+
+
+def test_learned_trajectories_replay_bit_exact():
+    B = binding()
+    rng = np.random.default_rng(5)
+    for mat in (G.er_planted(120, 5.0, seed=31), G.random_weighted(40, 0.15, seed=32)):
+        p = rand_params(rng, 0.3)
+        model = ctx().model(p)
+        sched = B.Schedule(initial_dm=1, K0=30, precision=B.PREC_FP32_PROPOSAL, learned=model)
+        T = 100
+        g = ctx().trace(mat, T, 9, sched)
+        P = O.Prepared(mat, O.Schedule(initial_dm=1, K0=30, precision=O.PREC_FP32))
+        o = P.run_ext(seed=9, count=T, logits=g["logits"], threads=8)
+        assert np.array_equal(g["dead_step"], o["dead_step"])
+        assert np.array_equal(g["chosen"], o["chosen"])
+        assert np.array_equal(g["deg_v"], o["deg_v"])
+        assert logx_close(g["log_x"], o["log_x"], 1e-12) <= 1e-12
+        model.close()
+
+
+def test_training_reduces_the_loss():
+    B = binding()
+    mats = [G.er_planted(200, 6.0, seed=100 + i) for i in range(4)]
+    teacher = B.Schedule(initial_dm=1, K0=100, K=10, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
+    model = ctx().model(seed=1)
+    rep = model.train(mats, teacher, n_pairs=200000, epochs=4, batch=4096, lr=2e-3, seed=2)
+    assert rep["n_pairs"] == 200000
+    assert rep["loss_last"] < 0.5 * rep["loss_first"], rep
+    model.close()
+
+
+def test_learned_proposal_gains_over_the_plain_estimator():
+    """Trained on ER+permutation matrices (n = 150, average degree 6), evaluated
+    on held-out seeds: the learned proposal (no inner SK) must beat the plain
+    estimator (outer SK only, same vertex rule) in effective samples per
+    trajectory, and agree with the low-variance Fixed-SK estimate."""
+    B = binding()
+    train = [G.er_planted(150, 6.0, seed=1000 + i) for i in range(8)]
+    teacher = B.Schedule(initial_dm=1, K0=100, K=10, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
+    model = ctx().model(seed=3)
+    model.train(train, teacher, n_pairs=300000, epochs=6, batch=4096, lr=2e-3, seed=4)
+    plain = B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL)
+    learned = B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL, learned=model)
+    gains = []
+    for i in range(3):
+        m = G.er_planted(150, 6.0, seed=2000 + i)
+        a = ctx().estimate_permanent(m, 100000, 11, plain)
+        b = ctx().estimate_permanent(m, 100000, 11, learned)
+        ref = ctx().estimate_permanent(m, 20000, 11, teacher)
+        gains.append(b["ess"] / a["ess"])
+        assert abs(b["log_estimate"] - ref["log_estimate"]) < 5 * (b["rse"] + ref["rse"]) + 0.01
+    assert np.median(gains) > 5.0, gains
+    model.close()
