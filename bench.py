@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--traj", type=int, default=256, help="trajectories per matrix per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-compare", action="store_true",
+                   help="skip the learned-batched vs plain-unbatched comparison")
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--mats", type=int, default=N_MATS,
                    help="use the first K matrices (profiling of a smaller case)")
@@ -176,6 +178,49 @@ def cpu_baseline(mats, T_gpu_ess_per_traj, seconds_budget=20.0):
             "sample": f"{done} trajectories ({threads} per matrix per round, {rounds} rounds) on "
                       f"matrices 0,4,...,60 of the workload incl. preprocessing, {dt:.1f} s; "
                       f"{tps:.3f} traj/s x the GPU run's effective samples per trajectory"}
+
+
+def compare_learned_vs_plain(ctx, B, dev, args, T):
+    """The metric's comparison on the same 64 matrices and trajectory counts:
+    the learned proposal (network trained here, untimed, on pairs recorded
+    from an SK-scheduled run on 16 training matrices of the same family,
+    generator seed 7) run batched in one launch, against the plain estimator
+    (outer SK only, no inner scaling) run one matrix per launch.  Device time
+    from CUDA events on the launching stream, effective samples summed."""
+    import torch
+    stream = torch.cuda.current_stream()
+    train = [G.er_planted(m.n, 6.0, seed=7_000 + k) for k, m in
+             enumerate(G.batch_er(16, N_LO, N_HI, D_LO, D_HI, seed=7))]
+    teacher = B.Schedule(initial_dm=1, K0=100, K=10, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
+    model = ctx.model(seed=11)
+    t0 = time.perf_counter()
+    rep = model.train(train, teacher, n_pairs=2_000_000, epochs=4, batch=8192, lr=2e-3, seed=12)
+    t_train = time.perf_counter() - t0
+    learned = B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL, learned=model)
+    plain = B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL)
+    nt = [T] * len(dev)
+    ctx.estimate_batch_ex(dev, nt, args.seed, learned, first_traj=1 << 40)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res, _ = ctx.estimate_batch_ex(dev, nt, args.seed, learned, first_traj=(1 << 40) + T)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_l = e0.elapsed_time(e1) / 1e3
+    ess_l = sum(r["ess"] for r in res)
+    e0.record(stream)
+    ess_p = 0.0
+    for k, m in enumerate(dev):
+        r, _ = ctx.estimate_batch_ex([m], [T], args.seed, plain, first_traj=(1 << 41) + k * T)
+        ess_p += r[0]["ess"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_p = e0.elapsed_time(e1) / 1e3
+    model.close()
+    return {"learned_batched_ess_per_s": ess_l / t_l, "plain_unbatched_ess_per_s": ess_p / t_p,
+            "ratio": (ess_l / t_l) / (ess_p / t_p),
+            "learned_traj_per_s": len(dev) * T / t_l, "plain_traj_per_s": len(dev) * T / t_p,
+            "train": {"pairs": rep["n_pairs"], "loss_first": rep["loss_first"], "loss_last": rep["loss_last"],
+                      "seconds": t_train}}
 
 
 def run_reference(args, rank, world):
@@ -342,6 +387,8 @@ def main():
         "e2e": {"value": e2e_ess / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
     }
+    if not args.no_compare:
+        line["compare"] = compare_learned_vs_plain(ctx, B, dev, args, T)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mats, ess_per_traj)
     if rank == 0:

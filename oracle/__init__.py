@@ -86,6 +86,7 @@ def lib():
         L.or_prep_ok.restype = C.c_int
         L.or_prep_ok.argtypes = [P]
         L.or_prep_scaling.argtypes = [P, P, P]
+        L.or_prep_set_max_steps.argtypes = [P, C.c_int]
         L.or_prep_mask.argtypes = [P, P]
         L.or_forced_run.restype = C.c_int
         L.or_forced_run.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P]
@@ -201,6 +202,11 @@ class Prepared:
         if getattr(self, "h", None):
             lib().or_prep_free(self.h)
             self.h = None
+
+    def set_max_steps(self, steps: int):
+        """Stop trajectories after `steps` steps (0 = run to the end): a prefix
+        replay for orders where whole trajectories are too slow here."""
+        lib().or_prep_set_max_steps(self.h, int(steps))
 
     @property
     def ok(self) -> bool:

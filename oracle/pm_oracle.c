@@ -101,14 +101,19 @@ int64_t or_uniform_below(uint64_t W, uint64_t seed, uint64_t traj, uint32_t matr
  * arithmetic.  Result written as (hi, lo) two's complement halves. */
 void or_ryser_int(int n, const int64_t* a, uint64_t* out_hi, uint64_t* out_lo)
 {
+    /* subsets S visited in Gray-code order: step k flips column j = ctz(k), so
+     * the row sums sum_{j in S} a_ij change by +-a_ij (O(n) per subset) */
     __int128 total = 0;
-    for (uint64_t S = 1; S < ((uint64_t)1 << n); ++S) {
+    int64_t rs[64] = {0};
+    uint64_t S = 0;
+    for (uint64_t k = 1; k < ((uint64_t)1 << n); ++k) {
+        const int j = __builtin_ctzll(k);
+        S ^= (uint64_t)1 << j;
+        const int64_t sign = (S >> j & 1u) ? 1 : -1;
         __int128 prod = 1;
-        for (int i = 0; i < n && prod != 0; ++i) {
-            __int128 rs = 0;
-            for (int j = 0; j < n; ++j)
-                if (S >> j & 1u) rs += a[(int64_t)i * n + j];
-            prod *= rs;
+        for (int i = 0; i < n; ++i) {
+            rs[i] += sign * a[(int64_t)i * n + j];
+            prod *= rs[i];
         }
         int bits = __builtin_popcountll(S);
         if ((n - bits) & 1) total -= prod; else total += prod;
@@ -167,6 +172,7 @@ typedef struct {
     double* r0;         /* outer scaling, float-valued in FP32 mode */
     double* c0;
     int ok;             /* initial DM found a perfect matching */
+    int max_steps;      /* > 0: stop every trajectory after this many steps (prefix replay) */
 } or_prep;
 
 static double rnd(int fp32, double x) { return fp32 ? (double)(float)x : x; }
@@ -511,6 +517,7 @@ void or_prep_free(or_prep* P)
 }
 
 int or_prep_ok(const or_prep* P) { return P->ok; }
+void or_prep_set_max_steps(or_prep* P, int max_steps) { P->max_steps = max_steps; }
 void or_prep_scaling(const or_prep* P, double* r, double* c)
 {
     memcpy(r, P->r0, (size_t)P->n * 8);
@@ -725,6 +732,7 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
     const double theta = rnd(fp32, s->theta);
 
     for (int t = 0; t < n; ++t) {
+        if (P->max_steps > 0 && t >= P->max_steps) break;  /* prefix replay for large n */
         /* vertex selection R_V */
         int v = -1;
         if (s->vertex_rule == VR_ROW_ORDER) {
@@ -757,10 +765,17 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
             for (int q = 0; q < nc; ++q) sum_v += T->deg[v_is_row ? n + T->cand_p[q] : T->cand_p[q]];
             for (int q = 0; q < nc && Ln->rec_n < Ln->rec_cap; ++q) {
                 const int l = v_is_row ? n + T->cand_p[q] : T->cand_p[q];
-                edge_features(T, t, v, l, T->cand_e[q], sum_v, Ln->rec_feat + Ln->rec_n * OR_NF);
+                float* f = Ln->rec_feat + Ln->rec_n * OR_NF;
+                edge_features(T, t, v, l, T->cand_e[q], sum_v, f);
                 const double sv_ = v_is_row ? T->r[v] : T->c[v - n];
                 const double sl_ = v_is_row ? T->c[T->cand_p[q]] : T->r[T->cand_p[q]];
-                Ln->rec_target[Ln->rec_n] = (float)log(sv_ * sl_);
+                const float tgt = (float)log(sv_ * sl_);
+                /* a pair is kept only if every value is finite (an SK scale can
+                 * run to 0 or infinity on a residual without total support) */
+                int finite = isfinite(tgt);
+                for (int z = 0; z < OR_NF; ++z) finite = finite && isfinite(f[z]);
+                if (!finite) continue;
+                Ln->rec_target[Ln->rec_n] = tgt;
                 Ln->rec_key[Ln->rec_n] = (traj << 28) | ((uint64_t)t << 14) | (uint64_t)q;
                 Ln->rec_n++;
             }

@@ -107,7 +107,7 @@ pm_status check_csr(pm_context* ctx, const pm_csr* c)
 {
     if (!c) return fail(ctx, PM_EINVAL, "csr is NULL");
     if (c->n < 1) return fail(ctx, PM_EINVAL, "n must be >= 1");
-    if (c->n > kSmemMaxN) return fail(ctx, PM_EUNSUPPORTED, "n above the supported maximum (16383)");
+    if (c->n > kMaxN) return fail(ctx, PM_EUNSUPPORTED, "n above the supported maximum (2^22)");
     if (c->nnz < 0 || c->nnz >= ((int64_t)1 << 31)) return fail(ctx, PM_EINVAL, "bad nnz");
     if (!c->row_ptr || (c->nnz > 0 && !c->col_idx)) return fail(ctx, PM_EINVAL, "NULL csr array");
     if (c->on_device != 0 && c->on_device != 1) return fail(ctx, PM_EINVAL, "bad on_device");
@@ -177,6 +177,17 @@ Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max, bool lear
             best_score = score;
             if (score >= 1000) break;
         }
+    }
+    if (best_score < 4) {  // large n: trajectory state in the group's global slot
+        Plan p{};
+        p.gstate = 1;
+        p.rc_smem = need_rc;
+        p.lists = full;
+        p.g = full ? 4 : 1;
+        p.groups = kCtaWarps / p.g;
+        p.state_bytes = kGroupMiscInts * 4 + (learned ? 32 * 16 * 2 : 0);
+        p.mat_bytes = 0;
+        if (p.groups * p.state_bytes <= avail) best = p;
     }
     return best;
 }
@@ -357,7 +368,6 @@ pm_status execute(pm_context* ctx, Run& R)
         const bool scales = R.s.sk != 0;
         const bool local = R.s.sk == 3;
         const bool dm = R.s.dm != 0;
-        const SlotLayout sl = slot_layout(n_max, (int)m_max, (int)rb, scales, local, dm);
         const int smem_max = traj_max_smem_bytes();
         if (smem_max <= 0) return fail(ctx, PM_ECUDA, "cannot query the shared-memory limit");
         std::vector<Plan> plans(count);
@@ -369,6 +379,11 @@ pm_status execute(pm_context* ctx, Run& R)
             smem_need = std::max(smem_need, kCtaMiscBytes + (R.model ? (model_infer_bytes() + 15) / 16 * 16 : 0) +
                                                 plans[k].mat_bytes + plans[k].groups * plans[k].state_bytes);
         }
+        size_t gstate_bytes = 0;
+        for (int k = 0; k < count; ++k)
+            if (plans[k].gstate)
+                gstate_bytes = std::max(gstate_bytes, global_state_bytes(R.mats[k].n, (int)rb, plans[k].lists != 0));
+        const SlotLayout sl = slot_layout(n_max, (int)m_max, (int)rb, scales, local, dm, gstate_bytes);
         // chunks: most expensive matrices first, a few trajectories per group
         std::vector<int> order(count);
         for (int k = 0; k < count; ++k) order[k] = k;
@@ -471,6 +486,7 @@ pm_status execute(pm_context* ctx, Run& R)
         }
     }
     if (*h_status & ST_BAD_INPUT) return fail(ctx, PM_EINVAL, "malformed CSR (device validation)");
+    if (*h_status & ST_CAPACITY) return fail(ctx, PM_EUNSUPPORTED, "a row or column holds more than 65534 entries");
     if (*h_status) return fail(ctx, PM_EDEVICE, "device status " + std::to_string(*h_status));
 
     if (R.trace) {

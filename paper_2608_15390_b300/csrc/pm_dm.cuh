@@ -41,35 +41,43 @@ __device__ bool dm_serial(int n, const int* rp, const Idx* ci, const int* cp, co
             if (mc[j] < 0 && live.edge(e, i, j)) { mr[i] = j; mc[j] = i; break; }
         }
     }
-    for (int s = 0; s < n; ++s) {
-        if (!live.row(s) || mr[s] >= 0) continue;
-        int top = 0;
-        stk[0] = s;
-        cur[s] = rp[s];
-        bool found = false;
-        while (top >= 0) {
-            const int x = stk[top];
-            if (cur[x] >= rp[x + 1]) { --top; continue; }
-            const int e = cur[x]++;
-            int j = ci[e];
-            if (vis[j] == s || !live.edge(e, x, j)) continue;
-            vis[j] = s;
-            if (mc[j] < 0) {
-                for (int q = top; q >= 0; --q) {
-                    const int row = stk[q];
-                    const int prev = mr[row];
-                    mr[row] = j;
-                    mc[j] = row;
-                    j = prev;
+    // Augmenting-path phases: within a phase the visited marks are shared by
+    // all searches, so a phase costs O(m); a phase that augments nothing
+    // proves the matching maximum (a failed search only marks columns from
+    // which no free column is reachable).
+    for (int phase = 0;; ++phase) {
+        bool augmented = false, unmatched = false;
+        for (int s = 0; s < n; ++s) {
+            if (!live.row(s) || mr[s] >= 0) continue;
+            unmatched = true;
+            int top = 0;
+            stk[0] = s;
+            cur[s] = rp[s];
+            while (top >= 0) {
+                const int x = stk[top];
+                if (cur[x] >= rp[x + 1]) { --top; continue; }
+                const int e = cur[x]++;
+                int j = ci[e];
+                if (vis[j] == phase || !live.edge(e, x, j)) continue;
+                vis[j] = phase;
+                if (mc[j] < 0) {
+                    for (int q = top; q >= 0; --q) {
+                        const int row = stk[q];
+                        const int prev = mr[row];
+                        mr[row] = j;
+                        mc[j] = row;
+                        j = prev;
+                    }
+                    augmented = true;
+                    break;
                 }
-                found = true;
-                break;
+                const int y = mc[j];
+                stk[++top] = y;
+                cur[y] = rp[y];
             }
-            const int y = mc[j];
-            stk[++top] = y;
-            cur[y] = rp[y];
         }
-        if (!found) return false;
+        if (!unmatched) break;
+        if (!augmented) return false;
     }
 
     // strongly connected components (Tarjan, explicit stacks)

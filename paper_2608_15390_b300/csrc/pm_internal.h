@@ -7,9 +7,11 @@
 namespace pm {
 
 constexpr int kWarp = 32;
-// degrees above this never occur in the shared-memory trajectory kernel
-// (n <= kSmemMaxN), so uint16 holds every live degree plus the inactive mark
-constexpr int kSmemMaxN = 16383;
+// largest order accepted; live degrees are uint16 (0xFFFF marks an inactive
+// vertex), so a matrix whose rows or columns hold more than kMaxDegree
+// entries is rejected as unsupported
+constexpr int kMaxN = 1 << 22;
+constexpr int kMaxDegree = 65534;
 constexpr int kMaxTreeLevels = 4;
 constexpr int kMaxRngAttempts = 256;
 
@@ -91,6 +93,7 @@ __host__ __device__ inline TreeGeom tree_geom(int n)
 
 // per-warp global scratch layout for one trajectory slot
 struct SlotLayout {
+    size_t state;         // global-state plans: degrees, tree, r, c, lists
     size_t r, c;          // Real[n_max] each
     size_t stamp;         // int[n_max]
     size_t tmp_id;        // int[n_max]
@@ -105,11 +108,15 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 inline int dm_ws_ints(int n) { return 19 * n + 8; }
 
-inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales, bool local, bool dm)
+inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists, bool learned);
+
+inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales, bool local, bool dm,
+                              size_t gstate_bytes)
 {
     SlotLayout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t p = o; o = align_up(o + bytes, 256); return p; };
+    L.state = gstate_bytes ? take(gstate_bytes) : 0;
     L.r = scales ? take((size_t)n_max * real_bytes) : 0;
     L.c = scales ? take((size_t)n_max * real_bytes) : 0;
     L.stamp = local ? take((size_t)n_max * 4) : 0;
@@ -131,9 +138,9 @@ inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales,
 // shared memory (rc_smem) or in the group's global slot.
 struct Plan {
     int g, groups, staged, rc_smem, lists;
+    int gstate;        // trajectory state in the group's global slot (large n)
     int state_bytes;   // shared bytes of one group
     int mat_bytes;     // shared bytes of the staged matrix (0 if not staged)
-    int pad;
 };
 
 // a run of trajectories first .. first + count - 1 (indices inside matrix k)
@@ -178,6 +185,16 @@ struct TrajParams {
     unsigned long long* rec_count;
     unsigned long long rec_cap;
 };
+
+// bytes of a trajectory state kept in a global slot (uint32 active lists)
+inline size_t global_state_bytes(int n, int real_bytes, bool lists)
+{
+    const TreeGeom G = tree_geom(n);
+    size_t b = align_up((size_t)((2 * n + 7) & ~7) * 2, 16) + align_up((size_t)G.total * 4, 16);
+    b += 2 * align_up((size_t)n * real_bytes, 16);
+    if (lists) b += 2 * align_up((size_t)n * 4, 16);
+    return b;
+}
 
 // shared-memory sizes used by the plan
 inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists, bool learned)

@@ -220,10 +220,14 @@ __global__ void __launch_bounds__(1024) prepare_kernel(DevMatrix* mats, const De
     const TreeGeom G = tree_geom(n);
     const int n2pad = (2 * n + 7) & ~7;
     for (int x = tid; x < n2pad; x += nt) {
-        uint16_t d = kInact;
-        if (x < n) d = (uint16_t)(M.rp[x + 1] - M.rp[x]);
-        else if (x < 2 * n) d = (uint16_t)(M.cp[x - n + 1] - M.cp[x - n]);
-        M.deg0[x] = d;
+        int d = kInact;
+        if (x < n) d = M.rp[x + 1] - M.rp[x];
+        else if (x < 2 * n) d = M.cp[x - n + 1] - M.cp[x - n];
+        if (x < 2 * n && d > kMaxDegree) {  // live degrees are uint16
+            atomicOr(status, ST_CAPACITY);
+            d = kMaxDegree;
+        }
+        M.deg0[x] = (uint16_t)d;
     }
     __syncthreads();
     for (int l = 1; l <= G.nlev; ++l) {

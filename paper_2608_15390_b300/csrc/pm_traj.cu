@@ -220,8 +220,9 @@ __device__ __forceinline__ Real row_sum(const MV<Idx>& V, const uint8_t* mask, c
 // Compact the vertices this warp owns (a contiguous id range) that an SK
 // iteration updates: active with at least one live edge.  Degrees do not
 // change during the iterations of a step, so the lists serve all of them.
-__device__ __forceinline__ int compact_owned(const uint16_t* deg, int first, int last, int base_id,
-                                             uint16_t* out, int lane)
+template <typename ListT>
+__device__ __forceinline__ int compact_owned(const uint16_t* deg, int first, int last, int base_id, ListT* out,
+                                             int lane)
 {
     int cnt = 0;
     for (int x0 = first; x0 < last; x0 += 32) {
@@ -232,7 +233,7 @@ __device__ __forceinline__ int compact_owned(const uint16_t* deg, int first, int
             keep = d != kInact && d != 0;
         }
         const unsigned km = __ballot_sync(kFull, keep);
-        if (keep) out[cnt + __popc(km & ((1u << lane) - 1u))] = (uint16_t)x;
+        if (keep) out[cnt + __popc(km & ((1u << lane) - 1u))] = (ListT)x;
         cnt += __popc(km);
     }
     return cnt;
@@ -240,9 +241,9 @@ __device__ __forceinline__ int compact_owned(const uint16_t* deg, int first, int
 
 // one full SK iteration on the residual by the whole group (Sec. 3.3):
 // columns from r, then rows from the new c, each warp over its own list
-template <typename Real, typename Idx>
-__device__ void sk_iteration(const MV<Idx>& V, const uint8_t* mask, Real* r, Real* c, const uint16_t* lc,
-                             int nc, const uint16_t* lr, int nr, const Grp& G)
+template <typename Real, typename Idx, typename ListT>
+__device__ void sk_iteration(const MV<Idx>& V, const uint8_t* mask, Real* r, Real* c, const ListT* lc, int nc,
+                             const ListT* lr, int nr, const Grp& G)
 {
     for (int q = G.lane; q < nc; q += 32) {
         const int j = lc[q];
@@ -357,9 +358,9 @@ __device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* 
 enum { M_DEAD = 0, M_NIT = 1, M_DM = 2, M_CNTR = 3, M_CNTC = 4, M_STRIDE = 8, M_TMP = 16, M_TRAJ = 17, M_DMOK = 18 };
 
 // MODE: 0 scaled proposal, 1 learned proposal, 2 recording of (features, SK target) pairs
-template <typename Real, typename Idx, bool TRACE, int MODE>
+template <typename Real, typename Idx, bool TRACE, int MODE, typename ListT>
 __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>& V, int k, uint64_t gq,
-                          uint64_t local, uint16_t* deg, uint32_t* tree, Real* r_sm, uint16_t* lists, uint16_t* feat,
+                          uint64_t local, uint16_t* deg, uint32_t* tree, Real* r_sm, ListT* lists, uint16_t* feat,
                           const DevModel* Ms, uint8_t* slot, const Grp& G)
 {
     constexpr bool model = MODE == 1;
@@ -512,18 +513,29 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     const int li = live_base + __popc(lmk & ((1u << lane) - 1u));
                     if (TRACE && model && live && li < 32) P.trace_logits[(gq * n + t) * 32 + li] = lg;
                     if (rec) {
-                        unsigned long long base0 = 0;
-                        if (lane == 0 && lmk) base0 = atomicAdd(P.rec_count, (unsigned long long)__popc(lmk));
-                        base0 = __shfl_sync(kFull, base0, 0);
-                        const unsigned long long pos = base0 + __popc(lmk & ((1u << lane) - 1u));
-                        if (live && pos < P.rec_cap) {
-                            float f[8];
+                        // a pair is kept only if every value is finite (an SK
+                        // scale can run to 0 or infinity without total support)
+                        float f[8];
+                        float tgt = 0.f;
+                        bool keep = false;
+                        if (live) {
                             cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) P.rec_feat[pos * 8 + q] = f[q];
                             const double sv_cur = vrow ? (double)r[vi] : (double)c[vi];
                             const double sl_cur = vrow ? (double)c[pp] : (double)r[pp];
-                            P.rec_target[pos] = (float)log(sv_cur * sl_cur);
+                            tgt = (float)log(sv_cur * sl_cur);
+                            keep = isfinite(tgt);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) keep = keep && isfinite(f[q]);
+                        }
+                        const unsigned km2 = __ballot_sync(kFull, keep);
+                        unsigned long long base0 = 0;
+                        if (lane == 0 && km2) base0 = atomicAdd(P.rec_count, (unsigned long long)__popc(km2));
+                        base0 = __shfl_sync(kFull, base0, 0);
+                        const unsigned long long pos = base0 + __popc(km2 & ((1u << lane) - 1u));
+                        if (keep && pos < P.rec_cap) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) P.rec_feat[pos * 8 + q] = f[q];
+                            P.rec_target[pos] = tgt;
                             P.rec_key[pos] = (traj << 28) | ((unsigned long long)t << 14) | (unsigned long long)li;
                         }
                     }
@@ -792,7 +804,8 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
             const int nc = compact_owned(deg, lo, hi, n, lists + lo, lane);
             const int nr = compact_owned(deg, lo, hi, 0, lists + n + lo, lane);
             __syncwarp();
-            for (int q = 0; q < nit; ++q) sk_iteration<Real, Idx>(V, mask, r, c, lists + lo, nc, lists + n + lo, nr, G);
+            for (int q = 0; q < nit; ++q)
+                sk_iteration<Real, Idx, ListT>(V, mask, r, c, lists + lo, nc, lists + n + lo, nr, G);
             if (leader) {
                 n_full += nit;
                 alg_bytes += (uint64_t)16 * (uint64_t)m_live * (uint64_t)nit;
@@ -836,8 +849,11 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
     G.wig = G.tid >> 5;
     G.lane = lane;
     G.bar = 1 + gidx;
-    uint8_t* base = gstate + (size_t)gidx * pl.state_bytes;
+    uint8_t* sbase = gstate + (size_t)gidx * pl.state_bytes;
+    uint8_t* slot = P.slots + ((size_t)blockIdx.x * kCtaWarps + gidx) * P.slot.bytes;
     const TreeGeom T = tree_geom(n);
+    // trajectory state: in shared memory, or (large n) in the group's slot
+    uint8_t* base = pl.gstate ? slot + P.slot.state : sbase;
     uint16_t* deg = reinterpret_cast<uint16_t*>(base);
     size_t off = a16((size_t)((2 * n + 7) & ~7) * 2);
     uint32_t* tree = reinterpret_cast<uint32_t*>(base + off);
@@ -847,18 +863,18 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         r_sm = reinterpret_cast<Real*>(base + off);
         off += 2 * a16((size_t)n * sizeof(Real));
     }
-    uint16_t* lists = nullptr;  // [0, n): columns, [n, 2n): rows
+    uint8_t* lists = nullptr;  // [0, n): columns, [n, 2n): rows
     if (pl.lists) {
-        lists = reinterpret_cast<uint16_t*>(base + off);
-        off += 2 * a16((size_t)n * 2);
+        lists = base + off;
+        off += 2 * a16((size_t)n * (pl.gstate ? 4 : 2));
     }
-    uint16_t* feat = nullptr;   // [32][16] bf16 feature tile of the learned proposal
+    if (pl.gstate) off = 0;    // feature tile and control words stay in shared memory
+    uint16_t* feat = nullptr;  // [32][16] bf16 feature tile of the learned proposal
     if (Ms) {
-        feat = reinterpret_cast<uint16_t*>(base + off);
+        feat = reinterpret_cast<uint16_t*>(sbase + off);
         off += 32 * 16 * 2;
     }
-    G.misc = reinterpret_cast<int*>(base + off);
-    uint8_t* slot = P.slots + ((size_t)blockIdx.x * kCtaWarps + gidx) * P.slot.bytes;
+    G.misc = reinterpret_cast<int*>(sbase + off);
     for (;;) {
         if (G.wig == 0 && lane == 0) G.misc[M_TRAJ] = atomicAdd(ctr_traj, 1);
         gsync(G);
@@ -866,8 +882,12 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         gsync(G);
         if (q >= (int)ch.count) break;
         const uint64_t local = ch.first + (uint64_t)q;
-        run_group<Real, Idx, TRACE, MODE>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm, lists, feat, Ms, slot,
-                                          G);
+        if (pl.gstate)
+            run_group<Real, Idx, TRACE, MODE, uint32_t>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm,
+                                                        reinterpret_cast<uint32_t*>(lists), feat, Ms, slot, G);
+        else
+            run_group<Real, Idx, TRACE, MODE, uint16_t>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm,
+                                                        reinterpret_cast<uint16_t*>(lists), feat, Ms, slot, G);
     }
 }
 

@@ -144,17 +144,22 @@ def powerlaw_planted(n: int, seed: int, exponent: float = 2.5, dmin: int = 2) ->
     return csr_from_coo(n, np.concatenate(rows), np.concatenate(cols))
 
 
-def block_diagonal(n: int, p: float, seed: int, weighted: bool = False) -> Csr:
+def block_diagonal(n: int, p: float, seed: int, weighted: bool = False, orders=(20, 25)) -> Csr:
     """Known-permanent family of Sec. 4: dense diagonal blocks of order 20 or
     25 summing to n, every off-diagonal block entry deleted with probability
     p, the diagonal kept, weights U[1, 1.5] when ``weighted``; rows and
     columns are then permuted independently.  ``blocks`` holds the blocks."""
     rng = np.random.default_rng(seed)
-    comps = [(a, (n - 25 * a) // 20) for a in range(n // 25 + 1)
-             if (n - 25 * a) >= 0 and (n - 25 * a) % 20 == 0]
-    if not comps:
-        raise ValueError(f"n={n} is not a sum of 20s and 25s")
-    a, b = comps[rng.integers(len(comps))]
+    if tuple(orders) == (20,):
+        if n % 20:
+            raise ValueError(f"n={n} is not a sum of 20s")
+        a, b = 0, n // 20
+    else:
+        comps = [(a, (n - 25 * a) // 20) for a in range(n // 25 + 1)
+                 if (n - 25 * a) >= 0 and (n - 25 * a) % 20 == 0]
+        if not comps:
+            raise ValueError(f"n={n} is not a sum of 20s and 25s")
+        a, b = comps[rng.integers(len(comps))]
     orders = rng.permutation([25] * a + [20] * b)
     blocks, rows, cols, vals = [], [], [], []
     base = 0

@@ -1,0 +1,54 @@
+"""Large orders: trajectory state in global memory (n above what shared
+memory holds), against the oracle (whole trajectories at n = 20000; the first
+steps of every trajectory at the n = 100000 band + random configuration) and
+against an exactly known permanent (block-diagonal family of Sec. 4)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2608_15390_b300 import inputs as G
+from tests._gpu_common import compare_trace, ctx, binding, to_gpu_sched, logx_close
+
+pytestmark = pytest.mark.gpu
+
+
+def test_global_state_whole_trajectories_n20000():
+    m = G.er_planted(20000, 3.0, seed=5)
+    compare_trace(m, O.Schedule(initial_dm=1, K0=20, precision=O.PREC_FP32), count=16, seed=3)
+
+
+def _prefix_compare(m, sched, count, steps, seed=1):
+    g = ctx().trace(m, count, seed, to_gpu_sched(sched))
+    P = O.Prepared(m, sched)
+    P.set_max_steps(steps)
+    o = P.run(seed=seed, count=count, threads=8, trace=True)
+    assert np.array_equal(g["chosen"][:, :steps], o["chosen"][:, :steps])
+    assert np.array_equal(g["deg_v"][:, :steps], o["deg_v"][:, :steps])
+    return g
+
+
+@pytest.mark.parametrize("sk", [O.SK_LOCAL, O.SK_ADAPTIVE])
+def test_global_state_prefixes_n20000(sk):
+    m = G.er_planted(20000, 4.0, seed=6)
+    _prefix_compare(m, O.Schedule(initial_dm=1, K0=20, K=4, sk=sk, precision=O.PREC_FP32), count=8, steps=400)
+
+
+def test_band_random_n100000_prefixes():
+    # the large sparse configuration: n = 100000, nnz = 500000 from a |i-j| <= 1
+    # band, a planted permutation and uniform off-band entries; Local SK
+    m = G.band_random(100000, 500000, seed=3)
+    sched = O.Schedule(initial_dm=1, K0=100, sk=O.SK_LOCAL, precision=O.PREC_FP32)
+    g = _prefix_compare(m, sched, count=4, steps=1500)
+    assert np.all(g["chosen"][:, 1500:2000] >= 0) or np.any(g["dead_step"] >= 0)
+
+
+def test_block_diagonal_known_permanent_n5000():
+    m = G.block_diagonal(5000, 0.5, seed=9, orders=(20,))
+    log_per = sum(math.log(O.ryser(b)) for b in m.blocks)
+    B = binding()
+    s = B.Schedule(initial_dm=1, K0=100, sk=B.SK_LOCAL, precision=B.PREC_FP32_PROPOSAL)
+    r = ctx().estimate_permanent(m, 4096, 4, s)
+    assert r["p_match"] > 0
+    assert abs(r["log_estimate"] - log_per) < 5 * r["rse"] + 0.05, (r["log_estimate"], log_per, r["rse"])

@@ -432,3 +432,14 @@ def test_sk_proxy_tracks_minor_ratios():
         xs.append(O.ryser(minor) / per)
         ys.append(r[i] * c[j])
     assert np.corrcoef(xs, ys)[0, 1] > 0.9
+
+
+def test_prefix_replay_matches_full_run():
+    A = G.er_planted(200, 4.0, seed=77)
+    P = O.Prepared(A, O.Schedule(K0=10, precision=O.PREC_FP32))
+    full = P.run(seed=2, count=16, trace=True)
+    P.set_max_steps(50)
+    pre = P.run(seed=2, count=16, trace=True)
+    alive = full["dead_step"] < 0
+    assert np.array_equal(pre["chosen"][:, :50], full["chosen"][:, :50])
+    assert np.all(pre["chosen"][alive, 50:] == -1)
