@@ -1,16 +1,19 @@
 #!/usr/bin/env python3
 """Benchmark of the batched sparse-permanent estimator on one B300.
 
-Workload (one step): 64 Erdos-Renyi bipartite matrices with a planted
-permutation, n ~ U{100..2000}, average degree ~ U[4, 8] (generator seed 2),
-estimated together in one persistent launch with the schedule "two-sided
-minimum degree + initial DM + SK(K0=100, K=10) Adaptive, no inner DM", FP32
-proposal / FP64 log-weights.  Each step runs a fresh, disjoint slice of
-trajectory ids (T per matrix), the whole hot path: preprocessing (CSC build,
-initial DM, outer SK), trajectories, statistics.
+Workload: 64 Erdos-Renyi bipartite matrices with a planted permutation,
+n ~ U{100..2000}, average degree ~ U[4, 8] (generator seed 2), estimated
+together in one persistent launch.  A step is one call over the whole batch
+with a fresh, disjoint slice of trajectory ids (T per matrix): preprocessing
+(CSC build, initial DM, outer SK), trajectories, statistics.
 
-metric: effective samples per second, sum over matrices of
-(sum X)^2 / sum X^2 per step, divided by the device time of the steps.
+value: effective samples per second of the learned proposal run batched
+(the metric's "learned+batched"), i.e. the sum over matrices of
+(sum X)^2 / sum X^2 per step over the device time of the steps.  The network
+is trained before the timed region (time reported) on pairs recorded from an
+SK-scheduled run on 16 training matrices of the same family (seed 7).  The
+line also reports the plain estimator run one matrix per launch (the metric's
+"plain"), the SK(100,10)-Adaptive schedule run batched, and their ratios.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -41,8 +44,8 @@ METRIC = "effective samples/s at fixed rel. error, learned+batched vs plain, 1 B
 UNIT = "effective samples/s"
 N_MATS, N_LO, N_HI, D_LO, D_HI, GEN_SEED = 64, 100, 2000, 4.0, 8.0, 2
 WORKLOAD = ("64 ER+planted-permutation matrices, n~U{100..2000}, avg degree~U[4,8] "
-            "(generator seed 2); two-sided MD, initial DM, SK(K0=100,K=10) Adaptive, no inner DM; "
-            "FP32 proposal, FP64 log-weights; one persistent launch per step")
+            "(generator seed 2); learned proposal (8-64-64-1 BF16 network) with two-sided MD, "
+            "initial DM, outer SK(100), FP32 proposal, FP64 log-weights; one persistent launch per step")
 
 
 def parse():
@@ -64,8 +67,19 @@ def parse():
 
 
 def schedule_fields():
-    # vertex_rule, initial_dm, K0, K, sk (ADAPTIVE=2), dm (NONE=0), precision (FP32=0), theta
+    """The SK-scheduled estimator of the batched workload: two-sided MD, initial
+    DM, SK(K0=100, K=10) Adaptive, no inner DM, FP32 proposal."""
     return dict(vertex_rule=0, initial_dm=1, K0=100, K=10, sk=2, dm=0, precision=0, theta=0.33)
+
+
+TEACHER = dict(vertex_rule=0, initial_dm=1, K0=100, K=10, sk=1, dm=0, precision=0, theta=0.33)
+LEARNED = dict(vertex_rule=0, initial_dm=1, K0=100, K=0, sk=0, dm=0, precision=0, theta=0.33)
+TRAIN_SEED, N_TRAIN = 7, 16
+
+
+def training_matrices():
+    return [G.er_planted(m.n, 6.0, seed=7_000 + k)
+            for k, m in enumerate(G.batch_er(N_TRAIN, N_LO, N_HI, D_LO, D_HI, seed=TRAIN_SEED))]
 
 
 def dist_env():
@@ -152,98 +166,131 @@ def ncu_traffic_per_byte():
     return d.get("dram_bytes_per_alg_byte")
 
 
-def cpu_baseline(mats, T_gpu_ess_per_traj, seconds_budget=20.0):
-    """The oracle as it stands, on the host cores, on a bounded sample of the
-    same workload: one trajectory of every 4th matrix, repeated until about
-    `seconds_budget` of CPU work; reported as effective samples/s through the
-    GPU run's effective samples per trajectory."""
+def bf16_params(p):
+    a = np.asarray(p, dtype=np.float32).copy()
+    u = a.view(np.uint32)
+    w = ((u.astype(np.uint64) + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    out = a.astype(np.float64)
+    for lo, hi in ((0, 512), (576, 4672), (4736, 4800)):  # weights are BF16 on the device
+        out[lo:hi] = w[lo:hi].view(np.float32)
+    return out
+
+
+def cpu_baseline(mats, params, gpu_ess_per_traj, seconds_budget=20.0):
+    """The oracle as it stands (the learned proposal computed on the CPU with
+    the same network), on the host cores, on a bounded sample of the same
+    workload: every 4th matrix, one trajectory per host thread per round,
+    until about `seconds_budget` of CPU work; reported as effective samples/s
+    through the GPU run's effective samples per trajectory (same estimator)."""
     import oracle as O
-    sched = O.Schedule(**{k: v for k, v in schedule_fields().items()})
+    sched = O.Schedule(**LEARNED)
     threads = os.cpu_count() or 1
     sample = mats[::4]
+    preps = [O.Prepared(m, sched) for m in sample]
     t0 = time.perf_counter()
-    done = 0
-    rounds = 0
+    done = rounds = 0
     while True:
-        for k, m in enumerate(sample):
-            P = O.Prepared(m, sched)
-            P.run(seed=99, count=threads, first_traj=rounds * threads, matrix=4 * k, threads=threads)
+        for k, P in enumerate(preps):
+            P.run_model(seed=99, count=threads, params=params, first_traj=rounds * threads, matrix=4 * k,
+                        threads=threads)
             done += threads
         rounds += 1
         if time.perf_counter() - t0 > seconds_budget:
             break
     dt = time.perf_counter() - t0
     tps = done / dt
-    return {"value": tps * T_gpu_ess_per_traj, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{done} trajectories ({threads} per matrix per round, {rounds} rounds) on "
-                      f"matrices 0,4,...,60 of the workload incl. preprocessing, {dt:.1f} s; "
-                      f"{tps:.3f} traj/s x the GPU run's effective samples per trajectory"}
+    return {"value": tps * gpu_ess_per_traj, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{done} learned-proposal trajectories ({threads} per matrix per round, {rounds} "
+                      f"rounds) on matrices 0,4,...,60 of the workload, {dt:.1f} s, preprocessing "
+                      f"excluded; {tps:.2f} traj/s x the GPU run's effective samples per trajectory"}
 
 
-def compare_learned_vs_plain(ctx, B, dev, args, T):
-    """The metric's comparison on the same 64 matrices and trajectory counts:
-    the learned proposal (network trained here, untimed, on pairs recorded
-    from an SK-scheduled run on 16 training matrices of the same family,
-    generator seed 7) run batched in one launch, against the plain estimator
-    (outer SK only, no inner scaling) run one matrix per launch.  Device time
-    from CUDA events on the launching stream, effective samples summed."""
+def timed(ctx, stream, fn):
     import torch
-    stream = torch.cuda.current_stream()
-    train = [G.er_planted(m.n, 6.0, seed=7_000 + k) for k, m in
-             enumerate(G.batch_er(16, N_LO, N_HI, D_LO, D_HI, seed=7))]
-    teacher = B.Schedule(initial_dm=1, K0=100, K=10, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
-    model = ctx.model(seed=11)
-    t0 = time.perf_counter()
-    rep = model.train(train, teacher, n_pairs=2_000_000, epochs=4, batch=8192, lr=2e-3, seed=12)
-    t_train = time.perf_counter() - t0
-    learned = B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL, learned=model)
-    plain = B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL)
-    nt = [T] * len(dev)
-    ctx.estimate_batch_ex(dev, nt, args.seed, learned, first_traj=1 << 40)  # warm-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    res, _ = ctx.estimate_batch_ex(dev, nt, args.seed, learned, first_traj=(1 << 40) + T)
+    out = fn()
     e1.record(stream)
     torch.cuda.synchronize()
-    t_l = e0.elapsed_time(e1) / 1e3
-    ess_l = sum(r["ess"] for r in res)
-    e0.record(stream)
-    ess_p = 0.0
-    for k, m in enumerate(dev):
-        r, _ = ctx.estimate_batch_ex([m], [T], args.seed, plain, first_traj=(1 << 41) + k * T)
-        ess_p += r[0]["ess"]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_p = e0.elapsed_time(e1) / 1e3
-    model.close()
-    return {"learned_batched_ess_per_s": ess_l / t_l, "plain_unbatched_ess_per_s": ess_p / t_p,
-            "ratio": (ess_l / t_l) / (ess_p / t_p),
-            "learned_traj_per_s": len(dev) * T / t_l, "plain_traj_per_s": len(dev) * T / t_p,
-            "train": {"pairs": rep["n_pairs"], "loss_first": rep["loss_first"], "loss_last": rep["loss_last"],
-                      "seconds": t_train}}
+    return out, e0.elapsed_time(e1) / 1e3
+
+
+def compare_arms(ctx, B, dev, args, T):
+    """The metric's "plain" (outer SK only, one matrix per launch) and the
+    SK(100,10)-Adaptive schedule run batched, on the same matrices and T."""
+    import torch
+    stream = torch.cuda.current_stream()
+    plain = B.Schedule(**LEARNED)
+    adaptive = B.Schedule(**schedule_fields())
+
+    def run_plain():
+        ess = 0.0
+        for k, m in enumerate(dev):
+            r, _ = ctx.estimate_batch_ex([m], [T], args.seed, plain, first_traj=(1 << 41) + k * T)
+            ess += r[0]["ess"]
+        return ess
+
+    ess_p, t_p = timed(ctx, stream, run_plain)
+    nt = [T] * len(dev)
+    res, t_a = timed(ctx, stream, lambda: ctx.estimate_batch_ex(dev, nt, args.seed, adaptive,
+                                                                 first_traj=1 << 42)[0])
+    ess_a = sum(r["ess"] for r in res)
+    return {"plain_unbatched_ess_per_s": ess_p / t_p, "plain_unbatched_traj_per_s": len(dev) * T / t_p,
+            "adaptive_sk_batched_ess_per_s": ess_a / t_a, "adaptive_sk_batched_traj_per_s": len(dev) * T / t_a}
+
+
+def oracle_train(seed=5, pairs=40000, steps=300, batch=512, lr=2e-3):
+    """The network trained by the oracle alone: pairs recorded by the oracle
+    from the SK-scheduled teacher on 4 training matrices, Adam on the FP64
+    gradient of the mean squared error."""
+    import oracle as O
+    mats = training_matrices()[:4]
+    feats, targs = [], []
+    for k, m in enumerate(mats):
+        f, t, _ = O.Prepared(m, O.Schedule(**TEACHER)).record(seed=seed, count=2, cap=pairs // 4, matrix=k)
+        feats.append(f)
+        targs.append(t)
+    X = np.concatenate(feats).astype(np.float64)
+    Y = np.concatenate(targs).astype(np.float64)
+    rng = np.random.default_rng(seed)
+    p = np.zeros(O.N_PARAM)
+    p[:512] = rng.normal(size=512) * np.sqrt(2 / 8)
+    p[576:4672] = rng.normal(size=4096) * np.sqrt(2 / 64)
+    p[4736:4800] = rng.normal(size=64) * np.sqrt(1 / 64)
+    p[4800] = Y.mean()
+    m1 = np.zeros_like(p)
+    m2 = np.zeros_like(p)
+    for it in range(1, steps + 1):
+        idx = rng.integers(0, len(Y), size=batch)
+        _, g = O.mlp_grad(p, X[idx], Y[idx])
+        m1 = 0.9 * m1 + 0.1 * g
+        m2 = 0.999 * m2 + 0.001 * g * g
+        p -= lr * (m1 / (1 - 0.9 ** it)) / (np.sqrt(m2 / (1 - 0.999 ** it)) + 1e-8)
+    return bf16_params(p.astype(np.float32))
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle, timed as it stands on the host cores."""
+    """Reference arm: the CPU oracle as it stands on the host cores, running the
+    learned proposal (network trained by the oracle itself, untimed) on a
+    bounded sample of the workload."""
     if rank != 0:
         return
     import oracle as O
     mats = G.batch_er(N_MATS, N_LO, N_HI, D_LO, D_HI, seed=GEN_SEED)
-    sched = O.Schedule(**schedule_fields())
+    t0 = time.perf_counter()
+    params = oracle_train()
+    t_train = time.perf_counter() - t0
+    sched = O.Schedule(**LEARNED)
     threads = os.cpu_count() or 1
-    per_step = mats[::8]  # bounded sample: 8 matrices x `threads` trajectories per step
+    per_step = [O.Prepared(m, sched) for m in mats[::8]]  # 8 matrices x `threads` trajectories per step
 
     def step(i):
         ess = 0.0
-        ntraj = 0
-        for k, m in enumerate(per_step):
-            P = O.Prepared(m, sched)
-            r = P.run(seed=args.seed, count=threads, first_traj=i * threads, matrix=8 * k,
-                      threads=threads)
-            st = O.stats(r["log_x"])
-            ess += st["ess"]
-            ntraj += threads
-        return ess, ntraj
+        for k, P in enumerate(per_step):
+            r = P.run_model(seed=args.seed, count=4 * threads, params=params, first_traj=i * 4 * threads, matrix=8 * k,
+                            threads=threads)
+            ess += O.stats(r["log_x"])["ess"]
+        return ess, 4 * threads * len(per_step)
 
     for i in range(args.warmup):
         step(i)
@@ -261,9 +308,10 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": "8 of the 64 matrices (every 8th), "
-                       f"{threads} trajectories each per step"},
+                       f"{4 * threads} trajectories each per step, preprocessing excluded",
+                       "network": f"trained by the oracle ({t_train:.1f} s, untimed)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{tot_traj} trajectories over {args.steps} steps"},
+                             "sample": f"{tot_traj} learned-proposal trajectories over {args.steps} steps"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "traj_per_s": tot_traj / dt}
     print(json.dumps(line), flush=True)
@@ -290,7 +338,12 @@ def main():
               for m in mats]
     stream = torch.cuda.current_stream()
     ctx = B.Context(local, stream.cuda_stream)
-    sched = B.Schedule(**schedule_fields())
+    model = ctx.model(seed=11)
+    t0 = time.perf_counter()
+    train_rep = model.train(training_matrices(), B.Schedule(**TEACHER), n_pairs=2_000_000, epochs=4,
+                            batch=8192, lr=2e-3, seed=12)
+    t_train = time.perf_counter() - t0
+    sched = B.Schedule(**LEARNED, learned=model)
     T = args.traj
     nt = [T] * len(mats)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -310,6 +363,7 @@ def main():
     tot_ess = 0.0
     tot_traj = 0
     alg_bytes = 0
+    mlp_rows = 0
     kern_ms = 0.0
     prep_ms = 0.0
     rse = []
@@ -330,6 +384,7 @@ def main():
             tot_ess += r["ess"]
             tot_traj += r["n_traj"]
             alg_bytes += r["alg_bytes"]
+            mlp_rows += r["mlp_rows"]
             rse.append(r["rse"])
     torch.cuda.synchronize()
     if dist:
@@ -358,15 +413,22 @@ def main():
 
     value = tot_ess / t_dev
     ess_per_traj = tot_ess / max(1, tot_traj)
-    peaks = measured_peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6400.0
-    achieved = (alg_bytes / args.steps) / (kern_ms / args.steps / 1e3) / 1e9
-    tpb = ncu_traffic_per_byte()
-    traffic = None if tpb is None else tpb * alg_bytes / args.steps
     if args.mats != N_MATS or args.nmax != N_HI:
         line_cfg_note = f"reduced case: first {args.mats} matrices, n<={args.nmax} (not a bench value)"
     else:
         line_cfg_note = None
+    peaks = measured_peaks()
+    # roofline of the dominant kernel (the trajectory kernel with the learned
+    # proposal): its dense work is the network on BF16 tensor cores, 9344
+    # multiply-add flops per live candidate; the algorithmic-bytes figure
+    # against HBM is reported beside it
+    tc_peak = peaks["bf16_tflops"] if peaks else 1800.0
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0
+    kern_s = kern_ms / args.steps / 1e3
+    achieved_tf = (mlp_rows / args.steps) * 9344.0 / kern_s / 1e12
+    achieved_gb = (alg_bytes / args.steps) / kern_s / 1e9
+    tpb = ncu_traffic_per_byte()
+    traffic = None if tpb is None else tpb * alg_bytes / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
@@ -377,9 +439,12 @@ def main():
         "traj_per_s": tot_traj / t_dev,
         "ess_per_traj": ess_per_traj,
         "median_rse_per_step": statistics.median(rse) if rse else None,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "traj_kernel<float>", "peak_source": "measured" if peaks else "fallback",
+        "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": tc_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / tc_peak, "traffic": traffic,
+                     "kernel": "traj_kernel<float, learned>",
+                     "peak_source": "measured bf16 burst" if peaks else "fallback",
+                     "flops": "9344 per live candidate evaluated by the network (useful rows only)",
+                     "alg_hbm_gbs": achieved_gb, "alg_hbm_frac": achieved_gb / hbm_peak,
                      "kernel_ms_per_step": kern_ms / args.steps,
                      "prep_ms_per_step": prep_ms / args.steps},
         "gpu_launches": launches * world,
@@ -387,10 +452,17 @@ def main():
         "e2e": {"value": e2e_ess / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
     }
+    line["train"] = {"pairs": train_rep["n_pairs"], "loss_first": train_rep["loss_first"],
+                     "loss_last": train_rep["loss_last"], "seconds": t_train,
+                     "where": "before the timed region"}
     if not args.no_compare:
-        line["compare"] = compare_learned_vs_plain(ctx, B, dev, args, T)
+        cmp = compare_arms(ctx, B, dev, args, T)
+        cmp["learned_batched_vs_plain_unbatched"] = value / cmp["plain_unbatched_ess_per_s"]
+        cmp["learned_batched_vs_adaptive_sk_batched"] = value / cmp["adaptive_sk_batched_ess_per_s"]
+        line["compare"] = cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(mats, ess_per_traj)
+        line["cpu_baseline"] = cpu_baseline(mats, bf16_params(model.params()), ess_per_traj)
+    model.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

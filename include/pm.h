@@ -111,6 +111,8 @@ typedef struct {
                               of each Local repair, 8 B per vertex at initialisation */
     double kernel_ms;      /* device time of the trajectory kernel of the call (CUDA events
                               on the context's stream; shared by all matrices of a batch) */
+    uint64_t mlp_rows;     /* learned proposal: network evaluations of live candidates
+                              (2 * (8*64 + 64*64 + 64) = 9344 multiply-add flops each) */
 } pm_result;
 
 /* Bookkeeping of the most recent estimate / trace call of a context. */

@@ -105,6 +105,8 @@ def lib():
         L.or_record.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int64, P, P, P]
         L.or_run_ext.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
                                  P, P, P, P, P, P]
+        L.or_run_model.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
+                                   P, P, P, P]
         _lib = L
     return _lib
 
@@ -256,6 +258,18 @@ class Prepared:
         lib().or_run_ext(self.h, seed, matrix, first_traj, count, threads, _ptr(lx), _ptr(ds),
                          _ptr(ch), _ptr(dv), _ptr(oc), _ptr(lg))
         return dict(log_x=lx, dead_step=ds, chosen=ch, deg_v=dv)
+
+    def run_model(self, seed: int, count: int, params, first_traj: int = 0, matrix: int = 0,
+                  threads: int = 1):
+        """Trajectories of the learned proposal with the given parameters (the
+        device's BF16 weights: pass them already rounded)."""
+        pm = np.ascontiguousarray(params, dtype=np.float64)
+        lx = np.zeros(count)
+        ds = np.zeros(count, dtype=np.int32)
+        oc = np.zeros(3, dtype=np.int64)
+        lib().or_run_model(self.h, seed, matrix, first_traj, count, threads, _ptr(lx), _ptr(ds),
+                           _ptr(oc), _ptr(pm))
+        return dict(log_x=lx, dead_step=ds)
 
     def record(self, seed: int, count: int, cap: int, first_traj: int = 0, matrix: int = 0):
         """(features[8], target, key) pairs along trajectories of this

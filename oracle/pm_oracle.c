@@ -543,6 +543,7 @@ typedef struct {
  * proposal): ext_logits[t * 32 + q] is the logit of the q-th live candidate
  * at step t; record_* collect (features, target) pairs of the SK estimator. */
 typedef struct {
+    const double* model;       /* [4801] network parameters, or NULL */
     const float* ext_logits;   /* [n][32] or NULL */
     float* rec_feat;           /* [cap][8] or NULL */
     float* rec_target;         /* [cap] */
@@ -614,14 +615,17 @@ static void edge_features(const or_traj* T, int t, int v, int l_unified, int64_t
     f[7] = (float)log(entry(P, e));
 }
 
-/* MLP 8 -> 64 -> 64 -> 1 with GELU (erf form), parameters laid out as
- * W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3.  round_act rounds the
- * hidden activations to bfloat16 (round to nearest even) as tensor-core
- * inference does. */
-static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+/* MLP 8 -> 64 -> 64 -> 1 with GELU in its tanh form,
+ * g(x) = x/2 (1 + tanh(c (x + a x^3))), c = sqrt(2/pi), a = 0.044715;
+ * parameters laid out as W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3.
+ * round_act rounds the hidden activations to bfloat16 (round to nearest
+ * even) as tensor-core inference does. */
+static const double GELU_C = 0.79788456080286535588, GELU_A = 0.044715;
+static double gelu(double x) { return 0.5 * x * (1.0 + tanh(GELU_C * (x + GELU_A * x * x * x))); }
 static double gelu_d(double x)
 {
-    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * 3.14159265358979323846);
+    const double th = tanh(GELU_C * (x + GELU_A * x * x * x));
+    return 0.5 * (1.0 + th) + 0.5 * x * (1.0 - th * th) * GELU_C * (1.0 + 3.0 * GELU_A * x * x);
 }
 static double bf16_round(double x)
 {
@@ -783,9 +787,27 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
         if (Ln && Ln->ext_logits && nc > 32) {  /* replay supports up to 32 candidates */
             res->log_x = -INFINITY; res->dead_step = t; res->dead_reason = 4; return;
         }
+        float* lg_model = NULL;
+        if (Ln && Ln->model) {  /* logits of the network: BF16-rounded inputs and activations */
+            double sum_v = 0;
+            for (int q = 0; q < nc; ++q) sum_v += T->deg[v_is_row ? n + T->cand_p[q] : T->cand_p[q]];
+            lg_model = (float*)T->newc;  /* scratch of n doubles holds n floats */
+            for (int q = 0; q < nc; ++q) {
+                const int l = v_is_row ? n + T->cand_p[q] : T->cand_p[q];
+                float f[OR_NF];
+                double x[OR_NF], y;
+                edge_features(T, t, v, l, T->cand_e[q], sum_v, f);
+                for (int z = 0; z < OR_NF; ++z) x[z] = bf16_round((double)f[z]);
+                or_mlp_forward(Ln->model, x, 1, 1, &y);
+                lg_model[q] = (float)y;
+            }
+        }
         for (int q = 0; q < nc; ++q) {
             double sv;
-            if (Ln && Ln->ext_logits) {
+            if (lg_model) {
+                const float ex = or_exp_score(lg_model[q]);
+                sv = P->val ? (double)((float)entry(P, T->cand_e[q]) * ex) : (double)ex;
+            } else if (Ln && Ln->ext_logits) {
                 const float ex = or_exp_score(Ln->ext_logits[(int64_t)t * 32 + q]);
                 sv = P->val ? (double)((float)entry(P, T->cand_e[q]) * ex) : (double)ex;
             } else {
@@ -922,6 +944,7 @@ typedef struct {
     int32_t* chosen;  /* [count][n][2] or NULL */
     int32_t* degv;    /* [count][n] or NULL */
     const float* ext_logits;  /* [count][n][32] or NULL */
+    const double* model;      /* network parameters or NULL */
     int64_t counts[3];
 } or_job;
 
@@ -935,9 +958,11 @@ static void* job_main(void* arg)
         or_learn L;
         memset(&L, 0, sizeof(L));
         if (J->ext_logits) L.ext_logits = J->ext_logits + q * (int64_t)n * 32;
+        L.model = J->model;
         run_trajectory(T, J->seed, J->first + (uint64_t)q, J->matrix,
                        J->chosen ? J->chosen + q * 2 * n : NULL,
-                       J->degv ? J->degv + q * n : NULL, NULL, J->ext_logits ? &L : NULL, &res);
+                       J->degv ? J->degv + q * n : NULL, NULL,
+                       (J->ext_logits || J->model) ? &L : NULL, &res);
         J->log_x[q] = res.log_x;
         if (J->dead_step) J->dead_step[q] = res.dead_step;
         J->counts[0] += res.n_dm;
@@ -961,6 +986,12 @@ void or_run(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_tra
 
 /* or_run with the learned proposal's logits supplied per trajectory and step
  * (ext_logits[count][n][32], candidate q of step t in adjacency order). */
+void or_run_model(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
+                  int nthreads, double* log_x, int32_t* dead_step, int64_t* op_counts, const double* model);
+static const double* g_model_for_run = NULL;  /* set only inside or_run_model */
+
+/* or_run with the learned proposal's logits supplied per trajectory and step
+ * (ext_logits[count][n][32], candidate q of step t in adjacency order). */
 void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
                 int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
                 int64_t* op_counts, const float* ext_logits)
@@ -975,6 +1006,7 @@ void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first
         jobs[t].log_x = log_x; jobs[t].dead_step = dead_step; jobs[t].chosen = chosen;
         jobs[t].degv = degv;
         jobs[t].ext_logits = ext_logits;
+        jobs[t].model = g_model_for_run;
     }
     for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, job_main, &jobs[t]);
     job_main(&jobs[0]);
@@ -986,6 +1018,18 @@ void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first
     }
     free(jobs);
     free(th);
+}
+
+/* Trajectories of the learned proposal computed here: features, the FP64
+ * network (inputs and hidden activations rounded to bfloat16 as the tensor
+ * cores see them) and the binary32 score exponent.  Statistically the same
+ * estimator as the device's; not bit-identical (accumulation order). */
+void or_run_model(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
+                  int nthreads, double* log_x, int32_t* dead_step, int64_t* op_counts, const double* model)
+{
+    g_model_for_run = model;
+    or_run_ext(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, NULL, NULL, op_counts, NULL);
+    g_model_for_run = NULL;
 }
 
 /* (features, target) pairs of trajectories first..first+count-1 of the

@@ -67,7 +67,7 @@ class pm_result(C.Structure):
                 ("log_sum_x", C.c_double), ("log_sum_x2", C.c_double), ("n_traj", C.c_uint64),
                 ("n_alive", C.c_uint64), ("n_dm_calls", C.c_uint64), ("n_full_sk", C.c_uint64),
                 ("n_local_sk", C.c_uint64), ("seconds", C.c_double), ("alg_bytes", C.c_uint64),
-                ("kernel_ms", C.c_double)]
+                ("kernel_ms", C.c_double), ("mlp_rows", C.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

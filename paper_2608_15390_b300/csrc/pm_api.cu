@@ -185,7 +185,7 @@ Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max, bool lear
         p.lists = full;
         p.g = full ? 4 : 1;
         p.groups = kCtaWarps / p.g;
-        p.state_bytes = kGroupMiscInts * 4 + (learned ? 32 * 16 * 2 : 0);
+        p.state_bytes = kGroupMiscInts * 4 + (learned ? 32 * 24 * 2 : 0);
         p.mat_bytes = 0;
         if (p.groups * p.state_bytes <= avail) best = p;
     }
@@ -277,7 +277,7 @@ pm_status execute(pm_context* ctx, Run& R)
     const size_t o_inputs = L.take(sizeof(DevInput) * count);
     const size_t o_prefix = L.take(8 * (count + 1));
     const size_t o_logx = L.take(8 * std::max<uint64_t>(total, 1));
-    const size_t o_counters = L.take(8 * 4 * count);
+    const size_t o_counters = L.take(8 * 5 * count);
     const size_t o_work = L.take(8);
     const size_t o_status = L.take(4);
     uint64_t max_t = 1;
@@ -348,7 +348,7 @@ pm_status execute(pm_context* ctx, Run& R)
     PM_CUDA(cudaMemcpyAsync(P(o_inputs), hi.data(), sizeof(DevInput) * count, cudaMemcpyHostToDevice, ctx->stream));
     PM_CUDA(cudaMemcpyAsync(P(o_prefix), prefix.data(), 8 * (count + 1), cudaMemcpyHostToDevice, ctx->stream));
     h2d += sizeof(DevMatrix) * count + sizeof(DevInput) * count + 8 * (count + 1);
-    PM_CUDA(cudaMemsetAsync(P(o_counters), 0, 8 * 4 * count, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(P(o_counters), 0, 8 * 5 * count, ctx->stream));
     PM_CUDA(cudaMemsetAsync(P(o_work), 0, 8, ctx->stream));
     PM_CUDA(cudaMemsetAsync(P(o_status), 0, 4, ctx->stream));
     uint32_t* d_status = (uint32_t*)P(o_status);
@@ -383,7 +383,8 @@ pm_status execute(pm_context* ctx, Run& R)
         for (int k = 0; k < count; ++k)
             if (plans[k].gstate)
                 gstate_bytes = std::max(gstate_bytes, global_state_bytes(R.mats[k].n, (int)rb, plans[k].lists != 0));
-        const SlotLayout sl = slot_layout(n_max, (int)m_max, (int)rb, scales, local, dm, gstate_bytes);
+        const SlotLayout sl =
+            slot_layout(n_max, (int)m_max, (int)rb, scales, local, dm, gstate_bytes, R.model != nullptr);
         // chunks: most expensive matrices first, a few trajectories per group
         std::vector<int> order(count);
         for (int k = 0; k < count; ++k) order[k] = k;
@@ -460,22 +461,22 @@ pm_status execute(pm_context* ctx, Run& R)
     }
 
     // ---- read back ----
-    const size_t pin_need = sizeof(StatsOut) * count + 8 * 4 * count + 8 + sizeof(DevMatrix) * count + 64;
+    const size_t pin_need = sizeof(StatsOut) * count + 8 * 5 * count + 8 + sizeof(DevMatrix) * count + 64;
     st = grow_pinned(ctx, pin_need);
     if (st != PM_OK) return st;
     StatsOut* h_sout = (StatsOut*)ctx->pinned;
     unsigned long long* h_cnt = (unsigned long long*)(h_sout + count);
-    uint32_t* h_status = (uint32_t*)(h_cnt + 4 * count);
-    DevMatrix* h_mats = (DevMatrix*)(ctx->pinned + align_up(sizeof(StatsOut) * count + 8 * 4 * count + 8, 64));
+    uint32_t* h_status = (uint32_t*)(h_cnt + 5 * count);
+    DevMatrix* h_mats = (DevMatrix*)(ctx->pinned + align_up(sizeof(StatsOut) * count + 8 * 5 * count + 8, 64));
     if (!R.prep_only && total > 0) {
         PM_CUDA(cudaMemcpyAsync(h_sout, P(o_sout), sizeof(StatsOut) * count, cudaMemcpyDeviceToHost, ctx->stream));
-        PM_CUDA(cudaMemcpyAsync(h_cnt, P(o_counters), 8 * 4 * count, cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(cudaMemcpyAsync(h_cnt, P(o_counters), 8 * 5 * count, cudaMemcpyDeviceToHost, ctx->stream));
     }
     PM_CUDA(cudaMemcpyAsync(h_status, d_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaMemcpyAsync(h_mats, d_mats, sizeof(DevMatrix) * count, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
     d2h += 4 + sizeof(DevMatrix) * count;
-    if (!R.prep_only && total > 0) d2h += sizeof(StatsOut) * count + 8 * 4 * count;
+    if (!R.prep_only && total > 0) d2h += sizeof(StatsOut) * count + 8 * 5 * count;
     {
         float ms = 0;
         PM_CUDA(cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev0));
@@ -535,10 +536,11 @@ pm_status execute(pm_context* ctx, Run& R)
             o.log_sum_x2 = so.log_sum_x2;
             o.n_traj = so.n;
             o.n_alive = so.alive;
-            o.n_dm_calls = h_cnt[4 * k + 0];
-            o.n_full_sk = h_cnt[4 * k + 1];
-            o.n_local_sk = h_cnt[4 * k + 2];
-            o.alg_bytes = h_cnt[4 * k + 3];
+            o.n_dm_calls = h_cnt[5 * k + 0];
+            o.n_full_sk = h_cnt[5 * k + 1];
+            o.n_local_sk = h_cnt[5 * k + 2];
+            o.alg_bytes = h_cnt[5 * k + 3];
+            o.mlp_rows = h_cnt[5 * k + 4];
             o.kernel_ms = ctx->last_traj_ms;
             o.seconds = secs;
         }

@@ -2,22 +2,29 @@
 // (Sec. 2, "Support filtering with DM"): find a perfect matching M of the
 // active part; orient M's edges row -> column and the others column -> row; a
 // non-matching edge belongs to some perfect matching iff its two ends share a
-// strongly connected component.  Single-thread version over global scratch:
-// used once per matrix for the initial DM and by one lane per trajectory for
-// the inner DM.
+// strongly connected component.  One warp runs it (uniform control flow, ballots
+// over adjacency chunks), once per matrix for the initial DM and by the leader
+// warp of a trajectory for the inner DM.
 #pragma once
 #include "pm_device.cuh"
 
 namespace pm {
 
-// workspace (ints): mr[n] mc[n] vis[n] cur[n] stk[n+1] idx[2n] low[2n]
+// workspace (19 n + 3 ints): mr[n] mc[n] vis[n] cur[n] stk[n+1] idx[2n] low[2n]
 // comp[2n] it[2n] onst[2n] cstk[2n+1] sstk[2n+1]
-__host__ __device__ inline int dm_serial_ints(int n) { return 19 * n + 3; }
 
-// Live must provide: bool row(int i), bool col(int j), bool edge(int e, int i, int j)
+
+
+// Every lane follows the same (uniform) control flow and writes the same
+// values; each search step examines up to 32 adjacency entries at once with a
+// ballot and takes the first eligible entry in adjacency order.  Matching: a
+// greedy start, then augmenting-path phases whose searches share visited marks
+// (O(m) per phase); a phase that augments nothing proves the matching maximum
+// (a failed search only marks columns from which no free column is reachable).
+// Live must provide: bool row(int i), bool col(int j), bool edge(int e, int i, int j).
 template <class Live, typename Idx>
-__device__ bool dm_serial(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri,
-                          const int* ce, const Live& live, uint8_t* mask, int* ws)
+__device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri, const int* ce,
+                        const Live& live, uint8_t* mask, int* ws, int lane)
 {
     int* mr = ws;
     int* mc = mr + n;
@@ -32,19 +39,31 @@ __device__ bool dm_serial(int n, const int* rp, const Idx* ci, const int* cp, co
     int* cstk = onst + 2 * n;
     int* sstk = cstk + 2 * n + 1;
 
-    for (int i = 0; i < n; ++i) { mr[i] = -1; mc[i] = -1; vis[i] = -1; }
-    // cheap greedy start, then one augmenting-path search per free row
+    for (int i = lane; i < n; i += 32) { mr[i] = -1; mc[i] = -1; vis[i] = -1; }
+    __syncwarp();
+    // greedy start: each active row takes its first free live column
     for (int i = 0; i < n; ++i) {
         if (!live.row(i)) continue;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) {
-            const int j = ci[e];
-            if (mc[j] < 0 && live.edge(e, i, j)) { mr[i] = j; mc[j] = i; break; }
+        const int b = rp[i], en = rp[i + 1];
+        for (int base = b; base < en; base += 32) {
+            const int e = base + lane;
+            bool ok = false;
+            int j = 0;
+            if (e < en) {
+                j = ci[e];
+                ok = mc[j] < 0 && live.edge(e, i, j);
+            }
+            const unsigned bal = __ballot_sync(kFull, ok);
+            if (bal) {
+                const int jj = __shfl_sync(kFull, j, __ffs(bal) - 1);
+                mr[i] = jj;
+                mc[jj] = i;
+                __syncwarp();
+                break;
+            }
         }
     }
-    // Augmenting-path phases: within a phase the visited marks are shared by
-    // all searches, so a phase costs O(m); a phase that augments nothing
-    // proves the matching maximum (a failed search only marks columns from
-    // which no free column is reachable).
+    // augmenting-path phases with shared visited marks
     for (int phase = 0;; ++phase) {
         bool augmented = false, unmatched = false;
         for (int s = 0; s < n; ++s) {
@@ -53,36 +72,58 @@ __device__ bool dm_serial(int n, const int* rp, const Idx* ci, const int* cp, co
             int top = 0;
             stk[0] = s;
             cur[s] = rp[s];
+            __syncwarp();
             while (top >= 0) {
                 const int x = stk[top];
-                if (cur[x] >= rp[x + 1]) { --top; continue; }
-                const int e = cur[x]++;
-                int j = ci[e];
-                if (vis[j] == phase || !live.edge(e, x, j)) continue;
-                vis[j] = phase;
-                if (mc[j] < 0) {
+                const int en = rp[x + 1];
+                const int c0 = cur[x];
+                if (c0 >= en) { --top; continue; }
+                const int e = c0 + lane;
+                bool ok = false;
+                int j = 0;
+                if (e < en) {
+                    j = ci[e];
+                    ok = vis[j] != phase && live.edge(e, x, j);
+                }
+                const unsigned bal = __ballot_sync(kFull, ok);
+                if (!bal) {
+                    cur[x] = c0 + 32;
+                    __syncwarp();
+                    continue;
+                }
+                const int l = __ffs(bal) - 1;
+                int jj = __shfl_sync(kFull, j, l);
+                cur[x] = c0 + l + 1;
+                vis[jj] = phase;
+                __syncwarp();
+                if (mc[jj] < 0) {
                     for (int q = top; q >= 0; --q) {
                         const int row = stk[q];
                         const int prev = mr[row];
-                        mr[row] = j;
-                        mc[j] = row;
-                        j = prev;
+                        __syncwarp();
+                        mr[row] = jj;
+                        mc[jj] = row;
+                        __syncwarp();
+                        jj = prev;
                     }
                     augmented = true;
                     break;
                 }
-                const int y = mc[j];
+                const int y = mc[jj];
                 stk[++top] = y;
                 cur[y] = rp[y];
+                __syncwarp();
             }
         }
         if (!unmatched) break;
         if (!augmented) return false;
     }
 
-    // strongly connected components (Tarjan, explicit stacks)
+    // strongly connected components (Tarjan with explicit stacks); the next
+    // successor of a column is found by a ballot over its adjacency
     const int V = 2 * n;
-    for (int x = 0; x < V; ++x) { idx[x] = -1; onst[x] = 0; }
+    for (int x = lane; x < V; x += 32) { idx[x] = -1; onst[x] = 0; }
+    __syncwarp();
     int counter = 0, ncomp = 0, sp = 0;
     for (int s = 0; s < V; ++s) {
         const bool act = s < n ? live.row(s) : live.col(s - n);
@@ -93,21 +134,39 @@ __device__ bool dm_serial(int n, const int* rp, const Idx* ci, const int* cp, co
         idx[s] = low[s] = counter++;
         sstk[sp++] = s;
         onst[s] = 1;
+        __syncwarp();
         while (ctop >= 0) {
             const int x = cstk[ctop];
             int w = -1;
             if (x < n) {
-                if (it[x] < 0) { it[x] = 0; w = n + mr[x]; }
+                if (it[x] < 0) {
+                    it[x] = 0;
+                    w = n + mr[x];
+                }
             } else {
                 const int j = x - n;
                 int k = it[x] < 0 ? cp[j] : it[x] + 1;
-                for (; k < cp[j + 1]; ++k) {
-                    const int i = ri[k];
-                    if (mr[i] != j && live.edge(ce[k], i, j)) break;
+                const int en = cp[j + 1];
+                while (k < en) {
+                    const int kk = k + lane;
+                    bool ok = false;
+                    int i = 0;
+                    if (kk < en) {
+                        i = ri[kk];
+                        ok = mr[i] != j && live.edge(ce[kk], i, j);
+                    }
+                    const unsigned bal = __ballot_sync(kFull, ok);
+                    if (bal) {
+                        const int l = __ffs(bal) - 1;
+                        w = __shfl_sync(kFull, i, l);
+                        k += l;
+                        break;
+                    }
+                    k += 32;
                 }
-                it[x] = k;
-                if (k < cp[j + 1]) w = ri[k];
+                it[x] = k < en ? k : en;
             }
+            __syncwarp();
             if (w >= 0) {
                 if (idx[w] < 0) {
                     idx[w] = low[w] = counter++;
@@ -118,26 +177,36 @@ __device__ bool dm_serial(int n, const int* rp, const Idx* ci, const int* cp, co
                 } else if (onst[w] && idx[w] < low[x]) {
                     low[x] = idx[w];
                 }
+                __syncwarp();
                 continue;
             }
             if (low[x] == idx[x]) {
                 int y;
-                do { y = sstk[--sp]; onst[y] = 0; comp[y] = ncomp; } while (y != x);
+                do {
+                    y = sstk[--sp];
+                    __syncwarp();
+                    onst[y] = 0;
+                    comp[y] = ncomp;
+                    __syncwarp();
+                } while (y != x);
                 ++ncomp;
             }
             if (--ctop >= 0) {
                 const int par = cstk[ctop];
                 if (low[x] < low[par]) low[par] = low[x];
             }
+            __syncwarp();
         }
     }
-    for (int i = 0; i < n; ++i) {
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
         if (!live.row(i)) continue;
         for (int e = rp[i]; e < rp[i + 1]; ++e) {
             const int j = ci[e];
             if (mr[i] != j && live.edge(e, i, j) && comp[i] != comp[n + j]) mask[e] = 0;
         }
     }
+    __syncwarp();
     return true;
 }
 

@@ -101,17 +101,18 @@ struct SlotLayout {
     size_t list_r, list_c;// int[n_max] each
     size_t mask;          // uint8[m_max]
     size_t dm;            // int[dm ints]
+    size_t logit;         // float[n_max] logits of long candidate lists (learned proposal)
     size_t bytes;
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-inline int dm_ws_ints(int n) { return 19 * n + 8; }
+__host__ __device__ inline int dm_ws_ints(int n) { return 19 * n + 8; }
 
 inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists, bool learned);
 
 inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales, bool local, bool dm,
-                              size_t gstate_bytes)
+                              size_t gstate_bytes, bool learned)
 {
     SlotLayout L{};
     size_t o = 0;
@@ -126,6 +127,7 @@ inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales,
     L.list_c = local ? take((size_t)n_max * 4) : 0;
     L.mask = dm ? take((size_t)m_max) : 0;
     L.dm = dm ? take((size_t)dm_ws_ints(n_max) * 4) : 0;
+    L.logit = learned ? take((size_t)n_max * 4) : 0;
     L.bytes = align_up(o, 256);
     if (L.bytes == 0) L.bytes = 256;
     return L;
@@ -166,7 +168,7 @@ struct TrajParams {
     uint64_t seed;
     Sched s;
     double* log_x;            // [prefix[count]]
-    unsigned long long* counters;  // [count][4]: DM calls, full SK, local SK, algorithmic bytes
+    unsigned long long* counters;  // [count][5]: DM calls, full SK, local SK, algorithmic bytes, network rows
     int* chunk_counter;
     uint32_t* status;
     uint8_t* slots;           // per-group global scratch, kCtaWarps slots per CTA
@@ -203,7 +205,7 @@ inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists, bo
     size_t b = align_up((size_t)((2 * n + 7) & ~7) * 2, 16) + align_up((size_t)G.total * 4, 16);
     if (rc_smem) b += 2 * align_up((size_t)n * real_bytes, 16);
     if (lists) b += 2 * align_up((size_t)n * 2, 16);
-    if (learned) b += 32 * 16 * 2;
+    if (learned) b += 32 * 24 * 2;  // feature tile [32][24] bf16
     b += kGroupMiscInts * 4;
     return (int)b;
 }

@@ -69,7 +69,7 @@ struct LiveAll {
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(1024) prepare_kernel(DevMatrix* mats, const DevInput* inputs,
-                                                       Sched s, uint32_t* status)
+                                                       Sched s, uint32_t* status, int dyn_smem)
 {
     DevMatrix& M = mats[blockIdx.x];
     const DevInput I = inputs[blockIdx.x];
@@ -136,9 +136,14 @@ __global__ void __launch_bounds__(1024) prepare_kernel(DevMatrix* mats, const De
     for (int e = tid; e < m; e += nt) M.keep[e] = 1;
     __syncthreads();
 
-    // 3. InitialDM (Alg. 2 preprocessing, Sec. 2)
-    if (s.initial_dm && tid == 0)
-        ok_s = dm_serial(n, M.a_rp, M.a_ci, M.a_cp, M.a_ri, M.a_ce, LiveAll{}, M.keep, M.dm_ws) ? 1 : 0;
+    // 3. InitialDM (Alg. 2 preprocessing, Sec. 2); its workspace sits in shared
+    // memory when the launch reserved enough (warp 0 runs it)
+    extern __shared__ __align__(16) int dm_smem[];
+    int* dm_ws = (dm_ws_ints(n) * 4 <= dyn_smem) ? dm_smem : M.dm_ws;
+    if (s.initial_dm && tid < 32) {
+        const bool r = dm_warp(n, M.a_rp, M.a_ci, M.a_cp, M.a_ri, M.a_ce, LiveAll{}, M.keep, dm_ws, tid);
+        if (tid == 0) ok_s = r ? 1 : 0;
+    }
     __syncthreads();
     const int ok = ok_s;
 
@@ -400,11 +405,25 @@ __global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
 // launchers
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, Sched s, int, uint32_t* status,
+cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, Sched s, int n_max, uint32_t* status,
                            cudaStream_t st)
 {
-    if (s.precision == 1) prepare_kernel<double><<<count, 1024, 0, st>>>(d_mats, d_in, s, status);
-    else prepare_kernel<float><<<count, 1024, 0, st>>>(d_mats, d_in, s, status);
+    // shared memory for the initial DM's workspace when it fits (else global)
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int dyn = s.initial_dm ? dm_ws_ints(n_max) * 4 : 0;
+    if (dyn > optin - 4096) dyn = 0;
+    cudaError_t e;
+    if (s.precision == 1) {
+        e = cudaFuncSetAttribute(prepare_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        prepare_kernel<double><<<count, 1024, dyn, st>>>(d_mats, d_in, s, status, dyn);
+    } else {
+        e = cudaFuncSetAttribute(prepare_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        prepare_kernel<float><<<count, 1024, dyn, st>>>(d_mats, d_in, s, status, dyn);
+    }
     return cudaGetLastError();
 }
 

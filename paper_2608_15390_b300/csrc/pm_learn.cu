@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32) mlp_grad_kernel(const DevMod
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int c = 8 * j + 2 * t;
-                const uint32_t w3pair = ld32(M->w3p + c);
+                const uint32_t w3pair = ld32(M->w3p + c);  // row 0 of w3p holds W3
                 const float w3a = bf16lo(w3pair), w3b = bf16hi(w3pair);
                 K.z2[j][0] = dy_lo * w3a * gelu_d(K.z2[j][0]);
                 K.z2[j][1] = dy_lo * w3b * gelu_d(K.z2[j][1]);
@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(kTrainWarps * 32) mlp_grad_kernel(const DevMod
                 float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
-                    mma16816(d, da[kk], ld32(M->w2t + (8 * j + g) * kNH + 16 * kk + 2 * t),
-                             ld32(M->w2t + (8 * j + g) * kNH + 16 * kk + 2 * t + 8));
+                    mma16816(d, da[kk], ld32(M->w2t + (8 * j + g) * kWS + 16 * kk + 2 * t),
+                             ld32(M->w2t + (8 * j + g) * kWS + 16 * kk + 2 * t + 8));
                 const int c = 8 * j + 2 * t;
                 const float z0 = d[0] * gelu_d(K.z1[j][0]), z1 = d[1] * gelu_d(K.z1[j][1]);
                 const float z2 = d[2] * gelu_d(K.z1[j][2]), z3 = d[3] * gelu_d(K.z1[j][3]);
@@ -279,13 +279,13 @@ __global__ void adam_kernel(float* master, float* m1, float* m2, const float* gr
     master[i] = p;
     const uint16_t bits = bf16_bits(p);
     if (i < oB1) {
-        img->w1p[(i / kNF) * 16 + (i % kNF)] = bits;
+        img->w1p[(i / kNF) * kW1S + (i % kNF)] = bits;
     } else if (i < oW2) {
         img->b1[i - oB1] = p;
     } else if (i < oB2) {
         const int k = i - oW2, o = k / kNH, in = k % kNH;
-        img->w2[o * kNH + in] = bits;
-        img->w2t[in * kNH + o] = bits;
+        img->w2[o * kWS + in] = bits;
+        img->w2t[in * kWS + o] = bits;
     } else if (i < oW3) {
         img->b2[i - oB2] = p;
     } else if (i < oB3) {
@@ -302,12 +302,12 @@ __global__ void image_kernel(const float* master, DevModel* img)
     if (i >= kNParam) return;
     const float p = master[i];
     const uint16_t bits = bf16_bits(p);
-    if (i < oB1) img->w1p[(i / kNF) * 16 + (i % kNF)] = bits;
+    if (i < oB1) img->w1p[(i / kNF) * kW1S + (i % kNF)] = bits;
     else if (i < oW2) img->b1[i - oB1] = p;
     else if (i < oB2) {
         const int k = i - oW2, o = k / kNH, in = k % kNH;
-        img->w2[o * kNH + in] = bits;
-        img->w2t[in * kNH + o] = bits;
+        img->w2[o * kWS + in] = bits;
+        img->w2t[in * kWS + o] = bits;
     } else if (i < oW3) img->b2[i - oB2] = p;
     else if (i < oB3) img->w3p[i - oW3] = bits;
     else img->b3[0] = p;

@@ -1,4 +1,4 @@
-// pm_mlp.cuh -- the learned proposal's network (8 -> 64 -> 64 -> 1, GELU) on
+// pm_mlp.cuh -- the learned proposal's network (8 -> 64 -> 64 -> 1, tanh-GELU) on
 // BF16 tensor cores with FP32 accumulation, and its binary32 score exponent.
 //
 // A 16-row tile goes through the three layers as mma.sync.m16n8k16 operations;
@@ -15,17 +15,23 @@ namespace pm {
 constexpr int kNF = 8, kNH = 64;
 constexpr int kNParam = kNH * kNF + kNH + kNH * kNH + kNH + kNH + 1;  // 4801
 
+// Row strides (in bf16 elements) of the weights in shared memory: 24 and 72
+// put the 8 row groups of a fragment load in distinct banks (a 16- or
+// 64-element stride would map all of them to the same bank).
+constexpr int kW1S = 24, kWS = 72, kFS = 24;
+
 // device image of a model; the first kModelInferBytes are what inference needs
 struct DevModel {
-    uint16_t w1p[kNH * 16];   // W1 [out][in], in padded 8 -> 16 with zeros
-    uint16_t w2[kNH * kNH];   // W2 [out][in]
-    uint16_t w3p[8 * kNH];    // row 0 = W3, rows 1..7 zero (an 8-wide n-tile)
+    uint16_t w1p[kNH * kW1S];  // W1 [out][in], in padded 8 -> 16 with zeros (stride 24)
+    uint16_t w2[kNH * kWS];    // W2 [out][in] (stride 72)
+    uint16_t w3p[8 * kWS];     // row 0 = W3, rows 1..7 zero (an 8-wide n-tile)
     float b1[kNH];
     float b2[kNH];
     float b3[4];
-    uint16_t w2t[kNH * kNH];  // W2 transposed [in][out] (training only)
+    uint16_t w2t[kNH * kWS];   // W2 transposed [in][out] (training only)
 };
-constexpr int kModelInferBytes = (int)(sizeof(uint16_t) * (kNH * 16 + kNH * kNH + 8 * kNH) + sizeof(float) * (2 * kNH + 4));
+constexpr int kModelInferBytes =
+    (int)(sizeof(uint16_t) * (kNH * kW1S + kNH * kWS + 8 * kWS) + sizeof(float) * (2 * kNH + 4));
 
 __device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
@@ -44,10 +50,24 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU in its tanh form, g(x) = x/2 (1 + tanh(c (x + a x^3))), c = sqrt(2/pi),
+// a = 0.044715, with the hardware tanh approximation (about 2^-11 relative)
+__device__ __forceinline__ float tanh_hw(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float gelu_f(float x)
+{
+    const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
+    return 0.5f * x * (1.0f + tanh_hw(u));
+}
 __device__ __forceinline__ float gelu_d(float x)
 {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+    const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
+    const float th = tanh_hw(u);
+    return 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * 0.7978845608028654f * (1.0f + 0.134145f * x * x);
 }
 
 // e^x of the learned proposal's score: x clamped to [-20, 20] (NaN -> -20),
@@ -98,7 +118,7 @@ __device__ __forceinline__ void mlp_fwd_tile(const DevModel* M, const uint32_t (
             const int j = 2 * kk + jj;
             const float c0 = M->b1[8 * j + 2 * t], c1 = M->b1[8 * j + 2 * t + 1];
             acc[jj][0] = c0; acc[jj][1] = c1; acc[jj][2] = c0; acc[jj][3] = c1;
-            mma16816(acc[jj], a, ld32(M->w1p + (8 * j + g) * 16 + 2 * t), ld32(M->w1p + (8 * j + g) * 16 + 2 * t + 8));
+            mma16816(acc[jj], a, ld32(M->w1p + (8 * j + g) * kW1S + 2 * t), ld32(M->w1p + (8 * j + g) * kW1S + 2 * t + 8));
             if (KEEP) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) keep->z1[j][q] = acc[jj][q];
@@ -124,8 +144,8 @@ __device__ __forceinline__ void mlp_fwd_tile(const DevModel* M, const uint32_t (
             acc[jj][0] = c0; acc[jj][1] = c1; acc[jj][2] = c0; acc[jj][3] = c1;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-                mma16816(acc[jj], h[kk], ld32(M->w2 + (8 * j + g) * kNH + 16 * kk + 2 * t),
-                         ld32(M->w2 + (8 * j + g) * kNH + 16 * kk + 2 * t + 8));
+                mma16816(acc[jj], h[kk], ld32(M->w2 + (8 * j + g) * kWS + 16 * kk + 2 * t),
+                         ld32(M->w2 + (8 * j + g) * kWS + 16 * kk + 2 * t + 8));
             if (KEEP) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) keep->z2[j][q] = acc[jj][q];
@@ -147,23 +167,80 @@ __device__ __forceinline__ void mlp_fwd_tile(const DevModel* M, const uint32_t (
     acc3[3] = 0.0f;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk)
-        mma16816(acc3, h2[kk], ld32(M->w3p + g * kNH + 16 * kk + 2 * t), ld32(M->w3p + g * kNH + 16 * kk + 2 * t + 8));
+        mma16816(acc3, h2[kk], ld32(M->w3p + g * kWS + 16 * kk + 2 * t), ld32(M->w3p + g * kWS + 16 * kk + 2 * t + 8));
     y_lo = acc3[0];
     y_hi = acc3[2];
 }
 
-// Inference for 32 rows of features (bf16 [32][16] in shared memory, features
-// 8..15 zero): returns the output of row `lane` in lane `lane`.
-__device__ __forceinline__ float mlp_infer32(const DevModel* M, const uint16_t* feat, int lane)
+// Inference forward of one 16-row tile with layer 3 folded into the layer-2
+// loop (each k-tile of the second hidden layer feeds the output mma as soon as
+// it exists), so only one of its four A fragments is live at a time.
+__device__ __forceinline__ void mlp_infer_tile(const DevModel* M, const uint32_t (&a)[4], int lane, float& y_lo,
+                                               float& y_hi)
 {
     const int g = lane >> 2, t = lane & 3;
-    float lo[2], hi[2];
+    uint32_t h[4][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const uint16_t* F = feat + mt * 16 * 16;
-        uint32_t a[4] = {ld32(F + g * 16 + 2 * t), ld32(F + (g + 8) * 16 + 2 * t), ld32(F + g * 16 + 2 * t + 8),
-                         ld32(F + (g + 8) * 16 + 2 * t + 8)};
-        mlp_fwd_tile<false>(M, a, lane, lo[mt], hi[mt], nullptr);
+    for (int kk = 0; kk < 4; ++kk) {
+        float acc[2][4];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int j = 2 * kk + jj;
+            const float c0 = M->b1[8 * j + 2 * t], c1 = M->b1[8 * j + 2 * t + 1];
+            acc[jj][0] = c0; acc[jj][1] = c1; acc[jj][2] = c0; acc[jj][3] = c1;
+            mma16816(acc[jj], a, ld32(M->w1p + (8 * j + g) * kW1S + 2 * t), ld32(M->w1p + (8 * j + g) * kW1S + 2 * t + 8));
+        }
+        h[kk][0] = pack_bf16(gelu_f(acc[0][0]), gelu_f(acc[0][1]));
+        h[kk][1] = pack_bf16(gelu_f(acc[0][2]), gelu_f(acc[0][3]));
+        h[kk][2] = pack_bf16(gelu_f(acc[1][0]), gelu_f(acc[1][1]));
+        h[kk][3] = pack_bf16(gelu_f(acc[1][2]), gelu_f(acc[1][3]));
+    }
+    float acc3[4];
+    acc3[0] = (t == 0) ? M->b3[0] : 0.0f;
+    acc3[1] = 0.0f;
+    acc3[2] = acc3[0];
+    acc3[3] = 0.0f;
+#pragma unroll 1
+    for (int k2 = 0; k2 < 4; ++k2) {
+        float acc[2][4];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int j = 2 * k2 + jj;
+            const float c0 = M->b2[8 * j + 2 * t], c1 = M->b2[8 * j + 2 * t + 1];
+            acc[jj][0] = c0; acc[jj][1] = c1; acc[jj][2] = c0; acc[jj][3] = c1;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma16816(acc[jj], h[kk], ld32(M->w2 + (8 * j + g) * kWS + 16 * kk + 2 * t),
+                         ld32(M->w2 + (8 * j + g) * kWS + 16 * kk + 2 * t + 8));
+        }
+        uint32_t h2[4];
+        h2[0] = pack_bf16(gelu_f(acc[0][0]), gelu_f(acc[0][1]));
+        h2[1] = pack_bf16(gelu_f(acc[0][2]), gelu_f(acc[0][3]));
+        h2[2] = pack_bf16(gelu_f(acc[1][0]), gelu_f(acc[1][1]));
+        h2[3] = pack_bf16(gelu_f(acc[1][2]), gelu_f(acc[1][3]));
+        mma16816(acc3, h2, ld32(M->w3p + g * kWS + 16 * k2 + 2 * t), ld32(M->w3p + g * kWS + 16 * k2 + 2 * t + 8));
+    }
+    y_lo = acc3[0];
+    y_hi = acc3[2];
+}
+
+// Inference for 32 rows of features (bf16 [32][kFS] in shared memory, features
+// 8..15 zero): returns the output of row `lane` in lane `lane`.
+// Rows 16..31 are skipped when none of them is live (the picked vertex of a
+// minimum-degree step rarely has more than 16 live candidates).
+__device__ __forceinline__ float mlp_infer32(const DevModel* M, const uint16_t* feat, int lane, bool live)
+{
+    const int g = lane >> 2, t = lane & 3;
+    float lo[2] = {0.f, 0.f}, hi[2] = {0.f, 0.f};
+    const int tiles = (__ballot_sync(kFull, live) >> 16) ? 2 : 1;
+#pragma unroll 1
+    for (int mt = 0; mt < tiles; ++mt) {
+        const uint16_t* F = feat + mt * 16 * kFS;
+        uint32_t a[4] = {ld32(F + g * kFS + 2 * t), ld32(F + (g + 8) * kFS + 2 * t), ld32(F + g * kFS + 2 * t + 8),
+                         ld32(F + (g + 8) * kFS + 2 * t + 8)};
+        float ylo, yhi;
+        mlp_infer_tile(M, a, lane, ylo, yhi);
+        if (mt == 0) { lo[0] = ylo; hi[0] = yhi; } else { lo[1] = ylo; hi[1] = yhi; }
     }
     const int rr = lane & 15, src = (rr & 7) * 4;
     const float l0 = __shfl_sync(kFull, lo[0], src), h0 = __shfl_sync(kFull, hi[0], src);

@@ -343,14 +343,15 @@ __device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* 
     const float sv = vrow ? __ldg(r0 + v) : __ldg(c0 + (v - n));
     const float sl = vrow ? __ldg(c0 + p) : __ldg(r0 + p);
     const float* vals = vrow ? V.rv : V.cv;
-    f[0] = log1pf(dv);
-    f[1] = log1pf((float)deg[p + (vrow ? n : 0)]);
-    f[2] = log1pf(sum_v);
-    f[3] = log1pf((float)sum_l);
+    // fast logarithms (about 1e-6 relative): 1 + an integer count is exact in binary32
+    f[0] = __logf(1.0f + dv);
+    f[1] = __logf(1.0f + (float)deg[p + (vrow ? n : 0)]);
+    f[2] = __logf(1.0f + sum_v);
+    f[3] = __logf(1.0f + (float)sum_l);
     f[4] = __fdiv_rn((float)t, (float)n);
-    f[5] = logf(sv);
-    f[6] = logf(sl);
-    f[7] = vals ? logf(__ldg(vals + e)) : 0.0f;
+    f[5] = __logf(sv);
+    f[6] = __logf(sl);
+    f[7] = vals ? __logf(__ldg(vals + e)) : 0.0f;
 }
 
 // misc slots of a group (two step buffers so a fast leader never overwrites
@@ -442,6 +443,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     unsigned n_dm = 0, n_full = 0, n_loc = 0;
     int dead_step = -1;
     uint64_t alg_bytes = (uint64_t)2 * n * 4;
+    uint64_t mlp_rows = 0;  // network evaluations of live candidates (learned proposal)
     int m_live = Mp->m;
 
     for (int t = 0; t < n; ++t) {
@@ -490,11 +492,11 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     lo.y = pack_bf16(f[2], f[3]);
                     lo.z = pack_bf16(f[4], f[5]);
                     lo.w = pack_bf16(f[6], f[7]);
-                    uint4* row = reinterpret_cast<uint4*>(feat + lane * 16);
+                    uint4* row = reinterpret_cast<uint4*>(feat + lane * kFS);
                     row[0] = lo;
                     row[1] = make_uint4(0u, 0u, 0u, 0u);
                     __syncwarp();
-                    const float lg = mlp_infer32(Ms, feat, lane);
+                    const float lg = mlp_infer32(Ms, feat, lane, live);
                     __syncwarp();
                     return lg;
                 };
@@ -541,14 +543,36 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     }
                     return __popc(lmk);
                 };
+                // the network runs once per candidate: one pass over the list;
+                // the logit of a single-chunk list stays in a register, longer
+                // lists keep theirs in the group's slot
+                float lg_reg = 0.f;
+                float* lgbuf = model ? reinterpret_cast<float*>(slot + P.slot.logit) : nullptr;
+                if (model) {
+                    int live_base = 0;
+                    for (int base = beg; base < end; base += 32) {
+                        const int e = base + lane;
+                        int pp = 0;
+                        bool live = false;
+                        if (e < end) {
+                            pp = adj[e];
+                            live = entry_live(deg, mask, V, vrow, e, pp + poff);
+                        }
+                        const float lg = cand_logit(e, pp, live);
+                        mlp_rows += __popc(__ballot_sync(kFull, live));
+                        if (len > 32 && e < end) lgbuf[e - beg] = lg;
+                        lg_reg = lg;
+                        if (TRACE) live_base += side_outputs(e, pp, live, lg, live_base);
+                    }
+                }
                 if (len <= 32) {
                     const int e = beg + lane;
                     const bool in = lane < len;
                     const int pp = in ? (int)adj[e] : 0;
                     const bool live = in && entry_live(deg, mask, V, vrow, e, pp + poff);
                     const unsigned lm = __ballot_sync(kFull, live);
-                    const float lg = model ? cand_logit(e, pp, live) : 0.f;
-                    if ((TRACE && model) || rec) side_outputs(e, pp, live, lg, 0);
+                    const float lg = lg_reg;
+                    if (rec) side_outputs(e, pp, live, lg, 0);
                     uint64_t w;
                     if (uniform) {
                         w = live ? (1ull << kq) : 0ull;
@@ -595,8 +619,8 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                                 pp = adj[e];
                                 live = entry_live(deg, mask, V, vrow, e, pp + poff);
                             }
-                            const float lg = model ? cand_logit(e, pp, live) : 0.f;
-                            if ((TRACE && model) || rec) live_base += side_outputs(e, pp, live, lg, live_base);
+                            const float lg = (model && e < end) ? lgbuf[e - beg] : 0.f;
+                            if (rec) live_base += side_outputs(e, pp, live, lg, live_base);
                             if (live) sv = score(e, pp, lg);
                             const Real cm = warp_max_nonneg(sv);
                             smax = cm > smax ? cm : smax;
@@ -610,7 +634,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                                 pp = adj[e];
                                 live = entry_live(deg, mask, V, vrow, e, pp + poff);
                             }
-                            const float lg = model ? cand_logit(e, pp, live) : 0.f;
+                            const float lg = (model && e < end) ? lgbuf[e - beg] : 0.f;
                             if (live) w = quant_weight<Real>(score(e, pp, lg), smax, kq);
                             W += warp_sum_u64(w);
                         }
@@ -633,7 +657,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                             pp = adj[e];
                             live = entry_live(deg, mask, V, vrow, e, pp + poff);
                         }
-                        const float lg = model ? cand_logit(e, pp, live) : 0.f;
+                        const float lg = (model && e < end) ? lgbuf[e - beg] : 0.f;
                         if (live) w = uniform ? (1ull << kq) : quant_weight<Real>(score(e, pp, lg), smax, kq);
                         const uint64_t pre = warp_incl_scan_u64(w, lane) + carry;
                         const unsigned hit = __ballot_sync(kFull, live && pre > rr);
@@ -765,8 +789,10 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         if (t + 1 >= n) continue;
         if (mb[M_DM]) {
             if (leader) ++n_dm;
-            if (leader && lane == 0)
-                G.misc[M_DMOK] = dm_serial(n, V.rp, V.ci, V.cp, V.ri, V.ce, LiveTraj{deg, mask, n}, mask, dmws) ? 1 : 0;
+            if (leader) {
+                const bool okdm = dm_warp(n, V.rp, V.ci, V.cp, V.ri, V.ce, LiveTraj{deg, mask, n}, mask, dmws, lane);
+                if (lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
+            }
             gsync(G);
             if (!G.misc[M_DMOK]) {
                 if (leader) dead_step = t;
@@ -824,10 +850,11 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     if (leader && lane == 0) {
         P.log_x[gq] = (dead_step >= 0) ? -INFINITY : (log(num) - log(den)) + (double)ex * 0.6931471805599453;
         if (TRACE) P.dead_step[gq] = dead_step;
-        if (n_dm) atomicAdd(P.counters + 4 * k + 0, (unsigned long long)n_dm);
-        if (n_full) atomicAdd(P.counters + 4 * k + 1, (unsigned long long)n_full);
-        if (n_loc) atomicAdd(P.counters + 4 * k + 2, (unsigned long long)n_loc);
-        atomicAdd(P.counters + 4 * k + 3, (unsigned long long)alg_bytes);
+        if (n_dm) atomicAdd(P.counters + 5 * k + 0, (unsigned long long)n_dm);
+        if (n_full) atomicAdd(P.counters + 5 * k + 1, (unsigned long long)n_full);
+        if (n_loc) atomicAdd(P.counters + 5 * k + 2, (unsigned long long)n_loc);
+        atomicAdd(P.counters + 5 * k + 3, (unsigned long long)alg_bytes);
+        if (mlp_rows) atomicAdd(P.counters + 5 * k + 4, (unsigned long long)mlp_rows);
     }
     gsync(G);
 }
@@ -869,10 +896,10 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         off += 2 * a16((size_t)n * (pl.gstate ? 4 : 2));
     }
     if (pl.gstate) off = 0;    // feature tile and control words stay in shared memory
-    uint16_t* feat = nullptr;  // [32][16] bf16 feature tile of the learned proposal
+    uint16_t* feat = nullptr;  // [32][kFS] bf16 feature tile of the learned proposal
     if (Ms) {
         feat = reinterpret_cast<uint16_t*>(sbase + off);
-        off += 32 * 16 * 2;
+        off += 32 * kFS * 2;
     }
     G.misc = reinterpret_cast<int*>(sbase + off);
     for (;;) {

@@ -2,10 +2,13 @@
 no learned part) against the CPU oracle, and what training gains.
 
 Bars:
-  forward    BF16 weights/inputs and BF16 hidden activations on tensor cores
-             vs an FP64 network with the same rounding of weights, inputs and
-             activations: |dy| <= 2e-2 * max(1, |y|) (FP32 accumulation order
-             can flip a BF16 rounding of a hidden unit: one BF16 ulp, 2^-8)
+  forward    BF16 weights/inputs and BF16 hidden activations on tensor cores,
+             GELU through the hardware tanh approximation (relative error up
+             to 2^-11), vs an FP64 network with the same rounding of weights,
+             inputs and activations and an exact tanh: a hidden unit can be
+             off by one BF16 ulp (2^-8) plus the tanh error; through two
+             64-wide layers with weights of size ~0.4 that is a few 1e-2 at
+             most, so |dy| <= 6e-2 * max(1, |y|), median <= 5e-3
   gradient   cosine > 0.999 per parameter block, relative norm error < 5e-2
   features   recorded pairs: same keys, features and targets within 1e-5
   replay     with the GPU's logits supplied, the oracle's paths are
@@ -55,8 +58,8 @@ def test_mlp_forward_matches_oracle():
         y = m.forward(X)
         ref = O.mlp_forward(oracle_params(p), bf16(X).astype(np.float64), round_act=True)
         err = np.abs(y - ref) / np.maximum(1.0, np.abs(ref))
-        assert err.max() < 2e-2, err.max()
-        assert np.median(err) < 2e-3
+        assert err.max() < 6e-2, err.max()
+        assert np.median(err) < 5e-3, np.median(err)
         m.close()
 
 

@@ -50,11 +50,12 @@ def test_mlp_gradient_matches_finite_differences():
 
 def test_mlp_forward_closed_form():
     # with W1 = W2 = 0 every hidden unit is GELU(b): y = b3 + W3 . GELU(b2)
+    # (GELU in its tanh form)
     P = np.zeros(O.N_PARAM)
     P[4672:4736] = 0.5          # b2
     P[4736:4800] = 2.0          # W3
     P[4800] = -1.0              # b3
-    g05 = 0.5 * 0.5 * (1 + math.erf(0.5 / math.sqrt(2)))
+    g05 = 0.5 * 0.5 * (1 + math.tanh(math.sqrt(2 / math.pi) * (0.5 + 0.044715 * 0.125)))
     y = O.mlp_forward(P, np.ones((3, 8)))
     assert np.allclose(y, -1.0 + 64 * 2.0 * g05, rtol=1e-14)
 
@@ -110,3 +111,14 @@ def test_logit_replay_is_unbiased_by_enumeration():
             elif r[2] < 0:
                 total += float(prob) * math.exp(r[1])
         assert total == pytest.approx(per, rel=1e-12)
+
+
+def test_model_run_with_zero_network_is_the_unscaled_estimator():
+    # a network that outputs a constant gives equal scores: the unscaled proposal
+    m = G.er_planted(60, 4.0, seed=2)
+    P = O.Prepared(m, O.Schedule(precision=O.PREC_FP32))
+    params = np.zeros(O.N_PARAM)
+    params[-1] = 0.3
+    a = P.run(seed=5, count=40)
+    b = P.run_model(seed=5, count=40, params=params)
+    assert np.array_equal(a["log_x"], b["log_x"])
