@@ -247,7 +247,7 @@ def oracle_train(seed=5, pairs=40000, steps=300, batch=512, lr=2e-3):
     mats = training_matrices()[:4]
     feats, targs = [], []
     for k, m in enumerate(mats):
-        f, t, _ = O.Prepared(m, O.Schedule(**TEACHER)).record(seed=seed, count=2, cap=pairs // 4, matrix=k)
+        f, t, _, _ = O.Prepared(m, O.Schedule(**TEACHER)).record(seed=seed, count=2, cap=pairs // 4, matrix=k)
         feats.append(f)
         targs.append(t)
     X = np.concatenate(feats).astype(np.float64)

@@ -99,10 +99,12 @@ def lib():
         L.or_exp_score.restype = C.c_float
         L.or_exp_score.argtypes = [C.c_float]
         L.or_mlp_forward.argtypes = [P, P, C.c_int64, C.c_int, P]
-        L.or_mlp_grad.restype = C.c_double
-        L.or_mlp_grad.argtypes = [P, P, P, C.c_int64, P]
+        L.or_mlp_grad_ex.restype = C.c_double
+        L.or_mlp_grad_ex.argtypes = [P, P, P, P, C.c_int64, P]
         L.or_record.restype = C.c_int64
-        L.or_record.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int64, P, P, P]
+        L.or_record.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int64, P, P, P, P]
+        L.or_run_ext_model.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
+                                       P, P, P, P, P, P, P]
         L.or_run_ext.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
                                  P, P, P, P, P, P]
         L.or_run_model.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
@@ -272,13 +274,33 @@ class Prepared:
         return dict(log_x=lx, dead_step=ds)
 
     def record(self, seed: int, count: int, cap: int, first_traj: int = 0, matrix: int = 0):
-        """(features[8], target, key) pairs along trajectories of this
-        schedule; key = traj << 28 | step << 14 | candidate index."""
+        """(features[8], target, key, group) pairs along trajectories of this
+        schedule; key = traj << 28 | step << 14 | candidate index; the kept
+        pairs of a step are contiguous, group = index within them << 16 |
+        their count (steps with fewer than two kept pairs are skipped)."""
         f = np.zeros((cap, 8), dtype=np.float32)
         t = np.zeros(cap, dtype=np.float32)
         k = np.zeros(cap, dtype=np.uint64)
-        m = lib().or_record(self.h, seed, matrix, first_traj, count, cap, _ptr(f), _ptr(t), _ptr(k))
-        return f[:m], t[:m], k[:m]
+        g = np.zeros(cap, dtype=np.uint32)
+        m = lib().or_record(self.h, seed, matrix, first_traj, count, cap, _ptr(f), _ptr(t), _ptr(k), _ptr(g))
+        return f[:m], t[:m], k[:m], g[:m]
+
+    def run_ext_model(self, seed: int, count: int, logits, params, first_traj: int = 0, matrix: int = 0,
+                      threads: int = 1):
+        """Paths that follow the supplied logits[count, n, 32] (as run_ext),
+        with this side's network evaluated at every visited state: returns
+        run_ext's dict plus model_logits[count, n, 32]."""
+        lg = np.ascontiguousarray(logits, dtype=np.float32)
+        assert lg.shape == (count, self.n, 32)
+        pm = np.ascontiguousarray(params, dtype=np.float64)
+        lx = np.zeros(count)
+        ds = np.zeros(count, dtype=np.int32)
+        ch = np.zeros((count, self.n, 2), dtype=np.int32)
+        dv = np.zeros((count, self.n), dtype=np.int32)
+        ml = np.zeros((count, self.n, 32), dtype=np.float32)
+        lib().or_run_ext_model(self.h, seed, matrix, first_traj, count, threads, _ptr(lx), _ptr(ds), _ptr(ch),
+                               _ptr(dv), _ptr(lg), _ptr(pm), _ptr(ml))
+        return dict(log_x=lx, dead_step=ds, chosen=ch, deg_v=dv, model_logits=ml)
 
     def forced(self, choices, logits=None):
         """Replay with forced candidate indices.  Returns ("need", w[], W,
@@ -330,7 +352,7 @@ def stats(log_x) -> dict:
 
 
 # ---------------------------------------------------------------------------
-# learned proposal (spec extension; the paper has no learned part)
+# learned proposal (an extension; the paper has no learned part)
 # ---------------------------------------------------------------------------
 
 N_PARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
@@ -349,11 +371,15 @@ def mlp_forward(params, X, round_act: bool = False):
     return out
 
 
-def mlp_grad(params, X, T):
-    """(loss, gradient) of the mean squared error of the MLP on (X, T)."""
+def mlp_grad(params, X, T, group=None):
+    """(loss, gradient) of the MLP on (X, T): the mean squared error, or with
+    group (index within the step << 16 | step's pair count, rows of a step
+    contiguous) the mean squared error after removing each step's mean
+    residual."""
     p = np.ascontiguousarray(params, dtype=np.float64)
     x = np.ascontiguousarray(X, dtype=np.float64)
     t = np.ascontiguousarray(T, dtype=np.float64)
+    gr = None if group is None else np.ascontiguousarray(group, dtype=np.uint32)
     g = np.zeros(N_PARAM)
-    loss = lib().or_mlp_grad(_ptr(p), _ptr(x), _ptr(t), x.shape[0], _ptr(g))
+    loss = lib().or_mlp_grad_ex(_ptr(p), _ptr(x), _ptr(t), _ptr(gr), x.shape[0], _ptr(g))
     return loss, g

@@ -18,7 +18,7 @@
  *   statistics                 Sec. 2 (ESS, p_match), Sec. 3.2 (relative
  *                              spread), Sec. 4 "Metrics" (RSE, s_X with M-1)
  *
- * Readings where the paper is silent (also listed in the design doc):
+ * Readings where the paper is silent:
  *   R1 MD ties: the active vertex of smallest (live degree, unified id) where
  *      row i has id i and column j has id n+j.
  *   R2 the proposal of Eq. 3 is realised with integer weights
@@ -32,6 +32,14 @@
  *      binary32 (computed in binary64 and rounded: for +,-,*,/ this equals
  *      direct binary32 arithmetic because 53 >= 2*24+2); log-weights and
  *      statistics are binary64.
+ *
+ * Learned proposal (an extension with no counterpart in the paper): per-edge
+ * features, an 8-64-64-1 tanh-GELU network in FP64 (optionally rounding its
+ * inputs and hidden activations to bfloat16), its own binary32 exponent of
+ * the score, recording of (features, SK target) pairs grouped by step, and the
+ * training losses with their gradients by back-propagation: the mean squared
+ * error and the per-step centred squared error (the proposal of Eq. 3 only
+ * sees a step's logits up to a common offset).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -pthread -lm
  */
@@ -78,6 +86,10 @@ uint64_t or_draw_u64(uint64_t seed, uint64_t traj, uint32_t matrix, uint32_t ste
 }
 
 #define OR_MAX_ATTEMPTS 256
+/* learned proposal: features, hidden width, parameter count */
+#define OR_NF 8
+#define OR_NH 64
+#define OR_NPARAM (OR_NH * OR_NF + OR_NH + OR_NH * OR_NH + OR_NH + OR_NH + 1)
 
 /* Uniform integer in [0, W) (W >= 1): multiply-shift with rejection (Lemire,
  * "Fast random integer generation in an interval", 2019).  Returns -1 if all
@@ -201,6 +213,7 @@ typedef struct {
     int32_t* cand_p;
     uint64_t* w;
     int32_t *nbrR, *nbrC;
+    float* recbuf;   /* recording scratch: n rows of 8 features, n targets, n indices */
 } or_traj;
 
 static int edge_live(const or_traj* T, int64_t e, int row, int col)
@@ -456,6 +469,7 @@ static or_traj* traj_alloc(const or_prep* P)
     T->w = (uint64_t*)xcalloc(n, 8);
     T->nbrR = (int32_t*)xcalloc(n, 4);
     T->nbrC = (int32_t*)xcalloc(n, 4);
+    T->recbuf = (float*)xcalloc((size_t)n * (OR_NF + 2), 4);
     return T;
 }
 
@@ -464,7 +478,7 @@ static void traj_free(or_traj* T)
     if (!T) return;
     void* ptrs[] = { T->act, T->deg, T->mask, T->r, T->c, T->mr, T->mc, T->vis, T->stk, T->it,
                      T->idx, T->low, T->comp, T->sstk, T->onst, T->stampr, T->stampc, T->listr,
-                     T->listc, T->newr, T->newc, T->cand_e, T->cand_p, T->w, T->nbrR, T->nbrC };
+                     T->listc, T->newr, T->newc, T->cand_e, T->cand_p, T->w, T->nbrR, T->nbrC, T->recbuf };
     for (size_t q = 0; q < sizeof(ptrs) / sizeof(ptrs[0]); ++q) free(ptrs[q]);
     free(T);
 }
@@ -539,7 +553,7 @@ typedef struct {
 /* forced-choice interface for exhaustive enumeration: when forced != NULL the
  * t-th step takes candidate forced[t] instead of a Philox draw; when t reaches
  * n_forced the function stops and reports the candidate weights (need_choice). */
-/* learned-proposal hooks (spec extension; the paper has no learned
+/* learned-proposal hooks (an extension; the paper has no learned
  * proposal): ext_logits[t * 32 + q] is the logit of the q-th live candidate
  * at step t; record_* collect (features, target) pairs of the SK estimator. */
 typedef struct {
@@ -548,7 +562,10 @@ typedef struct {
     float* rec_feat;           /* [cap][8] or NULL */
     float* rec_target;         /* [cap] */
     uint64_t* rec_key;         /* [cap]: traj << 28 | t << 14 | q */
+    uint32_t* rec_group;       /* [cap] or NULL: index within the step's pairs << 16 | their count */
     int64_t rec_cap, rec_n;
+    int rec_full;              /* a step's pairs no longer fit: recording has stopped */
+    float* model_logits_out;   /* [n][32] or NULL: the network's own logits along the path */
 } or_learn;
 
 typedef struct {
@@ -582,12 +599,9 @@ float or_exp_score(float x)
     return ldexpf(p, (int)nn);
 }
 
-#define OR_NF 8
-#define OR_NH 64
-#define OR_NPARAM (OR_NH * OR_NF + OR_NH + OR_NH * OR_NH + OR_NH + OR_NH + 1)
 
-/* Per-edge features of candidate (v, l) at step t (reading of the north
- * star's list): log1p deg(v), log1p deg(l), log1p of the degree sum over v's
+/* Per-edge features of candidate (v, l) at step t (residual degrees,
+ * neighbour-degree sums, depth fraction, current scale): log1p deg(v), log1p deg(l), log1p of the degree sum over v's
  * live candidates, log1p of the degree sum over l's live neighbours, t / n,
  * ln of the outer scale of v and of l (r for rows, c for columns), ln B_vl. */
 static void edge_features(const or_traj* T, int t, int v, int l_unified, int64_t e, double sum_v, float* f)
@@ -660,56 +674,92 @@ void or_mlp_forward(const double* Pm, const double* X, int64_t B, int round_act,
     }
 }
 
-/* Loss L = mean over rows of (y - target)^2 and its gradient dL/dparams by
- * the chain rule (back-propagation through the three layers). */
-double or_mlp_grad(const double* Pm, const double* X, const double* Tg, int64_t B, double* G)
+/* Forward of one row keeping the pre-activations z and activations h. */
+static double mlp_row(const double* Pm, const double* x, double* z1, double* h1, double* z2, double* h2)
 {
     const double *W1 = Pm, *b1 = W1 + OR_NH * OR_NF, *W2 = b1 + OR_NH, *b2 = W2 + OR_NH * OR_NH,
                  *W3 = b2 + OR_NH, *b3 = W3 + OR_NH;
+    for (int o = 0; o < OR_NH; ++o) {
+        double z = b1[o];
+        for (int i = 0; i < OR_NF; ++i) z += W1[o * OR_NF + i] * x[i];
+        z1[o] = z;
+        h1[o] = gelu(z);
+    }
+    for (int o = 0; o < OR_NH; ++o) {
+        double z = b2[o];
+        for (int i = 0; i < OR_NH; ++i) z += W2[o * OR_NH + i] * h1[i];
+        z2[o] = z;
+        h2[o] = gelu(z);
+    }
+    double y = b3[0];
+    for (int i = 0; i < OR_NH; ++i) y += W3[i] * h2[i];
+    return y;
+}
+
+/* Adds dy * dy/dparams of one row to G (back-propagation through the three
+ * layers by the chain rule). */
+static void mlp_row_backward(const double* Pm, const double* x, double dy, double* G)
+{
+    const double *W2 = Pm + OR_NH * OR_NF + OR_NH, *W3 = W2 + OR_NH * OR_NH + OR_NH;
     double *gW1 = G, *gb1 = gW1 + OR_NH * OR_NF, *gW2 = gb1 + OR_NH, *gb2 = gW2 + OR_NH * OR_NH,
            *gW3 = gb2 + OR_NH, *gb3 = gW3 + OR_NH;
-    memset(G, 0, sizeof(double) * OR_NPARAM);
     double z1[OR_NH], h1[OR_NH], z2[OR_NH], h2[OR_NH], d2[OR_NH], d1[OR_NH];
+    mlp_row(Pm, x, z1, h1, z2, h2);
+    gb3[0] += dy;
+    for (int i = 0; i < OR_NH; ++i) {
+        gW3[i] += dy * h2[i];
+        d2[i] = dy * W3[i] * gelu_d(z2[i]);
+    }
+    for (int o = 0; o < OR_NH; ++o) {
+        gb2[o] += d2[o];
+        for (int i = 0; i < OR_NH; ++i) gW2[o * OR_NH + i] += d2[o] * h1[i];
+    }
+    for (int i = 0; i < OR_NH; ++i) {
+        double s = 0;
+        for (int o = 0; o < OR_NH; ++o) s += W2[o * OR_NH + i] * d2[o];
+        d1[i] = s * gelu_d(z1[i]);
+    }
+    for (int o = 0; o < OR_NH; ++o) {
+        gb1[o] += d1[o];
+        for (int i = 0; i < OR_NF; ++i) gW1[o * OR_NF + i] += d1[o] * x[i];
+    }
+}
+
+/* Training losses and their gradients dL/dparams (G, OR_NPARAM doubles).
+ * group == NULL: L = (1/B) sum_r (y_r - t_r)^2.
+ * group != NULL: rows come in contiguous groups (the candidates of one step;
+ * group[r] = index within the group << 16 | group size) and
+ * L = (1/B) sum_r ((y_r - t_r) - mean over r's group of (y - t))^2, the squared
+ * error after removing each step's common offset, which the proposal of
+ * Eq. 3 cannot see (it is proportional within a step).  Its gradient is
+ * dL/dy_r = (2/B) (e_r - mean_group e) because the centred residuals of a
+ * group sum to zero. */
+double or_mlp_grad_ex(const double* Pm, const double* X, const double* Tg, const uint32_t* group, int64_t B,
+                      double* G)
+{
+    memset(G, 0, sizeof(double) * OR_NPARAM);
+    double z1[OR_NH], h1[OR_NH], z2[OR_NH], h2[OR_NH];
+    double* e = (double*)xcalloc((size_t)(B > 0 ? B : 1), sizeof(double));
+    for (int64_t r = 0; r < B; ++r) e[r] = mlp_row(Pm, X + r * OR_NF, z1, h1, z2, h2) - Tg[r];
     double loss = 0;
     for (int64_t r = 0; r < B; ++r) {
-        const double* x = X + r * OR_NF;
-        for (int o = 0; o < OR_NH; ++o) {
-            double z = b1[o];
-            for (int i = 0; i < OR_NF; ++i) z += W1[o * OR_NF + i] * x[i];
-            z1[o] = z;
-            h1[o] = gelu(z);
+        double c = e[r];
+        if (group) {
+            const int64_t q = group[r] >> 16, size = group[r] & 0xFFFFu, s0 = r - q;
+            double mean = 0;
+            for (int64_t k = 0; k < size; ++k) mean += e[s0 + k];
+            c -= mean / (double)size;
         }
-        for (int o = 0; o < OR_NH; ++o) {
-            double z = b2[o];
-            for (int i = 0; i < OR_NH; ++i) z += W2[o * OR_NH + i] * h1[i];
-            z2[o] = z;
-            h2[o] = gelu(z);
-        }
-        double y = b3[0];
-        for (int i = 0; i < OR_NH; ++i) y += W3[i] * h2[i];
-        const double err = y - Tg[r];
-        loss += err * err / (double)B;
-        const double dy = 2.0 * err / (double)B;
-        gb3[0] += dy;
-        for (int i = 0; i < OR_NH; ++i) {
-            gW3[i] += dy * h2[i];
-            d2[i] = dy * W3[i] * gelu_d(z2[i]);
-        }
-        for (int o = 0; o < OR_NH; ++o) {
-            gb2[o] += d2[o];
-            for (int i = 0; i < OR_NH; ++i) gW2[o * OR_NH + i] += d2[o] * h1[i];
-        }
-        for (int i = 0; i < OR_NH; ++i) {
-            double s = 0;
-            for (int o = 0; o < OR_NH; ++o) s += W2[o * OR_NH + i] * d2[o];
-            d1[i] = s * gelu_d(z1[i]);
-        }
-        for (int o = 0; o < OR_NH; ++o) {
-            gb1[o] += d1[o];
-            for (int i = 0; i < OR_NF; ++i) gW1[o * OR_NF + i] += d1[o] * x[i];
-        }
+        loss += c * c / (double)B;
+        mlp_row_backward(Pm, X + r * OR_NF, 2.0 * c / (double)B, G);
     }
+    free(e);
     return loss;
+}
+
+double or_mlp_grad(const double* Pm, const double* X, const double* Tg, int64_t B, double* G)
+{
+    return or_mlp_grad_ex(Pm, X, Tg, NULL, B, G);
 }
 
 static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t matrix,
@@ -764,24 +814,43 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
         /* nc == deg[v] by construction of deg[] */
         double smax = 0.0;
         double* sc = T->newr;  /* scratch of size n */
-        if (Ln && Ln->rec_feat) {  /* (features, SK target) pairs of this step */
+        if (Ln && Ln->rec_feat && !Ln->rec_full) {
+            /* (features, SK target) pairs of this step.  A pair is kept only
+             * if every value is finite (an SK scale can run to 0 or infinity
+             * on a residual without total support); a step contributes its
+             * kept pairs together, and only if there are at least two of
+             * them (one candidate says nothing about the proposal's shape),
+             * so the pairs of a step form one contiguous group. */
             double sum_v = 0;
             for (int q = 0; q < nc; ++q) sum_v += T->deg[v_is_row ? n + T->cand_p[q] : T->cand_p[q]];
-            for (int q = 0; q < nc && Ln->rec_n < Ln->rec_cap; ++q) {
+            float* fbuf = T->recbuf;
+            float* tbuf = fbuf + (size_t)nc * OR_NF;
+            int* qbuf = (int*)(tbuf + nc);
+            int kept = 0;
+            for (int q = 0; q < nc; ++q) {
                 const int l = v_is_row ? n + T->cand_p[q] : T->cand_p[q];
-                float* f = Ln->rec_feat + Ln->rec_n * OR_NF;
+                float* f = fbuf + (size_t)kept * OR_NF;
                 edge_features(T, t, v, l, T->cand_e[q], sum_v, f);
                 const double sv_ = v_is_row ? T->r[v] : T->c[v - n];
                 const double sl_ = v_is_row ? T->c[T->cand_p[q]] : T->r[T->cand_p[q]];
                 const float tgt = (float)log(sv_ * sl_);
-                /* a pair is kept only if every value is finite (an SK scale can
-                 * run to 0 or infinity on a residual without total support) */
                 int finite = isfinite(tgt);
                 for (int z = 0; z < OR_NF; ++z) finite = finite && isfinite(f[z]);
                 if (!finite) continue;
-                Ln->rec_target[Ln->rec_n] = tgt;
-                Ln->rec_key[Ln->rec_n] = (traj << 28) | ((uint64_t)t << 14) | (uint64_t)q;
-                Ln->rec_n++;
+                tbuf[kept] = tgt;
+                qbuf[kept] = q;
+                ++kept;
+            }
+            if (kept >= 2 && Ln->rec_n + kept > Ln->rec_cap) Ln->rec_full = 1;
+            if (kept >= 2 && !Ln->rec_full) {
+                for (int i = 0; i < kept; ++i) {
+                    const int64_t pos = Ln->rec_n + i;
+                    memcpy(Ln->rec_feat + pos * OR_NF, fbuf + (size_t)i * OR_NF, sizeof(float) * OR_NF);
+                    Ln->rec_target[pos] = tbuf[i];
+                    Ln->rec_key[pos] = (traj << 28) | ((uint64_t)t << 14) | (uint64_t)qbuf[i];
+                    if (Ln->rec_group) Ln->rec_group[pos] = ((uint32_t)i << 16) | (uint32_t)kept;
+                }
+                Ln->rec_n += kept;
             }
         }
         if (Ln && Ln->ext_logits && nc > 32) {  /* replay supports up to 32 candidates */
@@ -802,13 +871,15 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
                 lg_model[q] = (float)y;
             }
         }
+        if (lg_model && Ln->model_logits_out)
+            for (int q = 0; q < nc && q < 32; ++q) Ln->model_logits_out[(int64_t)t * 32 + q] = lg_model[q];
         for (int q = 0; q < nc; ++q) {
             double sv;
-            if (lg_model) {
-                const float ex = or_exp_score(lg_model[q]);
-                sv = P->val ? (double)((float)entry(P, T->cand_e[q]) * ex) : (double)ex;
-            } else if (Ln && Ln->ext_logits) {
+            if (Ln && Ln->ext_logits) {  /* supplied logits take precedence */
                 const float ex = or_exp_score(Ln->ext_logits[(int64_t)t * 32 + q]);
+                sv = P->val ? (double)((float)entry(P, T->cand_e[q]) * ex) : (double)ex;
+            } else if (lg_model) {
+                const float ex = or_exp_score(lg_model[q]);
                 sv = P->val ? (double)((float)entry(P, T->cand_e[q]) * ex) : (double)ex;
             } else {
                 double scale = v_is_row ? T->c[T->cand_p[q]] : T->r[T->cand_p[q]];
@@ -945,6 +1016,7 @@ typedef struct {
     int32_t* degv;    /* [count][n] or NULL */
     const float* ext_logits;  /* [count][n][32] or NULL */
     const double* model;      /* network parameters or NULL */
+    float* model_logits;      /* [count][n][32] or NULL: the network's logits along the path */
     int64_t counts[3];
 } or_job;
 
@@ -959,6 +1031,7 @@ static void* job_main(void* arg)
         memset(&L, 0, sizeof(L));
         if (J->ext_logits) L.ext_logits = J->ext_logits + q * (int64_t)n * 32;
         L.model = J->model;
+        if (J->model_logits) L.model_logits_out = J->model_logits + q * (int64_t)n * 32;
         run_trajectory(T, J->seed, J->first + (uint64_t)q, J->matrix,
                        J->chosen ? J->chosen + q * 2 * n : NULL,
                        J->degv ? J->degv + q * n : NULL, NULL,
@@ -984,17 +1057,12 @@ void or_run(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_tra
     or_run_ext(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, op_counts, NULL);
 }
 
-/* or_run with the learned proposal's logits supplied per trajectory and step
- * (ext_logits[count][n][32], candidate q of step t in adjacency order). */
-void or_run_model(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
-                  int nthreads, double* log_x, int32_t* dead_step, int64_t* op_counts, const double* model);
-static const double* g_model_for_run = NULL;  /* set only inside or_run_model */
-
-/* or_run with the learned proposal's logits supplied per trajectory and step
- * (ext_logits[count][n][32], candidate q of step t in adjacency order). */
-void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
-                int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
-                int64_t* op_counts, const float* ext_logits)
+/* Trajectories lo..hi of one call spread over nthreads host threads: plain,
+ * with supplied logits (ext_logits), with this side's network (model) or
+ * both (the network's logits then go to model_logits). */
+static void run_jobs(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
+                     int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
+                     int64_t* op_counts, const float* ext_logits, const double* model, float* model_logits)
 {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > count) nthreads = count > 0 ? (int)count : 1;
@@ -1006,7 +1074,8 @@ void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first
         jobs[t].log_x = log_x; jobs[t].dead_step = dead_step; jobs[t].chosen = chosen;
         jobs[t].degv = degv;
         jobs[t].ext_logits = ext_logits;
-        jobs[t].model = g_model_for_run;
+        jobs[t].model = model;
+        jobs[t].model_logits = model_logits;
     }
     for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, job_main, &jobs[t]);
     job_main(&jobs[0]);
@@ -1020,6 +1089,29 @@ void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first
     free(th);
 }
 
+/* or_run with the learned proposal's logits supplied per trajectory and step
+ * (ext_logits[count][n][32], candidate q of step t in adjacency order). */
+void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
+                int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
+                int64_t* op_counts, const float* ext_logits)
+{
+    run_jobs(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, op_counts, ext_logits,
+             NULL, NULL);
+}
+
+/* Paths that follow supplied logits (ext_logits, as or_run_ext) while the
+ * network with parameters `model` is evaluated at every step on this side's
+ * own features: its logits go to model_logits[count][n][32] (candidate q < 32
+ * of step t in adjacency order), so a device network can be compared with
+ * this one on exactly the states the device visited. */
+void or_run_ext_model(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
+                      int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
+                      const float* ext_logits, const double* model, float* model_logits)
+{
+    run_jobs(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, NULL, ext_logits, model,
+             model_logits);
+}
+
 /* Trajectories of the learned proposal computed here: features, the FP64
  * network (inputs and hidden activations rounded to bfloat16 as the tensor
  * cores see them) and the binary32 score exponent.  Statistically the same
@@ -1027,15 +1119,17 @@ void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first
 void or_run_model(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
                   int nthreads, double* log_x, int32_t* dead_step, int64_t* op_counts, const double* model)
 {
-    g_model_for_run = model;
-    or_run_ext(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, NULL, NULL, op_counts, NULL);
-    g_model_for_run = NULL;
+    run_jobs(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, NULL, NULL, op_counts, NULL, model,
+             NULL);
 }
 
 /* (features, target) pairs of trajectories first..first+count-1 of the
- * prepared schedule (one thread, trajectory order); returns the pair count. */
+ * prepared schedule (one thread, trajectory order), the kept pairs of a step
+ * contiguous with group[] = index within the step << 16 | the step's count
+ * (group may be NULL).  Recording stops at the first step whose pairs do not
+ * all fit in cap.  Returns the pair count. */
 int64_t or_record(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first, int64_t count,
-                  int64_t cap, float* feat, float* target, uint64_t* key)
+                  int64_t cap, float* feat, float* target, uint64_t* key, uint32_t* group)
 {
     or_traj* T = traj_alloc(P);
     or_learn L;
@@ -1043,8 +1137,9 @@ int64_t or_record(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t fir
     L.rec_feat = feat;
     L.rec_target = target;
     L.rec_key = key;
+    L.rec_group = group;
     L.rec_cap = cap;
-    for (int64_t q = 0; q < count && L.rec_n < cap; ++q) {
+    for (int64_t q = 0; q < count && !L.rec_full; ++q) {
         or_traj_result res;
         run_trajectory(T, seed, first + (uint64_t)q, matrix, NULL, NULL, NULL, &L, &res);
     }

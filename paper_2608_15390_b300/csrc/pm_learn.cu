@@ -1,4 +1,4 @@
-// pm_learn.cu -- training of the learned proposal (a spec extension:
+// pm_learn.cu -- training of the learned proposal (an extension:
 // the paper has no learned part).  Forward and backward run on BF16 tensor
 // cores (mma.sync.m16n8k16, FP32 accumulation); Adam keeps FP32 master
 // weights and refreshes the BF16 device image after every step.

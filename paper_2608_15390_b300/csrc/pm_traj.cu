@@ -317,7 +317,7 @@ __device__ __forceinline__ Real cand_score(const MV<Idx>& V, bool vrow, int e, i
 }
 
 // Per-edge features of candidate p of the picked vertex v at step t (the
-// learned proposal's inputs; see DESIGN.md): log1p deg(v), log1p deg(p),
+// learned proposal's inputs): log1p deg(v), log1p deg(p),
 // log1p of the degree sum over v's live candidates, log1p of the degree sum
 // over p's live neighbours, t / n, ln of the outer scales of v and p, ln B_vp.
 template <typename Idx>

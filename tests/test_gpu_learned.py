@@ -1,4 +1,4 @@
-"""GPU parity of the learned proposal (a spec extension; the paper has
+"""GPU parity of the learned proposal (an extension; the paper has
 no learned part) against the CPU oracle, and what training gains.
 
 Bars:
@@ -89,7 +89,7 @@ def test_recorded_pairs_match_oracle():
     teacher = O.Schedule(initial_dm=1, K0=20, K=3, sk=O.SK_FIXED, precision=O.PREC_FP32)
     gt = B.Schedule(initial_dm=1, K0=20, K=3, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
     f, t, k = ctx().record_pairs(m, 8, 7, gt, cap=100000)
-    of, ot, ok = O.Prepared(m, teacher).record(seed=7, count=8, cap=100000)
+    of, ot, ok, og = O.Prepared(m, teacher).record(seed=7, count=8, cap=100000)
     assert len(k) == len(ok) and len(k) > 100
     order = np.argsort(k)
     assert np.array_equal(k[order], ok)

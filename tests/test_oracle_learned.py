@@ -1,4 +1,4 @@
-"""Pins of the oracle's learned-proposal parts (a spec extension: the
+"""Pins of the oracle's learned-proposal parts (an extension: the
 paper has no learned proposal, so these pin the pieces against mathematics
 and against the paper's own unscaled estimator)."""
 import math
@@ -66,7 +66,7 @@ def test_features_hand_worked():
     # col 1 (degree 3, neighbours row0 (3) row1 (2) row2 (3)); no scaling
     A = G.csr_from_coo(4, [0, 0, 0, 1, 1, 2, 2, 2, 3, 3], [0, 1, 2, 0, 1, 1, 2, 3, 2, 3])
     P = O.Prepared(A, O.Schedule(precision=O.PREC_FP32))
-    f, t, k = P.record(seed=1, count=1, cap=64)
+    f, t, k, _ = P.record(seed=1, count=1, cap=64)
     l1p = lambda x: np.float32(math.log1p(x))
     want0 = [l1p(2), l1p(2), l1p(5), l1p(5), 0, 0, 0, 0]
     want1 = [l1p(2), l1p(3), l1p(5), l1p(8), 0, 0, 0, 0]
@@ -122,3 +122,112 @@ def test_model_run_with_zero_network_is_the_unscaled_estimator():
     a = P.run(seed=5, count=40)
     b = P.run_model(seed=5, count=40, params=params)
     assert np.array_equal(a["log_x"], b["log_x"])
+
+
+def _groups(sizes):
+    """group codes (index << 16 | size) of consecutive groups of these sizes"""
+    return np.concatenate([(np.arange(s, dtype=np.uint32) << 16) | s for s in sizes]).astype(np.uint32)
+
+
+def test_centred_loss_is_the_within_step_variance_of_the_residual():
+    # sum_i (e_i - mean e)^2 = (1/s) sum_{i<j} (e_i - e_j)^2 for a group of s
+    # residuals: the loss from pairwise differences of plain forward outputs
+    rng = np.random.default_rng(2)
+    P = _rand_params(rng)
+    sizes = [2, 5, 3, 7, 2, 4]
+    grp = _groups(sizes)
+    B = len(grp)
+    X = rng.normal(size=(B, 8))
+    T = rng.normal(size=B)
+    e = O.mlp_forward(P, X) - T
+    want, r0 = 0.0, 0
+    for s in sizes:
+        blk = e[r0:r0 + s]
+        want += sum((blk[i] - blk[j]) ** 2 for i in range(s) for j in range(i + 1, s)) / s
+        r0 += s
+    loss, _ = O.mlp_grad(P, X, T, grp)
+    assert loss == pytest.approx(want / B, rel=1e-12)
+
+
+def test_centred_gradient_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    P = _rand_params(rng)
+    grp = _groups([3, 2, 6, 4, 1, 5])
+    B = len(grp)
+    X = rng.normal(size=(B, 8))
+    T = rng.normal(size=B)
+    loss, g = O.mlp_grad(P, X, T, grp)
+    idx = rng.choice(O.N_PARAM, size=50, replace=False)
+    idx = np.concatenate([idx, [0, 511, 512, 575, 576, 4671, 4672, 4735, 4736, 4799]])
+    for i in idx:
+        h = 1e-6
+        Pp = P.copy(); Pp[i] += h
+        Pm = P.copy(); Pm[i] -= h
+        fd = (O.mlp_grad(Pp, X, T, grp)[0] - O.mlp_grad(Pm, X, T, grp)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-9), i
+    # the output bias moves every prediction of a step alike: no gradient
+    assert abs(g[4800]) < 1e-14
+
+
+def test_centred_loss_ignores_a_per_step_offset():
+    # adding a constant to a step's targets (a common factor of that step's
+    # proposal scores, which Eq. 3 normalises away) changes nothing
+    rng = np.random.default_rng(4)
+    P = _rand_params(rng)
+    sizes = [4, 2, 3, 5]
+    grp = _groups(sizes)
+    X = rng.normal(size=(len(grp), 8))
+    T = rng.normal(size=len(grp))
+    T2 = T + np.repeat(rng.normal(size=len(sizes)) * 5, sizes)
+    l1, g1 = O.mlp_grad(P, X, T, grp)
+    l2, g2 = O.mlp_grad(P, X, T2, grp)
+    assert l2 == pytest.approx(l1, rel=1e-10)
+    assert np.allclose(g1, g2, rtol=1e-8, atol=1e-12)
+    # singleton groups carry no information
+    l0, g0 = O.mlp_grad(P, X, T, _groups([1] * len(grp)))
+    assert l0 == 0.0 and not g0.any()
+
+
+def test_recorded_steps_form_contiguous_groups():
+    # every step with at least two live candidates is recorded (finite
+    # targets here), as one contiguous group in candidate order; no other
+    m = G.er_planted(50, 4.0, seed=9)
+    sched = O.Schedule(initial_dm=1, K0=20, K=3, sk=O.SK_FIXED, precision=O.PREC_FP32)
+    P = O.Prepared(m, sched)
+    f, t, k, g = P.record(seed=2, count=6, cap=1 << 20)
+    tr = P.run(seed=2, count=6, trace=True)
+    traj, step, cand = k >> 28, (k >> 14) & 0x3FFF, k & 0x3FFF
+    r = 0
+    want_steps = [(q, s) for q in range(6) for s in range(m.n) if tr["deg_v"][q, s] >= 2]
+    for q, s in want_steps:
+        d = tr["deg_v"][q, s]
+        assert np.array_equal(traj[r:r + d], np.full(d, q)) and np.array_equal(step[r:r + d], np.full(d, s))
+        assert np.array_equal(cand[r:r + d], np.arange(d))
+        assert np.array_equal(g[r:r + d], (np.arange(d, dtype=np.uint32) << 16) | d)
+        r += d
+    assert r == len(k)
+    # a capacity that cuts a step stops the recording before that step
+    first = int(g[0] & 0xFFFF)
+    f2, _, k2, g2 = P.record(seed=2, count=6, cap=first + 1)
+    assert len(k2) == first and np.array_equal(k2, k[:first])
+
+
+def test_network_logits_along_supplied_paths():
+    # with K0 = 0 the features' scale terms vanish and zero logits give the
+    # unscaled proposal, so the recorded pairs of a no-SK teacher walk the same
+    # paths: the network's logits there are f(bf16(features)) pair by pair
+    m = G.er_planted(40, 4.0, seed=10)
+    P = O.Prepared(m, O.Schedule(precision=O.PREC_FP32))
+    rng = np.random.default_rng(6)
+    params = _rand_params(rng)
+    T = 5
+    out = P.run_ext_model(seed=4, count=T, logits=np.zeros((T, m.n, 32), np.float32), params=params, threads=2)
+    base = P.run(seed=4, count=T, trace=True)
+    assert np.array_equal(out["chosen"], base["chosen"])
+    f, _, k, _ = P.record(seed=4, count=T, cap=1 << 20)
+    bf = lambda a: np.asarray(a, np.float32).view(np.uint32)
+    fb = ((bf(f).astype(np.uint64) + 0x7FFF + ((bf(f) >> 16) & 1)) & 0xFFFF0000).astype(np.uint32).view(np.float32)
+    want = O.mlp_forward(params, fb.astype(np.float64), round_act=True).astype(np.float32)
+    traj, step, cand = k >> 28, (k >> 14) & 0x3FFF, k & 0x3FFF
+    got = out["model_logits"][traj.astype(int), step.astype(int), cand.astype(int)]
+    assert len(k) > 20 and np.array_equal(got, want)
