@@ -203,11 +203,21 @@ typedef struct {
     pm_schedule teacher;     /* SK-scheduled estimator producing the targets (sk FIXED or
                                 ADAPTIVE, FP32 proposal); its current scales at each step
                                 are the targets */
+    int32_t objective;       /* PM_OBJ_MSE or PM_OBJ_CENTRED */
+    int32_t reserved;        /* must be 0 */
 } pm_train_cfg;
 
+/* Training losses over the recorded pairs (e = network output - target):
+ * PM_OBJ_MSE      mean of e^2;
+ * PM_OBJ_CENTRED  mean of (e - mean of e over the pair's step)^2.  Eq. 3
+ *                 normalises the scores of a step, so only the differences of
+ *                 a step's logits reach the proposal; this loss ignores the
+ *                 part of the target (ln r_v) that all candidates share. */
+enum { PM_OBJ_MSE = 0, PM_OBJ_CENTRED = 1 };
+
 typedef struct {
-    double loss_first;       /* mean squared error of the first step */
-    double loss_last;        /* mean squared error over the last epoch */
+    double loss_first;       /* loss of the first Adam step's batch */
+    double loss_last;        /* mean loss over the last epoch */
     uint64_t n_pairs;        /* pairs recorded */
     int32_t steps;           /* Adam steps taken */
     int32_t reserved;
@@ -222,24 +232,33 @@ pm_status pm_model_destroy(pm_model* model);
 pm_status pm_model_get_params(pm_context* ctx, const pm_model* model, float* params);
 pm_status pm_model_set_params(pm_context* ctx, pm_model* model, const float* params);
 /* Train on pairs recorded from cfg->teacher running on mats[count] (matrix k
- * uses matrix index k): record, shuffle, then epochs of Adam on the mean
- * squared error, gradients from the tensor-core backward kernel. */
+ * uses matrix index k): record, shuffle (whole steps for PM_OBJ_CENTRED),
+ * then epochs of Adam on cfg->objective, gradients from the tensor-core
+ * backward kernel. */
 pm_status pm_model_train(pm_context* ctx, pm_model* model, const pm_csr* mats, int32_t count,
                          const pm_train_cfg* cfg, pm_train_report* report);
 /* Network outputs for B feature rows (host X[B][8] -> host out[B]). */
 pm_status pm_mlp_forward(pm_context* ctx, const pm_model* model, const float* X, uint64_t B,
                          float* out);
-/* Gradient of the mean squared error over (X[B][8], T[B]) w.r.t. the
- * parameters (host grad[4801]) and the loss, from the training kernel. */
+/* Gradient of the training loss over (X[B][8], T[B]) w.r.t. the parameters
+ * (host grad[4801]) and the loss, from the training kernel.  group == NULL:
+ * PM_OBJ_MSE.  Otherwise PM_OBJ_CENTRED with group[B] (host) = index within
+ * the step << 16 | the step's row count, the rows of a step consecutive and
+ * complete; codes that do not tile [0, B) that way give PM_EINVAL. */
 pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* model, const float* X, const float* T,
-                          uint64_t B, float* grad, double* loss);
+                          const uint32_t* group, uint64_t B, float* grad, double* loss);
 /* Record (features, target) pairs along trajectories first_traj ..
  * first_traj + count - 1 of `teacher` on one matrix; key = traj << 28 |
- * step << 14 | candidate.  Host outputs of capacity cap; *n_out = pairs kept. */
+ * step << 14 | candidate (live-candidate index).  A pair is kept if all its
+ * values are finite; a step's kept pairs are stored consecutively, and only
+ * if there are at least two; group (may be NULL) = index within the step's
+ * pairs << 16 | their count.  Host outputs of capacity cap (a step that does
+ * not fit is dropped, the order of steps is not deterministic); *n_out =
+ * pairs stored. */
 pm_status pm_record_pairs(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index,
                           uint64_t first_traj, uint32_t count, uint64_t seed,
                           const pm_schedule* teacher, uint64_t cap, float* feat, float* target,
-                          uint64_t* key, uint64_t* n_out);
+                          uint64_t* key, uint32_t* group, uint64_t* n_out);
 
 /* Statistics of a set of log-weights; fields as in pm_result. */
 typedef struct {

@@ -27,6 +27,7 @@ VR_MIN_DEGREE_2SIDED, VR_ROW_ORDER = 0, 1
 SK_NONE, SK_FIXED, SK_ADAPTIVE, SK_LOCAL = 0, 1, 2, 3
 DM_NONE, DM_ALL, DM_THRS, DM_TRCK = 0, 1, 2, 3
 PREC_FP32_PROPOSAL, PREC_FP64 = 0, 1
+OBJ_MSE, OBJ_CENTRED = 0, 1
 
 
 class PmError(RuntimeError):
@@ -49,7 +50,8 @@ class pm_schedule(C.Structure):
 class pm_train_cfg(C.Structure):
     _fields_ = [("n_pairs", C.c_uint64), ("seed", C.c_uint64), ("epochs", C.c_int32),
                 ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float), ("teacher", pm_schedule)]
+                ("eps", C.c_float), ("teacher", pm_schedule), ("objective", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class pm_train_report(C.Structure):
@@ -103,9 +105,9 @@ def _load():
     L.pm_model_train.argtypes = [P, P, C.POINTER(pm_csr), C.c_int32, C.POINTER(pm_train_cfg),
                                  C.POINTER(pm_train_report)]
     L.pm_mlp_forward.argtypes = [P, P, P, C.c_uint64, P]
-    L.pm_mlp_gradient.argtypes = [P, P, P, P, C.c_uint64, P, P]
+    L.pm_mlp_gradient.argtypes = [P, P, P, P, P, C.c_uint64, P, P]
     L.pm_record_pairs.argtypes = [P, C.POINTER(pm_csr), C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64,
-                                  C.POINTER(pm_schedule), C.c_uint64, P, P, P, P]
+                                  C.POINTER(pm_schedule), C.c_uint64, P, P, P, P, P]
     for name in ("pm_model_create", "pm_model_destroy", "pm_model_get_params", "pm_model_set_params",
                  "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs"):
         getattr(L, name).restype = C.c_int
@@ -295,13 +297,14 @@ class Context:
         f = np.zeros((cap, 8), dtype=np.float32)
         t = np.zeros(cap, dtype=np.float32)
         k = np.zeros(cap, dtype=np.uint64)
+        g = np.zeros(cap, dtype=np.uint32)
         n_out = C.c_uint64()
         s = teacher.c()
         self._check(_lib.pm_record_pairs(self.h, C.byref(c), matrix_index, first_traj, count, seed,
                                          C.byref(s), cap, f.ctypes.data, t.ctypes.data,
-                                         k.ctypes.data, C.byref(n_out)))
+                                         k.ctypes.data, g.ctypes.data, C.byref(n_out)))
         n = n_out.value
-        return f[:n], t[:n], k[:n]
+        return f[:n], t[:n], k[:n], g[:n]
 
     def model(self, params=None, seed: int = 0) -> "Model":
         return Model(self, params, seed)
@@ -370,24 +373,31 @@ class Model:
         self.ctx._check(_lib.pm_mlp_forward(self.ctx.h, self.h, x.ctypes.data, x.shape[0], out.ctypes.data))
         return out
 
-    def gradient(self, X, T):
+    def gradient(self, X, T, group=None):
+        """(loss, gradient): mean squared error, or with group codes (index
+        within the step << 16 | step size, steps consecutive) the per-step
+        centred loss."""
         x = np.ascontiguousarray(X, dtype=np.float32)
         t = np.ascontiguousarray(T, dtype=np.float32)
+        gr = None if group is None else np.ascontiguousarray(group, dtype=np.uint32)
         g = np.zeros(N_PARAM, dtype=np.float32)
         loss = C.c_double()
         self.ctx._check(_lib.pm_mlp_gradient(self.ctx.h, self.h, x.ctypes.data, t.ctypes.data,
-                                             x.shape[0], g.ctypes.data, C.byref(loss)))
+                                             None if gr is None else gr.ctypes.data, x.shape[0],
+                                             g.ctypes.data, C.byref(loss)))
         return loss.value, g
 
     def train(self, mats, teacher: Schedule, n_pairs: int, epochs: int = 2, batch: int = 4096,
-              lr: float = 2e-3, seed: int = 1) -> dict:
+              lr: float = 2e-3, seed: int = 1, objective: int = 1) -> dict:
+        """Record pairs from `teacher` on mats, then Adam on `objective`
+        (OBJ_MSE or OBJ_CENTRED, the default)."""
         cs, keeps = [], []
         for m in mats:
             c, k = make_csr(m)
             cs.append(c)
             keeps.append(k)
         arr = (pm_csr * len(cs))(*cs)
-        cfg = pm_train_cfg(n_pairs, seed, epochs, batch, lr, 0.9, 0.999, 1e-8, teacher.c())
+        cfg = pm_train_cfg(n_pairs, seed, epochs, batch, lr, 0.9, 0.999, 1e-8, teacher.c(), objective, 0)
         rep = pm_train_report()
         self.ctx._check(_lib.pm_model_train(self.ctx.h, self.h, arr, len(cs), C.byref(cfg), C.byref(rep)))
         return rep.as_dict()

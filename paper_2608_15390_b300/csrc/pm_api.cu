@@ -213,6 +213,7 @@ struct Run {
     float* rec_feat = nullptr;
     float* rec_target = nullptr;
     unsigned long long* rec_key = nullptr;
+    uint32_t* rec_group = nullptr;
     unsigned long long* rec_count = nullptr;
     unsigned long long rec_cap = 0;
     int32_t* ok_out = nullptr;
@@ -449,6 +450,7 @@ pm_status execute(pm_context* ctx, Run& R)
         tp.rec_feat = R.rec_feat;
         tp.rec_target = R.rec_target;
         tp.rec_key = R.rec_key;
+        tp.rec_group = R.rec_group;
         tp.rec_count = R.rec_count;
         tp.rec_cap = R.rec_cap;
         PM_CUDA(launch_trajectories(tp, grid, smem_need, R.trace, ctx->stream));
@@ -827,16 +829,37 @@ pm_status pm_mlp_forward(pm_context* ctx, const pm_model* m, const float* X, uin
     return PM_OK;
 }
 
-pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, const float* T, uint64_t B, float* grad,
-                          double* loss)
+// group codes (index within the group << 16 | group size) that tile rows
+// [0, B) with consecutive, complete groups
+static bool groups_valid(const uint32_t* g, uint64_t B)
+{
+    uint64_t r = 0;
+    while (r < B) {
+        const uint32_t size = g[r] & 0xFFFFu;
+        if ((g[r] >> 16) != 0 || size == 0 || r + size > B) return false;
+        for (uint32_t k = 0; k < size; ++k)
+            if (g[r + k] != ((k << 16) | size)) return false;
+        r += size;
+    }
+    return true;
+}
+
+pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, const float* T, const uint32_t* group,
+                          uint64_t B, float* grad, double* loss)
 {
     if (!ctx || !m || !X || !T || !grad || B == 0 || B > (1ull << 30)) return PM_EINVAL;
+    if (group && !groups_valid(group, B)) return fail(ctx, PM_EINVAL, "group codes do not tile the rows");
     PM_CUDA(cudaSetDevice(ctx->device));
-    DevBuf bx, bt, bp, bl;
+    DevBuf bx, bt, bp, bl, bg, br;
     PM_CUDA(cudaMalloc(&bx.p, 32 * B));
     PM_CUDA(cudaMalloc(&bt.p, 4 * B));
     PM_CUDA(cudaMalloc(&bp.p, 4 * B));
     PM_CUDA(cudaMalloc(&bl.p, 8));
+    if (group) {
+        PM_CUDA(cudaMalloc(&bg.p, 4 * B));
+        PM_CUDA(cudaMalloc(&br.p, 4 * B));
+        PM_CUDA(cudaMemcpyAsync(bg.p, group, 4 * B, cudaMemcpyHostToDevice, ctx->stream));
+    }
     std::vector<int> perm(B);
     for (uint64_t i = 0; i < B; ++i) perm[i] = (int)i;
     PM_CUDA(cudaMemcpyAsync(bx.p, X, 32 * B, cudaMemcpyHostToDevice, ctx->stream));
@@ -844,8 +867,8 @@ pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, co
     PM_CUDA(cudaMemcpyAsync(bp.p, perm.data(), 4 * B, cudaMemcpyHostToDevice, ctx->stream));
     PM_CUDA(cudaMemsetAsync(m->grad, 0, 4 * model_param_count(), ctx->stream));
     PM_CUDA(cudaMemsetAsync(bl.p, 0, 8, ctx->stream));
-    PM_CUDA(launch_mlp_grad(m->img, (const float*)bx.p, (const float*)bt.p, (const int*)bp.p, 0, (int)B, m->grad,
-                            (double*)bl.p, ctx->sm_count, ctx->stream));
+    PM_CUDA(launch_mlp_grad(m->img, (const float*)bx.p, (const float*)bt.p, (const int*)bp.p, 0, (int)B,
+                            (const uint32_t*)bg.p, (float*)br.p, m->grad, (double*)bl.p, ctx->sm_count, ctx->stream));
     PM_CUDA(cudaMemcpyAsync(grad, m->grad, 4 * model_param_count(), cudaMemcpyDeviceToHost, ctx->stream));
     double l = 0;
     PM_CUDA(cudaMemcpyAsync(&l, bl.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -857,8 +880,8 @@ pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, co
 // record pairs of one or more matrices into device buffers (trajectory kernel in record mode)
 static pm_status record_into(pm_context* ctx, const pm_csr* mats, int32_t count, const uint64_t* ntraj,
                              uint64_t first, uint32_t matrix_index0, uint64_t seed, const pm_schedule* teacher,
-                             float* dfeat, float* dtarget, unsigned long long* dkey, unsigned long long* dcount,
-                             unsigned long long cap)
+                             float* dfeat, float* dtarget, unsigned long long* dkey, uint32_t* dgroup,
+                             unsigned long long* dcount, unsigned long long cap)
 {
     Run R;
     R.mats = mats;
@@ -871,6 +894,7 @@ static pm_status record_into(pm_context* ctx, const pm_csr* mats, int32_t count,
     R.rec_feat = dfeat;
     R.rec_target = dtarget;
     R.rec_key = dkey;
+    R.rec_group = dgroup;
     R.rec_count = dcount;
     R.rec_cap = cap;
     std::vector<pm_result> outs(count);
@@ -889,7 +913,7 @@ static pm_status check_teacher(pm_context* ctx, const pm_schedule* t)
 
 pm_status pm_record_pairs(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index, uint64_t first_traj, uint32_t count,
                           uint64_t seed, const pm_schedule* teacher, uint64_t cap, float* feat, float* target,
-                          uint64_t* key, uint64_t* n_out)
+                          uint64_t* key, uint32_t* group, uint64_t* n_out)
 {
     if (!ctx || !csr || !feat || !target || !key || !n_out || cap == 0 || count == 0 || matrix_index > 0xFFFF)
         return PM_EINVAL;
@@ -898,22 +922,24 @@ pm_status pm_record_pairs(pm_context* ctx, const pm_csr* csr, uint32_t matrix_in
     st = check_csr(ctx, csr);
     if (st != PM_OK) return st;
     PM_CUDA(cudaSetDevice(ctx->device));
-    DevBuf bf, bt, bk, bc;
+    DevBuf bf, bt, bk, bg, bc;
     PM_CUDA(cudaMalloc(&bf.p, 32 * cap));
     PM_CUDA(cudaMalloc(&bt.p, 4 * cap));
     PM_CUDA(cudaMalloc(&bk.p, 8 * cap));
-    PM_CUDA(cudaMalloc(&bc.p, 8));
-    PM_CUDA(cudaMemsetAsync(bc.p, 0, 8, ctx->stream));
+    PM_CUDA(cudaMalloc(&bg.p, 4 * cap));
+    PM_CUDA(cudaMalloc(&bc.p, 16));
+    PM_CUDA(cudaMemsetAsync(bc.p, 0, 16, ctx->stream));
     const uint64_t nt = count;
     st = record_into(ctx, csr, 1, &nt, first_traj, matrix_index, seed, teacher, (float*)bf.p, (float*)bt.p,
-                     (unsigned long long*)bk.p, (unsigned long long*)bc.p, cap);
+                     (unsigned long long*)bk.p, (uint32_t*)bg.p, (unsigned long long*)bc.p, cap);
     if (st != PM_OK) return st;
-    unsigned long long c = 0;
-    PM_CUDA(cudaMemcpy(&c, bc.p, 8, cudaMemcpyDeviceToHost));
-    const uint64_t kept = std::min<uint64_t>(c, cap);
+    unsigned long long c[2] = {0, 0};
+    PM_CUDA(cudaMemcpy(c, bc.p, 16, cudaMemcpyDeviceToHost));
+    const uint64_t kept = std::min<uint64_t>(c[1], cap);  // the filled prefix
     PM_CUDA(cudaMemcpy(feat, bf.p, 32 * kept, cudaMemcpyDeviceToHost));
     PM_CUDA(cudaMemcpy(target, bt.p, 4 * kept, cudaMemcpyDeviceToHost));
     PM_CUDA(cudaMemcpy(key, bk.p, 8 * kept, cudaMemcpyDeviceToHost));
+    if (group) PM_CUDA(cudaMemcpy(group, bg.p, 4 * kept, cudaMemcpyDeviceToHost));
     *n_out = kept;
     return PM_OK;
 }
@@ -922,7 +948,8 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
                          pm_train_report* report)
 {
     if (!ctx || !m || !mats || count < 1 || count > 65535 || !cfg || cfg->n_pairs == 0 || cfg->epochs < 1 ||
-        cfg->batch < 16 || cfg->n_pairs > (1ull << 31))
+        cfg->batch < 16 || cfg->n_pairs > (1ull << 31) || (cfg->objective != PM_OBJ_MSE && cfg->objective != PM_OBJ_CENTRED) ||
+        cfg->reserved != 0)
         return fail(ctx, PM_EINVAL, "bad training arguments");
     pm_status st = check_teacher(ctx, &cfg->teacher);
     if (st != PM_OK) return st;
@@ -933,28 +960,30 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
     PM_CUDA(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
     const uint64_t cap = cfg->n_pairs;
-    DevBuf bf, bt, bk, bc, bp, bl;
+    const bool centred = cfg->objective == PM_OBJ_CENTRED;
+    DevBuf bf, bt, bk, bg, bc, bp, bl, br;
     PM_CUDA(cudaMalloc(&bf.p, 32 * cap));
     PM_CUDA(cudaMalloc(&bt.p, 4 * cap));
     PM_CUDA(cudaMalloc(&bk.p, 8 * cap));
-    PM_CUDA(cudaMalloc(&bc.p, 8));
-    PM_CUDA(cudaMemsetAsync(bc.p, 0, 8, ctx->stream));
+    PM_CUDA(cudaMalloc(&bg.p, 4 * cap));
+    PM_CUDA(cudaMalloc(&bc.p, 16));
+    PM_CUDA(cudaMemsetAsync(bc.p, 0, 16, ctx->stream));
     // record until the buffer is full: about 2 pairs per step and trajectory
     uint64_t first = 0;
-    unsigned long long have = 0;
-    for (int round = 0; round < 64 && have < cap; ++round) {
+    unsigned long long cnt[2] = {0, 0};
+    for (int round = 0; round < 64 && cnt[0] < cap; ++round) {
         std::vector<uint64_t> nt(count);
         for (int k = 0; k < count; ++k) {
             const uint64_t per_traj = 2ull * (uint64_t)mats[k].n;
-            nt[k] = std::max<uint64_t>(1, (cap - have) / ((uint64_t)count * per_traj) + 1);
+            nt[k] = std::max<uint64_t>(1, (cap - cnt[1]) / ((uint64_t)count * per_traj) + 1);
         }
         st = record_into(ctx, mats, count, nt.data(), first, 0, cfg->seed, &cfg->teacher, (float*)bf.p, (float*)bt.p,
-                         (unsigned long long*)bk.p, (unsigned long long*)bc.p, cap);
+                         (unsigned long long*)bk.p, (uint32_t*)bg.p, (unsigned long long*)bc.p, cap);
         if (st != PM_OK) return st;
-        PM_CUDA(cudaMemcpy(&have, bc.p, 8, cudaMemcpyDeviceToHost));
+        PM_CUDA(cudaMemcpy(cnt, bc.p, 16, cudaMemcpyDeviceToHost));
         first += *std::max_element(nt.begin(), nt.end());
     }
-    const uint64_t N = std::min<uint64_t>(have, cap);
+    const uint64_t N = std::min<uint64_t>(cnt[1], cap);  // the filled prefix: whole steps only
     const auto t1 = std::chrono::steady_clock::now();
     if (N < 16) return fail(ctx, PM_EINVAL, "the teacher produced too few pairs");
     // start the output bias at the mean target
@@ -968,25 +997,55 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
         PM_CUDA(cudaMemcpy(m->master + 4800, &b3, 4, cudaMemcpyHostToDevice));
         PM_CUDA(launch_model_image(m->master, m->img, ctx->stream));
     }
-    // shuffled order
-    std::vector<int> perm(N);
-    for (uint64_t i = 0; i < N; ++i) perm[i] = (int)i;
+    // shuffled order and batches: single pairs for the squared error; whole
+    // steps (kept consecutive, batches cut between steps) for the centred loss
     std::mt19937_64 rng(cfg->seed ^ 0x9E3779B97F4A7C15ull);
-    std::shuffle(perm.begin(), perm.end(), rng);
+    std::vector<int> perm;
+    std::vector<uint64_t> cuts;  // batch b = perm[cuts[b] .. cuts[b + 1])
+    perm.reserve(N);
+    if (centred) {
+        std::vector<uint32_t> gc(N);
+        PM_CUDA(cudaMemcpy(gc.data(), bg.p, 4 * N, cudaMemcpyDeviceToHost));
+        std::vector<uint64_t> starts;
+        for (uint64_t i = 0; i < N;) {
+            const uint32_t size = gc[i] & 0xFFFFu;
+            if ((gc[i] >> 16) != 0 || size == 0 || i + size > N) return fail(ctx, PM_EDEVICE, "recorded groups are torn");
+            starts.push_back(i);
+            i += size;
+        }
+        std::shuffle(starts.begin(), starts.end(), rng);
+        cuts.push_back(0);
+        for (uint64_t s0 : starts) {
+            const uint32_t size = gc[s0] & 0xFFFFu;
+            if (perm.size() - cuts.back() + size > (uint64_t)cfg->batch && perm.size() > cuts.back())
+                cuts.push_back(perm.size());
+            for (uint32_t k = 0; k < size; ++k) perm.push_back((int)(s0 + k));
+        }
+        cuts.push_back(perm.size());
+    } else {
+        for (uint64_t i = 0; i < N; ++i) perm.push_back((int)i);
+        std::shuffle(perm.begin(), perm.end(), rng);
+        for (uint64_t r = 0; r < N; r += (uint64_t)cfg->batch) cuts.push_back(r);
+        cuts.push_back(N);
+    }
+    uint64_t max_batch = 0;
+    for (size_t b = 0; b + 1 < cuts.size(); ++b) max_batch = std::max<uint64_t>(max_batch, cuts[b + 1] - cuts[b]);
     PM_CUDA(cudaMalloc(&bp.p, 4 * N));
     PM_CUDA(cudaMemcpy(bp.p, perm.data(), 4 * N, cudaMemcpyHostToDevice));
-    const uint64_t steps_per_epoch = (N + cfg->batch - 1) / cfg->batch;
+    if (centred) PM_CUDA(cudaMalloc(&br.p, 4 * max_batch));
+    const uint64_t steps_per_epoch = cuts.size() - 1;
     const uint64_t total_steps = steps_per_epoch * (uint64_t)cfg->epochs;
     PM_CUDA(cudaMalloc(&bl.p, 8 * total_steps));
     PM_CUDA(cudaMemsetAsync(bl.p, 0, 8 * total_steps, ctx->stream));
     uint64_t sidx = 0;
     for (int ep = 0; ep < cfg->epochs; ++ep) {
         for (uint64_t b = 0; b < steps_per_epoch; ++b, ++sidx) {
-            const uint64_t row0 = b * (uint64_t)cfg->batch;
-            const int B = (int)std::min<uint64_t>((uint64_t)cfg->batch, N - row0);
+            const uint64_t row0 = cuts[b];
+            const int B = (int)(cuts[b + 1] - cuts[b]);
             PM_CUDA(cudaMemsetAsync(m->grad, 0, 4 * model_param_count(), ctx->stream));
             PM_CUDA(launch_mlp_grad(m->img, (const float*)bf.p, (const float*)bt.p, (const int*)bp.p, (int64_t)row0, B,
-                                    m->grad, (double*)bl.p + sidx, ctx->sm_count, ctx->stream));
+                                    centred ? (const uint32_t*)bg.p : nullptr, (float*)br.p, m->grad,
+                                    (double*)bl.p + sidx, ctx->sm_count, ctx->stream));
             ++m->step;
             PM_CUDA(launch_adam(m->master, m->m1, m->m2, m->grad, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, m->step,
                                 m->img, ctx->stream));

@@ -184,7 +184,8 @@ struct TrajParams {
     float* rec_feat;          // [cap][8]
     float* rec_target;        // [cap]
     unsigned long long* rec_key;   // [cap]: traj << 28 | step << 14 | candidate
-    unsigned long long* rec_count;
+    uint32_t* rec_group;      // [cap]: index within the step's pairs << 16 | their count
+    unsigned long long* rec_count;  // [2]: slots claimed, end of the filled prefix
     unsigned long long rec_cap;
 };
 
@@ -243,8 +244,11 @@ int model_image_bytes();
 int model_infer_bytes();
 int model_param_count();
 cudaError_t launch_model_image(const float* master, void* img, cudaStream_t st);
+// group == nullptr: mean squared error; else the per-step centred loss (resid:
+// device scratch of B floats for the batch's residuals)
 cudaError_t launch_mlp_grad(const void* img, const float* feat, const float* target, const int* perm, int64_t row0,
-                            int B, float* grad, double* loss, int sm_count, cudaStream_t st);
+                            int B, const uint32_t* group, float* resid, float* grad, double* loss, int sm_count,
+                            cudaStream_t st);
 cudaError_t launch_mlp_forward(const void* img, const float* feat, int B, float* out, int sm_count, cudaStream_t st);
 cudaError_t launch_adam(float* master, float* m1, float* m2, const float* grad, float lr, float b1, float b2, float eps,
                         int step, void* img, cudaStream_t st);

@@ -3,8 +3,12 @@
 // cores (mma.sync.m16n8k16, FP32 accumulation); Adam keeps FP32 master
 // weights and refreshes the BF16 device image after every step.
 //
-// Loss: mean squared error between the network output and the SK target
-// ln(r_v c_l) of the recorded (features, target) pairs.
+// Losses on the recorded (features, target) pairs, target = the SK scale
+// product ln(r_v c_l): the mean squared error, or the per-step centred squared
+// error, which removes each step's mean residual first (the proposal of Eq. 3
+// normalises a step's scores, so a step-wide offset of the logits is
+// invisible to it).  For the latter a forward pass writes the residuals of
+// the batch, and the backward kernel reads its group's mean from them.
 #include <cmath>
 #include "pm_mlp.cuh"
 
@@ -43,11 +47,16 @@ struct TrainSmem {
     uint16_t xt[8 * kTrainRows];      // [feature][row]
 };
 
-// Gradient of the mean squared error over rows perm[row0 .. row0 + B) of
-// (feat, target), accumulated into grad[kNParam] (FP32 atomics) and loss.
+// Gradient of the loss over rows perm[row0 .. row0 + B) of (feat, target),
+// accumulated into grad[kNParam] (FP32 atomics) and loss.  resid == nullptr:
+// mean squared error.  Otherwise the centred loss: resid[r] is the residual
+// of batch row r (from mlp_resid_kernel, the same forward), group[] the group
+// code of a pair (index within its step << 16 | the step's pair count), and
+// the rows of a step are consecutive in the batch.
 __global__ void __launch_bounds__(kTrainWarps * 32) mlp_grad_kernel(const DevModel* Mg, const float* feat,
                                                                     const float* target, const int* perm,
                                                                     int64_t row0, int B, float inv_b,
+                                                                    const float* resid, const uint32_t* group,
                                                                     float* grad, double* loss_out)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -113,11 +122,26 @@ __global__ void __launch_bounds__(kTrainWarps * 32) mlp_grad_kernel(const DevMod
                 S.h1t[(c + 8) * kTrainRows + lr0 + g + 8] = (uint16_t)(K.h1[kk][3] & 0xFFFFu);
                 S.h1t[(c + 9) * kTrainRows + lr0 + g + 8] = (uint16_t)(K.h1[kk][3] >> 16);
             }
-            // output gradient dL/dy = 2 (y - target) / B
+            // output gradient dL/dy = 2 e / B, e the (centred) residual
+            auto centred = [&](int r) -> float {
+                const uint32_t code = group[perm[row0 + r]];
+                const int q = (int)(code >> 16), size = (int)(code & 0xFFFFu);
+                float mean = 0.f;
+                for (int k = 0; k < size; ++k) mean += resid[r - q + k];
+                return resid[r] - mean / (float)size;
+            };
             float dy_lo = 0.f, dy_hi = 0.f;
             if (t == 0) {
-                if (v_g) { const float e = y_lo - t_g; dy_lo = 2.f * e * inv_b; loss += (double)e * e * inv_b; }
-                if (v_g8) { const float e = y_hi - t_g8; dy_hi = 2.f * e * inv_b; loss += (double)e * e * inv_b; }
+                if (v_g) {
+                    const float e = resid ? centred(r_g) : y_lo - t_g;
+                    dy_lo = 2.f * e * inv_b;
+                    loss += (double)e * e * inv_b;
+                }
+                if (v_g8) {
+                    const float e = resid ? centred(r_g8) : y_hi - t_g8;
+                    dy_hi = 2.f * e * inv_b;
+                    loss += (double)e * e * inv_b;
+                }
                 acc_b3 += dy_lo + dy_hi;
             }
             dy_lo = __shfl_sync(kFull, dy_lo, g * 4);
@@ -264,6 +288,45 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const DevModel* Mg, co
     }
 }
 
+// residuals y - target of rows perm[row0 .. row0 + B) (one warp per 16-row
+// tile), the forward of mlp_grad_kernel without its bookkeeping
+__global__ void __launch_bounds__(128) mlp_resid_kernel(const DevModel* Mg, const float* feat, const float* target,
+                                                        const int* perm, int64_t row0, int B, float* resid)
+{
+    __shared__ __align__(16) uint8_t mraw[kModelInferBytes + 16];
+    DevModel* M = reinterpret_cast<DevModel*>(mraw);
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(Mg);
+        uint4* dst = reinterpret_cast<uint4*>(mraw);
+        for (int q = threadIdx.x; q < (kModelInferBytes + 15) / 16; q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < B; tile += warps) {
+        const int r0 = tile * 16 + g, r1 = r0 + 8;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
+        int64_t s0 = 0, s1 = 0;
+        if (r0 < B) {
+            s0 = perm[row0 + r0];
+            x0 = feat[s0 * kNF + 2 * t];
+            x1 = feat[s0 * kNF + 2 * t + 1];
+        }
+        if (r1 < B) {
+            s1 = perm[row0 + r1];
+            x2 = feat[s1 * kNF + 2 * t];
+            x3 = feat[s1 * kNF + 2 * t + 1];
+        }
+        uint32_t a[4] = {pack_bf16(x0, x1), pack_bf16(x2, x3), 0u, 0u};
+        float ylo, yhi;
+        mlp_fwd_tile<false>(M, a, lane, ylo, yhi, nullptr);
+        if (t == 0) {
+            if (r0 < B) resid[r0] = ylo - target[s0];
+            if (r1 < B) resid[r1] = yhi - target[s1];
+        }
+    }
+}
+
 // Adam on the FP32 master weights, then the BF16 device image
 __global__ void adam_kernel(float* master, float* m1, float* m2, const float* grad, float lr, float b1, float b2,
                             float eps, float c1, float c2, DevModel* img)
@@ -326,15 +389,23 @@ cudaError_t launch_model_image(const float* master, void* img, cudaStream_t st)
 }
 
 cudaError_t launch_mlp_grad(const void* img, const float* feat, const float* target, const int* perm, int64_t row0,
-                            int B, float* grad, double* loss, int sm_count, cudaStream_t st)
+                            int B, const uint32_t* group, float* resid, float* grad, double* loss, int sm_count,
+                            cudaStream_t st)
 {
+    const DevModel* M = reinterpret_cast<const DevModel*>(img);
+    if (group) {  // centred loss: the batch's residuals first
+        const int tiles = (B + 15) / 16;
+        int rg = (tiles + 3) / 4;
+        if (rg > 4 * sm_count) rg = 4 * sm_count;
+        mlp_resid_kernel<<<rg, 128, 0, st>>>(M, feat, target, perm, row0, B, resid);
+    }
     const int smem = (int)sizeof(TrainSmem);
     cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int iters = (B + kTrainRows - 1) / kTrainRows;
     const int grid = iters < 2 * sm_count ? iters : 2 * sm_count;
-    mlp_grad_kernel<<<grid, kTrainWarps * 32, smem, st>>>(reinterpret_cast<const DevModel*>(img), feat, target, perm,
-                                                           row0, B, 1.0f / (float)B, grad, loss);
+    mlp_grad_kernel<<<grid, kTrainWarps * 32, smem, st>>>(M, feat, target, perm, row0, B, 1.0f / (float)B,
+                                                           group ? resid : nullptr, group, grad, loss);
     return cudaGetLastError();
 }
 

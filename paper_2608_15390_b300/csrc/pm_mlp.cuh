@@ -1,11 +1,14 @@
 // pm_mlp.cuh -- the learned proposal's network (8 -> 64 -> 64 -> 1, tanh-GELU) on
 // BF16 tensor cores with FP32 accumulation, and its binary32 score exponent.
 //
-// A 16-row tile goes through the three layers as mma.sync.m16n8k16 operations;
-// the FP32 accumulator fragments of one layer become the BF16 A fragments of
-// the next without leaving registers (the accumulator of n-tiles 2k, 2k+1 is
-// exactly the A fragment of k-tile k).  Weights sit in shared memory in the
-// [out][in] row-major layout, so every B fragment is one 32-bit load.
+// Training: a 16-row tile goes through the three layers as mma.sync.m16n8k16
+// operations; the FP32 accumulator fragments of one layer become the BF16 A
+// fragments of the next without leaving registers (the accumulator of n-tiles
+// 2k, 2k+1 is exactly the A fragment of k-tile k).  Inference inside the
+// trajectory kernel runs transposed (hidden units x 8 candidates, see
+// mlp_infer8).  Weights sit in shared memory in the [out][in] row-major
+// layout, so every B fragment is one 32-bit load and every A fragment of the
+// transposed form one ldmatrix.
 #pragma once
 #include <cuda_bf16.h>
 #include "pm_device.cuh"
@@ -172,81 +175,66 @@ __device__ __forceinline__ void mlp_fwd_tile(const DevModel* M, const uint32_t (
     y_hi = acc3[2];
 }
 
-// Inference forward of one 16-row tile with layer 3 folded into the layer-2
-// loop (each k-tile of the second hidden layer feeds the output mma as soon as
-// it exists), so only one of its four A fragments is live at a time.
-__device__ __forceinline__ void mlp_infer_tile(const DevModel* M, const uint32_t (&a)[4], int lane, float& y_lo,
-                                               float& y_hi)
+// 8x8 transpose of a bf16 fragment (row lane/4, columns 2(lane%4), +1)
+__device__ __forceinline__ uint32_t trans8x8(uint32_t x)
 {
-    const int g = lane >> 2, t = lane & 3;
-    uint32_t h[4][4];
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        float acc[2][4];
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int j = 2 * kk + jj;
-            const float c0 = M->b1[8 * j + 2 * t], c1 = M->b1[8 * j + 2 * t + 1];
-            acc[jj][0] = c0; acc[jj][1] = c1; acc[jj][2] = c0; acc[jj][3] = c1;
-            mma16816(acc[jj], a, ld32(M->w1p + (8 * j + g) * kW1S + 2 * t), ld32(M->w1p + (8 * j + g) * kW1S + 2 * t + 8));
-        }
-        h[kk][0] = pack_bf16(gelu_f(acc[0][0]), gelu_f(acc[0][1]));
-        h[kk][1] = pack_bf16(gelu_f(acc[0][2]), gelu_f(acc[0][3]));
-        h[kk][2] = pack_bf16(gelu_f(acc[1][0]), gelu_f(acc[1][1]));
-        h[kk][3] = pack_bf16(gelu_f(acc[1][2]), gelu_f(acc[1][3]));
-    }
-    float acc3[4];
-    acc3[0] = (t == 0) ? M->b3[0] : 0.0f;
-    acc3[1] = 0.0f;
-    acc3[2] = acc3[0];
-    acc3[3] = 0.0f;
-#pragma unroll 1
-    for (int k2 = 0; k2 < 4; ++k2) {
-        float acc[2][4];
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int j = 2 * k2 + jj;
-            const float c0 = M->b2[8 * j + 2 * t], c1 = M->b2[8 * j + 2 * t + 1];
-            acc[jj][0] = c0; acc[jj][1] = c1; acc[jj][2] = c0; acc[jj][3] = c1;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma16816(acc[jj], h[kk], ld32(M->w2 + (8 * j + g) * kWS + 16 * kk + 2 * t),
-                         ld32(M->w2 + (8 * j + g) * kWS + 16 * kk + 2 * t + 8));
-        }
-        uint32_t h2[4];
-        h2[0] = pack_bf16(gelu_f(acc[0][0]), gelu_f(acc[0][1]));
-        h2[1] = pack_bf16(gelu_f(acc[0][2]), gelu_f(acc[0][3]));
-        h2[2] = pack_bf16(gelu_f(acc[1][0]), gelu_f(acc[1][1]));
-        h2[3] = pack_bf16(gelu_f(acc[1][2]), gelu_f(acc[1][3]));
-        mma16816(acc3, h2, ld32(M->w3p + g * kWS + 16 * k2 + 2 * t), ld32(M->w3p + g * kWS + 16 * k2 + 2 * t + 8));
-    }
-    y_lo = acc3[0];
-    y_hi = acc3[2];
+    uint32_t y;
+    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;\n" : "=r"(y) : "r"(x));
+    return y;
 }
 
-// Inference for 32 rows of features (bf16 [32][kFS] in shared memory, features
-// 8..15 zero): returns the output of row `lane` in lane `lane`.
-// Rows 16..31 are skipped when none of them is live (the picked vertex of a
-// minimum-degree step rarely has more than 16 live candidates).
-__device__ __forceinline__ float mlp_infer32(const DevModel* M, const uint16_t* feat, int lane, bool live)
+// A fragment (16 x 16 bf16, row-major with stride kWS) of shared memory by one
+// ldmatrix.x4: lane l supplies row (l & 7) + 8 ((l >> 3) & 1), column
+// 8 (l >> 4); the four 8x8 matrices come back as a0..a3 of mma.m16n8k16
+__device__ __forceinline__ void ldsm_a(uint32_t (&a)[4], const uint16_t* tile, int lane)
+{
+    const uint16_t* p = tile + ((lane & 7) + 8 * ((lane >> 3) & 1)) * kWS + 8 * (lane >> 4);
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr));
+}
+
+// Inference for up to 8 candidates, transposed: the hidden units are the M
+// dimension (four 16-row m-tiles) and the candidates the N dimension (8), so
+// a minimum-degree step, which has 2 or 3 live candidates most of the time,
+// pays for 8 columns instead of a 16-row tile.  Features are rows 0..7 of
+// `feat` (bf16 [8][kFS], model and features in shared memory).  An
+// accumulator fragment of hidden units x candidates, packed to bf16 and
+// transposed 8x8 by movmatrix, is exactly the B fragment of the next layer
+// (and the A fragment of the output layer).  Returns the output of candidate
+// lane >> 2 in lanes with (lane & 3) == 0.
+__device__ __forceinline__ float mlp_infer8(const DevModel* M, const uint16_t* feat, int lane)
 {
     const int g = lane >> 2, t = lane & 3;
-    float lo[2] = {0.f, 0.f}, hi[2] = {0.f, 0.f};
-    const int tiles = (__ballot_sync(kFull, live) >> 16) ? 2 : 1;
-#pragma unroll 1
-    for (int mt = 0; mt < tiles; ++mt) {
-        const uint16_t* F = feat + mt * 16 * kFS;
-        uint32_t a[4] = {ld32(F + g * kFS + 2 * t), ld32(F + (g + 8) * kFS + 2 * t), ld32(F + g * kFS + 2 * t + 8),
-                         ld32(F + (g + 8) * kFS + 2 * t + 8)};
-        float ylo, yhi;
-        mlp_infer_tile(M, a, lane, ylo, yhi);
-        if (mt == 0) { lo[0] = ylo; hi[0] = yhi; } else { lo[1] = ylo; hi[1] = yhi; }
+    const uint32_t xb = ld32(feat + g * kFS + 2 * t);  // features 2t, 2t+1 of candidate g
+    uint32_t hb[4][2];
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+        const int h0 = 16 * mt + g;
+        float acc[4] = {M->b1[h0], M->b1[h0], M->b1[h0 + 8], M->b1[h0 + 8]};
+        const uint32_t a[4] = {ld32(M->w1p + h0 * kW1S + 2 * t), ld32(M->w1p + (h0 + 8) * kW1S + 2 * t), 0u, 0u};
+        mma16816(acc, a, xb, 0u);
+        hb[mt][0] = trans8x8(pack_bf16(gelu_f(acc[0]), gelu_f(acc[1])));
+        hb[mt][1] = trans8x8(pack_bf16(gelu_f(acc[2]), gelu_f(acc[3])));
     }
-    const int rr = lane & 15, src = (rr & 7) * 4;
-    const float l0 = __shfl_sync(kFull, lo[0], src), h0 = __shfl_sync(kFull, hi[0], src);
-    const float l1 = __shfl_sync(kFull, lo[1], src), h1 = __shfl_sync(kFull, hi[1], src);
-    const float r0 = rr < 8 ? l0 : h0, r1 = rr < 8 ? l1 : h1;
-    return lane < 16 ? r0 : r1;
+    float acc3[4] = {t == 0 ? M->b3[0] : 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int mt = 0; mt < 4; ++mt) {
+        const int h0 = 16 * mt + g;
+        float acc[4] = {M->b2[h0], M->b2[h0], M->b2[h0 + 8], M->b2[h0 + 8]};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            uint32_t a[4];
+            ldsm_a(a, M->w2 + 16 * mt * kWS + 16 * kk, lane);
+            mma16816(acc, a, hb[kk][0], hb[kk][1]);
+        }
+        // output layer: rows = candidates (8 of 16 used), k = these 16 hidden units
+        const uint32_t a3[4] = {trans8x8(pack_bf16(gelu_f(acc[0]), gelu_f(acc[1]))), 0u,
+                                trans8x8(pack_bf16(gelu_f(acc[2]), gelu_f(acc[3]))), 0u};
+        mma16816(acc3, a3, ld32(M->w3p + g * kWS + 16 * mt + 2 * t), ld32(M->w3p + g * kWS + 16 * mt + 2 * t + 8));
+    }
+    return acc3[0];
 }
 
 }  // namespace pm

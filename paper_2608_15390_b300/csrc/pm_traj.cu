@@ -484,19 +484,30 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     for (int o = 16; o; o >>= 1) sv_i += __shfl_xor_sync(kFull, sv_i, o);
                     sum_v = (float)sv_i;
                 }
+                // logits of the live candidates of one chunk: their features
+                // go to rows 0..nl-1 of the tile (live order), the network
+                // runs on 8 candidates at a time
                 auto cand_logit = [&](int e, int pp, bool live) -> float {
-                    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                    if (live) cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
-                    uint4 lo;
-                    lo.x = pack_bf16(f[0], f[1]);
-                    lo.y = pack_bf16(f[2], f[3]);
-                    lo.z = pack_bf16(f[4], f[5]);
-                    lo.w = pack_bf16(f[6], f[7]);
-                    uint4* row = reinterpret_cast<uint4*>(feat + lane * kFS);
-                    row[0] = lo;
-                    row[1] = make_uint4(0u, 0u, 0u, 0u);
+                    const unsigned lmk = __ballot_sync(kFull, live);
+                    const int nl = __popc(lmk);
+                    const int li = __popc(lmk & ((1u << lane) - 1u));
+                    if (live) {
+                        float f[8];
+                        cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
+                        uint4 lo;
+                        lo.x = pack_bf16(f[0], f[1]);
+                        lo.y = pack_bf16(f[2], f[3]);
+                        lo.z = pack_bf16(f[4], f[5]);
+                        lo.w = pack_bf16(f[6], f[7]);
+                        *reinterpret_cast<uint4*>(feat + li * kFS) = lo;
+                    }
                     __syncwarp();
-                    const float lg = mlp_infer32(Ms, feat, lane, live);
+                    float lg = 0.f;
+                    for (int tile = 0; 8 * tile < nl; ++tile) {
+                        const float y = mlp_infer8(Ms, feat + 8 * tile * kFS, lane);
+                        const float yv = __shfl_sync(kFull, y, 4 * (li & 7));
+                        if (live && (li >> 3) == tile) lg = yv;
+                    }
                     __syncwarp();
                     return lg;
                 };
@@ -509,46 +520,85 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     if (!(sv >= (Real)0)) sv = 0;
                     return sv;
                 };
-                // recording of (features, SK target) pairs and of trace logits
+                // trace logits of the live candidates (learned proposal)
                 auto side_outputs = [&](int e, int pp, bool live, float lg, int live_base) {
                     const unsigned lmk = __ballot_sync(kFull, live);
                     const int li = live_base + __popc(lmk & ((1u << lane) - 1u));
                     if (TRACE && model && live && li < 32) P.trace_logits[(gq * n + t) * 32 + li] = lg;
-                    if (rec) {
-                        // a pair is kept only if every value is finite (an SK
-                        // scale can run to 0 or infinity without total support)
-                        float f[8];
-                        float tgt = 0.f;
-                        bool keep = false;
-                        if (live) {
-                            cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
-                            const double sv_cur = vrow ? (double)r[vi] : (double)c[vi];
-                            const double sl_cur = vrow ? (double)c[pp] : (double)r[pp];
-                            tgt = (float)log(sv_cur * sl_cur);
-                            keep = isfinite(tgt);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) keep = keep && isfinite(f[q]);
-                        }
-                        const unsigned km2 = __ballot_sync(kFull, keep);
-                        unsigned long long base0 = 0;
-                        if (lane == 0 && km2) base0 = atomicAdd(P.rec_count, (unsigned long long)__popc(km2));
-                        base0 = __shfl_sync(kFull, base0, 0);
-                        const unsigned long long pos = base0 + __popc(km2 & ((1u << lane) - 1u));
-                        if (keep && pos < P.rec_cap) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) P.rec_feat[pos * 8 + q] = f[q];
-                            P.rec_target[pos] = tgt;
-                            P.rec_key[pos] = (traj << 28) | ((unsigned long long)t << 14) | (unsigned long long)li;
-                        }
-                    }
                     return __popc(lmk);
                 };
+                // recording of (features, SK target) pairs: a pair is kept
+                // only if every value is finite (an SK scale can run to 0 or
+                // infinity without total support); a step's kept pairs are
+                // written together as one group, and only if there are at
+                // least two (pass 1 counts them, pass 2 writes them)
+                if (rec) {
+                    auto pair_at = [&](int e, int pp, bool live, float (&f)[8], float& tgt) -> bool {
+                        if (!live) return false;
+                        cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
+                        const double sv_cur = vrow ? (double)r[vi] : (double)c[vi];
+                        const double sl_cur = vrow ? (double)c[pp] : (double)r[pp];
+                        tgt = (float)log(sv_cur * sl_cur);
+                        bool keep = isfinite(tgt);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) keep = keep && isfinite(f[q]);
+                        return keep;
+                    };
+                    int kept = 0;
+                    for (int base = beg; base < end; base += 32) {
+                        const int e = base + lane;
+                        int pp = 0;
+                        bool live = false;
+                        if (e < end) {
+                            pp = adj[e];
+                            live = entry_live(deg, mask, V, vrow, e, pp + poff);
+                        }
+                        float f[8], tgt = 0.f;
+                        kept += __popc(__ballot_sync(kFull, pair_at(e, pp, live, f, tgt)));
+                    }
+                    if (kept >= 2) {
+                        unsigned long long b0 = 0;
+                        if (lane == 0) b0 = atomicAdd(P.rec_count, (unsigned long long)kept);
+                        b0 = __shfl_sync(kFull, b0, 0);
+                        if (b0 + (unsigned long long)kept <= P.rec_cap) {
+                            int qi = 0, li0 = 0;
+                            for (int base = beg; base < end; base += 32) {
+                                const int e = base + lane;
+                                int pp = 0;
+                                bool live = false;
+                                if (e < end) {
+                                    pp = adj[e];
+                                    live = entry_live(deg, mask, V, vrow, e, pp + poff);
+                                }
+                                float f[8], tgt = 0.f;
+                                const bool keep = pair_at(e, pp, live, f, tgt);
+                                const unsigned lt = (1u << lane) - 1u;
+                                const unsigned lmk = __ballot_sync(kFull, live), kmk = __ballot_sync(kFull, keep);
+                                if (keep) {
+                                    const int qq = qi + __popc(kmk & lt);
+                                    const unsigned long long pos = b0 + (unsigned long long)qq;
+                                    const int li = li0 + __popc(lmk & lt);
+#pragma unroll
+                                    for (int q = 0; q < 8; ++q) P.rec_feat[pos * 8 + q] = f[q];
+                                    P.rec_target[pos] = tgt;
+                                    P.rec_key[pos] = (traj << 28) | ((unsigned long long)t << 14) | (unsigned long long)li;
+                                    P.rec_group[pos] = ((uint32_t)qq << 16) | (uint32_t)kept;
+                                }
+                                qi += __popc(kmk);
+                                li0 += __popc(lmk);
+                            }
+                            if (lane == 0) atomicMax(P.rec_count + 1, b0 + (unsigned long long)kept);
+                        }
+                    }
+                }
                 // the network runs once per candidate: one pass over the list;
                 // the logit of a single-chunk list stays in a register, longer
                 // lists keep theirs in the group's slot
                 float lg_reg = 0.f;
                 float* lgbuf = model ? reinterpret_cast<float*>(slot + P.slot.logit) : nullptr;
-                if (model) {
+                // a single live candidate is taken with probability 1 whatever
+                // its score (W = w): no network evaluation, logit 0
+                if (model && dv >= 2) {
                     int live_base = 0;
                     for (int base = beg; base < end; base += 32) {
                         const int e = base + lane;
@@ -572,7 +622,6 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     const bool live = in && entry_live(deg, mask, V, vrow, e, pp + poff);
                     const unsigned lm = __ballot_sync(kFull, live);
                     const float lg = lg_reg;
-                    if (rec) side_outputs(e, pp, live, lg, 0);
                     uint64_t w;
                     if (uniform) {
                         w = live ? (1ull << kq) : 0ull;
@@ -609,7 +658,6 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 } else {
                     Real smax = 0;
                     if (!uniform) {
-                        int live_base = 0;
                         for (int base = beg; base < end; base += 32) {
                             const int e = base + lane;
                             Real sv = 0;
@@ -619,8 +667,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                                 pp = adj[e];
                                 live = entry_live(deg, mask, V, vrow, e, pp + poff);
                             }
-                            const float lg = (model && e < end) ? lgbuf[e - beg] : 0.f;
-                            if (rec) live_base += side_outputs(e, pp, live, lg, live_base);
+                            const float lg = (model && dv >= 2 && e < end) ? lgbuf[e - beg] : 0.f;
                             if (live) sv = score(e, pp, lg);
                             const Real cm = warp_max_nonneg(sv);
                             smax = cm > smax ? cm : smax;
@@ -634,7 +681,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                                 pp = adj[e];
                                 live = entry_live(deg, mask, V, vrow, e, pp + poff);
                             }
-                            const float lg = (model && e < end) ? lgbuf[e - beg] : 0.f;
+                            const float lg = (model && dv >= 2 && e < end) ? lgbuf[e - beg] : 0.f;
                             if (live) w = quant_weight<Real>(score(e, pp, lg), smax, kq);
                             W += warp_sum_u64(w);
                         }
@@ -657,7 +704,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                             pp = adj[e];
                             live = entry_live(deg, mask, V, vrow, e, pp + poff);
                         }
-                        const float lg = (model && e < end) ? lgbuf[e - beg] : 0.f;
+                        const float lg = (model && dv >= 2 && e < end) ? lgbuf[e - beg] : 0.f;
                         if (live) w = uniform ? (1ull << kq) : quant_weight<Real>(score(e, pp, lg), smax, kq);
                         const uint64_t pre = warp_incl_scan_u64(w, lane) + carry;
                         const unsigned hit = __ballot_sync(kFull, live && pre > rr);

@@ -10,7 +10,12 @@ Bars:
              64-wide layers with weights of size ~0.4 that is a few 1e-2 at
              most, so |dy| <= 6e-2 * max(1, |y|), median <= 5e-3
   gradient   cosine > 0.999 per parameter block, relative norm error < 5e-2
-  features   recorded pairs: same keys, features and targets within 1e-5
+             (mean squared error and the per-step centred loss)
+  features   recorded pairs: same keys, step groups, features and targets
+             within 1e-5
+  in-path    the network inside the trajectory kernel, on the states the
+             device visited, against the oracle's network on its own features
+             of those states: the forward bar above
   replay     with the GPU's logits supplied, the oracle's paths are
              bit-exact and ln X agrees within 1e-12
 """
@@ -63,23 +68,49 @@ def test_mlp_forward_matches_oracle():
         m.close()
 
 
-def test_mlp_gradient_matches_oracle():
+def step_groups(rng, B):
+    """group codes (index << 16 | size) of consecutive steps of 1..9 rows"""
+    codes = []
+    while len(codes) < B:
+        s = int(min(rng.integers(1, 10), B - len(codes)))
+        codes += [(k << 16) | s for k in range(s)]
+    return np.array(codes, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("centred", [False, True])
+def test_mlp_gradient_matches_oracle(centred):
     rng = np.random.default_rng(4)
     p = rand_params(rng, 0.3)
     m = ctx().model(p)
     X = rng.normal(size=(4099, 8)).astype(np.float32)
     T = rng.normal(size=4099).astype(np.float32)
-    loss, g = m.gradient(X, T)
-    ref_loss, ref = O.mlp_grad(oracle_params(p), bf16(X).astype(np.float64), T.astype(np.float64))
+    grp = step_groups(rng, 4099) if centred else None
+    loss, g = m.gradient(X, T, grp)
+    ref_loss, ref = O.mlp_grad(oracle_params(p), bf16(X).astype(np.float64), T.astype(np.float64), grp)
     assert loss == pytest.approx(ref_loss, rel=2e-2)
     for name, (a, b) in BLOCKS.items():
         u, v = g[a:b].astype(np.float64), ref[a:b]
         if name == "b3":
-            assert u[0] == pytest.approx(v[0], rel=2e-2, abs=1e-4)
+            if centred:  # a step-wide offset has no gradient
+                assert abs(u[0]) < 1e-4 and abs(v[0]) < 1e-12
+            else:
+                assert u[0] == pytest.approx(v[0], rel=2e-2, abs=1e-4)
             continue
         cos = float(u @ v / (np.linalg.norm(u) * np.linalg.norm(v)))
         rel = float(np.linalg.norm(u - v) / np.linalg.norm(v))
         assert cos > 0.999 and rel < 5e-2, (name, cos, rel)
+    m.close()
+
+
+def test_mlp_gradient_rejects_torn_groups():
+    rng = np.random.default_rng(5)
+    m = ctx().model(rand_params(rng))
+    X = rng.normal(size=(6, 8)).astype(np.float32)
+    T = rng.normal(size=6).astype(np.float32)
+    bad = np.array([(0 << 16) | 3, (1 << 16) | 3, (2 << 16) | 3, (0 << 16) | 4, (1 << 16) | 4, (2 << 16) | 4],
+                   dtype=np.uint32)  # the second step runs past the rows
+    with pytest.raises(Exception):
+        m.gradient(X, T, bad)
     m.close()
 
 
@@ -88,11 +119,15 @@ def test_recorded_pairs_match_oracle():
     m = G.er_planted(80, 5.0, seed=21)
     teacher = O.Schedule(initial_dm=1, K0=20, K=3, sk=O.SK_FIXED, precision=O.PREC_FP32)
     gt = B.Schedule(initial_dm=1, K0=20, K=3, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
-    f, t, k = ctx().record_pairs(m, 8, 7, gt, cap=100000)
+    f, t, k, g = ctx().record_pairs(m, 8, 7, gt, cap=100000)
     of, ot, ok, og = O.Prepared(m, teacher).record(seed=7, count=8, cap=100000)
     assert len(k) == len(ok) and len(k) > 100
     order = np.argsort(k)
     assert np.array_equal(k[order], ok)
+    assert np.array_equal(g[order], og)
+    # on the device a step's pairs are consecutive as well
+    start = np.arange(len(g)) - (g >> 16).astype(np.int64)
+    assert np.array_equal(k[start] >> 14, k >> 14)
     assert np.allclose(f[order], of, rtol=1e-5, atol=1e-6)
     assert np.allclose(t[order], ot, rtol=1e-5, atol=1e-6)
 
@@ -119,11 +154,13 @@ def test_training_reduces_the_loss():
     B = binding()
     mats = [G.er_planted(200, 6.0, seed=100 + i) for i in range(4)]
     teacher = B.Schedule(initial_dm=1, K0=100, K=10, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
-    model = ctx().model(seed=1)
-    rep = model.train(mats, teacher, n_pairs=200000, epochs=4, batch=4096, lr=2e-3, seed=2)
-    assert rep["n_pairs"] == 200000
-    assert rep["loss_last"] < 0.5 * rep["loss_first"], rep
-    model.close()
+    for objective in (B.OBJ_MSE, B.OBJ_CENTRED):
+        model = ctx().model(seed=1)
+        rep = model.train(mats, teacher, n_pairs=200000, epochs=4, batch=4096, lr=2e-3, seed=2,
+                          objective=objective)
+        assert 199000 < rep["n_pairs"] <= 200000  # whole steps only
+        assert rep["loss_last"] < 0.5 * rep["loss_first"], (objective, rep)
+        model.close()
 
 
 def test_learned_proposal_gains_over_the_plain_estimator():
@@ -147,4 +184,36 @@ def test_learned_proposal_gains_over_the_plain_estimator():
         gains.append(b["ess"] / a["ess"])
         assert abs(b["log_estimate"] - ref["log_estimate"]) < 5 * (b["rse"] + ref["rse"]) + 0.01
     assert np.median(gains) > 5.0, gains
+    model.close()
+
+
+def test_network_inside_the_trajectory_kernel_matches_oracle():
+    """The logits the trajectory kernel computed for the live candidates of
+    every step (features from the device's residual state, the in-kernel
+    tensor-core network) against the oracle's features and FP64 network on the
+    same states, with the oracle following the device's paths."""
+    B = binding()
+    rng = np.random.default_rng(8)
+    m = G.er_planted(150, 6.0, seed=41)
+    p = rand_params(rng, 0.3)
+    model = ctx().model(p)
+    sched = B.Schedule(initial_dm=1, K0=50, precision=B.PREC_FP32_PROPOSAL, learned=model)
+    T = 40
+    g = ctx().trace(m, T, 13, sched)
+    P = O.Prepared(m, O.Schedule(initial_dm=1, K0=50, precision=O.PREC_FP32))
+    o = P.run_ext_model(seed=13, count=T, logits=g["logits"], params=oracle_params(p), threads=8)
+    assert np.array_equal(o["chosen"], g["chosen"])
+    # compare the candidates of steps with at least two (a single candidate
+    # is taken with probability 1, whatever its logit)
+    dv = g["deg_v"]
+    sel = np.zeros(g["logits"].shape, dtype=bool)
+    for q in range(T):
+        for t in range(m.n):
+            if dv[q, t] >= 2:
+                sel[q, t, :min(dv[q, t], 32)] = True
+    y, ref = g["logits"][sel], o["model_logits"][sel].astype(np.float64)
+    assert y.size > 1000
+    err = np.abs(y - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() < 6e-2, err.max()
+    assert np.median(err) < 5e-3, np.median(err)
     model.close()
