@@ -8,12 +8,14 @@ with a fresh, disjoint slice of trajectory ids (T per matrix): preprocessing
 (CSC build, initial DM, outer SK), trajectories, statistics.
 
 value: effective samples per second of the learned proposal run batched
-(the metric's "learned+batched"), i.e. the sum over matrices of
-(sum X)^2 / sum X^2 per step over the device time of the steps.  The network
-is trained before the timed region (time reported) on pairs recorded from an
+(the metric's "learned+batched"): per matrix, (sum X)^2 / sum X^2 over all of
+its trajectories of the timed steps (steps x T, default 5 x 1024), summed
+over the matrices, over the device time of the steps.  The network is trained
+before the timed region (time reported) on pairs recorded from an
 SK-scheduled run on 16 training matrices of the same family (seed 7).  The
 line also reports the plain estimator run one matrix per launch (the metric's
-"plain"), the SK(100,10)-Adaptive schedule run batched, and their ratios.
+"plain"), the SK(100,10)-Adaptive schedule run batched, with the same
+trajectories per matrix and the same pooling, and their ratios.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,6 +41,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2608_15390_b300 import inputs as G  # noqa: E402
+from paper_2608_15390_b300.merge import merge  # noqa: E402
 
 METRIC = "effective samples/s at fixed rel. error, learned+batched vs plain, 1 B300"
 UNIT = "effective samples/s"
@@ -54,7 +57,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--traj", type=int, default=256, help="trajectories per matrix per step")
+    p.add_argument("--traj", type=int, default=1024, help="trajectories per matrix per step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true",
                    help="skip the learned-batched vs plain-unbatched comparison")
@@ -215,28 +218,50 @@ def timed(ctx, stream, fn):
     return out, e0.elapsed_time(e1) / 1e3
 
 
+def pooled_ess(per_matrix):
+    """Effective samples of the job: per matrix, the statistics of all its
+    trajectories of the timed steps merged (Sec. 2 ESS of the pooled run),
+    summed over the matrices; and the median pooled RSE."""
+    ess, rse = 0.0, []
+    for runs in per_matrix:
+        mrg = merge(runs)
+        ess += mrg["ess"]
+        rse.append(mrg["rse"])
+    return ess, statistics.median(rse)
+
+
 def compare_arms(ctx, B, dev, args, T):
     """The metric's "plain" (outer SK only, one matrix per launch) and the
-    SK(100,10)-Adaptive schedule run batched, on the same matrices and T."""
+    SK(100,10)-Adaptive schedule run batched, on the same matrices, with the
+    same trajectories per matrix as the timed learned run (steps x T),
+    effective samples pooled per matrix the same way."""
     import torch
     stream = torch.cuda.current_stream()
     plain = B.Schedule(**LEARNED)
     adaptive = B.Schedule(**schedule_fields())
-
-    def run_plain():
-        ess = 0.0
-        for k, m in enumerate(dev):
-            r, _ = ctx.estimate_batch_ex([m], [T], args.seed, plain, first_traj=(1 << 41) + k * T)
-            ess += r[0]["ess"]
-        return ess
-
-    ess_p, t_p = timed(ctx, stream, run_plain)
     nt = [T] * len(dev)
-    res, t_a = timed(ctx, stream, lambda: ctx.estimate_batch_ex(dev, nt, args.seed, adaptive,
-                                                                 first_traj=1 << 42)[0])
-    ess_a = sum(r["ess"] for r in res)
-    return {"plain_unbatched_ess_per_s": ess_p / t_p, "plain_unbatched_traj_per_s": len(dev) * T / t_p,
-            "adaptive_sk_batched_ess_per_s": ess_a / t_a, "adaptive_sk_batched_traj_per_s": len(dev) * T / t_a}
+    runs_p = [[] for _ in dev]
+    runs_a = [[] for _ in dev]
+    t_p = t_a = 0.0
+    for i in range(args.steps):
+        def run_plain():
+            for k, m in enumerate(dev):
+                r, _ = ctx.estimate_batch_ex([m], [T], args.seed, plain, first_traj=(1 << 41) + (i * len(dev) + k) * T)
+                runs_p[k].append(r[0])
+        _, dt = timed(ctx, stream, run_plain)
+        t_p += dt
+        res, dt = timed(ctx, stream, lambda: ctx.estimate_batch_ex(dev, nt, args.seed, adaptive,
+                                                                    first_traj=(1 << 42) + i * T)[0])
+        t_a += dt
+        for k, r in enumerate(res):
+            runs_a[k].append(r)
+    ess_p, rse_p = pooled_ess(runs_p)
+    ess_a, rse_a = pooled_ess(runs_a)
+    n_traj = args.steps * len(dev) * T
+    return {"plain_unbatched_ess_per_s": ess_p / t_p, "plain_unbatched_traj_per_s": n_traj / t_p,
+            "plain_unbatched_median_rse": rse_p,
+            "adaptive_sk_batched_ess_per_s": ess_a / t_a, "adaptive_sk_batched_traj_per_s": n_traj / t_a,
+            "adaptive_sk_batched_median_rse": rse_a}
 
 
 def oracle_train(seed=5, pairs=40000, steps=300, batch=512, lr=2e-3):
@@ -291,23 +316,20 @@ def run_reference(args, rank, world):
     per_step = [O.Prepared(m, sched) for m in mats[::8]]  # 8 matrices x `threads` trajectories per step
 
     def step(i):
-        ess = 0.0
-        for k, P in enumerate(per_step):
-            r = P.run_model(seed=args.seed, count=4 * threads, params=params, first_traj=i * 4 * threads, matrix=8 * k,
-                            threads=threads)
-            ess += O.stats(r["log_x"])["ess"]
-        return ess, 4 * threads * len(per_step)
+        return [P.run_model(seed=args.seed, count=4 * threads, params=params, first_traj=i * 4 * threads,
+                            matrix=8 * k, threads=threads)["log_x"] for k, P in enumerate(per_step)]
 
     for i in range(args.warmup):
         step(i)
     t0 = time.perf_counter()
-    tot_ess = 0.0
-    tot_traj = 0
+    logs = [[] for _ in per_step]
     for i in range(args.steps):
-        e, n = step(args.warmup + i)
-        tot_ess += e
-        tot_traj += n
+        for k, lx in enumerate(step(args.warmup + i)):
+            logs[k].append(lx)
     dt = time.perf_counter() - t0
+    # effective samples pooled per matrix over the timed steps, as in our arm
+    tot_ess = sum(O.stats(np.concatenate(lx))["ess"] for lx in logs)
+    tot_traj = sum(sum(len(a) for a in lx) for lx in logs)
     val = tot_ess / dt
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -366,13 +388,12 @@ def main():
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    tot_ess = 0.0
+    runs = [[] for _ in mats]  # per matrix: the result of every timed step
     tot_traj = 0
     alg_bytes = 0
     mlp_rows = 0
     kern_ms = 0.0
     prep_ms = 0.0
-    rse = []
     launches = 0
     if dist:
         dist.barrier()
@@ -386,12 +407,11 @@ def main():
         kern_ms += info["traj_kernel_ms"]
         prep_ms += info["prep_kernel_ms"]
         launches += 4  # prepare, trajectories, stats partial, stats merge
-        for r in res:
-            tot_ess += r["ess"]
+        for k, r in enumerate(res):
+            runs[k].append(r)
             tot_traj += r["n_traj"]
             alg_bytes += r["alg_bytes"]
             mlp_rows += r["mlp_rows"]
-            rse.append(r["rse"])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -401,22 +421,31 @@ def main():
     # e2e: the same steps through the public API from pinned host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_ess = 0.0
+    runs_e2e = [[] for _ in mats]
     for i in range(args.steps):
         res = step(10_000 + i, host=True)
-        e2e_ess += sum(r["ess"] for r in res)
+        for k, r in enumerate(res):
+            runs_e2e[k].append(r)
     t_e2e = time.perf_counter() - t0
     info = ctx.last_call_info()
     h2d, d2h = info["h2d_bytes"], info["d2h_bytes"]
 
     if dist:
+        # every rank ran disjoint trajectories of the same matrices: pool them
         t = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        s = torch.tensor([tot_ess, float(tot_traj), e2e_ess], dtype=torch.float64, device="cuda")
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
         t_dev, t_e2e = float(t[0]), float(t[1])
-        tot_ess, tot_traj, e2e_ess = float(s[0]), int(s[1]), float(s[2])
+        s = torch.tensor([float(tot_traj)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        tot_traj = int(s[0])
+        for lst in (runs, runs_e2e):
+            got = [None] * world
+            dist.all_gather_object(got, lst)
+            for k in range(len(lst)):
+                lst[k] = [r for g in got for r in g[k]]
 
+    tot_ess, med_rse = pooled_ess(runs)
+    e2e_ess, _ = pooled_ess(runs_e2e)
     value = tot_ess / t_dev
     ess_per_traj = tot_ess / max(1, tot_traj)
     if args.mats != N_MATS or args.nmax != N_HI:
@@ -444,7 +473,8 @@ def main():
                    "parallelism": f"replicas{world}", "note": line_cfg_note},
         "traj_per_s": tot_traj / t_dev,
         "ess_per_traj": ess_per_traj,
-        "median_rse_per_step": statistics.median(rse) if rse else None,
+        "median_rse": med_rse,
+        "ess_definition": "per matrix, Sec. 2 ESS of all its timed trajectories pooled, summed over matrices",
         "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": tc_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / tc_peak, "traffic": traffic,
                      "kernel": "traj_kernel<float, learned>",

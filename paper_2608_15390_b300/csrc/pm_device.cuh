@@ -132,15 +132,33 @@ __device__ __forceinline__ uint32_t leaf_key(const uint16_t* deg, int x, const T
 // bit length of a positive 32-bit value
 __device__ __forceinline__ int bitlen(uint32_t x) { return 32 - __clz(x); }
 
-// split a positive normal x into mant * 2^e with mant in [1, 2): x becomes
-// mant and e is returned
-__device__ __forceinline__ int renorm(double& x)
-{
-    long long b = __double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7FF) - 1023;
-    b = (b & ~(0x7FFll << 52)) | (1023ll << 52);
-    x = __longlong_as_double(b);
-    return e;
-}
+// A positive number kept as m * 2^e with a 64-bit mantissa m in [2^63, 2^64):
+// the running products of Algorithm 2's correction (prod W B and prod w)
+// without floating-point units.  Multiplying by an integer keeps the top 64
+// bits of the exact 128-bit product (truncation: relative error below 2^-63
+// per product, finer than binary64).
+struct Mant64 {
+    uint64_t m = 1ull << 63;
+    int e = -63;
+    __device__ __forceinline__ void mul(uint64_t w)  // w >= 1
+    {
+        const uint64_t lo = m * w, hi = __umul64hi(m, w);
+        if (hi == 0) return;  // w == 1
+        const int lz = __clzll(hi);
+        m = (hi << lz) | (lz ? (lo >> (64 - lz)) : 0ull);
+        e += 64 - lz;
+    }
+    // multiply by a positive finite binary32 value, exactly its 24-bit
+    // integer significand times a power of two
+    __device__ __forceinline__ void mul(float x)
+    {
+        const uint32_t b = __float_as_uint(x);
+        const uint32_t ef = (b >> 23) & 0xFFu;
+        const uint32_t sig = ef ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
+        mul((uint64_t)sig);
+        e += (ef ? (int)ef : 1) - 127 - 23;
+    }
+    __device__ __forceinline__ double log_value() const { return log((double)m) + (double)e * 0.6931471805599453; }
+};
 
 }  // namespace pm

@@ -436,9 +436,8 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
 
     const bool uniform = Mp->unit_scale && !inner_sk;
     const Real theta = (Real)S.theta;
-    // leader-lane state: X = num / den * 2^ex
-    double num = 1.0, den = 1.0;
-    int ex = 0;
+    // leader-lane state: X = num / den
+    Mant64 num, den;
     Real track = 1;
     unsigned n_dm = 0, n_full = 0, n_loc = 0;
     int dead_step = -1;
@@ -730,12 +729,10 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     P.chosen[(gq * n + t) * 2 + 1] = sel_p + poff;
                 }
                 if (lane == 0) {  // X <- X * B_vu * W / w_u
-                    num = num * (double)W;
+                    num.mul(W);
                     const float* vals = vrow ? V.rv : V.cv;
-                    if (vals) num = num * (double)__ldg(vals + sel_e);
-                    den = den * (double)w_sel;
-                    ex += renorm(num);
-                    ex -= renorm(den);
+                    if (vals) num.mul(__ldg(vals + sel_e));
+                    den.mul(w_sel);
                 }
                 const Real z = RA<Real>::mul(r[R], c[C]);
 
@@ -895,7 +892,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         }
     }
     if (leader && lane == 0) {
-        P.log_x[gq] = (dead_step >= 0) ? -INFINITY : (log(num) - log(den)) + (double)ex * 0.6931471805599453;
+        P.log_x[gq] = (dead_step >= 0) ? -INFINITY : num.log_value() - den.log_value();
         if (TRACE) P.dead_step[gq] = dead_step;
         if (n_dm) atomicAdd(P.counters + 5 * k + 0, (unsigned long long)n_dm);
         if (n_full) atomicAdd(P.counters + 5 * k + 1, (unsigned long long)n_full);
