@@ -183,6 +183,54 @@ pm_status pm_philox_blocks(pm_context* ctx, const uint32_t ctr[4], const uint32_
 /* Copy the bookkeeping of the context's most recent call into *info. */
 pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info);
 
+/* ---- resident batches (no counterpart in the paper) -----------------------
+ * A batch is a set of matrices estimated together again and again, each run
+ * with a fresh trajectory range: the serving and benchmarking pattern.  It
+ * owns device copies of its matrices (taken at creation from host or device
+ * CSR; the caller's arrays are not retained) and a workspace sized once.
+ * Every run executes the whole path of Algorithm 2 (preprocessing, one
+ * persistent trajectory launch over all matrices, statistics) and returns
+ * what pm_estimate_batch_ex returns for the same arguments: ln X of every
+ * trajectory is identical whatever the layout.
+ *   PM_BATCH_GRAPH     the launch sequence is captured once as a CUDA graph;
+ *                      a run sets the trajectory kernel's range and seed in
+ *                      the instantiated graph and launches it.
+ *   PM_BATCH_AUTOTUNE  for each size class (half-octave of n) the layout --
+ *                      staging of the matrix in shared memory, placement of
+ *                      the trajectory state, warps per trajectory -- is chosen
+ *                      by timing every candidate layout on a probe launch of
+ *                      the class's largest matrix (fastest trajectories/s);
+ *                      the choice is cached in the context per class and
+ *                      schedule.  Without it a fixed heuristic decides.
+ * The context (and a learned model in the schedule) must outlive the batch;
+ * runs of one batch must not overlap.  Errors: as pm_estimate_batch_ex;
+ * PM_ECUDA if capture or instantiation fails. */
+typedef struct pm_batch pm_batch;
+enum { PM_BATCH_GRAPH = 1, PM_BATCH_AUTOTUNE = 2 };
+
+typedef struct {
+    int32_t g;               /* warps per trajectory */
+    int32_t groups;          /* trajectories in flight per CTA (one CTA per SM) */
+    int32_t staged;          /* matrix adjacency staged in shared memory */
+    int32_t rc_smem;         /* scaling vectors in shared memory */
+    int32_t gstate;          /* trajectory state in global memory (large n) */
+    int32_t tuned;           /* 1 if the autotuner chose this layout */
+    double probe_traj_per_s;      /* the chosen layout's probe rate (-1: not probed) */
+    double heuristic_traj_per_s;  /* the heuristic layout's probe rate (-1: not probed) */
+} pm_plan_info;
+
+pm_status pm_batch_create(pm_context* ctx, const pm_csr* mats, int32_t count,
+                          const uint64_t* n_traj, const pm_schedule* schedule, uint32_t flags,
+                          pm_batch** out);
+/* One run over trajectories first_traj .. first_traj + n_traj[k] - 1 of every
+ * matrix k: outs[count] as pm_estimate_batch_ex, log_x (host, may be NULL) the
+ * per-trajectory ln X, matrix-major. */
+pm_status pm_batch_run(pm_batch* batch, uint64_t first_traj, uint64_t seed, pm_result* outs,
+                       double* log_x);
+/* The layout matrix k runs with. */
+pm_status pm_batch_plan_info(const pm_batch* batch, int32_t k, pm_plan_info* info);
+pm_status pm_batch_destroy(pm_batch* batch);
+
 /* ---- learned proposal (no counterpart in the paper) ----------------------
  * A small network f: 8 edge features -> 64 -> 64 (GELU) -> 1 predicts
  * ln(r_v c_l), the scale product an SK-scheduled run would use for edge

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 from dataclasses import dataclass
 from typing import List, Optional, Sequence
 
@@ -28,6 +29,7 @@ SK_NONE, SK_FIXED, SK_ADAPTIVE, SK_LOCAL = 0, 1, 2, 3
 DM_NONE, DM_ALL, DM_THRS, DM_TRCK = 0, 1, 2, 3
 PREC_FP32_PROPOSAL, PREC_FP64 = 0, 1
 OBJ_MSE, OBJ_CENTRED = 0, 1
+BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
 
 
 class PmError(RuntimeError):
@@ -61,6 +63,15 @@ class pm_train_report(C.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class pm_plan_info(C.Structure):
+    _fields_ = [("g", C.c_int32), ("groups", C.c_int32), ("staged", C.c_int32), ("rc_smem", C.c_int32),
+                ("gstate", C.c_int32), ("tuned", C.c_int32), ("probe_traj_per_s", C.c_double),
+                ("heuristic_traj_per_s", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class pm_result(C.Structure):
@@ -111,6 +122,13 @@ def _load():
     for name in ("pm_model_create", "pm_model_destroy", "pm_model_get_params", "pm_model_set_params",
                  "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs"):
         getattr(L, name).restype = C.c_int
+    L.pm_batch_create.argtypes = [P, C.POINTER(pm_csr), C.c_int32, P, C.POINTER(pm_schedule), C.c_uint32,
+                                  C.POINTER(P)]
+    L.pm_batch_run.argtypes = [P, C.c_uint64, C.c_uint64, C.POINTER(pm_result), P]
+    L.pm_batch_plan_info.argtypes = [P, C.c_int32, C.POINTER(pm_plan_info)]
+    L.pm_batch_destroy.argtypes = [P]
+    for name in ("pm_batch_create", "pm_batch_run", "pm_batch_plan_info", "pm_batch_destroy"):
+        getattr(L, name).restype = C.c_int
     L.pm_preprocess.argtypes = [P, C.POINTER(pm_csr), C.POINTER(pm_schedule), P, P, P, P]
     L.pm_philox_blocks.argtypes = [P, P, P, C.c_uint32, P]
     L.pm_last_call_info.argtypes = [P, C.POINTER(pm_call_info)]
@@ -142,7 +160,8 @@ EXPORTED = ["pm_context_create", "pm_context_destroy", "estimate_permanent",
             "estimate_permanent_batch", "pm_estimate_batch_ex", "pm_trace", "pm_preprocess", "pm_philox_blocks",
             "pm_last_call_info", "pm_log_weight_stats_noalloc", "pm_status_string", "pm_last_error",
             "pm_model_create", "pm_model_destroy", "pm_model_get_params", "pm_model_set_params",
-            "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs"]
+            "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs",
+            "pm_batch_create", "pm_batch_run", "pm_batch_plan_info", "pm_batch_destroy"]
 
 
 @dataclass
@@ -212,10 +231,13 @@ class Context:
 
     def __init__(self, device: int = 0, stream: Optional[int] = None):
         self.h = C.c_void_p()
+        self._batches = weakref.WeakSet()
         self._check(_lib.pm_context_create(C.byref(self.h), device, stream), ctx=False)
 
     def close(self):
         if self.h:
+            for b in list(self._batches):
+                b.close()
             _lib.pm_context_destroy(self.h)
             self.h = C.c_void_p()
 
@@ -271,6 +293,15 @@ class Context:
                                               C.byref(s), outs,
                                               None if lx is None else lx.ctypes.data))
         return [o.as_dict() for o in outs], lx
+
+    def batch(self, mats: Sequence, n_traj: Sequence[int], schedule: Schedule, graph: bool = True,
+              autotune: bool = False) -> "Batch":
+        """A resident batch (pm_batch_create): device copies of mats, one
+        persistent launch per run, optionally a CUDA graph and autotuned
+        layouts.  Closing the context closes its batches first."""
+        b = Batch(self, mats, n_traj, schedule, graph, autotune)
+        self._batches.add(b)
+        return b
 
     def trace(self, m, count: int, seed: int, schedule: Schedule, first_traj: int = 0,
               matrix_index: int = 0) -> dict:
@@ -401,3 +432,50 @@ class Model:
         rep = pm_train_report()
         self.ctx._check(_lib.pm_model_train(self.ctx.h, self.h, arr, len(cs), C.byref(cfg), C.byref(rep)))
         return rep.as_dict()
+
+
+class Batch:
+    """pm_batch: matrices kept on the device and estimated again and again,
+    each run over a fresh trajectory range."""
+
+    def __init__(self, ctx: Context, mats, n_traj, schedule: Schedule, graph: bool, autotune: bool):
+        self.ctx = ctx
+        self.h = None
+        cs, keeps = [], []
+        for m in mats:
+            c, k = make_csr(m)
+            cs.append(c)
+            keeps.append(k)
+        arr = (pm_csr * len(cs))(*cs)
+        self.count = len(cs)
+        self.n_traj = np.ascontiguousarray(n_traj, dtype=np.uint64)
+        self._sched = schedule.c()
+        self._keep = (schedule, keeps)
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+        h = C.c_void_p()
+        ctx._check(_lib.pm_batch_create(ctx.h, arr, self.count, self.n_traj.ctypes.data, C.byref(self._sched),
+                                        flags, C.byref(h)))
+        self.h = h
+
+    def run(self, first_traj: int, seed: int, want_log_x: bool = False):
+        """Returns (results, log_x or None) as Context.estimate_batch_ex."""
+        outs = (pm_result * self.count)()
+        lx = np.zeros(int(self.n_traj.sum()), dtype=np.float64) if want_log_x else None
+        self.ctx._check(_lib.pm_batch_run(self.h, first_traj, seed, outs, None if lx is None else lx.ctypes.data))
+        return [o.as_dict() for o in outs], lx
+
+    def plan(self, k: int) -> dict:
+        info = pm_plan_info()
+        self.ctx._check(_lib.pm_batch_plan_info(self.h, k, C.byref(info)))
+        return info.as_dict()
+
+    def close(self):
+        if self.h and self.ctx.h:
+            _lib.pm_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

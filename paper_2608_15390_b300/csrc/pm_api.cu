@@ -2,6 +2,8 @@
 // argument checks, the context's device arena, launch sequencing on the
 // context's stream, and result read-back.
 #include <algorithm>
+#include <array>
+#include <map>
 #include <chrono>
 #include <random>
 #include <cmath>
@@ -14,20 +16,37 @@
 
 using namespace pm;
 
+// Device and pinned buffers a launch sequence runs in: the context's own
+// (grown as calls need) or a batch's (sized once when the batch is made).
+struct Workspace {
+    uint8_t* arena = nullptr;
+    size_t arena_cap = 0;
+    uint8_t* slots = nullptr;   // per-group global slots
+    size_t slots_cap = 0;
+    uint8_t* pinned = nullptr;  // read-back of statistics, counters, status
+    size_t pinned_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;  // prepare | trajectories
+    void release()
+    {
+        if (arena) cudaFree(arena);
+        if (slots) cudaFree(slots);
+        if (pinned) cudaFreeHost(pinned);
+        if (ev0) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); }
+        *this = Workspace{};
+    }
+};
+
+struct pm_batch;
+
 struct pm_context {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int sm_count = 0;
     std::string last_error;
-    uint8_t* arena = nullptr;
-    size_t arena_cap = 0;
-    uint8_t* slots = nullptr;
-    size_t slots_cap = 0;
-    uint8_t* pinned = nullptr;
-    size_t pinned_cap = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the trajectory kernel
-    cudaEvent_t ev2 = nullptr;
+    Workspace ws;
+    std::map<std::string, std::array<int, 4>> tuned;  // autotuned layout policy per size class
+    std::vector<pm_batch*> batches;                     // live batches (destroyed with the context)
     double last_traj_ms = 0, last_prep_ms = 0;
     uint64_t last_h2d = 0, last_d2h = 0;
     int last_grid = 0, last_wpc = 0;
@@ -64,19 +83,25 @@ pm_status grow(pm_context* ctx, uint8_t** buf, size_t* cap, size_t need)
     return PM_OK;
 }
 
-pm_status grow_pinned(pm_context* ctx, size_t need)
+pm_status grow_pinned(pm_context* ctx, Workspace& ws, size_t need)
 {
-    if (need <= ctx->pinned_cap) return PM_OK;
-    if (ctx->pinned) {
+    if (need <= ws.pinned_cap) return PM_OK;
+    if (ws.pinned) {
         PM_CUDA(cudaStreamSynchronize(ctx->stream));
-        PM_CUDA(cudaFreeHost(ctx->pinned));
-        ctx->pinned = nullptr;
-        ctx->pinned_cap = 0;
+        PM_CUDA(cudaFreeHost(ws.pinned));
+        ws.pinned = nullptr;
+        ws.pinned_cap = 0;
     }
-    PM_CUDA(cudaMallocHost(&ctx->pinned, need));
-    ctx->pinned_cap = need;
+    PM_CUDA(cudaMallocHost(&ws.pinned, need));
+    ws.pinned_cap = need;
     return PM_OK;
 }
+
+// a device allocation freed when it goes out of scope
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
 
 // bump layout over the arena (256-byte aligned pieces)
 struct Layout {
@@ -131,66 +156,123 @@ struct pm_model {
 
 namespace {
 
-// Execution plan of one matrix (see Plan in pm_internal.h).  Preference
-// order: matrix and scaling vectors in shared memory, then scaling vectors
-// only, then neither; full-SK schedules spread a trajectory over the fewest
-// warps that still keep all 16 warps of the CTA busy.
-Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learned)
+// Layout policy of one matrix: which of the plan's choices to take.  The
+// heuristic below and the autotuner (pm_batch_create) both produce a policy;
+// plan_for() turns it into a Plan for a given matrix and shared-memory budget.
+struct Policy {
+    int staged = 0, rc_smem = 0, gstate = 0, g = 1;
+    bool operator==(const Policy& o) const
+    {
+        return staged == o.staged && rc_smem == o.rc_smem && gstate == o.gstate && g == o.g;
+    }
+};
+
+int learned_smem(bool learned) { return learned ? (model_infer_bytes() + 15) / 16 * 16 : 0; }
+
+// Plan of one matrix under a policy, or groups = 0 if it does not fit.
+Plan plan_for(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learned, const Policy& pol)
 {
     const bool full = s.sk == 1 || s.sk == 2;
     const bool need_rc = s.sk != 0;
     const bool dm = s.dm != 0;
-    const int avail = smem_max - kCtaMiscBytes - (learned ? (model_infer_bytes() + 15) / 16 * 16 : 0);
+    const int avail = smem_max - kCtaMiscBytes - learned_smem(learned);
+    Plan p{};
+    p.lists = full;
+    p.g = pol.g;
+    if (pol.g < 1 || pol.g > kCtaWarps || (pol.g & (pol.g - 1)) || (!full && pol.g != 1)) return p;
+    if (pol.gstate) {
+        p.gstate = 1;
+        p.rc_smem = need_rc;
+        p.state_bytes = kGroupMiscInts * 4 + (learned ? 32 * 24 * 2 : 0);
+        p.mat_bytes = 0;
+        p.groups = kCtaWarps / p.g;
+        if (p.groups * p.state_bytes > avail) p.groups = 0;
+        return p;
+    }
+    if ((pol.rc_smem && !need_rc) || (pol.staged && n > 65535)) return p;
+    p.staged = pol.staged;
+    p.rc_smem = pol.rc_smem;
+    p.mat_bytes = pol.staged ? staged_matrix_bytes(n, m, dm) : 0;
+    if (p.mat_bytes >= avail) return p;
+    p.state_bytes = group_state_bytes(n, rb, pol.rc_smem, full, learned);
+    const int fit = (avail - p.mat_bytes) / p.state_bytes;
+    p.groups = std::min(fit, kCtaWarps / p.g);
+    if (p.groups < 0) p.groups = 0;
+    return p;
+}
+
+// Candidate policies of a matrix (those whose plan fits), heuristic first.
+std::vector<Policy> candidate_policies(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learned)
+{
+    const bool full = s.sk == 1 || s.sk == 2;
+    const bool need_rc = s.sk != 0;
+    std::vector<Policy> out;
+    const int combos[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
+    for (int g = 1; g <= (full ? kCtaWarps : 1); g *= 2) {
+        for (const auto& cb : combos) {
+            Policy pol;
+            pol.staged = cb[0];
+            pol.rc_smem = cb[1];
+            pol.g = g;
+            if (pol.rc_smem && !need_rc) continue;
+            const Plan p = plan_for(n, m, rb, s, smem_max, learned, pol);
+            if (p.groups >= 1 && (p.groups * p.g >= 4 || !full)) out.push_back(pol);
+        }
+        Policy gs;
+        gs.gstate = 1;
+        gs.rc_smem = need_rc;
+        gs.g = g;
+        if (plan_for(n, m, rb, s, smem_max, learned, gs).groups >= 1) out.push_back(gs);
+    }
+    return out;
+}
+
+// Heuristic plan: matrix and scaling vectors in shared memory if they fit,
+// then scaling vectors only, then neither; full-SK schedules spread a
+// trajectory over the fewest warps that keep >= 8 warps of the CTA busy,
+// other schedules run one warp per trajectory with as many groups as fit; a
+// matrix whose state fits fewer than four groups keeps it in global memory.
+Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learned)
+{
+    const bool full = s.sk == 1 || s.sk == 2;
+    const bool need_rc = s.sk != 0;
     Plan best{};
     int best_score = -1;
     const int combos[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
     for (const auto& cb : combos) {
-        const bool staged = cb[0] != 0, rc = cb[1] != 0;
-        if (rc && !need_rc) continue;
-        if (staged && n > 65535) continue;
-        const int mb = staged ? staged_matrix_bytes(n, m, dm) : 0;
-        if (mb >= avail) continue;
-        const int sb = group_state_bytes(n, rb, rc, full, learned);
-        const int fit = (avail - mb) / sb;
-        if (fit < 1) continue;
-        Plan p{};
-        p.staged = staged;
-        p.rc_smem = rc;
-        p.lists = full;
-        p.state_bytes = sb;
-        p.mat_bytes = mb;
-        if (full) {
-            for (int g = 1; g <= kCtaWarps; g *= 2) {
-                p.g = g;
-                p.groups = std::min(fit, kCtaWarps / g);
-                if (p.groups * g == kCtaWarps) break;
-            }
-        } else {
-            p.g = 1;
-            p.groups = std::min(fit, kCtaWarps);
+        if (cb[1] && !need_rc) continue;
+        Plan chosen{};
+        for (int g = 1; g <= (full ? kCtaWarps : 1); g *= 2) {
+            Policy pol;
+            pol.staged = cb[0];
+            pol.rc_smem = cb[1];
+            pol.g = g;
+            const Plan p = plan_for(n, m, rb, s, smem_max, learned, pol);
+            if (p.groups < 1) break;
+            chosen = p;
+            if (p.groups * g == kCtaWarps) break;
         }
-        const int busy = p.g * p.groups;
-        // full SK: accept the first layout that keeps >= 8 warps busy
+        if (chosen.groups < 1) continue;
+        const int busy = chosen.g * chosen.groups;
         const int score = busy >= (full ? 8 : 12) ? 1000 : busy;
         if (score > best_score) {
-            best = p;
+            best = chosen;
             best_score = score;
             if (score >= 1000) break;
         }
     }
     if (best_score < 4) {  // large n: trajectory state in the group's global slot
-        Plan p{};
-        p.gstate = 1;
-        p.rc_smem = need_rc;
-        p.lists = full;
-        p.g = full ? 4 : 1;
-        p.groups = kCtaWarps / p.g;
-        p.state_bytes = kGroupMiscInts * 4 + (learned ? 32 * 24 * 2 : 0);
-        p.mat_bytes = 0;
-        if (p.groups * p.state_bytes <= avail) best = p;
+        Policy gs;
+        gs.gstate = 1;
+        gs.rc_smem = need_rc;
+        gs.g = full ? 4 : 1;
+        const Plan p = plan_for(n, m, rb, s, smem_max, learned, gs);
+        if (p.groups >= 1) best = p;
     }
     return best;
 }
+
+Policy policy_of(const Plan& p) { Policy o; o.staged = p.staged; o.rc_smem = p.rc_smem; o.gstate = p.gstate; o.g = p.g; return o; }
 
 struct Run {
     // inputs
@@ -221,36 +303,63 @@ struct Run {
     double *r_out = nullptr, *c_out = nullptr;
 };
 
-pm_status execute(pm_context* ctx, Run& R)
-{
-    const auto t0 = std::chrono::steady_clock::now();
-    PM_CUDA(cudaSetDevice(ctx->device));
-    const int count = R.count;
-    const bool fp64 = R.s.precision == 1;
-    const size_t rb = fp64 ? 8 : 4;
+struct MatOff {
+    size_t rp64, ci_in, val_in, a_rp, a_ci, a_val, a_cp, a_ri, a_ce, keep, rp, ci, rv, cp, ri, cv, ce, r0, c0, deg0,
+        tree0, dmws;
+};
+
+// Everything the launch sequence of a Run needs, laid out in a workspace.
+struct Staged {
+    bool fp64 = false;
+    size_t rb = 4;
     int n_max = 1;
     int64_t m_max = 1;
-    for (int k = 0; k < count; ++k) {
-        n_max = std::max(n_max, R.mats[k].n);
-        m_max = std::max<int64_t>(m_max, R.mats[k].nnz);
-    }
-    std::vector<uint64_t> prefix(count + 1, 0);
-    for (int k = 0; k < count; ++k) prefix[k + 1] = prefix[k] + R.ntraj[k];
-    const uint64_t total = prefix[count];
+    std::vector<uint64_t> prefix;
+    uint64_t total = 0;
+    std::vector<MatOff> mo;
+    size_t o_mats = 0, o_inputs = 0, o_prefix = 0, o_logx = 0, o_counters = 0, o_work = 0, o_status = 0;
+    size_t o_parts = 0, o_sout = 0, o_chosen = 0, o_degv = 0, o_dead = 0, o_logits = 0;
+    size_t o_plans = 0, o_chunks = 0, o_cctr = 0, layout_end = 0, chunk_cap = 0;
+    int chunks_stats = 1;
+    std::vector<Plan> plans;
+    std::vector<Chunk> chunks;
+    int smem_need = kCtaMiscBytes;
+    int grid = 0;
+    TrajParams tp{};
+    uint64_t h2d = 0, d2h = 0;
+    bool launch_traj = false;
+    // pinned read-back
+    StatsOut* h_sout = nullptr;
+    unsigned long long* h_cnt = nullptr;
+    uint32_t* h_status = nullptr;
+    DevMatrix* h_mats = nullptr;
+};
 
-    // ---- arena layout ----
+// Phase 1: arena layout, inputs and matrix descriptors (uploads on the stream).
+pm_status stage_inputs(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, size_t min_chunks = 0)
+{
+    const int count = R.count;
+    S.fp64 = R.s.precision == 1;
+    S.rb = S.fp64 ? 8 : 4;
+    S.n_max = 1;
+    S.m_max = 1;
+    for (int k = 0; k < count; ++k) {
+        S.n_max = std::max(S.n_max, R.mats[k].n);
+        S.m_max = std::max<int64_t>(S.m_max, R.mats[k].nnz);
+    }
+    S.prefix.assign(count + 1, 0);
+    for (int k = 0; k < count; ++k) S.prefix[k + 1] = S.prefix[k] + R.ntraj[k];
+    S.total = S.prefix[count];
+    const size_t rb = S.rb;
+
     Layout L;
-    struct MatOff {
-        size_t rp64, ci_in, val_in, a_rp, a_ci, a_val, a_cp, a_ri, a_ce, keep, rp, ci, rv, cp, ri, cv, ce, r0,
-            c0, deg0, tree0, dmws;
-    };
-    std::vector<MatOff> mo(count);
+    S.mo.resize(count);
     for (int k = 0; k < count; ++k) {
         const pm_csr& c = R.mats[k];
         const int n = c.n;
         const size_t m = (size_t)c.nnz;
         const bool w = c.values != nullptr;
-        MatOff& o = mo[k];
+        MatOff& o = S.mo[k];
         o.rp64 = c.on_device ? 0 : L.take((n + 1) * 8);
         o.ci_in = c.on_device ? 0 : L.take(m * 4);
         o.val_in = (c.on_device || !w) ? 0 : L.take(m * 4);
@@ -274,47 +383,46 @@ pm_status execute(pm_context* ctx, Run& R)
         o.tree0 = L.take((size_t)std::max(1, tree_geom(n).total) * 4);
         o.dmws = L.take((size_t)dm_ws_ints(n) * 4);
     }
-    const size_t o_mats = L.take(sizeof(DevMatrix) * count);
-    const size_t o_inputs = L.take(sizeof(DevInput) * count);
-    const size_t o_prefix = L.take(8 * (count + 1));
-    const size_t o_logx = L.take(8 * std::max<uint64_t>(total, 1));
-    const size_t o_counters = L.take(8 * 5 * count);
-    const size_t o_work = L.take(8);
-    const size_t o_status = L.take(4);
+    S.o_mats = L.take(sizeof(DevMatrix) * count);
+    S.o_inputs = L.take(sizeof(DevInput) * count);
+    S.o_prefix = L.take(8 * (count + 1));
+    S.o_logx = L.take(8 * std::max<uint64_t>(S.total, 1));
+    S.o_counters = L.take(8 * 5 * count);
+    S.o_work = L.take(8);
+    S.o_status = L.take(4);
     uint64_t max_t = 1;
     for (int k = 0; k < count; ++k) max_t = std::max(max_t, R.ntraj[k]);
-    const int chunks_stats = (int)std::min<uint64_t>(1024, std::max<uint64_t>(1, max_t / 16384));
-    const size_t o_parts = L.take(sizeof(StatsPartial) * (size_t)count * chunks_stats);
-    const size_t o_sout = L.take(sizeof(StatsOut) * count);
-    size_t o_chosen = 0, o_degv = 0, o_dead = 0, o_logits = 0;
+    S.chunks_stats = (int)std::min<uint64_t>(1024, std::max<uint64_t>(1, max_t / 16384));
+    S.o_parts = L.take(sizeof(StatsPartial) * (size_t)count * S.chunks_stats);
+    S.o_sout = L.take(sizeof(StatsOut) * count);
     if (R.trace) {
-        o_chosen = L.take(4 * total * 2 * (size_t)n_max);
-        o_degv = L.take(4 * total * (size_t)n_max);
-        o_dead = L.take(4 * std::max<uint64_t>(total, 1));
-        if (R.model) o_logits = L.take(4 * total * (size_t)n_max * 32);
+        S.o_chosen = L.take(4 * S.total * 2 * (size_t)S.n_max);
+        S.o_degv = L.take(4 * S.total * (size_t)S.n_max);
+        S.o_dead = L.take(4 * std::max<uint64_t>(S.total, 1));
+        if (R.model) S.o_logits = L.take(4 * S.total * (size_t)S.n_max * 32);
     }
-    // room for the plans and the chunk list (at most one chunk per trajectory)
-    const size_t extra = align_up(sizeof(Plan) * count, 256) + align_up(sizeof(Chunk) * (total + count), 256) + 512;
-    pm_status st = grow(ctx, &ctx->arena, &ctx->arena_cap, L.off + extra);
+    // the plans and the chunk list (at most one chunk per trajectory)
+    S.chunk_cap = std::max<size_t>(S.total + count, min_chunks);
+    S.o_plans = L.take(sizeof(Plan) * count);
+    S.o_chunks = L.take(sizeof(Chunk) * S.chunk_cap);
+    S.o_cctr = L.take(8);
+    S.layout_end = L.off;
+    pm_status st = grow(ctx, &ws.arena, &ws.arena_cap, L.off);
     if (st != PM_OK) return st;
-    uint8_t* A = ctx->arena;
+    uint8_t* A = ws.arena;
     auto P = [&](size_t off) { return (void*)(A + off); };
 
-    // ---- inputs and matrix descriptors ----
-    uint64_t h2d = 0, d2h = 0;
-    ctx->last_traj_ms = ctx->last_prep_ms = 0;
-    ctx->last_grid = ctx->last_wpc = 0;
     std::vector<DevMatrix> hm(count);
     std::vector<DevInput> hi(count);
     for (int k = 0; k < count; ++k) {
         const pm_csr& c = R.mats[k];
-        const MatOff& o = mo[k];
+        const MatOff& o = S.mo[k];
         const int n = c.n;
         const size_t m = (size_t)c.nnz;
         DevInput& I = hi[k];
         I.n = n;
         I.m = (int)m;
-        if (!c.on_device) h2d += (n + 1) * 8 + m * 4 + (c.values ? m * 4 : 0);
+        if (!c.on_device) S.h2d += (n + 1) * 8 + m * 4 + (c.values ? m * 4 : 0);
         if (c.on_device) {
             I.rp64 = c.row_ptr;
             I.ci_in = c.col_idx;
@@ -344,190 +452,232 @@ pm_status execute(pm_context* ctx, Run& R)
         M.tree0 = (uint32_t*)P(o.tree0);
         M.dm_ws = (int*)P(o.dmws);
     }
-    DevMatrix* d_mats = (DevMatrix*)P(o_mats);
-    PM_CUDA(cudaMemcpyAsync(d_mats, hm.data(), sizeof(DevMatrix) * count, cudaMemcpyHostToDevice, ctx->stream));
-    PM_CUDA(cudaMemcpyAsync(P(o_inputs), hi.data(), sizeof(DevInput) * count, cudaMemcpyHostToDevice, ctx->stream));
-    PM_CUDA(cudaMemcpyAsync(P(o_prefix), prefix.data(), 8 * (count + 1), cudaMemcpyHostToDevice, ctx->stream));
-    h2d += sizeof(DevMatrix) * count + sizeof(DevInput) * count + 8 * (count + 1);
-    PM_CUDA(cudaMemsetAsync(P(o_counters), 0, 8 * 5 * count, ctx->stream));
-    PM_CUDA(cudaMemsetAsync(P(o_work), 0, 8, ctx->stream));
-    PM_CUDA(cudaMemsetAsync(P(o_status), 0, 4, ctx->stream));
-    uint32_t* d_status = (uint32_t*)P(o_status);
+    PM_CUDA(cudaMemcpyAsync(P(S.o_mats), hm.data(), sizeof(DevMatrix) * count, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(P(S.o_inputs), hi.data(), sizeof(DevInput) * count, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(P(S.o_prefix), S.prefix.data(), 8 * (count + 1), cudaMemcpyHostToDevice, ctx->stream));
+    S.h2d += sizeof(DevMatrix) * count + sizeof(DevInput) * count + 8 * (count + 1);
 
-    if (!ctx->ev0) {
-        PM_CUDA(cudaEventCreate(&ctx->ev0));
-        PM_CUDA(cudaEventCreate(&ctx->ev1));
-        PM_CUDA(cudaEventCreate(&ctx->ev2));
-    }
-    PM_CUDA(cudaEventRecord(ctx->ev2, ctx->stream));
-    PM_CUDA(launch_prepare(d_mats, (const DevInput*)P(o_inputs), count, R.s, n_max, d_status, ctx->stream));
-    PM_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
-    bool launched = false;
-
-    // ---- trajectories ----
-    if (!R.prep_only && total > 0) {
-        const bool scales = R.s.sk != 0;
-        const bool local = R.s.sk == 3;
-        const bool dm = R.s.dm != 0;
-        const int smem_max = traj_max_smem_bytes();
-        if (smem_max <= 0) return fail(ctx, PM_ECUDA, "cannot query the shared-memory limit");
-        std::vector<Plan> plans(count);
-        int smem_need = kCtaMiscBytes;
-        for (int k = 0; k < count; ++k) {
-            plans[k] = make_plan(R.mats[k].n, R.mats[k].nnz, (int)rb, R.s, smem_max, R.model != nullptr);
-            if (plans[k].groups < 1)
-                return fail(ctx, PM_EUNSUPPORTED, "trajectory state does not fit in shared memory");
-            smem_need = std::max(smem_need, kCtaMiscBytes + (R.model ? (model_infer_bytes() + 15) / 16 * 16 : 0) +
-                                                plans[k].mat_bytes + plans[k].groups * plans[k].state_bytes);
-        }
-        size_t gstate_bytes = 0;
-        for (int k = 0; k < count; ++k)
-            if (plans[k].gstate)
-                gstate_bytes = std::max(gstate_bytes, global_state_bytes(R.mats[k].n, (int)rb, plans[k].lists != 0));
-        const SlotLayout sl =
-            slot_layout(n_max, (int)m_max, (int)rb, scales, local, dm, gstate_bytes, R.model != nullptr);
-        // chunks: most expensive matrices first, a few trajectories per group
-        std::vector<int> order(count);
-        for (int k = 0; k < count; ++k) order[k] = k;
-        const bool full_sk = R.s.sk == 1 || R.s.sk == 2;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            const double ca = (double)R.mats[a].nnz * (full_sk ? R.mats[a].n : 1);
-            const double cb = (double)R.mats[b].nnz * (full_sk ? R.mats[b].n : 1);
-            return ca > cb;
-        });
-        std::vector<Chunk> chunks;
-        for (int k : order) {
-            const uint64_t csz = (uint64_t)plans[k].groups * 2;
-            for (uint64_t f = 0; f < R.ntraj[k]; f += csz) {
-                Chunk c;
-                c.k = k;
-                c.first = f;
-                c.count = (uint32_t)std::min<uint64_t>(csz, R.ntraj[k] - f);
-                chunks.push_back(c);
-            }
-        }
-        const int grid = ctx->sm_count;
-        Layout L2 = L;
-        const size_t o_plans = L2.take(sizeof(Plan) * count);
-        const size_t o_chunks = L2.take(sizeof(Chunk) * chunks.size());
-        const size_t o_cctr = L2.take(8);
-        if (L2.off > ctx->arena_cap) return fail(ctx, PM_EINVAL, "internal: arena layout");
-        PM_CUDA(cudaMemcpyAsync(P(o_plans), plans.data(), sizeof(Plan) * count, cudaMemcpyHostToDevice, ctx->stream));
-        PM_CUDA(cudaMemcpyAsync(P(o_chunks), chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice,
-                                ctx->stream));
-        PM_CUDA(cudaMemsetAsync(P(o_cctr), 0, 8, ctx->stream));
-        h2d += sizeof(Plan) * count + sizeof(Chunk) * chunks.size();
-        const size_t need_slots = sl.bytes * (size_t)grid * kCtaWarps;
-        st = grow(ctx, &ctx->slots, &ctx->slots_cap, need_slots);
-        if (st != PM_OK) return st;
-        TrajParams tp{};
-        tp.mats = d_mats;
-        tp.plans = (const Plan*)P(o_plans);
-        tp.chunks = (const Chunk*)P(o_chunks);
-        tp.n_chunks = (int)chunks.size();
-        tp.count = count;
-        tp.n_max = n_max;
-        tp.prefix = (const uint64_t*)P(o_prefix);
-        tp.first_traj = R.first_traj;
-        tp.seed = R.seed;
-        tp.s = R.s;
-        tp.log_x = (double*)P(o_logx);
-        tp.counters = (unsigned long long*)P(o_counters);
-        tp.chunk_counter = (int*)P(o_cctr);
-        tp.status = d_status;
-        tp.slots = ctx->slots;
-        tp.slot = sl;
-        if (R.trace) {
-            tp.chosen = (int32_t*)P(o_chosen);
-            tp.deg_v = (int32_t*)P(o_degv);
-            tp.dead_step = (int32_t*)P(o_dead);
-            if (R.model) {
-                tp.trace_logits = (float*)P(o_logits);
-                PM_CUDA(cudaMemsetAsync(tp.trace_logits, 0, 4 * total * (size_t)n_max * 32, ctx->stream));
-            }
-        }
-        tp.model = R.model;
-        tp.rec_feat = R.rec_feat;
-        tp.rec_target = R.rec_target;
-        tp.rec_key = R.rec_key;
-        tp.rec_group = R.rec_group;
-        tp.rec_count = R.rec_count;
-        tp.rec_cap = R.rec_cap;
-        PM_CUDA(launch_trajectories(tp, grid, smem_need, R.trace, ctx->stream));
-        PM_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
-        launched = true;
-        ctx->last_grid = grid;
-        ctx->last_wpc = kCtaWarps;
-        PM_CUDA(launch_stats((const double*)P(o_logx), prefix.data(), (const uint64_t*)P(o_prefix), count,
-                             (StatsPartial*)P(o_parts), chunks_stats, (StatsOut*)P(o_sout), ctx->stream));
-    }
-
-    // ---- read back ----
-    const size_t pin_need = sizeof(StatsOut) * count + 8 * 5 * count + 8 + sizeof(DevMatrix) * count + 64;
-    st = grow_pinned(ctx, pin_need);
+    // pinned read-back area
+    const size_t pin_need = sizeof(StatsOut) * count + 8 * 5 * count + 8 + sizeof(DevMatrix) * count + 128;
+    st = grow_pinned(ctx, ws, pin_need);
     if (st != PM_OK) return st;
-    StatsOut* h_sout = (StatsOut*)ctx->pinned;
-    unsigned long long* h_cnt = (unsigned long long*)(h_sout + count);
-    uint32_t* h_status = (uint32_t*)(h_cnt + 5 * count);
-    DevMatrix* h_mats = (DevMatrix*)(ctx->pinned + align_up(sizeof(StatsOut) * count + 8 * 5 * count + 8, 64));
-    if (!R.prep_only && total > 0) {
-        PM_CUDA(cudaMemcpyAsync(h_sout, P(o_sout), sizeof(StatsOut) * count, cudaMemcpyDeviceToHost, ctx->stream));
-        PM_CUDA(cudaMemcpyAsync(h_cnt, P(o_counters), 8 * 5 * count, cudaMemcpyDeviceToHost, ctx->stream));
+    S.h_sout = (StatsOut*)ws.pinned;
+    S.h_cnt = (unsigned long long*)(S.h_sout + count);
+    S.h_status = (uint32_t*)(S.h_cnt + 5 * count);
+    S.h_mats = (DevMatrix*)(ws.pinned + align_up(sizeof(StatsOut) * count + 8 * 5 * count + 8, 64));
+    if (!ws.ev0) {
+        PM_CUDA(cudaEventCreate(&ws.ev0));
+        PM_CUDA(cudaEventCreate(&ws.ev1));
+        PM_CUDA(cudaEventCreate(&ws.ev2));
     }
-    PM_CUDA(cudaMemcpyAsync(h_status, d_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
-    PM_CUDA(cudaMemcpyAsync(h_mats, d_mats, sizeof(DevMatrix) * count, cudaMemcpyDeviceToHost, ctx->stream));
-    PM_CUDA(cudaStreamSynchronize(ctx->stream));
-    d2h += 4 + sizeof(DevMatrix) * count;
-    if (!R.prep_only && total > 0) d2h += sizeof(StatsOut) * count + 8 * 5 * count;
+    return PM_OK;
+}
+
+// Phase 2: plans (heuristic, or the given ones), chunk list, slots and the
+// trajectory kernel's parameters.
+pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, const std::vector<Plan>* given)
+{
+    const int count = R.count;
+    S.launch_traj = !R.prep_only && S.total > 0;
+    if (!S.launch_traj) return PM_OK;
+    uint8_t* A = ws.arena;
+    auto P = [&](size_t off) { return (void*)(A + off); };
+    const bool scales = R.s.sk != 0;
+    const bool local = R.s.sk == 3;
+    const bool dm = R.s.dm != 0;
+    const int smem_max = traj_max_smem_bytes();
+    if (smem_max <= 0) return fail(ctx, PM_ECUDA, "cannot query the shared-memory limit");
+    S.plans.assign(count, Plan{});
+    S.smem_need = kCtaMiscBytes;
+    for (int k = 0; k < count; ++k) {
+        S.plans[k] = given ? (*given)[k] : make_plan(R.mats[k].n, R.mats[k].nnz, (int)S.rb, R.s, smem_max,
+                                                      R.model != nullptr);
+        if (S.plans[k].groups < 1)
+            return fail(ctx, PM_EUNSUPPORTED, "trajectory state does not fit in shared memory");
+        S.smem_need = std::max(S.smem_need, kCtaMiscBytes + learned_smem(R.model != nullptr) + S.plans[k].mat_bytes +
+                                                S.plans[k].groups * S.plans[k].state_bytes);
+    }
+    size_t gstate_bytes = 0;
+    for (int k = 0; k < count; ++k)
+        if (S.plans[k].gstate)
+            gstate_bytes = std::max(gstate_bytes, global_state_bytes(R.mats[k].n, (int)S.rb, S.plans[k].lists != 0));
+    const SlotLayout sl =
+        slot_layout(S.n_max, (int)S.m_max, (int)S.rb, scales, local, dm, gstate_bytes, R.model != nullptr);
+    // chunks: most expensive matrices first, a few trajectories per group
+    std::vector<int> order(count);
+    for (int k = 0; k < count; ++k) order[k] = k;
+    const bool full_sk = R.s.sk == 1 || R.s.sk == 2;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double ca = (double)R.mats[a].nnz * (full_sk ? R.mats[a].n : 1);
+        const double cb = (double)R.mats[b].nnz * (full_sk ? R.mats[b].n : 1);
+        return ca > cb;
+    });
+    S.chunks.clear();
+    for (int k : order) {
+        const uint64_t csz = (uint64_t)S.plans[k].groups * 2;
+        for (uint64_t f = 0; f < R.ntraj[k]; f += csz) {
+            Chunk c;
+            c.k = k;
+            c.first = f;
+            c.count = (uint32_t)std::min<uint64_t>(csz, R.ntraj[k] - f);
+            S.chunks.push_back(c);
+        }
+    }
+    if (S.chunks.size() > S.chunk_cap) return fail(ctx, PM_EINVAL, "internal: chunk list");
+    S.grid = ctx->sm_count;
+    PM_CUDA(cudaMemcpyAsync(P(S.o_plans), S.plans.data(), sizeof(Plan) * count, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(P(S.o_chunks), S.chunks.data(), sizeof(Chunk) * S.chunks.size(), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    S.h2d += sizeof(Plan) * count + sizeof(Chunk) * S.chunks.size();
+    const size_t need_slots = sl.bytes * (size_t)S.grid * kCtaWarps;
+    pm_status st = grow(ctx, &ws.slots, &ws.slots_cap, need_slots);
+    if (st != PM_OK) return st;
+    TrajParams& tp = S.tp;
+    tp = TrajParams{};
+    tp.mats = (const DevMatrix*)P(S.o_mats);
+    tp.plans = (const Plan*)P(S.o_plans);
+    tp.chunks = (const Chunk*)P(S.o_chunks);
+    tp.n_chunks = (int)S.chunks.size();
+    tp.count = count;
+    tp.n_max = S.n_max;
+    tp.prefix = (const uint64_t*)P(S.o_prefix);
+    tp.first_traj = R.first_traj;
+    tp.seed = R.seed;
+    tp.s = R.s;
+    tp.log_x = (double*)P(S.o_logx);
+    tp.counters = (unsigned long long*)P(S.o_counters);
+    tp.chunk_counter = (int*)P(S.o_cctr);
+    tp.status = (uint32_t*)P(S.o_status);
+    tp.slots = ws.slots;
+    tp.slot = sl;
+    if (R.trace) {
+        tp.chosen = (int32_t*)P(S.o_chosen);
+        tp.deg_v = (int32_t*)P(S.o_degv);
+        tp.dead_step = (int32_t*)P(S.o_dead);
+        if (R.model) tp.trace_logits = (float*)P(S.o_logits);
+    }
+    tp.model = R.model;
+    tp.rec_feat = R.rec_feat;
+    tp.rec_target = R.rec_target;
+    tp.rec_key = R.rec_key;
+    tp.rec_group = R.rec_group;
+    tp.rec_count = R.rec_count;
+    tp.rec_cap = R.rec_cap;
+    return PM_OK;
+}
+
+// Phase 3: the launch sequence of one run on the stream, in three segments
+// (each capturable: its host sources and destinations live in the workspace):
+// preprocessing, the trajectory kernel, statistics and read-back.
+pm_status enqueue_prep(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
+{
+    uint8_t* A = ws.arena;
+    auto P = [&](size_t off) { return (void*)(A + off); };
+    PM_CUDA(cudaMemsetAsync(P(S.o_counters), 0, 8 * 5 * R.count, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(P(S.o_work), 0, 8, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(P(S.o_status), 0, 4, ctx->stream));
+    PM_CUDA(launch_prepare((DevMatrix*)P(S.o_mats), (const DevInput*)P(S.o_inputs), R.count, R.s, S.n_max,
+                           (uint32_t*)P(S.o_status), ctx->stream));
+    return PM_OK;
+}
+
+pm_status enqueue_traj(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
+{
+    if (!S.launch_traj) return PM_OK;
+    PM_CUDA(cudaMemsetAsync(ws.arena + S.o_cctr, 0, 8, ctx->stream));
+    if (S.tp.trace_logits)
+        PM_CUDA(cudaMemsetAsync(S.tp.trace_logits, 0, 4 * S.total * (size_t)S.n_max * 32, ctx->stream));
+    PM_CUDA(launch_trajectories(S.tp, S.grid, S.smem_need, R.trace, ctx->stream));
+    return PM_OK;
+}
+
+pm_status enqueue_tail(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
+{
+    const int count = R.count;
+    uint8_t* A = ws.arena;
+    auto P = [&](size_t off) { return (void*)(A + off); };
+    if (S.launch_traj) {
+        PM_CUDA(launch_stats((const double*)P(S.o_logx), S.prefix.data(), (const uint64_t*)P(S.o_prefix), count,
+                             (StatsPartial*)P(S.o_parts), S.chunks_stats, (StatsOut*)P(S.o_sout), ctx->stream));
+        PM_CUDA(cudaMemcpyAsync(S.h_sout, P(S.o_sout), sizeof(StatsOut) * count, cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(cudaMemcpyAsync(S.h_cnt, P(S.o_counters), 8 * 5 * count, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    PM_CUDA(cudaMemcpyAsync(S.h_status, P(S.o_status), 4, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(S.h_mats, P(S.o_mats), sizeof(DevMatrix) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    return PM_OK;
+}
+
+// the three segments with the timing events between them
+pm_status enqueue(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
+{
+    PM_CUDA(cudaEventRecord(ws.ev2, ctx->stream));
+    pm_status st = enqueue_prep(ctx, ws, R, S);
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaEventRecord(ws.ev0, ctx->stream));
+    st = enqueue_traj(ctx, ws, R, S);
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaEventRecord(ws.ev1, ctx->stream));
+    return enqueue_tail(ctx, ws, R, S);
+}
+
+// Phase 4 (after the stream synchronised): errors, timings, outputs.
+pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, double secs)
+{
+    const int count = R.count;
+    uint8_t* A = ws.arena;
+    auto P = [&](size_t off) { return (void*)(A + off); };
+    uint64_t d2h = 4 + sizeof(DevMatrix) * count;
+    if (S.launch_traj) d2h += sizeof(StatsOut) * count + 8 * 5 * count;
     {
         float ms = 0;
-        PM_CUDA(cudaEventElapsedTime(&ms, ctx->ev2, ctx->ev0));
-        ctx->last_prep_ms = ms;
-        if (launched) {
-            PM_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-            ctx->last_traj_ms = ms;
-        }
+        ctx->last_prep_ms = (cudaEventElapsedTime(&ms, ws.ev2, ws.ev0) == cudaSuccess) ? ms : -1.0;
+        ctx->last_traj_ms = 0;
+        if (S.launch_traj) ctx->last_traj_ms = (cudaEventElapsedTime(&ms, ws.ev0, ws.ev1) == cudaSuccess) ? ms : -1.0;
+        cudaGetLastError();  // a timing that could not be taken is reported as -1
     }
-    if (*h_status & ST_BAD_INPUT) return fail(ctx, PM_EINVAL, "malformed CSR (device validation)");
-    if (*h_status & ST_CAPACITY) return fail(ctx, PM_EUNSUPPORTED, "a row or column holds more than 65534 entries");
-    if (*h_status) return fail(ctx, PM_EDEVICE, "device status " + std::to_string(*h_status));
+    ctx->last_grid = S.launch_traj ? S.grid : 0;
+    ctx->last_wpc = S.launch_traj ? kCtaWarps : 0;
+    const uint32_t status = *S.h_status;
+    if (status & ST_BAD_INPUT) return fail(ctx, PM_EINVAL, "malformed CSR (device validation)");
+    if (status & ST_CAPACITY) return fail(ctx, PM_EUNSUPPORTED, "a row or column holds more than 65534 entries");
+    if (status) return fail(ctx, PM_EDEVICE, "device status " + std::to_string(status));
 
     if (R.trace) {
-        const size_t T = total, n = R.mats[0].n;
-        if (R.chosen) PM_CUDA(cudaMemcpy(R.chosen, P(o_chosen), 4 * T * 2 * n, cudaMemcpyDeviceToHost));
-        if (R.deg_v) PM_CUDA(cudaMemcpy(R.deg_v, P(o_degv), 4 * T * n, cudaMemcpyDeviceToHost));
-        if (R.dead_step) PM_CUDA(cudaMemcpy(R.dead_step, P(o_dead), 4 * T, cudaMemcpyDeviceToHost));
-        if (R.logits && R.model) PM_CUDA(cudaMemcpy(R.logits, P(o_logits), 4 * T * n * 32, cudaMemcpyDeviceToHost));
+        const size_t T = S.total, n = R.mats[0].n;
+        if (R.chosen) PM_CUDA(cudaMemcpy(R.chosen, P(S.o_chosen), 4 * T * 2 * n, cudaMemcpyDeviceToHost));
+        if (R.deg_v) PM_CUDA(cudaMemcpy(R.deg_v, P(S.o_degv), 4 * T * n, cudaMemcpyDeviceToHost));
+        if (R.dead_step) PM_CUDA(cudaMemcpy(R.dead_step, P(S.o_dead), 4 * T, cudaMemcpyDeviceToHost));
+        if (R.logits && R.model) PM_CUDA(cudaMemcpy(R.logits, P(S.o_logits), 4 * T * n * 32, cudaMemcpyDeviceToHost));
     }
-    if (R.log_x && total) {
-        PM_CUDA(cudaMemcpy(R.log_x, P(o_logx), 8 * total, cudaMemcpyDeviceToHost));
-        d2h += 8 * total;
+    if (R.log_x && S.total) {
+        PM_CUDA(cudaMemcpy(R.log_x, P(S.o_logx), 8 * S.total, cudaMemcpyDeviceToHost));
+        d2h += 8 * S.total;
     }
     if (R.prep_only) {
         const pm_csr& c = R.mats[0];
-        if (R.ok_out) *R.ok_out = h_mats[0].ok;
-        if (R.keep_out && c.nnz) PM_CUDA(cudaMemcpy(R.keep_out, P(mo[0].keep), c.nnz, cudaMemcpyDeviceToHost));
+        const size_t rb = S.rb;
+        if (R.ok_out) *R.ok_out = S.h_mats[0].ok;
+        if (R.keep_out && c.nnz) PM_CUDA(cudaMemcpy(R.keep_out, P(S.mo[0].keep), c.nnz, cudaMemcpyDeviceToHost));
         if (R.r_out || R.c_out) {
             std::vector<uint8_t> tmp((size_t)c.n * rb * 2);
-            PM_CUDA(cudaMemcpy(tmp.data(), P(mo[0].r0), c.n * rb, cudaMemcpyDeviceToHost));
-            PM_CUDA(cudaMemcpy(tmp.data() + c.n * rb, P(mo[0].c0), c.n * rb, cudaMemcpyDeviceToHost));
+            PM_CUDA(cudaMemcpy(tmp.data(), P(S.mo[0].r0), c.n * rb, cudaMemcpyDeviceToHost));
+            PM_CUDA(cudaMemcpy(tmp.data() + c.n * rb, P(S.mo[0].c0), c.n * rb, cudaMemcpyDeviceToHost));
             for (int q = 0; q < c.n; ++q) {
-                const double rv = fp64 ? ((double*)tmp.data())[q] : (double)((float*)tmp.data())[q];
-                const double cv = fp64 ? ((double*)(tmp.data() + c.n * rb))[q]
-                                       : (double)((float*)(tmp.data() + c.n * rb))[q];
+                const double rv = S.fp64 ? ((double*)tmp.data())[q] : (double)((float*)tmp.data())[q];
+                const double cv = S.fp64 ? ((double*)(tmp.data() + c.n * rb))[q]
+                                         : (double)((float*)(tmp.data() + c.n * rb))[q];
                 if (R.r_out) R.r_out[q] = rv;
                 if (R.c_out) R.c_out[q] = cv;
             }
         }
     }
-    ctx->last_h2d = h2d;
+    ctx->last_h2d = S.h2d;
     ctx->last_d2h = d2h;
-    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (R.outs) {
         for (int k = 0; k < count; ++k) {
             pm_result& o = R.outs[k];
             std::memset(&o, 0, sizeof(o));
-            const StatsOut& so = h_sout[k];
+            const StatsOut& so = S.h_sout[k];
             o.log_estimate = so.log_estimate;
             o.estimate = std::exp(so.log_estimate);
             o.ess = so.ess;
@@ -538,16 +688,34 @@ pm_status execute(pm_context* ctx, Run& R)
             o.log_sum_x2 = so.log_sum_x2;
             o.n_traj = so.n;
             o.n_alive = so.alive;
-            o.n_dm_calls = h_cnt[5 * k + 0];
-            o.n_full_sk = h_cnt[5 * k + 1];
-            o.n_local_sk = h_cnt[5 * k + 2];
-            o.alg_bytes = h_cnt[5 * k + 3];
-            o.mlp_rows = h_cnt[5 * k + 4];
+            o.n_dm_calls = S.h_cnt[5 * k + 0];
+            o.n_full_sk = S.h_cnt[5 * k + 1];
+            o.n_local_sk = S.h_cnt[5 * k + 2];
+            o.alg_bytes = S.h_cnt[5 * k + 3];
+            o.mlp_rows = S.h_cnt[5 * k + 4];
             o.kernel_ms = ctx->last_traj_ms;
             o.seconds = secs;
         }
     }
     return PM_OK;
+}
+
+pm_status execute(pm_context* ctx, Run& R)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    PM_CUDA(cudaSetDevice(ctx->device));
+    Staged S;
+    ctx->last_traj_ms = ctx->last_prep_ms = 0;
+    ctx->last_grid = ctx->last_wpc = 0;
+    pm_status st = stage_inputs(ctx, ctx->ws, R, S);
+    if (st != PM_OK) return st;
+    st = stage_plans(ctx, ctx->ws, R, S, nullptr);
+    if (st != PM_OK) return st;
+    st = enqueue(ctx, ctx->ws, R, S);
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return collect(ctx, ctx->ws, R, S, secs);
 }
 
 }  // namespace
@@ -579,15 +747,16 @@ pm_status pm_context_create(pm_context** out, int device, void* cuda_stream)
     return PM_OK;
 }
 
+static void batch_delete(pm_batch* b);
+
 pm_status pm_context_destroy(pm_context* ctx)
 {
     if (!ctx) return PM_EINVAL;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    if (ctx->arena) cudaFree(ctx->arena);
-    if (ctx->slots) cudaFree(ctx->slots);
-    if (ctx->pinned) cudaFreeHost(ctx->pinned);
-    if (ctx->ev0) { cudaEventDestroy(ctx->ev0); cudaEventDestroy(ctx->ev1); cudaEventDestroy(ctx->ev2); }
+    for (pm_batch* b : ctx->batches) batch_delete(b);
+    ctx->batches.clear();
+    ctx->ws.release();
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return PM_OK;
@@ -697,10 +866,10 @@ pm_status pm_philox_blocks(pm_context* ctx, const uint32_t ctr[4], const uint32_
 {
     if (!ctx || !ctr || !key || !out || count == 0) return PM_EINVAL;
     PM_CUDA(cudaSetDevice(ctx->device));
-    pm_status st = grow(ctx, &ctx->arena, &ctx->arena_cap, (size_t)count * 16);
+    pm_status st = grow(ctx, &ctx->ws.arena, &ctx->ws.arena_cap, (size_t)count * 16);
     if (st != PM_OK) return st;
-    PM_CUDA(launch_philox(ctr, key, count, (uint32_t*)ctx->arena, ctx->stream));
-    PM_CUDA(cudaMemcpyAsync(out, ctx->arena, (size_t)count * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(launch_philox(ctr, key, count, (uint32_t*)ctx->ws.arena, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(out, ctx->ws.arena, (size_t)count * 16, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
     return PM_OK;
 }
@@ -733,6 +902,355 @@ const char* pm_status_string(pm_status s)
 }
 
 const char* pm_last_error(const pm_context* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+// ---------------------------------------------------------------------------
+// resident batches: device copies, a workspace sized once, an optional CUDA
+// graph of the launch sequence and an optional autotuned layout per size class
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+struct pm_batch {
+    pm_context* ctx = nullptr;
+    Workspace ws;
+    std::vector<pm_csr> mats;      // device copies owned by the batch
+    std::vector<void*> bufs;
+    Run R;
+    Staged S;
+    uint32_t flags = 0;
+    // captured segments: preprocessing, trajectories, statistics + read-back
+    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    cudaGraphNode_t traj_node = nullptr;
+    cudaKernelNodeParams traj_params{};
+    std::vector<pm_plan_info> info;
+    ~pm_batch()
+    {
+        for (int q = 0; q < 3; ++q) {
+            if (exec[q]) cudaGraphExecDestroy(exec[q]);
+            if (graph[q]) cudaGraphDestroy(graph[q]);
+        }
+        for (void* b : bufs) cudaFree(b);
+        ws.release();
+    }
+};
+
+static void batch_delete(pm_batch* b) { delete b; }
+
+namespace {
+
+// size class of a matrix for the autotuner: half-octaves of n
+int size_class(int n) { return (int)std::floor(2.0 * std::log2((double)std::max(1, n))); }
+
+std::string class_key(int cls, const Sched& s, bool learned)
+{
+    return std::to_string(cls) + "|" + std::to_string(s.vertex_rule) + std::to_string(s.sk) + std::to_string(s.dm) +
+           std::to_string(s.precision) + std::to_string(s.K) + "|" + (learned ? "L" : "-");
+}
+
+// Trajectories per second of matrix k under `plan`: a probe launch on up to
+// 32 SMs, two trajectories per group, ids far from any run's range.
+pm_status probe_plan(pm_context* ctx, pm_batch* b, int k, const Plan& plan, double* rate)
+{
+    Staged& S = b->S;
+    const Run& R = b->R;
+    const int count = R.count;
+    const int pgrid = std::min(ctx->sm_count, 32);
+    const uint32_t per_chunk = (uint32_t)plan.groups * 2;
+    const uint64_t ntr = (uint64_t)pgrid * per_chunk;
+    const bool scales = R.s.sk != 0, local = R.s.sk == 3, dm = R.s.dm != 0;
+    const size_t gstate_bytes = plan.gstate ? global_state_bytes(R.mats[k].n, (int)S.rb, plan.lists != 0) : 0;
+    const SlotLayout sl = slot_layout(S.n_max, (int)S.m_max, (int)S.rb, scales, local, dm, gstate_bytes,
+                                      R.model != nullptr);
+    // probe buffers: plans, chunks, zero prefix, ln X, counters, chunk counter, slots
+    Layout L;
+    const size_t o_pl = L.take(sizeof(Plan) * count), o_ch = L.take(sizeof(Chunk) * pgrid),
+                 o_pf = L.take(8 * (count + 1)), o_lx = L.take(8 * ntr), o_ct = L.take(8 * 5 * count),
+                 o_cc = L.take(8), o_sl = L.take(sl.bytes * (size_t)pgrid * kCtaWarps);
+    DevBuf buf;
+    PM_CUDA(cudaMalloc(&buf.p, L.off));
+    uint8_t* B = (uint8_t*)buf.p;
+    std::vector<Plan> plans = S.plans;
+    plans[k] = plan;
+    std::vector<Chunk> chunks(pgrid);
+    for (int c = 0; c < pgrid; ++c) {
+        chunks[c].k = k;
+        chunks[c].count = per_chunk;
+        chunks[c].first = (uint64_t)c * per_chunk;
+    }
+    PM_CUDA(cudaMemcpyAsync(B + o_pl, plans.data(), sizeof(Plan) * count, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(B + o_ch, chunks.data(), sizeof(Chunk) * pgrid, cudaMemcpyHostToDevice, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(B + o_pf, 0, 8 * (count + 1), ctx->stream));
+    PM_CUDA(cudaMemsetAsync(B + o_ct, 0, 8 * 5 * count, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(B + o_cc, 0, 8, ctx->stream));
+    TrajParams tp = S.tp;
+    tp.plans = (const Plan*)(B + o_pl);
+    tp.chunks = (const Chunk*)(B + o_ch);
+    tp.n_chunks = pgrid;
+    tp.prefix = (const uint64_t*)(B + o_pf);
+    tp.first_traj = (uint64_t)1 << 47;
+    tp.seed = 0x5eedULL;
+    tp.log_x = (double*)(B + o_lx);
+    tp.counters = (unsigned long long*)(B + o_ct);
+    tp.chunk_counter = (int*)(B + o_cc);
+    tp.slots = B + o_sl;
+    tp.slot = sl;
+    const int smem = kCtaMiscBytes + learned_smem(R.model != nullptr) + plan.mat_bytes + plan.groups * plan.state_bytes;
+    PM_CUDA(cudaEventRecord(b->ws.ev0, ctx->stream));
+    PM_CUDA(launch_trajectories(tp, pgrid, smem, false, ctx->stream));
+    PM_CUDA(cudaEventRecord(b->ws.ev1, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    float ms = 0;
+    PM_CUDA(cudaEventElapsedTime(&ms, b->ws.ev0, b->ws.ev1));
+    uint32_t status = 0;
+    PM_CUDA(cudaMemcpy(&status, S.tp.status, 4, cudaMemcpyDeviceToHost));
+    if (status) return fail(ctx, PM_EDEVICE, "device status " + std::to_string(status) + " in an autotuner probe");
+    *rate = ms > 0 ? (double)ntr / (ms * 1e-3) : 0.0;
+    return PM_OK;
+}
+
+// Layout per matrix: for each size class, time the candidate policies on the
+// class's largest matrix and keep the fastest (cached in the context).
+pm_status autotune(pm_context* ctx, pm_batch* b, std::vector<Plan>& plans)
+{
+    Staged& S = b->S;
+    const Run& R = b->R;
+    const int count = R.count;
+    const bool learned = R.model != nullptr;
+    const int smem_max = traj_max_smem_bytes();
+    // the matrices must be prepared before a probe runs on them
+    uint8_t* A = b->ws.arena;
+    PM_CUDA(cudaMemsetAsync(A + S.o_status, 0, 4, ctx->stream));
+    PM_CUDA(launch_prepare((DevMatrix*)(A + S.o_mats), (const DevInput*)(A + S.o_inputs), count, R.s, S.n_max,
+                           (uint32_t*)(A + S.o_status), ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    uint32_t status = 0;
+    PM_CUDA(cudaMemcpy(&status, A + S.o_status, 4, cudaMemcpyDeviceToHost));
+    if (status & ST_BAD_INPUT) return fail(ctx, PM_EINVAL, "malformed CSR (device validation)");
+    if (status) return fail(ctx, PM_EUNSUPPORTED, "device status " + std::to_string(status) + " in preprocessing");
+    plans = S.plans;  // heuristic plans from the first stage_plans
+    std::map<int, int> rep;  // class -> representative matrix
+    for (int k = 0; k < count; ++k) {
+        const int c = size_class(R.mats[k].n);
+        auto it = rep.find(c);
+        if (it == rep.end() || (double)R.mats[k].n * R.mats[k].nnz > (double)R.mats[it->second].n * R.mats[it->second].nnz)
+            rep[c] = k;
+    }
+    for (const auto& cr : rep) {
+        const int k = cr.second;
+        const int n = R.mats[k].n;
+        const int64_t m = R.mats[k].nnz;
+        const std::string key = class_key(cr.first, R.s, learned);
+        Policy best = policy_of(S.plans[k]);
+        double best_rate = -1.0, heur_rate = -1.0;
+        auto cached = ctx->tuned.find(key);
+        if (cached != ctx->tuned.end()) {
+            best.staged = cached->second[0]; best.rc_smem = cached->second[1];
+            best.gstate = cached->second[2]; best.g = cached->second[3];
+        } else {
+            const std::vector<Policy> cands = candidate_policies(n, m, (int)S.rb, R.s, smem_max, learned);
+            if (cands.size() > 1) {
+                for (const Policy& pol : cands) {
+                    const Plan pl = plan_for(n, m, (int)S.rb, R.s, smem_max, learned, pol);
+                    if (pl.groups < 1) continue;
+                    double rate = 0;
+                    pm_status st = probe_plan(ctx, b, k, pl, &rate);
+                    if (st != PM_OK) return st;
+                    if (pol == policy_of(S.plans[k])) heur_rate = rate;
+                    if (rate > best_rate) { best_rate = rate; best = pol; }
+                }
+            }
+            ctx->tuned[key] = {best.staged, best.rc_smem, best.gstate, best.g};
+        }
+        for (int q = 0; q < count; ++q) {
+            if (size_class(R.mats[q].n) != cr.first) continue;
+            const Plan pl = plan_for(R.mats[q].n, R.mats[q].nnz, (int)S.rb, R.s, smem_max, learned, best);
+            if (pl.groups >= 1) {
+                plans[q] = pl;
+                b->info[q].tuned = 1;
+            }
+            b->info[q].probe_traj_per_s = best_rate;
+            b->info[q].heuristic_traj_per_s = heur_rate;
+        }
+    }
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_batch_create(pm_context* ctx, const pm_csr* mats, int32_t count, const uint64_t* n_traj,
+                          const pm_schedule* schedule, uint32_t flags, pm_batch** out)
+{
+    if (!ctx) return PM_EINVAL;
+    if (!out || !mats || count < 1 || count > 65535 || !n_traj || (flags & ~3u))
+        return fail(ctx, PM_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    pm_status st = check_schedule(ctx, schedule);
+    if (st != PM_OK) return st;
+    for (int k = 0; k < count; ++k) {
+        st = check_csr(ctx, &mats[k]);
+        if (st != PM_OK) return st;
+        if (n_traj[k] >= ((uint64_t)1 << 48)) return fail(ctx, PM_EINVAL, "n_traj above 2^48");
+    }
+    PM_CUDA(cudaSetDevice(ctx->device));
+    pm_batch* b = new (std::nothrow) pm_batch();
+    if (!b) return PM_ENOMEM;
+    b->ctx = ctx;
+    b->flags = flags;
+    auto bail = [&](pm_status s2) { cudaStreamSynchronize(ctx->stream); delete b; return s2; };
+    // device copies of the inputs
+    b->mats.resize(count);
+    for (int k = 0; k < count; ++k) {
+        const pm_csr& c = mats[k];
+        const size_t m = (size_t)c.nnz;
+        void *rp = nullptr, *ci = nullptr, *va = nullptr;
+        cudaError_t e = cudaMalloc(&rp, (c.n + 1) * 8);
+        if (e == cudaSuccess) b->bufs.push_back(rp);
+        if (e == cudaSuccess) e = cudaMalloc(&ci, std::max<size_t>(m, 1) * 4);
+        if (e == cudaSuccess) b->bufs.push_back(ci);
+        if (e == cudaSuccess && c.values) e = cudaMalloc(&va, std::max<size_t>(m, 1) * 4);
+        if (e == cudaSuccess && va) b->bufs.push_back(va);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rp, c.row_ptr, (c.n + 1) * 8, cudaMemcpyDefault, ctx->stream);
+        if (e == cudaSuccess && m) e = cudaMemcpyAsync(ci, c.col_idx, m * 4, cudaMemcpyDefault, ctx->stream);
+        if (e == cudaSuccess && m && c.values) e = cudaMemcpyAsync(va, c.values, m * 4, cudaMemcpyDefault, ctx->stream);
+        if (e != cudaSuccess)
+            return bail(fail(ctx, e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA, cudaGetErrorString(e)));
+        pm_csr& d = b->mats[k];
+        d = c;
+        d.on_device = 1;
+        d.row_ptr = (const int64_t*)rp;
+        d.col_idx = (const int32_t*)ci;
+        d.values = (const float*)va;
+    }
+    Run& R = b->R;
+    R.mats = b->mats.data();
+    R.count = count;
+    R.ntraj.assign(n_traj, n_traj + count);
+    R.s = to_sched(schedule);
+    R.model = schedule->learned ? schedule->learned->img : nullptr;
+    b->info.assign(count, pm_plan_info{});
+    st = stage_inputs(ctx, b->ws, R, b->S, (size_t)ctx->sm_count + count);
+    if (st != PM_OK) return bail(st);
+    st = stage_plans(ctx, b->ws, R, b->S, nullptr);
+    if (st != PM_OK) return bail(st);
+    if ((flags & PM_BATCH_AUTOTUNE) && b->S.launch_traj) {
+        std::vector<Plan> plans;
+        st = autotune(ctx, b, plans);
+        if (st != PM_OK) return bail(st);
+        st = stage_plans(ctx, b->ws, R, b->S, &plans);
+        if (st != PM_OK) return bail(st);
+    }
+    for (int k = 0; k < count && b->S.launch_traj; ++k) {
+        const Plan& p = b->S.plans[k];
+        pm_plan_info& I = b->info[k];
+        I.g = p.g; I.groups = p.groups; I.staged = p.staged; I.rc_smem = p.rc_smem; I.gstate = p.gstate;
+    }
+    if (flags & PM_BATCH_GRAPH) {
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (int seg = 0; seg < 3; ++seg) {
+            cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed);
+            if (e != cudaSuccess) return bail(fail(ctx, PM_ECUDA, std::string("capture: ") + cudaGetErrorString(e)));
+            st = seg == 0 ? enqueue_prep(ctx, b->ws, R, b->S)
+                          : seg == 1 ? enqueue_traj(ctx, b->ws, R, b->S) : enqueue_tail(ctx, b->ws, R, b->S);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(ctx->stream, &g);
+            b->graph[seg] = g;
+            if (st != PM_OK) return bail(st);
+            if (e != cudaSuccess) return bail(fail(ctx, PM_ECUDA, std::string("capture: ") + cudaGetErrorString(e)));
+            e = cudaGraphInstantiate(&b->exec[seg], b->graph[seg], 0);
+            if (e != cudaSuccess)
+                return bail(fail(ctx, PM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e)));
+        }
+        if (b->S.launch_traj) {
+            cudaError_t e;
+            size_t nn = 0;
+            e = cudaGraphGetNodes(b->graph[1], nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (e == cudaSuccess && nn) e = cudaGraphGetNodes(b->graph[1], nodes.data(), &nn);
+            const void* fn = traj_kernel_entry(b->S.tp, false);
+            for (size_t q = 0; q < nn && e == cudaSuccess; ++q) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nodes[q], &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+                cudaKernelNodeParams kp{};
+                if (cudaGraphKernelNodeGetParams(nodes[q], &kp) != cudaSuccess) continue;
+                if (kp.func == fn) {
+                    b->traj_node = nodes[q];
+                    b->traj_params = kp;
+                }
+            }
+            cudaGetLastError();
+            if (!b->traj_node) return bail(fail(ctx, PM_ECUDA, "the trajectory kernel node was not found in the graph"));
+        }
+    }
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->batches.push_back(b);
+    *out = b;
+    return PM_OK;
+}
+
+pm_status pm_batch_run(pm_batch* b, uint64_t first_traj, uint64_t seed, pm_result* outs, double* log_x)
+{
+    if (!b) return PM_EINVAL;
+    pm_context* ctx = b->ctx;
+    if (!outs) return fail(ctx, PM_EINVAL, "outs is NULL");
+    if (first_traj >= ((uint64_t)1 << 48)) return fail(ctx, PM_EINVAL, "first_traj above 2^48");
+    const auto t0 = std::chrono::steady_clock::now();
+    PM_CUDA(cudaSetDevice(ctx->device));
+    Run& R = b->R;
+    R.first_traj = first_traj;
+    R.seed = seed;
+    R.outs = outs;
+    R.log_x = log_x;
+    b->S.tp.first_traj = first_traj;
+    b->S.tp.seed = seed;
+    if (b->exec[0]) {
+        if (b->traj_node) {
+            void* args[] = {&b->S.tp};
+            cudaKernelNodeParams kp = b->traj_params;
+            kp.kernelParams = args;
+            kp.extra = nullptr;
+            PM_CUDA(cudaGraphExecKernelNodeSetParams(b->exec[1], b->traj_node, &kp));
+        }
+        PM_CUDA(cudaEventRecord(b->ws.ev2, ctx->stream));
+        PM_CUDA(cudaGraphLaunch(b->exec[0], ctx->stream));
+        PM_CUDA(cudaEventRecord(b->ws.ev0, ctx->stream));
+        PM_CUDA(cudaGraphLaunch(b->exec[1], ctx->stream));
+        PM_CUDA(cudaEventRecord(b->ws.ev1, ctx->stream));
+        PM_CUDA(cudaGraphLaunch(b->exec[2], ctx->stream));
+    } else {
+        pm_status st = enqueue(ctx, b->ws, R, b->S);
+        if (st != PM_OK) return st;
+    }
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    b->S.h2d = 0;
+    pm_status st = collect(ctx, b->ws, R, b->S, secs);
+    R.outs = nullptr;
+    R.log_x = nullptr;
+    return st;
+}
+
+pm_status pm_batch_plan_info(const pm_batch* b, int32_t k, pm_plan_info* info)
+{
+    if (!b || !info || k < 0 || k >= (int32_t)b->info.size()) return PM_EINVAL;
+    *info = b->info[k];
+    return PM_OK;
+}
+
+pm_status pm_batch_destroy(pm_batch* b)
+{
+    if (!b) return PM_EINVAL;
+    pm_context* ctx = b->ctx;
+    auto it = std::find(ctx->batches.begin(), ctx->batches.end(), b);
+    if (it == ctx->batches.end()) return PM_EINVAL;  // not a live batch of its context
+    ctx->batches.erase(it);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    delete b;
+    return PM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // learned proposal: model, training, parity entry points
@@ -810,11 +1328,6 @@ pm_status pm_model_set_params(pm_context* ctx, pm_model* m, const float* params)
 }
 
 // small device buffers for the parity entry points (freed on return)
-struct DevBuf {
-    void* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
-};
-
 pm_status pm_mlp_forward(pm_context* ctx, const pm_model* m, const float* X, uint64_t B, float* out)
 {
     if (!ctx || !m || !X || !out || B == 0 || B > (1ull << 30)) return PM_EINVAL;

@@ -239,6 +239,9 @@ cudaError_t launch_stats(const double* log_x, const uint64_t* h_prefix, const ui
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t count, uint32_t* out,
                           cudaStream_t st);
 int traj_max_smem_bytes();
+// the kernel launch_trajectories would launch for these parameters (to find
+// its node in a captured graph)
+const void* traj_kernel_entry(const TrajParams& p, bool trace);
 // learned proposal (pm_learn.cu)
 int model_image_bytes();
 int model_infer_bytes();

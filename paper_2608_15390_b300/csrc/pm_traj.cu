@@ -1043,6 +1043,15 @@ int traj_max_smem_bytes()
     return v;
 }
 
+const void* traj_kernel_entry(const TrajParams& p, bool trace)
+{
+    if (p.s.precision == 1)
+        return trace ? (const void*)traj_kernel<double, true, 0> : (const void*)traj_kernel<double, false, 0>;
+    if (p.model) return trace ? (const void*)traj_kernel<float, true, 1> : (const void*)traj_kernel<float, false, 1>;
+    if (p.rec_feat) return (const void*)traj_kernel<float, false, 2>;
+    return trace ? (const void*)traj_kernel<float, true, 0> : (const void*)traj_kernel<float, false, 0>;
+}
+
 cudaError_t launch_trajectories(const TrajParams& p, int grid, int smem, bool trace, cudaStream_t st)
 {
     if (p.s.precision == 1) {
