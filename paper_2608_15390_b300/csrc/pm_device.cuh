@@ -41,13 +41,18 @@ __device__ __forceinline__ uint64_t draw_u64(uint64_t seed, uint64_t traj, uint3
 }
 
 // Exact uniform integer in [0, W): keep the high word of u*W unless the low
-// word falls below 2^64 mod W (Lemire 2019).  Returns ~0 when every allowed
-// attempt was rejected.
-__device__ __forceinline__ uint64_t uniform_below(uint64_t W, uint64_t seed, uint64_t traj,
+// word falls below 2^64 mod W (Lemire 2019).  u0 is draw 0 of the step, drawn
+// by the caller ahead of time.  A low word >= W is above 2^64 mod W (< W), so
+// the 64-bit remainder is only computed in the rare case (probability below
+// W / 2^64) where the low word is < W; the decisions are those of the plain
+// rule.  Returns ~0 when every allowed attempt was rejected.
+__device__ __forceinline__ uint64_t uniform_below(uint64_t W, uint64_t u0, uint64_t seed, uint64_t traj,
                                                   uint32_t matrix, uint32_t step)
 {
+    if (u0 * W >= W) return __umul64hi(u0, W);
     const uint64_t reject_below = (0ull - W) % W;
-    for (uint32_t a = 0; a < (uint32_t)kMaxRngAttempts; ++a) {
+    if (u0 * W >= reject_below) return __umul64hi(u0, W);
+    for (uint32_t a = 1; a < (uint32_t)kMaxRngAttempts; ++a) {
         const uint64_t u = draw_u64(seed, traj, matrix, step, a);
         if (u * W >= reject_below) return __umul64hi(u, W);
     }

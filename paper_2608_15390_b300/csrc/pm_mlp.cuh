@@ -219,7 +219,7 @@ __device__ __forceinline__ float mlp_infer8(const DevModel* M, const uint16_t* f
         hb[mt][1] = trans8x8(pack_bf16(gelu_f(acc[2]), gelu_f(acc[3])));
     }
     float acc3[4] = {t == 0 ? M->b3[0] : 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
+#pragma unroll 2
     for (int mt = 0; mt < 4; ++mt) {
         const int h0 = 16 * mt + g;
         float acc[4] = {M->b2[h0], M->b2[h0], M->b2[h0 + 8], M->b2[h0 + 8]};

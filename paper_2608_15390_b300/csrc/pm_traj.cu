@@ -69,25 +69,33 @@ struct LiveTraj {
 };
 
 // ---- minimum-degree tree ----
+// (the level loops run over the compile-time maximum so the geometry arrays
+// are indexed statically and stay in registers)
 __device__ __forceinline__ void tree_lower(uint32_t* tree, const TreeGeom& T, int x, uint32_t d)
 {
     const uint32_t key = ((d < T.dcap ? d : T.dcap) << T.idb) | (uint32_t)x;
-    for (int l = 1; l <= T.nlev; ++l) atomicMin(&tree[T.off[l] + (x >> (5 * l))], key);
+#pragma unroll
+    for (int l = 1; l <= kMaxTreeLevels; ++l)
+        if (l <= T.nlev) atomicMin(&tree[T.off[l] + (x >> (5 * l))], key);
 }
 
+// recompute the tree entries above leaves x and y (two independent chains)
 __device__ void tree_fix2(const uint16_t* deg, uint32_t* tree, const TreeGeom& T, int x, int y, int lane)
 {
-    for (int l = 1; l <= T.nlev; ++l) {
-        const int gx = x >> (5 * l), gy = y >> (5 * l);
 #pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            const int gi = w ? gy : gx;
-            if (w && gy == gx) break;
-            const int c = gi * 32 + lane;
-            uint32_t key = 0xFFFFFFFFu;
-            if (c < T.size[l - 1]) key = (l == 1) ? leaf_key(deg, c, T) : tree[T.off[l - 1] + c];
-            key = __reduce_min_sync(kFull, key);
-            if (lane == 0) tree[T.off[l] + gi] = key;
+    for (int l = 1; l <= kMaxTreeLevels; ++l) {
+        if (l > T.nlev) break;
+        const int gx = x >> (5 * l), gy = y >> (5 * l);
+        const bool two = gy != gx;
+        const int cx = gx * 32 + lane, cy = gy * 32 + lane;
+        uint32_t kx = 0xFFFFFFFFu, ky = 0xFFFFFFFFu;
+        if (cx < T.size[l - 1]) kx = (l == 1) ? leaf_key(deg, cx, T) : tree[T.off[l - 1] + cx];
+        if (two && cy < T.size[l - 1]) ky = (l == 1) ? leaf_key(deg, cy, T) : tree[T.off[l - 1] + cy];
+        kx = __reduce_min_sync(kFull, kx);
+        ky = __reduce_min_sync(kFull, ky);
+        if (lane == 0) {
+            tree[T.off[l] + gx] = kx;
+            if (two) tree[T.off[l] + gy] = ky;
         }
         __syncwarp();
     }
@@ -113,10 +121,14 @@ __device__ void tree_build(const uint16_t* deg, uint32_t* tree, const TreeGeom& 
 __device__ __forceinline__ int md_pick(const uint16_t* deg, const uint32_t* tree, const TreeGeom& T, int lane)
 {
     uint32_t key = 0xFFFFFFFFu;
+    int top_off = 0, top_size = T.n2;
+#pragma unroll
+    for (int l = 1; l <= kMaxTreeLevels; ++l)
+        if (l == T.nlev) { top_off = T.off[l]; top_size = T.size[l]; }
     if (T.nlev == 0) {
         if (lane < T.n2) key = leaf_key(deg, lane, T);
-    } else if (lane < T.size[T.nlev]) {
-        key = tree[T.off[T.nlev] + lane];
+    } else if (lane < top_size) {
+        key = tree[top_off + lane];
     }
     key = __reduce_min_sync(kFull, key);
     if ((key >> T.idb) < T.dcap) return (int)(key & ((1u << T.idb) - 1u));
@@ -320,38 +332,62 @@ __device__ __forceinline__ Real cand_score(const MV<Idx>& V, bool vrow, int e, i
 // learned proposal's inputs): log1p deg(v), log1p deg(p),
 // log1p of the degree sum over v's live candidates, log1p of the degree sum
 // over p's live neighbours, t / n, ln of the outer scales of v and p, ln B_vp.
+// Sum, over the live neighbours of each live lane's candidate p, of their live
+// degrees: the whole warp scans one candidate's adjacency at a time (one lane
+// per entry, an integer reduction), so the cost is one pass per candidate
+// instead of a serial loop per lane.  Integer sums: the result does not depend
+// on the order.
 template <typename Idx>
-__device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask,
-                                              const DevMatrix* Mp, int t, int v, bool vrow, int e, int p,
-                                              float sum_v, float dv, float (&f)[8])
+__device__ __forceinline__ int neighbour_degree_sum(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask,
+                                                    bool vrow, int pp, bool live, int lane)
 {
     const int n = V.n;
-    int sum_l = 0;
-    if (vrow) {  // p is a column: its live rows
-        for (int k = V.cp[p]; k < V.cp[p + 1]; ++k) {
-            const int i = V.ri[k];
-            if (deg[i] != kInact && (!mask || mask[V.ce[k]])) sum_l += deg[i];
+    int mine = 0;
+    unsigned lm = __ballot_sync(kFull, live);
+    while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1u;
+        const int p = __shfl_sync(kFull, pp, src);
+        const int b = vrow ? V.cp[p] : V.rp[p];
+        const int en = vrow ? V.cp[p + 1] : V.rp[p + 1];
+        unsigned acc = 0;
+        for (int k = b + lane; k < en; k += 32) {
+            if (vrow) {  // p is a column: its live rows
+                const int i = V.ri[k];
+                const unsigned d = deg[i];
+                if (d != kInact && (!mask || mask[V.ce[k]])) acc += d;
+            } else {     // p is a row: its live columns
+                const int j = V.ci[k];
+                const unsigned d = deg[n + j];
+                if (d != kInact && (!mask || mask[k])) acc += d;
+            }
         }
-    } else {     // p is a row: its live columns
-        for (int k = V.rp[p]; k < V.rp[p + 1]; ++k) {
-            const int j = V.ci[k];
-            if (deg[n + j] != kInact && (!mask || mask[k])) sum_l += deg[n + j];
-        }
+        const unsigned tot = __reduce_add_sync(kFull, acc);
+        if (lane == src) mine = (int)tot;
     }
+    return mine;
+}
+
+template <typename Idx>
+__device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* deg, const DevMatrix* Mp, int t,
+                                              bool vrow, int e, int p, float sum_v, int sum_l, float dv, float lsv,
+                                              float (&f)[8])
+{
+    const int n = V.n;
     const float* r0 = reinterpret_cast<const float*>(Mp->r0);
     const float* c0 = reinterpret_cast<const float*>(Mp->c0);
-    const float sv = vrow ? __ldg(r0 + v) : __ldg(c0 + (v - n));
     const float sl = vrow ? __ldg(c0 + p) : __ldg(r0 + p);
     const float* vals = vrow ? V.rv : V.cv;
+    const float bv = vals ? __ldg(vals + e) : 1.0f;
     // fast logarithms (about 1e-6 relative): 1 + an integer count is exact in binary32
     f[0] = __logf(1.0f + dv);
     f[1] = __logf(1.0f + (float)deg[p + (vrow ? n : 0)]);
     f[2] = __logf(1.0f + sum_v);
     f[3] = __logf(1.0f + (float)sum_l);
     f[4] = __fdiv_rn((float)t, (float)n);
-    f[5] = __logf(sv);
+    f[5] = lsv;
     f[6] = __logf(sl);
-    f[7] = vals ? __logf(__ldg(vals + e)) : 0.0f;
+    f[7] = vals ? __logf(bv) : 0.0f;
 }
 
 // misc slots of a group (two step buffers so a fast leader never overwrites
@@ -450,6 +486,9 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         if (leader) {
             int dead = 0, nit = 0, run_dm = 0, cnt_r = 0, cnt_c = 0;
             do {  // the sequential part of step t (breaks out on death)
+                // draw 0 of this step depends on (seed, trajectory, step) only:
+                // computed first, it overlaps the pick and the candidate scan
+                const uint64_t u0 = draw_u64(P.seed, traj, midx, (uint32_t)t, 0);
                 const int v = (S.vertex_rule == VR_ROW) ? t : md_pick(deg, tree, T, lane);
                 const int dv = deg[v];
                 if (TRACE && lane == 0) P.deg_v[gq * n + t] = dv;
@@ -470,7 +509,10 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 uint64_t rr;
                 // learned proposal: logits of the live candidates from their features
                 float sum_v = 0.f;  // degree sum over v's live candidates (feature)
+                float lsv = 0.f;    // ln of v's outer scale (feature)
                 if (model || rec) {
+                    const float* s0 = reinterpret_cast<const float*>(vrow ? Mp->r0 : Mp->c0);
+                    const float sv0 = __ldg(s0 + vi);
                     int sv_i = 0;
                     for (int base = beg; base < end; base += 32) {
                         const int e = base + lane;
@@ -482,6 +524,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
 #pragma unroll
                     for (int o = 16; o; o >>= 1) sv_i += __shfl_xor_sync(kFull, sv_i, o);
                     sum_v = (float)sv_i;
+                    lsv = __logf(sv0);
                 }
                 // logits of the live candidates of one chunk: their features
                 // go to rows 0..nl-1 of the tile (live order), the network
@@ -490,9 +533,10 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     const unsigned lmk = __ballot_sync(kFull, live);
                     const int nl = __popc(lmk);
                     const int li = __popc(lmk & ((1u << lane) - 1u));
+                    const int sum_l = neighbour_degree_sum<Idx>(V, deg, mask, vrow, pp, live, lane);
                     if (live) {
                         float f[8];
-                        cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
+                        cand_features<Idx>(V, deg, Mp, t, vrow, e, pp, sum_v, sum_l, (float)dv, lsv, f);
                         uint4 lo;
                         lo.x = pack_bf16(f[0], f[1]);
                         lo.y = pack_bf16(f[2], f[3]);
@@ -533,8 +577,9 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 // least two (pass 1 counts them, pass 2 writes them)
                 if (rec) {
                     auto pair_at = [&](int e, int pp, bool live, float (&f)[8], float& tgt) -> bool {
+                        const int sum_l = neighbour_degree_sum<Idx>(V, deg, mask, vrow, pp, live, lane);
                         if (!live) return false;
-                        cand_features<Idx>(V, deg, mask, Mp, t, v, vrow, e, pp, sum_v, (float)dv, f);
+                        cand_features<Idx>(V, deg, Mp, t, vrow, e, pp, sum_v, sum_l, (float)dv, lsv, f);
                         const double sv_cur = vrow ? (double)r[vi] : (double)c[vi];
                         const double sl_cur = vrow ? (double)c[pp] : (double)r[pp];
                         tgt = (float)log(sv_cur * sl_cur);
@@ -631,7 +676,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                         w = live ? quant_weight<Real>(sv, smax, kq) : 0ull;
                         W = warp_sum_u64(w);
                     }
-                    rr = uniform_below(W, P.seed, traj, midx, (uint32_t)t);
+                    rr = uniform_below(W, u0, P.seed, traj, midx, (uint32_t)t);
                     if (rr == ~0ull) {
                         if (lane == 0) atomicOr(P.status, ST_RNG_EXHAUSTED);
                         dead = 1;
@@ -687,7 +732,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     } else {
                         W = (uint64_t)dv << kq;
                     }
-                    rr = uniform_below(W, P.seed, traj, midx, (uint32_t)t);
+                    rr = uniform_below(W, u0, P.seed, traj, midx, (uint32_t)t);
                     if (rr == ~0ull) {
                         if (lane == 0) atomicOr(P.status, ST_RNG_EXHAUSTED);
                         dead = 1;
@@ -734,7 +779,9 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     if (vals) num.mul(__ldg(vals + sel_e));
                     den.mul(w_sel);
                 }
-                const Real z = RA<Real>::mul(r[R], c[C]);
+                // z = r_R c_C drives the Thrs / Trck DM policies and Adaptive SK only
+                const bool need_z = S.dm == DMP_THRS || S.dm == DMP_TRCK || S.sk == SKP_ADAPTIVE;
+                const Real z = need_z ? RA<Real>::mul(r[R], c[C]) : (Real)1;
 
                 // eliminate R and C (their per-trajectory scales become 0)
                 __syncwarp();
