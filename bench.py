@@ -65,6 +65,9 @@ def parse():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--mats", type=int, default=N_MATS,
                    help="use the first K matrices (profiling of a smaller case)")
+    p.add_argument("--workload", default="batch", choices=["batch", "serving"],
+                   help="batch: the 64-matrix batch (the metric); serving: the Poisson request stream")
+    p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of each serving load")
     p.add_argument("--nmax", type=int, default=N_HI,
                    help="draw n from U{100..nmax} instead (profiling of a smaller case)")
     return p.parse_args()
@@ -346,11 +349,116 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+SERVE_N_LO, SERVE_N_HI, SERVE_SEED, SERVE_RSE = 50, 50_000, 5, 1e-2
+SERVE_MAX_STEPS = 1 << 26  # work budget of a request: trajectory steps (n per trajectory)
+
+
+def serve_budget(m):
+    """trajectories a request may use: 2^26 steps, between 1024 and 2^16"""
+    return int(min(1 << 16, max(1024, SERVE_MAX_STEPS // m.n)))
+
+
+def serving_request(i):
+    """Request i of the serving stream: n = floor(exp U[ln 50, ln 5e4]), power-law
+    row degrees (exponent 2.5, minimum 2), planted permutation."""
+    rng = np.random.default_rng([SERVE_SEED, i])
+    n = int(math.exp(rng.uniform(math.log(SERVE_N_LO), math.log(SERVE_N_HI))))
+    return G.powerlaw_planted(n, seed=SERVE_SEED * 1_000_003 + i)
+
+
+def run_serving(args, local):
+    """The serving configuration: a capacity run (all requests present at
+    once), then Poisson arrivals at 0.3 / 0.6 / 0.9 of that capacity for
+    --serve-seconds each; every request asks for RSE <= 1e-2 with a work
+    budget of 2^26 trajectory steps (1024 to 2^16 trajectories); latency =
+    finish time - arrival time on the server
+    clock.  The learned proposal is trained first (untimed) on power-law
+    matrices of the same family."""
+    import torch
+    from paper_2608_15390_b300 import binding as B
+    torch.cuda.set_device(local)
+    ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
+    model = ctx.model(seed=21)
+    train = [G.powerlaw_planted(n, seed=900 + k) for k, n in enumerate(np.geomspace(50, 3000, 16).astype(int))]
+    model.train(train, B.Schedule(**TEACHER), n_pairs=1_000_000, epochs=4, batch=8192, lr=2e-3, seed=22,
+                objective=B.OBJ_CENTRED)
+    sched = B.Schedule(**LEARNED, learned=model)
+
+    def make_server():
+        return ctx.server(sched, seed=args.seed, device_budget_bytes=32 << 30, steps_per_round=1 << 22,
+                          traj_min=32, traj_max=1 << 15, min_traj_done=1024)
+
+    def summarise(done, arrivals, t_span):
+        lat = np.array([d["done_time"] - arrivals[d["id"]] for d in done])
+        ok = [d for d in done if d["status"] == B.REQ_DONE]
+        return {"requests": len(done), "throughput_req_per_s": len(done) / t_span,
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "target_met_frac": len(ok) / max(1, len(done)),
+                "budget_spent_frac": sum(d["status"] == B.REQ_BUDGET for d in done) / max(1, len(done)),
+                "median_rse": float(np.median([d["result"]["rse"] for d in done if d["result"]["n_alive"] > 1]))}
+
+    # capacity: 48 requests present at once, served to completion
+    reqs = [serving_request(i) for i in range(48)]
+    sv = make_server()
+    arrivals = {}
+    for m in reqs:
+        arrivals[sv.submit(m, SERVE_RSE, serve_budget(m))] = sv.clock()
+    t_start = sv.clock()
+    done = []
+    while len(done) < len(reqs):
+        out, _, _ = sv.round()
+        done += out
+    t_cap = sv.clock() - t_start
+    capacity = len(reqs) / t_cap
+    cap_line = summarise(done, arrivals, t_cap)
+    sv.close()
+    loads = []
+    for frac in (0.3, 0.6, 0.9):
+        rate = frac * capacity
+        rng = np.random.default_rng([SERVE_SEED, int(frac * 10)])
+        times = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * args.serve_seconds * 2) + 8))
+        times = times[times < args.serve_seconds]
+        base = 10_000 * int(frac * 10)
+        pending = [(t, serving_request(base + i)) for i, t in enumerate(times)]
+        sv = make_server()
+        t0 = sv.clock()
+        arrivals, done, nxt = {}, [], 0
+        while nxt < len(pending) or len(done) < len(pending):
+            now = sv.clock() - t0
+            while nxt < len(pending) and pending[nxt][0] <= now:
+                arrivals[sv.submit(pending[nxt][1], SERVE_RSE, serve_budget(pending[nxt][1]))] = t0 + pending[nxt][0]
+                nxt += 1
+            out, na, nq = sv.round()
+            done += out
+            if na == 0 and nq == 0 and nxt < len(pending):
+                time.sleep(max(0.0, min(0.05, pending[nxt][0] - (sv.clock() - t0))))
+        t_span = sv.clock() - t0
+        line = summarise(done, arrivals, t_span)
+        line.update({"load": frac, "arrival_rate_req_per_s": rate, "arrivals": len(pending)})
+        loads.append(line)
+        sv.close()
+    model.close()
+    out = {"metric": "serving: p50 / p99 latency and throughput at RSE <= 1e-2", "workload": "serving",
+           "config": {"requests": "n = floor(exp U[ln 50, ln 5e4]), power-law rows (2.5, min 2) + planted "
+                                  "permutation, RSE target 1e-2, budget 2^26 trajectory steps each "
+                                  "(1024 to 2^16 trajectories)",
+                      "estimator": "learned proposal, two-sided MD, initial DM, outer SK(100)",
+                      "admission": "device bytes of admitted requests <= 32 GiB, first come first served",
+                      "arrival_window_s": args.serve_seconds},
+           "capacity_req_per_s": capacity, "capacity_run": cap_line, "loads": loads, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            run_serving(args, local)
         return
     import torch
     torch.cuda.set_device(local)

@@ -231,6 +231,56 @@ pm_status pm_batch_run(pm_batch* batch, uint64_t first_traj, uint64_t seed, pm_r
 pm_status pm_batch_plan_info(const pm_batch* batch, int32_t k, pm_plan_info* info);
 pm_status pm_batch_destroy(pm_batch* batch);
 
+/* ---- serving (no counterpart in the paper) --------------------------------
+ * A server estimates a stream of requests, each until its RSE (Sec. 4
+ * "Metrics") reaches the request's target or its trajectory budget is spent.
+ * pm_server_submit copies a matrix to the device and queues it.  Every
+ * pm_server_round
+ *   1. admits queued requests first come first served while the device bytes
+ *      of the admitted requests stay within cfg.device_budget_bytes (a request
+ *      larger than the whole budget is refused) and prepares each once
+ *      (InitialDM, outer SK, degrees, tree: Algorithm 2's preprocessing);
+ *   2. runs one persistent trajectory launch over all admitted requests,
+ *      max(steps_per_round / n, the request's share of the GPU's trajectory
+ *      slots) trajectories each (clamped to [traj_min, traj_max] and to what
+ *      is left of the request's budget), with ids disjoint from every earlier
+ *      round;
+ *   3. merges each request's statistics with its earlier rounds and returns
+ *      the requests that are finished (target met with at least
+ *      min_traj_done trajectories and two alive, budget spent, refused).
+ * Times are seconds on the server's clock (pm_server_clock, from creation).
+ * The context (and a learned model) must outlive the server. */
+typedef struct pm_server pm_server;
+enum { PM_REQ_DONE = 0, PM_REQ_BUDGET = 1, PM_REQ_REFUSED = 2, PM_REQ_FAILED = 3 };
+
+typedef struct {
+    pm_schedule schedule;         /* estimator of every request */
+    uint64_t seed;                /* Philox seed of all rounds */
+    uint64_t device_budget_bytes; /* admission limit */
+    uint64_t steps_per_round;     /* trajectory steps per request per round (T = steps / n) */
+    uint32_t traj_min, traj_max;  /* per request and round; 1 <= traj_min <= traj_max < 2^24 */
+    uint64_t min_traj_done;       /* trajectories before the RSE target may end a request */
+} pm_server_cfg;
+
+typedef struct {
+    uint64_t id;
+    int32_t status;               /* PM_REQ_* */
+    uint32_t rounds;
+    pm_result result;             /* merged over all rounds (seconds, kernel_ms, alg_bytes: 0) */
+    double submit_time, done_time;
+} pm_request_done;
+
+pm_status pm_server_create(pm_context* ctx, const pm_server_cfg* cfg, pm_server** out);
+/* target_rse > 0; max_traj >= 1.  *id identifies the request in later results. */
+pm_status pm_server_submit(pm_server* server, const pm_csr* csr, double target_rse, uint64_t max_traj,
+                           uint64_t* id);
+/* done[cap] (host) receives the finished requests, *n_done of them; n_active,
+ * n_queued (may be NULL) the requests still admitted / waiting. */
+pm_status pm_server_round(pm_server* server, pm_request_done* done, uint32_t cap, uint32_t* n_done,
+                          uint32_t* n_active, uint32_t* n_queued);
+double pm_server_clock(const pm_server* server);
+pm_status pm_server_destroy(pm_server* server);
+
 /* ---- learned proposal (no counterpart in the paper) ----------------------
  * A small network f: 8 edge features -> 64 -> 64 (GELU) -> 1 predicts
  * ln(r_v c_l), the scale product an SK-scheduled run would use for edge

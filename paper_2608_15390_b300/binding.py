@@ -30,6 +30,7 @@ DM_NONE, DM_ALL, DM_THRS, DM_TRCK = 0, 1, 2, 3
 PREC_FP32_PROPOSAL, PREC_FP64 = 0, 1
 OBJ_MSE, OBJ_CENTRED = 0, 1
 BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
+REQ_DONE, REQ_BUDGET, REQ_REFUSED, REQ_FAILED = 0, 1, 2, 3
 
 
 class PmError(RuntimeError):
@@ -74,6 +75,12 @@ class pm_plan_info(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class pm_server_cfg(C.Structure):
+    _fields_ = [("schedule", pm_schedule), ("seed", C.c_uint64), ("device_budget_bytes", C.c_uint64),
+                ("steps_per_round", C.c_uint64), ("traj_min", C.c_uint32), ("traj_max", C.c_uint32),
+                ("min_traj_done", C.c_uint64)]
+
+
 class pm_result(C.Structure):
     _fields_ = [("log_estimate", C.c_double), ("estimate", C.c_double), ("ess", C.c_double),
                 ("p_match", C.c_double), ("rel_spread", C.c_double), ("rse", C.c_double),
@@ -84,6 +91,11 @@ class pm_result(C.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class pm_request_done(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("rounds", C.c_uint32), ("result", pm_result),
+                ("submit_time", C.c_double), ("done_time", C.c_double)]
 
 
 class pm_call_info(C.Structure):
@@ -129,6 +141,15 @@ def _load():
     L.pm_batch_destroy.argtypes = [P]
     for name in ("pm_batch_create", "pm_batch_run", "pm_batch_plan_info", "pm_batch_destroy"):
         getattr(L, name).restype = C.c_int
+    L.pm_server_create.argtypes = [P, C.POINTER(pm_server_cfg), C.POINTER(P)]
+    L.pm_server_submit.argtypes = [P, C.POINTER(pm_csr), C.c_double, C.c_uint64, C.POINTER(C.c_uint64)]
+    L.pm_server_round.argtypes = [P, C.POINTER(pm_request_done), C.c_uint32, C.POINTER(C.c_uint32),
+                                  C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    L.pm_server_destroy.argtypes = [P]
+    for name in ("pm_server_create", "pm_server_submit", "pm_server_round", "pm_server_destroy"):
+        getattr(L, name).restype = C.c_int
+    L.pm_server_clock.argtypes = [P]
+    L.pm_server_clock.restype = C.c_double
     L.pm_preprocess.argtypes = [P, C.POINTER(pm_csr), C.POINTER(pm_schedule), P, P, P, P]
     L.pm_philox_blocks.argtypes = [P, P, P, C.c_uint32, P]
     L.pm_last_call_info.argtypes = [P, C.POINTER(pm_call_info)]
@@ -161,7 +182,8 @@ EXPORTED = ["pm_context_create", "pm_context_destroy", "estimate_permanent",
             "pm_last_call_info", "pm_log_weight_stats_noalloc", "pm_status_string", "pm_last_error",
             "pm_model_create", "pm_model_destroy", "pm_model_get_params", "pm_model_set_params",
             "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs",
-            "pm_batch_create", "pm_batch_run", "pm_batch_plan_info", "pm_batch_destroy"]
+            "pm_batch_create", "pm_batch_run", "pm_batch_plan_info", "pm_batch_destroy",
+            "pm_server_create", "pm_server_submit", "pm_server_round", "pm_server_clock", "pm_server_destroy"]
 
 
 @dataclass
@@ -293,6 +315,14 @@ class Context:
                                               C.byref(s), outs,
                                               None if lx is None else lx.ctypes.data))
         return [o.as_dict() for o in outs], lx
+
+    def server(self, schedule: Schedule, seed: int = 1, device_budget_bytes: int = 8 << 30,
+               steps_per_round: int = 1 << 20, traj_min: int = 32, traj_max: int = 1 << 16,
+               min_traj_done: int = 1024) -> "Server":
+        """A serving loop (pm_server_create); closing the context closes it."""
+        sv = Server(self, schedule, seed, device_budget_bytes, steps_per_round, traj_min, traj_max, min_traj_done)
+        self._batches.add(sv)
+        return sv
 
     def batch(self, mats: Sequence, n_traj: Sequence[int], schedule: Schedule, graph: bool = True,
               autotune: bool = False) -> "Batch":
@@ -472,6 +502,53 @@ class Batch:
     def close(self):
         if self.h and self.ctx.h:
             _lib.pm_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """pm_server: requests submitted at any time, estimated in rounds of one
+    persistent launch each until their RSE target or budget."""
+
+    def __init__(self, ctx: Context, schedule: Schedule, seed, budget, steps, tmin, tmax, min_done):
+        self.ctx = ctx
+        self.h = None
+        self._sched = schedule
+        cfg = pm_server_cfg(schedule.c(), seed, budget, steps, tmin, tmax, min_done)
+        h = C.c_void_p()
+        ctx._check(_lib.pm_server_create(ctx.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self._buf = (pm_request_done * 4096)()
+
+    def submit(self, m, target_rse: float, max_traj: int) -> int:
+        c, keep = make_csr(m)
+        rid = C.c_uint64()
+        self.ctx._check(_lib.pm_server_submit(self.h, C.byref(c), target_rse, max_traj, C.byref(rid)))
+        return rid.value
+
+    def round(self):
+        """One round; returns (finished requests as dicts, n_active, n_queued)."""
+        nd, na, nq = C.c_uint32(), C.c_uint32(), C.c_uint32()
+        self.ctx._check(_lib.pm_server_round(self.h, self._buf, len(self._buf), C.byref(nd), C.byref(na),
+                                             C.byref(nq)))
+        out = []
+        for i in range(nd.value):
+            d = self._buf[i]
+            out.append({"id": d.id, "status": d.status, "rounds": d.rounds, "result": d.result.as_dict(),
+                        "submit_time": d.submit_time, "done_time": d.done_time})
+        return out, na.value, nq.value
+
+    def clock(self) -> float:
+        return _lib.pm_server_clock(self.h)
+
+    def close(self):
+        if self.h and self.ctx.h:
+            _lib.pm_server_destroy(self.h)
         self.h = None
 
     def __del__(self):

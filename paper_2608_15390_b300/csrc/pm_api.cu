@@ -301,6 +301,9 @@ struct Run {
     int32_t* ok_out = nullptr;
     uint8_t* keep_out = nullptr;
     double *r_out = nullptr, *c_out = nullptr;
+    // matrices already prepared in device memory that outlives the run
+    // (host copies of their descriptors; mats then supply n and nnz only)
+    const DevMatrix* prepared = nullptr;
 };
 
 struct MatOff {
@@ -353,8 +356,8 @@ pm_status stage_inputs(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, 
     const size_t rb = S.rb;
 
     Layout L;
-    S.mo.resize(count);
-    for (int k = 0; k < count; ++k) {
+    S.mo.resize(R.prepared ? 0 : count);
+    for (int k = 0; k < count && !R.prepared; ++k) {
         const pm_csr& c = R.mats[k];
         const int n = c.n;
         const size_t m = (size_t)c.nnz;
@@ -414,7 +417,8 @@ pm_status stage_inputs(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, 
 
     std::vector<DevMatrix> hm(count);
     std::vector<DevInput> hi(count);
-    for (int k = 0; k < count; ++k) {
+    if (R.prepared) std::copy(R.prepared, R.prepared + count, hm.begin());
+    for (int k = 0; k < count && !R.prepared; ++k) {
         const pm_csr& c = R.mats[k];
         const MatOff& o = S.mo[k];
         const int n = c.n;
@@ -576,8 +580,9 @@ pm_status enqueue_prep(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
     PM_CUDA(cudaMemsetAsync(P(S.o_counters), 0, 8 * 5 * R.count, ctx->stream));
     PM_CUDA(cudaMemsetAsync(P(S.o_work), 0, 8, ctx->stream));
     PM_CUDA(cudaMemsetAsync(P(S.o_status), 0, 4, ctx->stream));
-    PM_CUDA(launch_prepare((DevMatrix*)P(S.o_mats), (const DevInput*)P(S.o_inputs), R.count, R.s, S.n_max,
-                           (uint32_t*)P(S.o_status), ctx->stream));
+    if (!R.prepared)
+        PM_CUDA(launch_prepare((DevMatrix*)P(S.o_mats), (const DevInput*)P(S.o_inputs), R.count, R.s, S.n_max,
+                               (uint32_t*)P(S.o_status), ctx->stream));
     return PM_OK;
 }
 
@@ -1249,6 +1254,328 @@ pm_status pm_batch_destroy(pm_batch* b)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     delete b;
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// serving: a stream of requests, each run in rounds until its RSE target
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+// one request: its device copy and prepared state (own workspace), and the
+// statistics merged over its rounds
+struct Request {
+    uint64_t id = 0;
+    double target_rse = 0, t_submit = 0;
+    uint64_t max_traj = 0, done_traj = 0;
+    uint32_t rounds = 0;
+    pm_csr host{};                // n, nnz (pointers are the device copies)
+    std::vector<void*> bufs;
+    Workspace ws;                 // arena with the prepared matrix
+    DevMatrix dm{};               // prepared descriptor (device pointers into ws)
+    size_t bytes = 0;             // device bytes held
+    bool prepared = false;
+    // merged statistics (Sec. 2 / Sec. 4: sufficient statistics of all rounds)
+    uint64_t n = 0, alive = 0, n_dm = 0, n_full = 0, n_loc = 0;
+    double lse1 = -INFINITY, lse2 = -INFINITY;
+    void release()
+    {
+        for (void* b : bufs) cudaFree(b);
+        bufs.clear();
+        ws.release();
+    }
+};
+
+double lse_add(double a, double b)
+{
+    if (a == -INFINITY) return b;
+    if (b == -INFINITY) return a;
+    const double m = a > b ? a : b;
+    return m + std::log(std::exp(a - m) + std::exp(b - m));
+}
+
+// statistics of merged sufficient statistics (as the statistics kernels)
+void fill_result(const Request& q, pm_result& o)
+{
+    std::memset(&o, 0, sizeof(o));
+    o.n_traj = q.n;
+    o.n_alive = q.alive;
+    o.log_sum_x = q.lse1;
+    o.log_sum_x2 = q.lse2;
+    o.n_dm_calls = q.n_dm;
+    o.n_full_sk = q.n_full;
+    o.n_local_sk = q.n_loc;
+    o.p_match = q.n ? (double)q.alive / (double)q.n : 0.0;
+    if (q.n == 0 || q.lse1 == -INFINITY) {
+        o.log_estimate = -INFINITY;
+        o.rel_spread = o.rse = NAN;
+        return;
+    }
+    const double M = (double)q.n;
+    o.log_estimate = q.lse1 - std::log(M);
+    o.estimate = std::exp(o.log_estimate);
+    o.ess = std::exp(2 * q.lse1 - q.lse2);
+    if (q.n > 1) {
+        const double ratio = M * std::exp(q.lse2 - 2 * q.lse1);
+        o.rel_spread = std::sqrt(std::max(0.0, ratio - 1.0) * M / (M - 1.0));
+        o.rse = o.rel_spread / std::sqrt(M);
+    } else {
+        o.rel_spread = o.rse = NAN;
+    }
+}
+
+}  // namespace
+
+struct pm_server {
+    pm_context* ctx = nullptr;
+    pm_server_cfg cfg{};
+    Sched s{};
+    const void* model = nullptr;
+    std::vector<Request*> queue, active;
+    uint64_t next_id = 1, round = 0, bytes_active = 0;
+    Workspace ws;  // the rounds' workspace
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+    ~pm_server()
+    {
+        for (Request* q : queue) { q->release(); delete q; }
+        for (Request* q : active) { q->release(); delete q; }
+        ws.release();
+    }
+};
+
+namespace {
+
+// device bytes a request needs: its copy of A plus the prepared state (the
+// preprocessing layout of one matrix)
+size_t request_bytes(const pm_csr& c, bool fp64)
+{
+    const size_t n = (size_t)c.n, m = (size_t)c.nnz, rb = fp64 ? 8 : 4;
+    const size_t w = c.values ? 1 : 0;
+    return (n + 1) * 8 + m * 4 * (1 + w)                          // copy of the input
+           + (n + 1) * 4 * 3 + m * (4 * 6 + 1) + m * 4 * 2 * w     // A's int32 CSR/CSC, mask, B0
+           + n * rb * 2 + (2 * n + 8) * 2 + (2 * n / 32 + 64) * 4  // scales, degrees, tree
+           + (size_t)dm_ws_ints((int)c.n) * 4 + 16 * 256;
+}
+
+// copy and prepare (InitialDM, outer SK, degrees, tree) one request
+pm_status prepare_request(pm_server* sv, Request* q)
+{
+    pm_context* ctx = sv->ctx;
+    Run R;
+    R.mats = &q->host;
+    R.count = 1;
+    R.ntraj.assign(1, 0);
+    R.s = sv->s;
+    R.prep_only = true;
+    Staged S;
+    pm_status st = stage_inputs(ctx, q->ws, R, S);
+    if (st != PM_OK) return st;
+    S.launch_traj = false;
+    st = enqueue(ctx, q->ws, R, S);
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    const uint32_t status = *S.h_status;
+    if (status & ST_BAD_INPUT) return fail(ctx, PM_EINVAL, "malformed CSR (device validation)");
+    if (status) return fail(ctx, PM_EUNSUPPORTED, "device status " + std::to_string(status) + " in preprocessing");
+    q->dm = S.h_mats[0];
+    q->prepared = true;
+    // the pinned read-back area is not needed any more
+    if (q->ws.pinned) { cudaFreeHost(q->ws.pinned); q->ws.pinned = nullptr; q->ws.pinned_cap = 0; }
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_server_create(pm_context* ctx, const pm_server_cfg* cfg, pm_server** out)
+{
+    if (!ctx) return PM_EINVAL;
+    if (!cfg || !out || cfg->traj_min == 0 || cfg->traj_max < cfg->traj_min || cfg->traj_max >= (1u << 24) ||
+        cfg->steps_per_round == 0 || cfg->min_traj_done == 0 || cfg->device_budget_bytes == 0)
+        return fail(ctx, PM_EINVAL, "bad server configuration");
+    pm_status st = check_schedule(ctx, &cfg->schedule);
+    if (st != PM_OK) return st;
+    pm_server* sv = new (std::nothrow) pm_server();
+    if (!sv) return PM_ENOMEM;
+    sv->ctx = ctx;
+    sv->cfg = *cfg;
+    sv->s = to_sched(&cfg->schedule);
+    sv->model = cfg->schedule.learned ? cfg->schedule.learned->img : nullptr;
+    *out = sv;
+    return PM_OK;
+}
+
+pm_status pm_server_submit(pm_server* sv, const pm_csr* csr, double target_rse, uint64_t max_traj, uint64_t* id)
+{
+    if (!sv) return PM_EINVAL;
+    pm_context* ctx = sv->ctx;
+    if (!id || !(target_rse > 0) || max_traj == 0) return fail(ctx, PM_EINVAL, "bad request");
+    pm_status st = check_csr(ctx, csr);
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    Request* q = new (std::nothrow) Request();
+    if (!q) return PM_ENOMEM;
+    q->id = sv->next_id++;
+    q->target_rse = target_rse;
+    q->max_traj = max_traj;
+    q->t_submit = sv->now();
+    q->bytes = request_bytes(*csr, sv->s.precision == 1);
+    // the request keeps its own device copy from now on
+    const size_t m = (size_t)csr->nnz;
+    void *rp = nullptr, *ci = nullptr, *va = nullptr;
+    cudaError_t e = cudaMalloc(&rp, (csr->n + 1) * 8);
+    if (e == cudaSuccess) q->bufs.push_back(rp);
+    if (e == cudaSuccess) e = cudaMalloc(&ci, std::max<size_t>(m, 1) * 4);
+    if (e == cudaSuccess) q->bufs.push_back(ci);
+    if (e == cudaSuccess && csr->values) e = cudaMalloc(&va, std::max<size_t>(m, 1) * 4);
+    if (e == cudaSuccess && va) q->bufs.push_back(va);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rp, csr->row_ptr, (csr->n + 1) * 8, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(ci, csr->col_idx, m * 4, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess && m && va) e = cudaMemcpyAsync(va, csr->values, m * 4, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        q->release();
+        delete q;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA, cudaGetErrorString(e));
+    }
+    q->host = *csr;
+    q->host.on_device = 1;
+    q->host.row_ptr = (const int64_t*)rp;
+    q->host.col_idx = (const int32_t*)ci;
+    q->host.values = (const float*)va;
+    sv->queue.push_back(q);
+    *id = q->id;
+    return PM_OK;
+}
+
+pm_status pm_server_round(pm_server* sv, pm_request_done* done, uint32_t cap, uint32_t* n_done,
+                          uint32_t* n_active, uint32_t* n_queued)
+{
+    if (!sv) return PM_EINVAL;
+    pm_context* ctx = sv->ctx;
+    if (!done || !n_done || cap == 0) return fail(ctx, PM_EINVAL, "bad round arguments");
+    PM_CUDA(cudaSetDevice(ctx->device));
+    *n_done = 0;
+    auto finish = [&](Request* q, int32_t status) {
+        pm_request_done& d = done[(*n_done)++];
+        std::memset(&d, 0, sizeof(d));
+        d.id = q->id;
+        d.status = status;
+        fill_result(*q, d.result);
+        d.submit_time = q->t_submit;
+        d.done_time = sv->now();
+        d.rounds = q->rounds;
+        q->release();
+        delete q;
+    };
+    // admission: first come first served while the device budget allows; a
+    // request larger than the whole budget is refused
+    while (!sv->queue.empty() && *n_done < cap) {
+        Request* q = sv->queue.front();
+        if (q->bytes > sv->cfg.device_budget_bytes) {
+            sv->queue.erase(sv->queue.begin());
+            finish(q, PM_REQ_REFUSED);
+            continue;
+        }
+        if (sv->bytes_active + q->bytes > sv->cfg.device_budget_bytes && !sv->active.empty()) break;
+        sv->queue.erase(sv->queue.begin());
+        pm_status st = prepare_request(sv, q);
+        if (st != PM_OK) {
+            finish(q, PM_REQ_FAILED);
+            continue;
+        }
+        if (!q->dm.ok) {  // no perfect matching: per(A) = 0 exactly
+            finish(q, PM_REQ_DONE);
+            continue;
+        }
+        sv->bytes_active += q->bytes;
+        sv->active.push_back(q);
+    }
+    if (!sv->active.empty() && *n_done < cap) {
+        // one persistent launch over every active request
+        const int count = (int)std::min<size_t>(sv->active.size(), 65535);
+        std::vector<pm_csr> dims(count);
+        std::vector<DevMatrix> dms(count);
+        Run R;
+        R.count = count;
+        R.ntraj.resize(count);
+        // a round lasts about as long as its longest trajectory, so every
+        // request gets at least its share of the GPU's trajectory slots
+        const uint64_t share = (uint64_t)ctx->sm_count * kCtaWarps / (uint64_t)count;
+        for (int k = 0; k < count; ++k) {
+            Request* q = sv->active[k];
+            dims[k] = q->host;
+            dms[k] = q->dm;
+            dms[k].idx = k;
+            uint64_t T = sv->cfg.steps_per_round / (uint64_t)std::max(1, q->host.n);
+            T = std::max<uint64_t>(T, share);
+            T = std::min<uint64_t>(std::max<uint64_t>(T, sv->cfg.traj_min), sv->cfg.traj_max);
+            T = std::min<uint64_t>(T, q->max_traj - q->done_traj);
+            R.ntraj[k] = std::max<uint64_t>(T, 1);
+        }
+        R.mats = dims.data();
+        R.prepared = dms.data();
+        R.first_traj = (sv->round << 24) & (((uint64_t)1 << 48) - 1);
+        R.seed = sv->cfg.seed;
+        R.s = sv->s;
+        R.model = sv->model;
+        std::vector<pm_result> outs(count);
+        R.outs = outs.data();
+        ++sv->round;
+        Staged S;
+        pm_status st = stage_inputs(ctx, sv->ws, R, S);
+        if (st == PM_OK) st = stage_plans(ctx, sv->ws, R, S, nullptr);
+        if (st == PM_OK) st = enqueue(ctx, sv->ws, R, S);
+        if (st == PM_OK) {
+            PM_CUDA(cudaStreamSynchronize(ctx->stream));
+            st = collect(ctx, sv->ws, R, S, 0.0);
+        }
+        if (st != PM_OK) return st;
+        std::vector<Request*> keep;
+        for (int k = 0; k < count; ++k) {
+            Request* q = sv->active[k];
+            const pm_result& o = outs[k];
+            q->n += o.n_traj;
+            q->alive += o.n_alive;
+            q->lse1 = lse_add(q->lse1, o.log_sum_x);
+            q->lse2 = lse_add(q->lse2, o.log_sum_x2);
+            q->n_dm += o.n_dm_calls;
+            q->n_full += o.n_full_sk;
+            q->n_loc += o.n_local_sk;
+            q->done_traj += o.n_traj;
+            q->rounds += 1;
+            pm_result cur;
+            fill_result(*q, cur);
+            const bool met = q->n >= sv->cfg.min_traj_done && q->alive >= 2 && cur.rse <= q->target_rse;
+            const bool spent = q->done_traj >= q->max_traj;
+            if ((met || spent) && *n_done < cap) {
+                sv->bytes_active -= q->bytes;
+                finish(q, met ? PM_REQ_DONE : PM_REQ_BUDGET);
+            } else {
+                keep.push_back(q);
+            }
+        }
+        for (size_t k = count; k < sv->active.size(); ++k) keep.push_back(sv->active[k]);
+        sv->active.swap(keep);
+    }
+    if (n_active) *n_active = (uint32_t)sv->active.size();
+    if (n_queued) *n_queued = (uint32_t)sv->queue.size();
+    return PM_OK;
+}
+
+double pm_server_clock(const pm_server* sv) { return sv ? sv->now() : 0.0; }
+
+pm_status pm_server_destroy(pm_server* sv)
+{
+    if (!sv) return PM_EINVAL;
+    cudaSetDevice(sv->ctx->device);
+    cudaStreamSynchronize(sv->ctx->stream);
+    delete sv;
     return PM_OK;
 }
 

@@ -129,19 +129,20 @@ def band_random(n: int, nnz: int, seed: int, half_width: int = 1) -> Csr:
 
 def powerlaw_planted(n: int, seed: int, exponent: float = 2.5, dmin: int = 2) -> Csr:
     """Row degrees from the discrete power law P(d) ~ d^-exponent, d >= dmin,
-    capped at n; distinct uniform columns; plus a planted permutation."""
+    capped at n; uniform columns per row (a repeated draw is dropped, so a hub
+    row can hold slightly fewer than d); plus a planted permutation."""
     rng = np.random.default_rng(seed)
     perm = rng.permutation(n)
     support = np.arange(dmin, n + 1, dtype=np.float64)
     pmf = support ** (-exponent)
     pmf /= pmf.sum()
     deg = rng.choice(support.astype(np.int64), size=n, p=pmf)
-    rows, cols = [], []
-    for i in range(n):
-        c = rng.choice(n, size=int(deg[i]), replace=False)
-        rows.append(np.full(c.size + 1, i, dtype=np.int64))
-        cols.append(np.concatenate([c.astype(np.int64), [perm[i]]]))
-    return csr_from_coo(n, np.concatenate(rows), np.concatenate(cols))
+    rows = np.repeat(np.arange(n, dtype=np.int64), deg)
+    cols = rng.integers(0, n, size=rows.size, dtype=np.int64)
+    rows = np.concatenate([rows, np.arange(n, dtype=np.int64)])
+    cols = np.concatenate([cols, perm.astype(np.int64)])
+    key = np.unique(rows * n + cols)
+    return csr_from_coo(n, key // n, key % n)
 
 
 def block_diagonal(n: int, p: float, seed: int, weighted: bool = False, orders=(20, 25)) -> Csr:
