@@ -160,17 +160,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_byte():
-    """DRAM bytes per algorithmic byte of the trajectory kernel from the
-    committed ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "traj_kernel_traffic.json")
+def ncu_traffic_per_launch(T, n_mats):
+    """DRAM bytes (read + write) of one trajectory-kernel launch of this
+    workload from the committed one-pass ncu capture of a full-size bench
+    launch, if it was taken on the current kernel source and workload."""
+    path = os.path.join(ROOT, "profiles", "traj_kernel_learned_traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_alg_byte")
+    if d.get("traj_per_matrix_per_step") != T or d.get("matrices") != n_mats:
+        return None
+    return d.get("dram_bytes_per_launch")
 
 
 def bf16_params(p):
@@ -581,8 +584,7 @@ def main():
     kern_s = kern_ms / args.steps / 1e3
     achieved_tf = (mlp_rows / args.steps) * 9344.0 / kern_s / 1e12
     achieved_gb = (alg_bytes / args.steps) / kern_s / 1e9
-    tpb = ncu_traffic_per_byte()
-    traffic = None if tpb is None else tpb * alg_bytes / args.steps
+    traffic = ncu_traffic_per_launch(T, len(mats))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
