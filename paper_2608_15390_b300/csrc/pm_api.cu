@@ -581,7 +581,7 @@ pm_status enqueue_prep(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
     PM_CUDA(cudaMemsetAsync(P(S.o_work), 0, 8, ctx->stream));
     PM_CUDA(cudaMemsetAsync(P(S.o_status), 0, 4, ctx->stream));
     if (!R.prepared)
-        PM_CUDA(launch_prepare((DevMatrix*)P(S.o_mats), (const DevInput*)P(S.o_inputs), R.count, R.s, S.n_max,
+        PM_CUDA(launch_prepare((DevMatrix*)P(S.o_mats), (const DevInput*)P(S.o_inputs), R.count, R.s, S.m_max, S.n_max,
                                (uint32_t*)P(S.o_status), ctx->stream));
     return PM_OK;
 }
@@ -1026,7 +1026,7 @@ pm_status autotune(pm_context* ctx, pm_batch* b, std::vector<Plan>& plans)
     // the matrices must be prepared before a probe runs on them
     uint8_t* A = b->ws.arena;
     PM_CUDA(cudaMemsetAsync(A + S.o_status, 0, 4, ctx->stream));
-    PM_CUDA(launch_prepare((DevMatrix*)(A + S.o_mats), (const DevInput*)(A + S.o_inputs), count, R.s, S.n_max,
+    PM_CUDA(launch_prepare((DevMatrix*)(A + S.o_mats), (const DevInput*)(A + S.o_inputs), count, R.s, S.m_max, S.n_max,
                            (uint32_t*)(A + S.o_status), ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
     uint32_t status = 0;

@@ -18,13 +18,19 @@ namespace pm {
 // Every lane follows the same (uniform) control flow and writes the same
 // values; each search step examines up to 32 adjacency entries at once with a
 // ballot and takes the first eligible entry in adjacency order.  Matching: a
-// greedy start, then augmenting-path phases whose searches share visited marks
-// (O(m) per phase); a phase that augments nothing proves the matching maximum
-// (a failed search only marks columns from which no free column is reachable).
+// greedy start (or the repaired matching of the previous call), then
+// augmenting-path phases whose searches share visited marks; free rows and
+// unvisited vertices are found 32 at a time by ballots.
 // Live must provide: bool row(int i), bool col(int j), bool edge(int e, int i, int j).
+// repair: mr/mc already hold a matching of an earlier residual of the same
+// matrix (the trajectory's previous DM call).  Pairs whose other end has been
+// eliminated since are dropped and the search starts from that matching
+// instead of the greedy one: after k eliminations at most k rows are free, so
+// few augmenting searches remain.  The supported-edge set does not depend on
+// which perfect matching the SCC step starts from, so the result is the same.
 template <class Live, typename Idx>
 __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri, const int* ce,
-                        const Live& live, uint8_t* mask, int* ws, int lane)
+                        const Live& live, uint8_t* mask, int* ws, int lane, bool repair = false)
 {
     int* mr = ws;
     int* mc = mr + n;
@@ -39,10 +45,18 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
     int* cstk = onst + 2 * n;
     int* sstk = cstk + 2 * n + 1;
 
-    for (int i = lane; i < n; i += 32) { mr[i] = -1; mc[i] = -1; vis[i] = -1; }
+    if (repair) {
+        for (int i = lane; i < n; i += 32) {
+            vis[i] = -1;
+            if (live.row(i) && mr[i] >= 0 && !live.col(mr[i])) mr[i] = -1;
+            if (live.col(i) && mc[i] >= 0 && !live.row(mc[i])) mc[i] = -1;
+        }
+    } else {
+        for (int i = lane; i < n; i += 32) { mr[i] = -1; mc[i] = -1; vis[i] = -1; }
+    }
     __syncwarp();
     // greedy start: each active row takes its first free live column
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && !repair; ++i) {
         if (!live.row(i)) continue;
         const int b = rp[i], en = rp[i + 1];
         for (int base = b; base < en; base += 32) {
@@ -63,56 +77,64 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
             }
         }
     }
-    // augmenting-path phases with shared visited marks
+    // augmenting-path phases whose searches share visited marks (O(m) per
+    // phase); a phase that augments nothing proves the matching maximum (a
+    // failed search only marks columns from which no free column is reachable)
     for (int phase = 0;; ++phase) {
         bool augmented = false, unmatched = false;
-        for (int s = 0; s < n; ++s) {
-            if (!live.row(s) || mr[s] >= 0) continue;
-            unmatched = true;
-            int top = 0;
-            stk[0] = s;
-            cur[s] = rp[s];
-            __syncwarp();
-            while (top >= 0) {
-                const int x = stk[top];
-                const int en = rp[x + 1];
-                const int c0 = cur[x];
-                if (c0 >= en) { --top; continue; }
-                const int e = c0 + lane;
-                bool ok = false;
-                int j = 0;
-                if (e < en) {
-                    j = ci[e];
-                    ok = vis[j] != phase && live.edge(e, x, j);
-                }
-                const unsigned bal = __ballot_sync(kFull, ok);
-                if (!bal) {
-                    cur[x] = c0 + 32;
-                    __syncwarp();
-                    continue;
-                }
-                const int l = __ffs(bal) - 1;
-                int jj = __shfl_sync(kFull, j, l);
-                cur[x] = c0 + l + 1;
-                vis[jj] = phase;
+        for (int s0 = 0; s0 < n; s0 += 32) {
+            // the free active rows of this block of 32, in index order
+            unsigned freeb = __ballot_sync(kFull, s0 + lane < n && live.row(s0 + lane) && mr[s0 + lane] < 0);
+            while (freeb) {
+                const int s = s0 + __ffs(freeb) - 1;
+                freeb &= freeb - 1u;
+                if (mr[s] >= 0) continue;  // matched by an earlier search of this block
+                unmatched = true;
+                int top = 0;
+                stk[0] = s;
+                cur[s] = rp[s];
                 __syncwarp();
-                if (mc[jj] < 0) {
-                    for (int q = top; q >= 0; --q) {
-                        const int row = stk[q];
-                        const int prev = mr[row];
-                        __syncwarp();
-                        mr[row] = jj;
-                        mc[jj] = row;
-                        __syncwarp();
-                        jj = prev;
+                while (top >= 0) {
+                    const int x = stk[top];
+                    const int en = rp[x + 1];
+                    const int c0 = cur[x];
+                    if (c0 >= en) { --top; continue; }
+                    const int e = c0 + lane;
+                    bool ok = false;
+                    int j = 0;
+                    if (e < en) {
+                        j = ci[e];
+                        ok = vis[j] != phase && live.edge(e, x, j);
                     }
-                    augmented = true;
-                    break;
+                    const unsigned bal = __ballot_sync(kFull, ok);
+                    if (!bal) {
+                        cur[x] = c0 + 32;
+                        __syncwarp();
+                        continue;
+                    }
+                    const int l = __ffs(bal) - 1;
+                    int jj = __shfl_sync(kFull, j, l);
+                    cur[x] = c0 + l + 1;
+                    vis[jj] = phase;
+                    __syncwarp();
+                    if (mc[jj] < 0) {
+                        for (int q = top; q >= 0; --q) {
+                            const int row = stk[q];
+                            const int prev = mr[row];
+                            __syncwarp();
+                            mr[row] = jj;
+                            mc[jj] = row;
+                            __syncwarp();
+                            jj = prev;
+                        }
+                        augmented = true;
+                        break;
+                    }
+                    const int y = mc[jj];
+                    stk[++top] = y;
+                    cur[y] = rp[y];
+                    __syncwarp();
                 }
-                const int y = mc[jj];
-                stk[++top] = y;
-                cur[y] = rp[y];
-                __syncwarp();
             }
         }
         if (!unmatched) break;
@@ -125,9 +147,13 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
     for (int x = lane; x < V; x += 32) { idx[x] = -1; onst[x] = 0; }
     __syncwarp();
     int counter = 0, ncomp = 0, sp = 0;
-    for (int s = 0; s < V; ++s) {
-        const bool act = s < n ? live.row(s) : live.col(s - n);
-        if (!act || idx[s] >= 0) continue;
+    for (int s0 = 0; s0 < V; s0 += 32) {
+      const int sl = s0 + lane;
+      unsigned todo = __ballot_sync(kFull, sl < V && (sl < n ? live.row(sl) : live.col(sl - n)) && idx[sl] < 0);
+      while (todo) {
+        const int s = s0 + __ffs(todo) - 1;
+        todo &= todo - 1u;
+        if (idx[s] >= 0) continue;  // reached by an earlier search of this block
         int ctop = 0;
         cstk[0] = s;
         it[s] = -1;
@@ -197,6 +223,7 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
             }
             __syncwarp();
         }
+      }
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) {

@@ -109,6 +109,15 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline int dm_ws_ints(int n) { return 19 * n + 8; }
 
+// shared bytes of the initial DM with A's adjacency staged beside its
+// workspace: int32 row/column pointers, uint16 column/row indices
+__host__ __device__ inline size_t prep_stage_bytes(int n, int64_t m)
+{
+    const size_t a = 16;
+    auto up = [a](size_t x) { return (x + a - 1) / a * a; };
+    return up((size_t)dm_ws_ints(n) * 4) + 2 * up((size_t)(n + 1) * 4) + 2 * up((size_t)m * 2);
+}
+
 inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists, bool learned);
 
 inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales, bool local, bool dm,
@@ -230,7 +239,7 @@ struct StatsOut {
 };
 
 // ---- launchers (pm_kernels.cu) ----
-cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, Sched s,
+cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, Sched s, int64_t m_max,
                            int n_max, uint32_t* status, cudaStream_t st);
 cudaError_t launch_trajectories(const TrajParams& p, int grid, int smem_bytes, bool trace, cudaStream_t st);
 cudaError_t launch_stats(const double* log_x, const uint64_t* h_prefix, const uint64_t* d_prefix,

@@ -140,7 +140,26 @@ __global__ void __launch_bounds__(1024) prepare_kernel(DevMatrix* mats, const De
     // memory when the launch reserved enough (warp 0 runs it)
     extern __shared__ __align__(16) int dm_smem[];
     int* dm_ws = (dm_ws_ints(n) * 4 <= dyn_smem) ? dm_smem : M.dm_ws;
-    if (s.initial_dm && tid < 32) {
+    if (s.initial_dm && n < 65536 && prep_stage_bytes(n, m) <= (size_t)dyn_smem) {
+        // the search chases indices: stage A's adjacency in shared memory too
+        // (the whole CTA copies, warp 0 searches)
+        uint8_t* base = reinterpret_cast<uint8_t*>(dm_smem);
+        size_t off = ((size_t)dm_ws_ints(n) * 4 + 15) / 16 * 16;
+        int* s_rp = reinterpret_cast<int*>(base + off);
+        off += ((size_t)(n + 1) * 4 + 15) / 16 * 16;
+        int* s_cp = reinterpret_cast<int*>(base + off);
+        off += ((size_t)(n + 1) * 4 + 15) / 16 * 16;
+        uint16_t* s_ci = reinterpret_cast<uint16_t*>(base + off);
+        off += ((size_t)m * 2 + 15) / 16 * 16;
+        uint16_t* s_ri = reinterpret_cast<uint16_t*>(base + off);
+        for (int i = tid; i <= n; i += nt) { s_rp[i] = M.a_rp[i]; s_cp[i] = M.a_cp[i]; }
+        for (int e = tid; e < m; e += nt) { s_ci[e] = (uint16_t)M.a_ci[e]; s_ri[e] = (uint16_t)M.a_ri[e]; }
+        __syncthreads();
+        if (tid < 32) {
+            const bool r = dm_warp(n, s_rp, s_ci, s_cp, s_ri, M.a_ce, LiveAll{}, M.keep, dm_smem, tid);
+            if (tid == 0) ok_s = r ? 1 : 0;
+        }
+    } else if (s.initial_dm && tid < 32) {
         const bool r = dm_warp(n, M.a_rp, M.a_ci, M.a_cp, M.a_ri, M.a_ce, LiveAll{}, M.keep, dm_ws, tid);
         if (tid == 0) ok_s = r ? 1 : 0;
     }
@@ -405,15 +424,20 @@ __global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
 // launchers
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, Sched s, int n_max, uint32_t* status,
-                           cudaStream_t st)
+cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, Sched s, int64_t m_max, int n_max,
+                           uint32_t* status, cudaStream_t st)
 {
-    // shared memory for the initial DM's workspace when it fits (else global)
+    // shared memory for the initial DM: workspace and staged adjacency when
+    // they fit, else the workspace only, else none (global memory)
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int dyn = s.initial_dm ? dm_ws_ints(n_max) * 4 : 0;
-    if (dyn > optin - 4096) dyn = 0;
+    int dyn = 0;
+    if (s.initial_dm) {
+        const size_t staged = prep_stage_bytes(n_max, m_max);
+        if (staged <= (size_t)(optin - 4096)) dyn = (int)staged;
+        else if (dm_ws_ints(n_max) * 4 <= optin - 4096) dyn = dm_ws_ints(n_max) * 4;
+    }
     cudaError_t e;
     if (s.precision == 1) {
         e = cudaFuncSetAttribute(prepare_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);

@@ -368,17 +368,32 @@ __device__ __forceinline__ int neighbour_degree_sum(const MV<Idx>& V, const uint
     return mine;
 }
 
+// the global inputs of a candidate's features (outer scale of p, entry B_vp),
+// loaded as soon as p is known so the loads overlap the neighbour scan
+struct CandLoads {
+    float sl, bv;
+};
 template <typename Idx>
-__device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* deg, const DevMatrix* Mp, int t,
-                                              bool vrow, int e, int p, float sum_v, int sum_l, float dv, float lsv,
+__device__ __forceinline__ CandLoads cand_loads(const MV<Idx>& V, const DevMatrix* Mp, bool vrow, int e, int p,
+                                                bool live)
+{
+    CandLoads c{1.0f, 1.0f};
+    if (!live) return c;
+    const float* s0 = reinterpret_cast<const float*>(vrow ? Mp->c0 : Mp->r0);
+    c.sl = __ldg(s0 + p);
+    const float* vals = vrow ? V.rv : V.cv;
+    if (vals) c.bv = __ldg(vals + e);
+    return c;
+}
+
+template <typename Idx>
+__device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* deg, int t, bool vrow, int p,
+                                              float sum_v, int sum_l, float dv, float lsv, const CandLoads& cl,
                                               float (&f)[8])
 {
     const int n = V.n;
-    const float* r0 = reinterpret_cast<const float*>(Mp->r0);
-    const float* c0 = reinterpret_cast<const float*>(Mp->c0);
-    const float sl = vrow ? __ldg(c0 + p) : __ldg(r0 + p);
+    const float sl = cl.sl, bv = cl.bv;
     const float* vals = vrow ? V.rv : V.cv;
-    const float bv = vals ? __ldg(vals + e) : 1.0f;
     // fast logarithms (about 1e-6 relative): 1 + an integer count is exact in binary32
     f[0] = __logf(1.0f + dv);
     f[1] = __logf(1.0f + (float)deg[p + (vrow ? n : 0)]);
@@ -476,6 +491,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     Mant64 num, den;
     Real track = 1;
     unsigned n_dm = 0, n_full = 0, n_loc = 0;
+    bool dm_matched = false;  // the DM workspace holds this trajectory's last perfect matching
     int dead_step = -1;
     uint64_t alg_bytes = (uint64_t)2 * n * 4;
     uint64_t mlp_rows = 0;  // network evaluations of live candidates (learned proposal)
@@ -533,10 +549,11 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     const unsigned lmk = __ballot_sync(kFull, live);
                     const int nl = __popc(lmk);
                     const int li = __popc(lmk & ((1u << lane) - 1u));
+                    const CandLoads cl = cand_loads<Idx>(V, Mp, vrow, e, pp, live);
                     const int sum_l = neighbour_degree_sum<Idx>(V, deg, mask, vrow, pp, live, lane);
                     if (live) {
                         float f[8];
-                        cand_features<Idx>(V, deg, Mp, t, vrow, e, pp, sum_v, sum_l, (float)dv, lsv, f);
+                        cand_features<Idx>(V, deg, t, vrow, pp, sum_v, sum_l, (float)dv, lsv, cl, f);
                         uint4 lo;
                         lo.x = pack_bf16(f[0], f[1]);
                         lo.y = pack_bf16(f[2], f[3]);
@@ -577,9 +594,10 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 // least two (pass 1 counts them, pass 2 writes them)
                 if (rec) {
                     auto pair_at = [&](int e, int pp, bool live, float (&f)[8], float& tgt) -> bool {
+                        const CandLoads cl = cand_loads<Idx>(V, Mp, vrow, e, pp, live);
                         const int sum_l = neighbour_degree_sum<Idx>(V, deg, mask, vrow, pp, live, lane);
                         if (!live) return false;
-                        cand_features<Idx>(V, deg, Mp, t, vrow, e, pp, sum_v, sum_l, (float)dv, lsv, f);
+                        cand_features<Idx>(V, deg, t, vrow, pp, sum_v, sum_l, (float)dv, lsv, cl, f);
                         const double sv_cur = vrow ? (double)r[vi] : (double)c[vi];
                         const double sl_cur = vrow ? (double)c[pp] : (double)r[pp];
                         tgt = (float)log(sv_cur * sl_cur);
@@ -881,7 +899,9 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         if (mb[M_DM]) {
             if (leader) ++n_dm;
             if (leader) {
-                const bool okdm = dm_warp(n, V.rp, V.ci, V.cp, V.ri, V.ce, LiveTraj{deg, mask, n}, mask, dmws, lane);
+                const bool okdm =
+                    dm_warp(n, V.rp, V.ci, V.cp, V.ri, V.ce, LiveTraj{deg, mask, n}, mask, dmws, lane, dm_matched);
+                dm_matched = okdm;
                 if (lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
             }
             gsync(G);
