@@ -200,6 +200,9 @@ pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info);
  *                      the trajectory state, warps per trajectory -- is chosen
  *                      by timing every candidate layout on a probe launch of
  *                      the class's largest matrix (fastest trajectories/s);
+ *                      with inner DM, also whether the DM workspace and edge
+ *                      mask sit in shared memory (fewer trajectories per SM,
+ *                      faster DM);
  *                      the choice is cached in the context per class and
  *                      schedule.  Without it a fixed heuristic decides.
  * The context (and a learned model in the schedule) must outlive the batch;
@@ -214,7 +217,9 @@ typedef struct {
     int32_t staged;          /* matrix adjacency staged in shared memory */
     int32_t rc_smem;         /* scaling vectors in shared memory */
     int32_t gstate;          /* trajectory state in global memory (large n) */
+    int32_t dm_smem;         /* inner DM's workspace and edge mask in shared memory */
     int32_t tuned;           /* 1 if the autotuner chose this layout */
+    int32_t reserved;
     double probe_traj_per_s;      /* the chosen layout's probe rate (-1: not probed) */
     double heuristic_traj_per_s;  /* the heuristic layout's probe rate (-1: not probed) */
 } pm_plan_info;

@@ -68,11 +68,11 @@ class pm_train_report(C.Structure):
 
 class pm_plan_info(C.Structure):
     _fields_ = [("g", C.c_int32), ("groups", C.c_int32), ("staged", C.c_int32), ("rc_smem", C.c_int32),
-                ("gstate", C.c_int32), ("tuned", C.c_int32), ("probe_traj_per_s", C.c_double),
-                ("heuristic_traj_per_s", C.c_double)]
+                ("gstate", C.c_int32), ("dm_smem", C.c_int32), ("tuned", C.c_int32), ("reserved", C.c_int32),
+                ("probe_traj_per_s", C.c_double), ("heuristic_traj_per_s", C.c_double)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class pm_server_cfg(C.Structure):

@@ -45,7 +45,7 @@ struct pm_context {
     int sm_count = 0;
     std::string last_error;
     Workspace ws;
-    std::map<std::string, std::array<int, 4>> tuned;  // autotuned layout policy per size class
+    std::map<std::string, std::array<int, 5>> tuned;  // autotuned layout policy per size class
     std::vector<pm_batch*> batches;                     // live batches (destroyed with the context)
     double last_traj_ms = 0, last_prep_ms = 0;
     uint64_t last_h2d = 0, last_d2h = 0;
@@ -160,10 +160,10 @@ namespace {
 // heuristic below and the autotuner (pm_batch_create) both produce a policy;
 // plan_for() turns it into a Plan for a given matrix and shared-memory budget.
 struct Policy {
-    int staged = 0, rc_smem = 0, gstate = 0, g = 1;
+    int staged = 0, rc_smem = 0, gstate = 0, g = 1, dm_smem = 0;
     bool operator==(const Policy& o) const
     {
-        return staged == o.staged && rc_smem == o.rc_smem && gstate == o.gstate && g == o.g;
+        return staged == o.staged && rc_smem == o.rc_smem && gstate == o.gstate && g == o.g && dm_smem == o.dm_smem;
     }
 };
 
@@ -189,12 +189,13 @@ Plan plan_for(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learn
         if (p.groups * p.state_bytes > avail) p.groups = 0;
         return p;
     }
-    if ((pol.rc_smem && !need_rc) || (pol.staged && n > 65535)) return p;
+    if ((pol.rc_smem && !need_rc) || (pol.staged && n > 65535) || (pol.dm_smem && !dm)) return p;
     p.staged = pol.staged;
     p.rc_smem = pol.rc_smem;
+    p.dm_smem = pol.dm_smem;
     p.mat_bytes = pol.staged ? staged_matrix_bytes(n, m, dm) : 0;
     if (p.mat_bytes >= avail) return p;
-    p.state_bytes = group_state_bytes(n, rb, pol.rc_smem, full, learned);
+    p.state_bytes = group_state_bytes(n, m, rb, pol.rc_smem, full, learned, pol.dm_smem != 0);
     const int fit = (avail - p.mat_bytes) / p.state_bytes;
     p.groups = std::min(fit, kCtaWarps / p.g);
     if (p.groups < 0) p.groups = 0;
@@ -206,17 +207,21 @@ std::vector<Policy> candidate_policies(int n, int64_t m, int rb, const Sched& s,
 {
     const bool full = s.sk == 1 || s.sk == 2;
     const bool need_rc = s.sk != 0;
+    const bool dm = s.dm != 0;
     std::vector<Policy> out;
     const int combos[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
     for (int g = 1; g <= (full ? kCtaWarps : 1); g *= 2) {
-        for (const auto& cb : combos) {
-            Policy pol;
-            pol.staged = cb[0];
-            pol.rc_smem = cb[1];
-            pol.g = g;
-            if (pol.rc_smem && !need_rc) continue;
-            const Plan p = plan_for(n, m, rb, s, smem_max, learned, pol);
-            if (p.groups >= 1 && (p.groups * p.g >= 4 || !full)) out.push_back(pol);
+        for (int dms = 0; dms <= (dm ? 1 : 0); ++dms) {
+            for (const auto& cb : combos) {
+                Policy pol;
+                pol.staged = cb[0];
+                pol.rc_smem = cb[1];
+                pol.g = g;
+                pol.dm_smem = dms;
+                if (pol.rc_smem && !need_rc) continue;
+                const Plan p = plan_for(n, m, rb, s, smem_max, learned, pol);
+                if (p.groups >= 1 && (p.groups * p.g >= 4 || !full || dms)) out.push_back(pol);
+            }
         }
         Policy gs;
         gs.gstate = 1;
@@ -272,7 +277,12 @@ Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max, bool lear
     return best;
 }
 
-Policy policy_of(const Plan& p) { Policy o; o.staged = p.staged; o.rc_smem = p.rc_smem; o.gstate = p.gstate; o.g = p.g; return o; }
+Policy policy_of(const Plan& p)
+{
+    Policy o;
+    o.staged = p.staged; o.rc_smem = p.rc_smem; o.gstate = p.gstate; o.g = p.g; o.dm_smem = p.dm_smem;
+    return o;
+}
 
 struct Run {
     // inputs
@@ -1051,7 +1061,7 @@ pm_status autotune(pm_context* ctx, pm_batch* b, std::vector<Plan>& plans)
         auto cached = ctx->tuned.find(key);
         if (cached != ctx->tuned.end()) {
             best.staged = cached->second[0]; best.rc_smem = cached->second[1];
-            best.gstate = cached->second[2]; best.g = cached->second[3];
+            best.gstate = cached->second[2]; best.g = cached->second[3]; best.dm_smem = cached->second[4];
         } else {
             const std::vector<Policy> cands = candidate_policies(n, m, (int)S.rb, R.s, smem_max, learned);
             if (cands.size() > 1) {
@@ -1065,7 +1075,7 @@ pm_status autotune(pm_context* ctx, pm_batch* b, std::vector<Plan>& plans)
                     if (rate > best_rate) { best_rate = rate; best = pol; }
                 }
             }
-            ctx->tuned[key] = {best.staged, best.rc_smem, best.gstate, best.g};
+            ctx->tuned[key] = {best.staged, best.rc_smem, best.gstate, best.g, best.dm_smem};
         }
         for (int q = 0; q < count; ++q) {
             if (size_class(R.mats[q].n) != cr.first) continue;
@@ -1151,6 +1161,7 @@ pm_status pm_batch_create(pm_context* ctx, const pm_csr* mats, int32_t count, co
         const Plan& p = b->S.plans[k];
         pm_plan_info& I = b->info[k];
         I.g = p.g; I.groups = p.groups; I.staged = p.staged; I.rc_smem = p.rc_smem; I.gstate = p.gstate;
+        I.dm_smem = p.dm_smem;
     }
     if (flags & PM_BATCH_GRAPH) {
         PM_CUDA(cudaStreamSynchronize(ctx->stream));

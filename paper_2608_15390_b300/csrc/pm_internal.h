@@ -118,7 +118,8 @@ __host__ __device__ inline size_t prep_stage_bytes(int n, int64_t m)
     return up((size_t)dm_ws_ints(n) * 4) + 2 * up((size_t)(n + 1) * 4) + 2 * up((size_t)m * 2);
 }
 
-inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists, bool learned);
+inline int group_state_bytes(int n, int64_t m, int real_bytes, bool rc_smem, bool lists, bool learned,
+                             bool dm_smem);
 
 inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales, bool local, bool dm,
                               size_t gstate_bytes, bool learned)
@@ -150,6 +151,7 @@ inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales,
 struct Plan {
     int g, groups, staged, rc_smem, lists;
     int gstate;        // trajectory state in the group's global slot (large n)
+    int dm_smem;       // the inner DM's workspace and edge mask in shared memory
     int state_bytes;   // shared bytes of one group
     int mat_bytes;     // shared bytes of the staged matrix (0 if not staged)
 };
@@ -209,12 +211,14 @@ inline size_t global_state_bytes(int n, int real_bytes, bool lists)
 }
 
 // shared-memory sizes used by the plan
-inline int group_state_bytes(int n, int real_bytes, bool rc_smem, bool lists, bool learned)
+inline int group_state_bytes(int n, int64_t m, int real_bytes, bool rc_smem, bool lists, bool learned,
+                             bool dm_smem)
 {
     const TreeGeom G = tree_geom(n);
     size_t b = align_up((size_t)((2 * n + 7) & ~7) * 2, 16) + align_up((size_t)G.total * 4, 16);
     if (rc_smem) b += 2 * align_up((size_t)n * real_bytes, 16);
     if (lists) b += 2 * align_up((size_t)n * 2, 16);
+    if (dm_smem) b += align_up((size_t)dm_ws_ints(n) * 4, 16) + align_up((size_t)m, 16);
     if (learned) b += 32 * 24 * 2;  // feature tile [32][24] bf16
     b += kGroupMiscInts * 4;
     return (int)b;

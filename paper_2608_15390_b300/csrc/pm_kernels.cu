@@ -438,13 +438,21 @@ cudaError_t launch_prepare(DevMatrix* d_mats, const DevInput* d_in, int count, S
         if (staged <= (size_t)(optin - 4096)) dyn = (int)staged;
         else if (dm_ws_ints(n_max) * 4 <= optin - 4096) dyn = dm_ws_ints(n_max) * 4;
     }
+    // the cap stays at the device maximum (captured graphs of other calls may
+    // hold larger launches of this kernel): opt-in less the static shared memory
+    cudaFuncAttributes fa{};
+    const cudaError_t ea = s.precision == 1 ? cudaFuncGetAttributes(&fa, (const void*)prepare_kernel<double>)
+                                            : cudaFuncGetAttributes(&fa, (const void*)prepare_kernel<float>);
+    if (ea != cudaSuccess) return ea;
+    int cap = optin - (int)fa.sharedSizeBytes;
+    if (cap < dyn) cap = dyn;
     cudaError_t e;
     if (s.precision == 1) {
-        e = cudaFuncSetAttribute(prepare_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        e = cudaFuncSetAttribute(prepare_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
         if (e != cudaSuccess) return e;
         prepare_kernel<double><<<count, 1024, dyn, st>>>(d_mats, d_in, s, status, dyn);
     } else {
-        e = cudaFuncSetAttribute(prepare_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        e = cudaFuncSetAttribute(prepare_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
         if (e != cudaSuccess) return e;
         prepare_kernel<float><<<count, 1024, dyn, st>>>(d_mats, d_in, s, status, dyn);
     }

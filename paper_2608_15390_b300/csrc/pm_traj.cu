@@ -413,7 +413,7 @@ enum { M_DEAD = 0, M_NIT = 1, M_DM = 2, M_CNTR = 3, M_CNTC = 4, M_STRIDE = 8, M_
 template <typename Real, typename Idx, bool TRACE, int MODE, typename ListT>
 __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>& V, int k, uint64_t gq,
                           uint64_t local, uint16_t* deg, uint32_t* tree, Real* r_sm, ListT* lists, uint16_t* feat,
-                          const DevModel* Ms, uint8_t* slot, const Grp& G)
+                          const DevModel* Ms, uint8_t* slot, int* dm_sm, uint8_t* mask_sm, const Grp& G)
 {
     constexpr bool model = MODE == 1;
     constexpr bool rec = MODE == 2;
@@ -468,8 +468,8 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     uint8_t* mask = nullptr;
     int* dmws = nullptr;
     if (use_dm) {
-        mask = slot + P.slot.mask;
-        dmws = reinterpret_cast<int*>(slot + P.slot.dm);
+        mask = mask_sm ? mask_sm : slot + P.slot.mask;
+        dmws = dm_sm ? dm_sm : reinterpret_cast<int*>(slot + P.slot.dm);
         const int m = Mp->m;
         for (int q = G.tid; q < m; q += G.nthr) mask[q] = 1;
     }
@@ -1006,6 +1006,14 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         lists = base + off;
         off += 2 * a16((size_t)n * (pl.gstate ? 4 : 2));
     }
+    int* dm_sm = nullptr;      // the inner DM's workspace and edge mask (dm_smem plans)
+    uint8_t* mask_sm = nullptr;
+    if (pl.dm_smem && !pl.gstate) {
+        dm_sm = reinterpret_cast<int*>(base + off);
+        off += a16((size_t)dm_ws_ints(n) * 4);
+        mask_sm = base + off;
+        off += a16((size_t)Mp->m_a);
+    }
     if (pl.gstate) off = 0;    // feature tile and control words stay in shared memory
     uint16_t* feat = nullptr;  // [32][kFS] bf16 feature tile of the learned proposal
     if (Ms) {
@@ -1022,10 +1030,10 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
         const uint64_t local = ch.first + (uint64_t)q;
         if (pl.gstate)
             run_group<Real, Idx, TRACE, MODE, uint32_t>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm,
-                                                        reinterpret_cast<uint32_t*>(lists), feat, Ms, slot, G);
+                                                        reinterpret_cast<uint32_t*>(lists), feat, Ms, slot, dm_sm, mask_sm, G);
         else
             run_group<Real, Idx, TRACE, MODE, uint16_t>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm,
-                                                        reinterpret_cast<uint16_t*>(lists), feat, Ms, slot, G);
+                                                        reinterpret_cast<uint16_t*>(lists), feat, Ms, slot, dm_sm, mask_sm, G);
     }
 }
 
@@ -1090,11 +1098,27 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
     }
 }
 
+// largest dynamic shared memory a launch of fn may request: the device's
+// opt-in maximum less the kernel's static shared memory
+int dyn_smem_cap(const void* fn)
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return 0;
+    return v - (int)a.sharedSizeBytes;
+}
+
 template <typename Real, bool TRACE, int MODE>
 cudaError_t launch_t(const TrajParams& p, int grid, int smem, cudaStream_t st)
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(traj_kernel<Real, TRACE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // the attribute is a per-function cap shared by every launch and by the
+    // kernel nodes of captured graphs: keep it at the device maximum so a
+    // later, smaller launch never lowers it below a captured node's size
+    const int cap = dyn_smem_cap((const void*)traj_kernel<Real, TRACE, MODE>);
+    cudaError_t e = cudaFuncSetAttribute(traj_kernel<Real, TRACE, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem > cap ? smem : cap);
     if (e != cudaSuccess) return e;
     traj_kernel<Real, TRACE, MODE><<<grid, kCtaWarps * 32, smem, st>>>(p);
     return cudaGetLastError();
