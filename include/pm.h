@@ -298,7 +298,7 @@ pm_status pm_server_destroy(pm_server* server);
 typedef struct pm_model pm_model;
 
 typedef struct {
-    uint64_t n_pairs;        /* (features, target) pairs to record from the teacher */
+    uint64_t n_pairs;        /* (features, target) pairs to train on: whole steps, at most this many */
     uint64_t seed;           /* Philox seed of the teacher trajectories and of the shuffle */
     int32_t epochs;          /* passes over the recorded pairs */
     int32_t batch;           /* rows per Adam step */
@@ -335,9 +335,11 @@ pm_status pm_model_destroy(pm_model* model);
 pm_status pm_model_get_params(pm_context* ctx, const pm_model* model, float* params);
 pm_status pm_model_set_params(pm_context* ctx, pm_model* model, const float* params);
 /* Train on pairs recorded from cfg->teacher running on mats[count] (matrix k
- * uses matrix index k): record, shuffle (whole steps for PM_OBJ_CENTRED),
- * then epochs of Adam on cfg->objective, gradients from the tensor-core
- * backward kernel. */
+ * uses matrix index k): record (one run sized for about 1.5 x n_pairs, into a
+ * buffer that cannot overflow), keep whole steps in a fixed order up to
+ * n_pairs, shuffle (whole steps for PM_OBJ_CENTRED), then epochs of Adam on
+ * cfg->objective, gradients from the tensor-core backward kernel reduced in a
+ * fixed order.  The same arguments give bit-identical parameters. */
 pm_status pm_model_train(pm_context* ctx, pm_model* model, const pm_csr* mats, int32_t count,
                          const pm_train_cfg* cfg, pm_train_report* report);
 /* Network outputs for B feature rows (host X[B][8] -> host out[B]). */

@@ -1718,8 +1718,11 @@ pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, co
     PM_CUDA(cudaMemcpyAsync(bp.p, perm.data(), 4 * B, cudaMemcpyHostToDevice, ctx->stream));
     PM_CUDA(cudaMemsetAsync(m->grad, 0, 4 * model_param_count(), ctx->stream));
     PM_CUDA(cudaMemsetAsync(bl.p, 0, 8, ctx->stream));
+    DevBuf bw;
+    PM_CUDA(cudaMalloc(&bw.p, mlp_grad_workspace_bytes(ctx->sm_count)));
     PM_CUDA(launch_mlp_grad(m->img, (const float*)bx.p, (const float*)bt.p, (const int*)bp.p, 0, (int)B,
-                            (const uint32_t*)bg.p, (float*)br.p, m->grad, (double*)bl.p, ctx->sm_count, ctx->stream));
+                            (const uint32_t*)bg.p, (float*)br.p, m->grad, (double*)bl.p, ctx->sm_count, bw.p,
+                            ctx->stream));
     PM_CUDA(cudaMemcpyAsync(grad, m->grad, 4 * model_param_count(), cudaMemcpyDeviceToHost, ctx->stream));
     double l = 0;
     PM_CUDA(cudaMemcpyAsync(&l, bl.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1810,8 +1813,21 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
     }
     PM_CUDA(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
-    const uint64_t cap = cfg->n_pairs;
+    const uint64_t want = cfg->n_pairs;
     const bool centred = cfg->objective == PM_OBJ_CENTRED;
+    // one recording run sized to give about 1.5 x `want` pairs (about 2 per
+    // step), into a buffer that cannot overflow (a trajectory records each
+    // edge at most once): the recorded set does not depend on the order in
+    // which the device's warps finish
+    std::vector<uint64_t> nt(count);
+    uint64_t cap = 1;
+    for (int k = 0; k < count; ++k) {
+        const uint64_t per_traj = 2ull * (uint64_t)mats[k].n;
+        const uint64_t goal = want + want / 2;
+        nt[k] = std::max<uint64_t>(1, (goal + (uint64_t)count * per_traj - 1) / ((uint64_t)count * per_traj));
+        cap += nt[k] * (uint64_t)std::max<int64_t>(1, mats[k].nnz);
+    }
+    cap = std::min<uint64_t>(std::min<uint64_t>(cap, 16 * want + 1024), (1ull << 31) - 1);
     DevBuf bf, bt, bk, bg, bc, bp, bl, br;
     PM_CUDA(cudaMalloc(&bf.p, 32 * cap));
     PM_CUDA(cudaMalloc(&bt.p, 4 * cap));
@@ -1819,29 +1835,51 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
     PM_CUDA(cudaMalloc(&bg.p, 4 * cap));
     PM_CUDA(cudaMalloc(&bc.p, 16));
     PM_CUDA(cudaMemsetAsync(bc.p, 0, 16, ctx->stream));
-    // record until the buffer is full: about 2 pairs per step and trajectory
-    uint64_t first = 0;
+    st = record_into(ctx, mats, count, nt.data(), 0, 0, cfg->seed, &cfg->teacher, (float*)bf.p, (float*)bt.p,
+                     (unsigned long long*)bk.p, (uint32_t*)bg.p, (unsigned long long*)bc.p, cap);
+    if (st != PM_OK) return st;
     unsigned long long cnt[2] = {0, 0};
-    for (int round = 0; round < 64 && cnt[0] < cap; ++round) {
-        std::vector<uint64_t> nt(count);
-        for (int k = 0; k < count; ++k) {
-            const uint64_t per_traj = 2ull * (uint64_t)mats[k].n;
-            nt[k] = std::max<uint64_t>(1, (cap - cnt[1]) / ((uint64_t)count * per_traj) + 1);
-        }
-        st = record_into(ctx, mats, count, nt.data(), first, 0, cfg->seed, &cfg->teacher, (float*)bf.p, (float*)bt.p,
-                         (unsigned long long*)bk.p, (uint32_t*)bg.p, (unsigned long long*)bc.p, cap);
-        if (st != PM_OK) return st;
-        PM_CUDA(cudaMemcpy(cnt, bc.p, 16, cudaMemcpyDeviceToHost));
-        first += *std::max_element(nt.begin(), nt.end());
-    }
-    const uint64_t N = std::min<uint64_t>(cnt[1], cap);  // the filled prefix: whole steps only
+    PM_CUDA(cudaMemcpy(cnt, bc.p, 16, cudaMemcpyDeviceToHost));
+    const uint64_t N_all = std::min<uint64_t>(cnt[1], cap);  // the filled prefix: whole steps only
     const auto t1 = std::chrono::steady_clock::now();
+    if (N_all < 16) return fail(ctx, PM_EINVAL, "the teacher produced too few pairs");
+    // the steps in a fixed order (key, then content: keys repeat across
+    // matrices), whole steps up to `want` pairs
+    std::vector<uint32_t> gc(N_all);
+    std::vector<unsigned long long> keys(N_all);
+    std::vector<float> fh(8 * N_all), tg(N_all);
+    PM_CUDA(cudaMemcpy(gc.data(), bg.p, 4 * N_all, cudaMemcpyDeviceToHost));
+    PM_CUDA(cudaMemcpy(keys.data(), bk.p, 8 * N_all, cudaMemcpyDeviceToHost));
+    PM_CUDA(cudaMemcpy(fh.data(), bf.p, 32 * N_all, cudaMemcpyDeviceToHost));
+    PM_CUDA(cudaMemcpy(tg.data(), bt.p, 4 * N_all, cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> starts;
+    for (uint64_t i = 0; i < N_all;) {
+        const uint32_t size = gc[i] & 0xFFFFu;
+        if ((gc[i] >> 16) != 0 || size == 0 || i + size > N_all) return fail(ctx, PM_EDEVICE, "recorded groups are torn");
+        starts.push_back(i);
+        i += size;
+    }
+    std::sort(starts.begin(), starts.end(), [&](uint64_t x, uint64_t y) {
+        if (keys[x] != keys[y]) return keys[x] < keys[y];
+        const uint32_t sx = gc[x] & 0xFFFFu, sy = gc[y] & 0xFFFFu;
+        if (sx != sy) return sx < sy;
+        const int c = std::memcmp(&fh[8 * x], &fh[8 * y], 32 * (size_t)sx);
+        if (c != 0) return c < 0;
+        return std::memcmp(&tg[x], &tg[y], 4 * (size_t)sx) < 0;
+    });
+    std::vector<uint64_t> kept;
+    uint64_t N = 0;
+    for (uint64_t s0 : starts) {
+        const uint32_t size = gc[s0] & 0xFFFFu;
+        if (N + size > want) break;
+        kept.push_back(s0);
+        N += size;
+    }
     if (N < 16) return fail(ctx, PM_EINVAL, "the teacher produced too few pairs");
     // start the output bias at the mean target
-    std::vector<float> tg(N);
-    PM_CUDA(cudaMemcpy(tg.data(), bt.p, 4 * N, cudaMemcpyDeviceToHost));
     double mean = 0;
-    for (float v : tg) mean += v;
+    for (uint64_t s0 : kept)
+        for (uint32_t q = 0; q < (gc[s0] & 0xFFFFu); ++q) mean += tg[s0 + q];
     mean /= (double)N;
     if (m->step == 0) {
         const float b3 = (float)mean;
@@ -1855,18 +1893,9 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
     std::vector<uint64_t> cuts;  // batch b = perm[cuts[b] .. cuts[b + 1])
     perm.reserve(N);
     if (centred) {
-        std::vector<uint32_t> gc(N);
-        PM_CUDA(cudaMemcpy(gc.data(), bg.p, 4 * N, cudaMemcpyDeviceToHost));
-        std::vector<uint64_t> starts;
-        for (uint64_t i = 0; i < N;) {
-            const uint32_t size = gc[i] & 0xFFFFu;
-            if ((gc[i] >> 16) != 0 || size == 0 || i + size > N) return fail(ctx, PM_EDEVICE, "recorded groups are torn");
-            starts.push_back(i);
-            i += size;
-        }
-        std::shuffle(starts.begin(), starts.end(), rng);
+        std::shuffle(kept.begin(), kept.end(), rng);
         cuts.push_back(0);
-        for (uint64_t s0 : starts) {
+        for (uint64_t s0 : kept) {
             const uint32_t size = gc[s0] & 0xFFFFu;
             if (perm.size() - cuts.back() + size > (uint64_t)cfg->batch && perm.size() > cuts.back())
                 cuts.push_back(perm.size());
@@ -1874,7 +1903,8 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
         }
         cuts.push_back(perm.size());
     } else {
-        for (uint64_t i = 0; i < N; ++i) perm.push_back((int)i);
+        for (uint64_t s0 : kept)
+            for (uint32_t k = 0; k < (gc[s0] & 0xFFFFu); ++k) perm.push_back((int)(s0 + k));
         std::shuffle(perm.begin(), perm.end(), rng);
         for (uint64_t r = 0; r < N; r += (uint64_t)cfg->batch) cuts.push_back(r);
         cuts.push_back(N);
@@ -1884,6 +1914,8 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
     PM_CUDA(cudaMalloc(&bp.p, 4 * N));
     PM_CUDA(cudaMemcpy(bp.p, perm.data(), 4 * N, cudaMemcpyHostToDevice));
     if (centred) PM_CUDA(cudaMalloc(&br.p, 4 * max_batch));
+    DevBuf bw;  // partial sums of the gradient reduction
+    PM_CUDA(cudaMalloc(&bw.p, mlp_grad_workspace_bytes(ctx->sm_count)));
     const uint64_t steps_per_epoch = cuts.size() - 1;
     const uint64_t total_steps = steps_per_epoch * (uint64_t)cfg->epochs;
     PM_CUDA(cudaMalloc(&bl.p, 8 * total_steps));
@@ -1896,7 +1928,7 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
             PM_CUDA(cudaMemsetAsync(m->grad, 0, 4 * model_param_count(), ctx->stream));
             PM_CUDA(launch_mlp_grad(m->img, (const float*)bf.p, (const float*)bt.p, (const int*)bp.p, (int64_t)row0, B,
                                     centred ? (const uint32_t*)bg.p : nullptr, (float*)br.p, m->grad,
-                                    (double*)bl.p + sidx, ctx->sm_count, ctx->stream));
+                                    (double*)bl.p + sidx, ctx->sm_count, bw.p, ctx->stream));
             ++m->step;
             PM_CUDA(launch_adam(m->master, m->m1, m->m2, m->grad, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, m->step,
                                 m->img, ctx->stream));

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32) mlp_grad_kernel(const DevMod
                                                                     const float* target, const int* perm,
                                                                     int64_t row0, int B, float inv_b,
                                                                     const float* resid, const uint32_t* group,
-                                                                    float* grad, double* loss_out)
+                                                                    float* part, double* loss_part)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
@@ -219,34 +219,41 @@ __global__ void __launch_bounds__(kTrainWarps * 32) mlp_grad_kernel(const DevMod
         }
         __syncthreads();
     }
-    // flush: every warp adds its share once
+    // flush into this CTA's row of partial sums (a fixed-order reduction over
+    // the CTAs follows, so the gradient does not depend on scheduling): the
+    // weight entries belong to one lane each, the bias and W3 entries of the
+    // four warps are added in warp order through shared memory
+    float* prow = part + (size_t)blockIdx.x * kNParam;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int row = 16 * w + g, col = 8 * j + 2 * t;
-        atomicAdd(grad + oW2 + row * kNH + col, acc_w2[j][0]);
-        atomicAdd(grad + oW2 + row * kNH + col + 1, acc_w2[j][1]);
-        atomicAdd(grad + oW2 + (row + 8) * kNH + col, acc_w2[j][2]);
-        atomicAdd(grad + oW2 + (row + 8) * kNH + col + 1, acc_w2[j][3]);
+        prow[oW2 + row * kNH + col] = acc_w2[j][0];
+        prow[oW2 + row * kNH + col + 1] = acc_w2[j][1];
+        prow[oW2 + (row + 8) * kNH + col] = acc_w2[j][2];
+        prow[oW2 + (row + 8) * kNH + col + 1] = acc_w2[j][3];
     }
     {
         const int row = 16 * w + g, col = 2 * t;
-        atomicAdd(grad + oW1 + row * kNF + col, acc_w1[0]);
-        atomicAdd(grad + oW1 + row * kNF + col + 1, acc_w1[1]);
-        atomicAdd(grad + oW1 + (row + 8) * kNF + col, acc_w1[2]);
-        atomicAdd(grad + oW1 + (row + 8) * kNF + col + 1, acc_w1[3]);
+        prow[oW1 + row * kNF + col] = acc_w1[0];
+        prow[oW1 + row * kNF + col + 1] = acc_w1[1];
+        prow[oW1 + (row + 8) * kNF + col] = acc_w1[2];
+        prow[oW1 + (row + 8) * kNF + col + 1] = acc_w1[3];
     }
+    float* red = reinterpret_cast<float*>(S.dz2t);  // [kTrainWarps][3 * kNH + 1], free after the last iteration
+    double* lred = reinterpret_cast<double*>(S.h1t);
+    constexpr int kRed = 3 * kNH + 1;
     if (g == 0) {
         for (int j = 0; j < 8; ++j) {
-            atomicAdd(grad + oB1 + 8 * j + 2 * t, acc_b1[2 * j]);
-            atomicAdd(grad + oB1 + 8 * j + 2 * t + 1, acc_b1[2 * j + 1]);
-            atomicAdd(grad + oB2 + 8 * j + 2 * t, acc_b2[2 * j]);
-            atomicAdd(grad + oB2 + 8 * j + 2 * t + 1, acc_b2[2 * j + 1]);
+            red[w * kRed + 8 * j + 2 * t] = acc_b1[2 * j];
+            red[w * kRed + 8 * j + 2 * t + 1] = acc_b1[2 * j + 1];
+            red[w * kRed + kNH + 8 * j + 2 * t] = acc_b2[2 * j];
+            red[w * kRed + kNH + 8 * j + 2 * t + 1] = acc_b2[2 * j + 1];
         }
         for (int kk = 0; kk < 4; ++kk) {
-            atomicAdd(grad + oW3 + 16 * kk + 2 * t, acc_w3[4 * kk + 0]);
-            atomicAdd(grad + oW3 + 16 * kk + 2 * t + 1, acc_w3[4 * kk + 1]);
-            atomicAdd(grad + oW3 + 16 * kk + 8 + 2 * t, acc_w3[4 * kk + 2]);
-            atomicAdd(grad + oW3 + 16 * kk + 8 + 2 * t + 1, acc_w3[4 * kk + 3]);
+            red[w * kRed + 2 * kNH + 16 * kk + 2 * t] = acc_w3[4 * kk + 0];
+            red[w * kRed + 2 * kNH + 16 * kk + 2 * t + 1] = acc_w3[4 * kk + 1];
+            red[w * kRed + 2 * kNH + 16 * kk + 8 + 2 * t] = acc_w3[4 * kk + 2];
+            red[w * kRed + 2 * kNH + 16 * kk + 8 + 2 * t + 1] = acc_w3[4 * kk + 3];
         }
     }
     if (t == 0) {
@@ -254,10 +261,38 @@ __global__ void __launch_bounds__(kTrainWarps * 32) mlp_grad_kernel(const DevMod
         b3 += __shfl_xor_sync(0x11111111u, b3, 4);
         b3 += __shfl_xor_sync(0x11111111u, b3, 8);
         b3 += __shfl_xor_sync(0x11111111u, b3, 16);
-        if (g == 0) atomicAdd(grad + oB3, b3);
+        if (g == 0) red[w * kRed + 3 * kNH] = b3;
     }
     for (int o = 16; o; o >>= 1) loss += __shfl_xor_sync(kFull, loss, o);
-    if (lane == 0) atomicAdd(loss_out, loss);
+    if (lane == 0) lred[w] = loss;
+    __syncthreads();
+    for (int i = tid; i < kRed; i += blockDim.x) {
+        float v = 0.f;
+        for (int q = 0; q < kTrainWarps; ++q) v += red[q * kRed + i];
+        const int dst = i < kNH ? oB1 + i : i < 2 * kNH ? oB2 + (i - kNH) : i < 3 * kNH ? oW3 + (i - 2 * kNH) : oB3;
+        prow[dst] = v;
+    }
+    if (tid == 0) {
+        double l = 0.0;
+        for (int q = 0; q < kTrainWarps; ++q) l += lred[q];
+        loss_part[blockIdx.x] = l;
+    }
+}
+
+// grad[i] = sum over the CTAs (in CTA order) of their partial sums; loss alike
+__global__ void grad_reduce_kernel(const float* part, const double* loss_part, int ctas, float* grad, double* loss)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNParam) {
+        float v = 0.f;
+        for (int c = 0; c < ctas; ++c) v += part[(size_t)c * kNParam + i];
+        grad[i] = v;
+    }
+    if (i == 0) {
+        double l = 0.0;
+        for (int c = 0; c < ctas; ++c) l += loss_part[c];
+        *loss = l;
+    }
 }
 
 // outputs of rows 0 .. B-1 of feat (one warp per 16-row tile)
@@ -388,9 +423,14 @@ cudaError_t launch_model_image(const float* master, void* img, cudaStream_t st)
     return cudaGetLastError();
 }
 
+size_t mlp_grad_workspace_bytes(int sm_count)
+{
+    return (size_t)2 * sm_count * (kNParam * sizeof(float) + sizeof(double)) + 256;
+}
+
 cudaError_t launch_mlp_grad(const void* img, const float* feat, const float* target, const int* perm, int64_t row0,
                             int B, const uint32_t* group, float* resid, float* grad, double* loss, int sm_count,
-                            cudaStream_t st)
+                            void* work, cudaStream_t st)
 {
     const DevModel* M = reinterpret_cast<const DevModel*>(img);
     if (group) {  // centred loss: the batch's residuals first
@@ -404,8 +444,14 @@ cudaError_t launch_mlp_grad(const void* img, const float* feat, const float* tar
     if (e != cudaSuccess) return e;
     const int iters = (B + kTrainRows - 1) / kTrainRows;
     const int grid = iters < 2 * sm_count ? iters : 2 * sm_count;
+    float* part = reinterpret_cast<float*>(work);
+    double* loss_part = reinterpret_cast<double*>(
+        reinterpret_cast<uint8_t*>(work) + ((size_t)2 * sm_count * kNParam * sizeof(float) + 255) / 256 * 256);
     mlp_grad_kernel<<<grid, kTrainWarps * 32, smem, st>>>(M, feat, target, perm, row0, B, 1.0f / (float)B,
-                                                           group ? resid : nullptr, group, grad, loss);
+                                                           group ? resid : nullptr, group, part, loss_part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    grad_reduce_kernel<<<(kNParam + 255) / 256, 256, 0, st>>>(part, loss_part, grid, grad, loss);
     return cudaGetLastError();
 }
 

@@ -217,3 +217,20 @@ def test_network_inside_the_trajectory_kernel_matches_oracle():
     assert err.max() < 6e-2, err.max()
     assert np.median(err) < 5e-3, np.median(err)
     model.close()
+
+
+def test_training_is_reproducible():
+    """The same matrices, teacher, seed and settings give bit-identical
+    parameters: the recorded set, its order and the gradient reduction do not
+    depend on how the device schedules its warps."""
+    B = binding()
+    mats = [G.er_planted(120, 6.0, seed=300 + i) for i in range(3)]
+    teacher = B.Schedule(initial_dm=1, K0=50, K=5, sk=B.SK_FIXED, precision=B.PREC_FP32_PROPOSAL)
+    out = []
+    for _ in range(2):
+        model = ctx().model(seed=5)
+        rep = model.train(mats, teacher, n_pairs=60000, epochs=2, batch=2048, lr=2e-3, seed=6)
+        out.append((model.params().copy(), rep["loss_last"], rep["n_pairs"]))
+        model.close()
+    assert out[0][2] == out[1][2] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
