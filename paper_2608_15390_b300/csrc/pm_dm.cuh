@@ -55,8 +55,13 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
         for (int i = lane; i < n; i += 32) { mr[i] = -1; mc[i] = -1; vis[i] = -1; }
     }
     __syncwarp();
-    // greedy start: each active row takes its first free live column
-    for (int i = 0; i < n && !repair; ++i) {
+    // greedy start: each active row takes its first free live column; rows
+    // with at most two entries go first (they have the fewest choices, so
+    // matching them early leaves fewer rows for the augmenting phases)
+    for (int it = 0; it < 2 * n && !repair; ++it) {
+        const int i = it < n ? it : it - n;
+        const bool short_row = rp[i + 1] - rp[i] <= 2;
+        if (it < n ? !short_row : (short_row || mr[i] >= 0)) continue;
         if (!live.row(i)) continue;
         const int b = rp[i], en = rp[i + 1];
         for (int base = b; base < en; base += 32) {

@@ -386,6 +386,60 @@ __device__ __forceinline__ CandLoads cand_loads(const MV<Idx>& V, const DevMatri
     return c;
 }
 
+// The same sums in one warp pass over all candidates' adjacency entries at
+// once (lane f takes flat entry f of the concatenated lists); the per-
+// candidate sums are formed by shared-memory atomics in `acc` (32 ints).
+// Integer sums: identical to neighbour_degree_sum.
+template <typename Idx>
+__device__ __forceinline__ int neighbour_degree_sum_flat(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask,
+                                                         bool vrow, int pp, bool live, int lane, int* acc)
+{
+    const int n = V.n;
+    int b = 0, len = 0;
+    if (live) {
+        b = vrow ? V.cp[pp] : V.rp[pp];
+        len = (vrow ? V.cp[pp + 1] : V.rp[pp + 1]) - b;
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - len;
+    const int total = __shfl_sync(kFull, incl, 31);
+    acc[lane] = 0;
+    __syncwarp();
+    const unsigned lm = __ballot_sync(kFull, live && len > 0);
+    for (int base = 0; base < total; base += 32) {
+        const int f = base + lane;
+        int owner = -1, pos = 0;
+        for (unsigned mk = lm; mk; mk &= mk - 1u) {  // the candidate whose range holds f
+            const int c = __ffs(mk) - 1;
+            const int ce0 = __shfl_sync(kFull, excl, c), cl = __shfl_sync(kFull, len, c), cb = __shfl_sync(kFull, b, c);
+            if (f >= ce0 && f < ce0 + cl) { owner = c; pos = cb + (f - ce0); }
+        }
+        if (owner >= 0) {
+            unsigned d;
+            bool ok;
+            if (vrow) {  // the candidate is a column: its live rows
+                const int i = V.ri[pos];
+                d = deg[i];
+                ok = d != kInact && (!mask || mask[V.ce[pos]]);
+            } else {     // the candidate is a row: its live columns
+                const int j = V.ci[pos];
+                d = deg[n + j];
+                ok = d != kInact && (!mask || mask[pos]);
+            }
+            if (ok) atomicAdd(acc + owner, (int)d);
+        }
+    }
+    __syncwarp();
+    const int mine = acc[lane];
+    __syncwarp();
+    return mine;
+}
+
 template <typename Idx>
 __device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* deg, int t, bool vrow, int p,
                                               float sum_v, int sum_l, float dv, float lsv, const CandLoads& cl,
@@ -550,7 +604,9 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     const int nl = __popc(lmk);
                     const int li = __popc(lmk & ((1u << lane) - 1u));
                     const CandLoads cl = cand_loads<Idx>(V, Mp, vrow, e, pp, live);
-                    const int sum_l = neighbour_degree_sum<Idx>(V, deg, mask, vrow, pp, live, lane);
+                    // the feature tile doubles as the sums' scratch until the features are written
+                    const int sum_l = neighbour_degree_sum_flat<Idx>(V, deg, mask, vrow, pp, live, lane,
+                                                                     reinterpret_cast<int*>(feat));
                     if (live) {
                         float f[8];
                         cand_features<Idx>(V, deg, t, vrow, pp, sum_v, sum_l, (float)dv, lsv, cl, f);
