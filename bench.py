@@ -46,10 +46,10 @@ from paper_2608_15390_b300.merge import merge  # noqa: E402
 METRIC = "effective samples/s at fixed rel. error, learned+batched vs plain, 1 B300"
 UNIT = "effective samples/s"
 N_MATS, N_LO, N_HI, D_LO, D_HI, GEN_SEED = 64, 100, 2000, 4.0, 8.0, 2
-WORKLOAD = ("64 ER+planted-permutation matrices, n~U{100..2000}, avg degree~U[4,8] "
-            "(generator seed 2); learned proposal (8-64-64-1 BF16 network) with two-sided MD, "
-            "initial DM, outer SK(100), FP32 proposal, FP64 log-weights; one persistent launch per step, "
-            "replayed from a CUDA graph, layouts autotuned")
+WORKLOAD_CORE = ("64 ER+planted-permutation matrices, n~U{100..2000}, avg degree~U[4,8] "
+                 "(generator seed 2); learned proposal (8-64-64-1 BF16 network) with two-sided MD, "
+                 "initial DM, outer SK(100), FP32 proposal, FP64 log-weights")
+WORKLOAD = WORKLOAD_CORE + "; one persistent launch per step, replayed from a CUDA graph, layouts autotuned"
 
 
 def parse():
@@ -343,7 +343,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "8 of the 64 matrices (every 8th), "
+            "config": {"workload": WORKLOAD_CORE + "; the CPU oracle on the host cores",
+                       "sample": "8 of the 64 matrices (every 8th), "
                        f"{4 * threads} trajectories each per step, preprocessing excluded",
                        "network": f"trained by the oracle ({t_train:.1f} s, untimed)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
