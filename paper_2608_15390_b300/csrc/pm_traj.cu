@@ -740,7 +740,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     const bool live = in && entry_live(deg, mask, V, vrow, e, pp + poff);
                     const unsigned lm = __ballot_sync(kFull, live);
                     const float lg = lg_reg;
-                    uint64_t w;
+                    uint64_t w, pre = 0;
                     if (uniform) {
                         w = live ? (1ull << kq) : 0ull;
                         W = (uint64_t)dv << kq;
@@ -748,7 +748,8 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                         const Real sv = live ? score(e, pp, lg) : (Real)0;
                         const Real smax = warp_max_nonneg(sv);
                         w = live ? quant_weight<Real>(sv, smax, kq) : 0ull;
-                        W = warp_sum_u64(w);
+                        pre = warp_incl_scan_u64(w, lane);  // W is its last element
+                        W = __shfl_sync(kFull, pre, 31);
                     }
                     rr = uniform_below(W, u0, P.seed, traj, midx, (uint32_t)t);
                     if (rr == ~0ull) {
@@ -762,7 +763,6 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                         for (int q = (int)(rr >> kq); q > 0; --q) mm &= mm - 1u;
                         sl = __ffs(mm) - 1;
                     } else {
-                        const uint64_t pre = warp_incl_scan_u64(w, lane);
                         const unsigned hit = __ballot_sync(kFull, live && pre > rr);
                         sl = __ffs(hit) - 1;
                     }
