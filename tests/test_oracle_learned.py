@@ -231,3 +231,54 @@ def test_network_logits_along_supplied_paths():
     traj, step, cand = k >> 28, (k >> 14) & 0x3FFF, k & 0x3FFF
     got = out["model_logits"][traj.astype(int), step.astype(int), cand.astype(int)]
     assert len(k) > 20 and np.array_equal(got, want)
+
+
+def test_ideal_proposal_gives_the_permanent_on_every_path():
+    # Eq. 4: proposing the partner u of the picked vertex v with probability
+    # proportional to B_vu per(minor without v's and u's lines) gives X = per(A)
+    # on every completed trajectory.  The logits are ln per(minor), computed
+    # here from the residual of each enumerated path (the pick re-derived: least
+    # live degree, then lowest unified id; candidates in adjacency order), so
+    # this also checks the pick rule, the candidate order and the correction.
+    for seed in (3, 4, 8):
+        m = G.planted_bernoulli(6, 0.5, seed)
+        D = m.to_dense().astype(np.float64)
+        n = m.n
+        per = O.ryser_real(D)
+        P = O.Prepared(m, O.Schedule(precision=O.PREC_FP64))
+
+        def ideal_step_logits(pairs):
+            rows = [i for i in range(n) if all(i != (a if a < n else b) for a, b in pairs)]
+            cols = [j for j in range(n) if all(j != (b - n if b >= n else a - n) for a, b in pairs)]
+            deg = {i: sum(D[i, j] != 0 for j in cols) for i in rows}
+            deg.update({n + j: sum(D[i, j] != 0 for i in rows) for j in cols})
+            v = min(deg, key=lambda x: (deg[x], x))
+            if v < n:
+                cand = [(v, j) for j in cols if D[v, j] != 0]
+            else:
+                cand = [(i, v - n) for i in rows if D[i, v - n] != 0]
+            out = []
+            for (i, j) in cand:
+                r2 = [x for x in rows if x != i]
+                c2 = [y for y in cols if y != j]
+                pm = O.ryser_real(D[np.ix_(r2, c2)]) if r2 else 1.0
+                out.append(math.log(pm) if pm > 0 else -30.0)
+            return out
+
+        completed = 0
+        stack = [([], np.zeros((n, 32), dtype=np.float32))]
+        while stack:
+            prefix, lg = stack.pop()
+            r = P.forced(prefix, logits=lg)
+            if r[0] == "need":
+                pairs = [tuple(x) for x in r[4]["chosen"][:len(prefix)]]
+                lg = lg.copy()
+                vals = ideal_step_logits(pairs)
+                lg[len(prefix), :len(vals)] = vals
+                r = P.forced(prefix, logits=lg)  # the step's weights under the ideal logits
+                for k in range(len(r[1])):
+                    stack.append((prefix + [k], lg))
+            elif r[2] < 0:  # completed: X = per(A) up to binary32 rounding of the scores
+                completed += 1
+                assert math.exp(r[1]) == pytest.approx(per, rel=1e-5), (seed, prefix)
+        assert completed >= 1
