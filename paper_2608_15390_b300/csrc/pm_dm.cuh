@@ -149,6 +149,7 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
     // strongly connected components (Tarjan with explicit stacks); the next
     // successor of a column is found by a ballot over its adjacency
     const int V = 2 * n;
+    int* ib = vis;  // [2n] over vis and cur, which the matching no longer needs
     for (int x = lane; x < V; x += 32) { idx[x] = -1; onst[x] = 0; }
     __syncwarp();
     int counter = 0, ncomp = 0, sp = 0;
@@ -175,27 +176,41 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
                     w = n + mr[x];
                 }
             } else {
+                // the eligible entries of the chunk scanned last stay in ib[x]
+                // (eligibility is fixed during the SCC step), so returning to
+                // a column takes its next successor without re-reading the chunk
                 const int j = x - n;
-                int k = it[x] < 0 ? cp[j] : it[x] + 1;
                 const int en = cp[j + 1];
-                while (k < en) {
-                    const int kk = k + lane;
-                    bool ok = false;
-                    int i = 0;
-                    if (kk < en) {
-                        i = ri[kk];
-                        ok = mr[i] != j && live.edge(ce[kk], i, j);
+                const unsigned bits = it[x] < 0 ? 0u : (unsigned)ib[x];
+                if (bits) {
+                    w = ri[it[x] + __ffs(bits) - 1];
+                    ib[x] = (int)(bits & (bits - 1u));
+                } else {
+                    int k = it[x] < 0 ? cp[j] : it[x] + 32;
+                    bool found = false;
+                    while (k < en) {
+                        const int kk = k + lane;
+                        bool ok = false;
+                        int i = 0;
+                        if (kk < en) {
+                            i = ri[kk];
+                            ok = mr[i] != j && live.edge(ce[kk], i, j);
+                        }
+                        const unsigned bal = __ballot_sync(kFull, ok);
+                        if (bal) {
+                            w = __shfl_sync(kFull, i, __ffs(bal) - 1);
+                            it[x] = k;
+                            ib[x] = (int)(bal & (bal - 1u));
+                            found = true;
+                            break;
+                        }
+                        k += 32;
                     }
-                    const unsigned bal = __ballot_sync(kFull, ok);
-                    if (bal) {
-                        const int l = __ffs(bal) - 1;
-                        w = __shfl_sync(kFull, i, l);
-                        k += l;
-                        break;
+                    if (!found) {
+                        it[x] = en;
+                        ib[x] = 0;
                     }
-                    k += 32;
                 }
-                it[x] = k < en ? k : en;
             }
             __syncwarp();
             if (w >= 0) {
