@@ -2,22 +2,34 @@
 """Benchmark of the batched sparse-permanent estimator on one B300.
 
 Workload: 64 Erdos-Renyi bipartite matrices with a planted permutation,
-n ~ U{100..2000}, average degree ~ U[4, 8] (generator seed 2), estimated
-together in one persistent launch.  A step is one call over the whole batch
-with a fresh, disjoint slice of trajectory ids (T per matrix): preprocessing
-(CSC build, initial DM, outer SK), trajectories, statistics.
+n ~ U{100..2000}, average degree ~ U[4, 8] (generator seed 2).
+
+A step is one whole job at fixed relative error: every matrix of the batch
+estimated until its RSE (Sec. 4 "Metrics") is at most eps (default 0.05;
+--eps), through the public call estimate_permanent_batch with
+rse_target = eps: preprocessing once (CSC build, initial DM, outer SK), then
+rounds of one persistent launch over the matrices still short of the target
+(consecutive trajectory ids per matrix, statistics merged after each round).
+Steps use disjoint trajectory ids.
 
 value: effective samples per second of the learned proposal run batched
-(the metric's "learned+batched"): per matrix, (sum X)^2 / sum X^2 over all of
-its trajectories of the timed steps (steps x T, default 5 x 1024), summed
-over the matrices, over the device time of the steps.  The network is trained
-before the timed region (time reported) on pairs recorded from an
-SK-scheduled run on 16 training matrices of the same family (seed 7).  The
-line also reports the plain estimator run one matrix per launch (the metric's
-"plain"), the SK(100,10)-Adaptive schedule run batched, with the same
-trajectories per matrix and the same pooling, and their ratios.
+(the metric's "learned+batched"): the Sec. 2 ESS of every matrix at its stop,
+summed over the matrices and steps, over the device time of the steps (CUDA
+events on the launching stream).  At a fixed RSE each matrix ends with
+ESS ~ 1/eps^2, so no matrix dominates the sum; the job time is set by the
+hardest matrices.  The network is trained before the timed region (time
+reported) on pairs recorded from an SK-scheduled run on 16 training matrices
+of the same family (seed 7).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+compare: the metric's "plain" (outer SK only) run one matrix per call and
+run batched, and SK(100,10)-Adaptive run batched, each as one job at the
+same eps under a time budget; a matrix that the budget stops before its
+target gets its time to target extrapolated from its own rate
+(t_k (rse_k / eps)^2, the RSE of a fixed estimator falling as 1/sqrt(M)),
+and the arm is marked extrapolated.  Per-matrix times come from each
+matrix's share of the device time (pm_result.traj_ns).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--eps E] [--impl ours|reference]
 
 Under torchrun every rank runs its own replica (independent trajectory ids);
 value = all ranks' effective samples / the slowest rank's time.
@@ -46,10 +58,14 @@ from paper_2608_15390_b300.merge import merge  # noqa: E402
 METRIC = "effective samples/s at fixed rel. error, learned+batched vs plain, 1 B300"
 UNIT = "effective samples/s"
 N_MATS, N_LO, N_HI, D_LO, D_HI, GEN_SEED = 64, 100, 2000, 4.0, 8.0, 2
+EPS = 0.05
+TRAJ_CAP = 1 << 26  # per matrix and job: an upper bound the RSE target ends first
 WORKLOAD_CORE = ("64 ER+planted-permutation matrices, n~U{100..2000}, avg degree~U[4,8] "
                  "(generator seed 2); learned proposal (8-64-64-1 BF16 network) with two-sided MD, "
                  "initial DM, outer SK(100), FP32 proposal, FP64 log-weights")
-WORKLOAD = WORKLOAD_CORE + "; one persistent launch per step, replayed from a CUDA graph, layouts autotuned"
+WORKLOAD = (WORKLOAD_CORE + "; a step estimates every matrix to RSE <= eps (estimate_permanent_batch with "
+            "rse_target: preprocessing, then rounds of one persistent launch over the unfinished matrices), "
+            "layouts autotuned")
 
 
 def parse():
@@ -58,10 +74,11 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--traj", type=int, default=1024, help="trajectories per matrix per step")
+    p.add_argument("--eps", type=float, default=EPS, help="RSE target of every matrix in a job")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-compare", action="store_true",
-                   help="skip the learned-batched vs plain-unbatched comparison")
+    p.add_argument("--no-compare", action="store_true", help="skip the comparison arms")
+    p.add_argument("--compare-budget", type=float, default=40.0,
+                   help="seconds of device time per comparison arm before extrapolating")
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--mats", type=int, default=N_MATS,
                    help="use the first K matrices (profiling of a smaller case)")
@@ -161,10 +178,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_launch(T, n_mats):
-    """DRAM bytes (read + write) of one trajectory-kernel launch of this
-    workload from the committed one-pass ncu capture of a full-size bench
-    launch, if it was taken on the current kernel source and workload."""
+def ncu_traffic_per_launch(eps, n_mats):
+    """DRAM bytes (read + write) per trajectory-kernel launch of this workload
+    from the committed one-pass ncu capture, if it was taken on the current
+    kernel source and workload (else None)."""
     path = os.path.join(ROOT, "profiles", "traj_kernel_learned_traffic.json")
     try:
         d = json.load(open(path))
@@ -172,7 +189,7 @@ def ncu_traffic_per_launch(T, n_mats):
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    if d.get("traj_per_matrix_per_step") != T or d.get("matrices") != n_mats:
+    if d.get("eps") != eps or d.get("matrices") != n_mats:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -213,7 +230,7 @@ def cpu_baseline(mats, params, gpu_ess_per_traj, seconds_budget=20.0):
     return {"value": tps * gpu_ess_per_traj, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{done} learned-proposal trajectories ({threads} per matrix per round, {rounds} "
                       f"rounds) on matrices 0,4,...,60 of the workload, {dt:.1f} s, preprocessing "
-                      f"excluded; {tps:.2f} traj/s x the GPU run's effective samples per trajectory"}
+                      f"excluded; {tps:.2f} traj/s x the GPU jobs' effective samples per trajectory"}
 
 
 def timed(ctx, stream, fn):
@@ -226,50 +243,81 @@ def timed(ctx, stream, fn):
     return out, e0.elapsed_time(e1) / 1e3
 
 
-def pooled_ess(per_matrix):
-    """Effective samples of the job: per matrix, the statistics of all its
-    trajectories of the timed steps merged (Sec. 2 ESS of the pooled run),
-    summed over the matrices; and the median pooled RSE."""
-    ess, rse = 0.0, []
-    for runs in per_matrix:
-        mrg = merge(runs)
-        ess += mrg["ess"]
-        rse.append(mrg["rse"])
-    return ess, statistics.median(rse)
+def job_summary(res, t_job):
+    """A job's figures from its per-matrix results and device time t_job:
+    effective samples (Sec. 2 ESS at each matrix's stop), trajectories, and
+    per matrix its share of the device time (traj_ns) and its ESS per
+    second of that share."""
+    ess = np.array([r["ess"] for r in res])
+    ns = np.array([float(r["traj_ns"]) for r in res])
+    share = ns / ns.sum() if ns.sum() > 0 else np.full(len(res), 1.0 / len(res))
+    t_k = t_job * share
+    return {"ess": float(ess.sum()), "traj": int(sum(r["n_traj"] for r in res)), "t_k": t_k,
+            "ess_k": ess, "rse_k": np.array([r["rse"] for r in res]),
+            "rounds": int(max(r["rounds"] for r in res)),
+            "met": int(sum(r["stop"] == 1 for r in res))}
 
 
-def compare_arms(ctx, B, dev, args, T):
-    """The metric's "plain" (outer SK only, one matrix per launch) and the
-    SK(100,10)-Adaptive schedule run batched, on the same matrices, with the
-    same trajectories per matrix as the timed learned run (steps x T),
-    effective samples pooled per matrix the same way."""
+def arm_at_eps(res, t_job, eps):
+    """An arm's job at eps: measured where every matrix met the target; a
+    matrix stopped by the time budget gets its time to target and its ESS
+    extrapolated from its own rate (RSE ~ 1/sqrt(M) at a fixed estimator):
+    t_k (rse_k / eps)^2 and ess_k (rse_k / eps)^2."""
+    js = job_summary(res, t_job)
+    t_k, ess_k = js["t_k"].copy(), js["ess_k"].copy()
+    extrap = 0
+    for k, r in enumerate(res):
+        if r["stop"] != 1:
+            f = (r["rse"] / eps) ** 2 if r["rse"] == r["rse"] and r["n_alive"] >= 2 else math.inf
+            t_k[k] *= max(1.0, f)
+            ess_k[k] *= max(1.0, f)
+            extrap += 1
+    return {"ess_per_s": float(ess_k.sum() / t_k.sum()), "job_seconds": float(t_k.sum()),
+            "extrapolated_matrices": extrap, "t_k": t_k, "ess_k": ess_k,
+            "traj_per_s": js["traj"] / t_job, "median_rse": float(np.nanmedian(js["rse_k"]))}
+
+
+def compare_arms(ctx, B, dev, args, learned_tk, learned_essk):
+    """The metric's "plain" (outer SK only) one matrix per call and batched,
+    and SK(100,10)-Adaptive batched, each one job at args.eps with a time
+    budget; the learned arm's per-matrix figures (first timed job) beside
+    them for the per-matrix ratios of ESS/s at eps."""
     import torch
     stream = torch.cuda.current_stream()
-    plain = B.Schedule(**LEARNED)
-    adaptive = B.Schedule(**schedule_fields())
-    nt = [T] * len(dev)
-    runs_p = [[] for _ in dev]
-    runs_a = [[] for _ in dev]
-    t_p = t_a = 0.0
-    for i in range(args.steps):
-        def run_plain():
-            for k, m in enumerate(dev):
-                r, _ = ctx.estimate_batch_ex([m], [T], args.seed, plain, first_traj=(1 << 41) + (i * len(dev) + k) * T)
-                runs_p[k].append(r[0])
-        _, dt = timed(ctx, stream, run_plain)
-        t_p += dt
-        res, dt = timed(ctx, stream, lambda: ctx.estimate_batch_ex(dev, nt, args.seed, adaptive,
-                                                                    first_traj=(1 << 42) + i * T)[0])
-        t_a += dt
-        for k, r in enumerate(res):
-            runs_a[k].append(r)
-    ess_p, rse_p = pooled_ess(runs_p)
-    ess_a, rse_a = pooled_ess(runs_a)
-    n_traj = args.steps * len(dev) * T
-    return {"plain_unbatched_ess_per_s": ess_p / t_p, "plain_unbatched_traj_per_s": n_traj / t_p,
-            "plain_unbatched_median_rse": rse_p,
-            "adaptive_sk_batched_ess_per_s": ess_a / t_a, "adaptive_sk_batched_traj_per_s": n_traj / t_a,
-            "adaptive_sk_batched_median_rse": rse_a}
+    out = {}
+    first = (1 << 44)
+    arms = {"plain_batched": B.Schedule(**LEARNED, rse_target=args.eps, time_budget_s=args.compare_budget),
+            "adaptive_sk_batched": B.Schedule(**schedule_fields(), rse_target=args.eps,
+                                              time_budget_s=args.compare_budget)}
+    for name, sched in arms.items():
+        (res, _), dt = timed(ctx, stream, lambda: ctx.estimate_batch_ex(dev, [TRAJ_CAP] * len(dev), args.seed, sched,
+                                                                       first_traj=first))
+        out[name] = arm_at_eps(res, dt, args.eps)
+    # plain, one matrix per call, each with its share of the budget
+    res_u, t_u = [], []
+    per = args.compare_budget / len(dev)
+    sched = B.Schedule(**LEARNED, rse_target=args.eps, time_budget_s=per)
+    for k, m in enumerate(dev):
+        (r, _), dt = timed(ctx, stream, lambda: ctx.estimate_batch_ex([m], [TRAJ_CAP], args.seed, sched,
+                                                                     first_traj=first + k))
+        res_u.append(r[0])
+        t_u.append(dt)
+    a = [arm_at_eps([r], t, args.eps) for r, t in zip(res_u, t_u)]
+    t_k = np.array([x["t_k"][0] for x in a])
+    ess_k = np.array([x["ess_k"][0] for x in a])
+    out["plain_unbatched"] = {"ess_per_s": float(ess_k.sum() / t_k.sum()), "job_seconds": float(t_k.sum()),
+                              "extrapolated_matrices": int(sum(x["extrapolated_matrices"] for x in a)),
+                              "t_k": t_k, "ess_k": ess_k,
+                              "traj_per_s": sum(r["n_traj"] for r in res_u) / sum(t_u),
+                              "median_rse": float(np.nanmedian([r["rse"] for r in res_u]))}
+    lr = learned_essk / learned_tk
+    cmp = {}
+    for name, d in out.items():
+        ratio_k = lr / (d["ess_k"] / d["t_k"])
+        cmp[name] = {k: v for k, v in d.items() if k not in ("t_k", "ess_k")}
+        cmp[name]["learned_vs_this_per_matrix_median"] = float(np.median(ratio_k))
+        cmp[name]["learned_vs_this_per_matrix_geomean"] = float(np.exp(np.mean(np.log(ratio_k))))
+    return cmp
 
 
 def oracle_train(seed=5, pairs=40000, steps=300, batch=512, lr=2e-3):
@@ -309,9 +357,12 @@ def oracle_train(seed=5, pairs=40000, steps=300, batch=512, lr=2e-3):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle as it stands on the host cores, running the
-    learned proposal (network trained by the oracle itself, untimed) on a
-    bounded sample of the workload."""
+    """Reference arm: the CPU oracle as it stands on the host cores, running
+    the learned proposal (network trained by the oracle itself, untimed) on a
+    bounded sample of the workload (every 8th matrix).  The oracle cannot
+    take a matrix to RSE <= eps within minutes, so each matrix's ESS and CPU
+    time at eps are extrapolated from its pooled sample by the rule the GPU's
+    comparison arms use: both scale with (rse_k / eps)^2."""
     if rank != 0:
         return
     import oracle as O
@@ -321,31 +372,43 @@ def run_reference(args, rank, world):
     t_train = time.perf_counter() - t0
     sched = O.Schedule(**LEARNED)
     threads = os.cpu_count() or 1
-    per_step = [O.Prepared(m, sched) for m in mats[::8]]  # 8 matrices x `threads` trajectories per step
+    sample = list(range(0, N_MATS, 8))
+    preps = [O.Prepared(mats[k], sched) for k in sample]
+    per = 4 * threads
 
-    def step(i):
-        return [P.run_model(seed=args.seed, count=4 * threads, params=params, first_traj=i * 4 * threads,
-                            matrix=8 * k, threads=threads)["log_x"] for k, P in enumerate(per_step)]
+    def step(i, logs, secs):
+        for q, (k, P) in enumerate(zip(sample, preps)):
+            t = time.perf_counter()
+            lx = P.run_model(seed=args.seed, count=per, params=params, first_traj=i * per, matrix=k,
+                             threads=threads)["log_x"]
+            if secs is not None:
+                secs[q] += time.perf_counter() - t
+                logs[q].append(lx)
 
     for i in range(args.warmup):
-        step(i)
+        step(i, None, None)
+    logs = [[] for _ in sample]
+    secs = [0.0] * len(sample)
     t0 = time.perf_counter()
-    logs = [[] for _ in per_step]
     for i in range(args.steps):
-        for k, lx in enumerate(step(args.warmup + i)):
-            logs[k].append(lx)
+        step(args.warmup + i, logs, secs)
     dt = time.perf_counter() - t0
-    # effective samples pooled per matrix over the timed steps, as in our arm
-    tot_ess = sum(O.stats(np.concatenate(lx))["ess"] for lx in logs)
-    tot_traj = sum(sum(len(a) for a in lx) for lx in logs)
-    val = tot_ess / dt
+    ess_eps, t_eps = 0.0, 0.0
+    for q in range(len(sample)):
+        st = O.stats(np.concatenate(logs[q]))
+        f = max(1.0, (st["rse"] / args.eps) ** 2) if st["n_alive"] >= 2 else math.inf
+        ess_eps += st["ess"] * f
+        t_eps += secs[q] * f
+    val = ess_eps / t_eps
+    tot_traj = len(sample) * per * args.steps
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_CORE + "; the CPU oracle on the host cores",
-                       "sample": "8 of the 64 matrices (every 8th), "
-                       f"{4 * threads} trajectories each per step, preprocessing excluded",
+            "config": {"workload": WORKLOAD_CORE + "; the CPU oracle on the host cores", "eps": args.eps,
+                       "sample": f"8 of the 64 matrices (every 8th), {per} trajectories each per step, "
+                                 "preprocessing excluded; ESS and time at eps extrapolated per matrix "
+                                 "as (rse/eps)^2 from the pooled sample",
                        "network": f"trained by the oracle ({t_train:.1f} s, untimed)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{tot_traj} learned-proposal trajectories over {args.steps} steps"},
@@ -535,44 +598,38 @@ def main():
               for m in mats]
     stream = torch.cuda.current_stream()
     ctx = B.Context(local, stream.cuda_stream)
+    bw = ctx.probe_bandwidth()
     model = ctx.model(seed=11)
     t0 = time.perf_counter()
     train_rep = model.train(training_matrices(), B.Schedule(**TEACHER), n_pairs=2_000_000, epochs=4,
                             batch=8192, lr=2e-3, seed=12, objective=B.OBJ_CENTRED)
     t_train = time.perf_counter() - t0
-    sched = B.Schedule(**LEARNED, learned=model)
-    T = args.traj
-    nt = [T] * len(mats)
+    sched = B.Schedule(**LEARNED, learned=model, rse_target=args.eps)
+    nt = [TRAJ_CAP] * len(mats)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    # the resident batch: device copies, layouts chosen by the autotuner, the
-    # launch sequence captured as a CUDA graph (all before the timed region)
+    # layouts: the autotuner times each size class once and caches its choice
+    # in the context, where every later call of the same schedule finds it
     t0 = time.perf_counter()
-    batch = ctx.batch(dev, nt, sched, graph=True, autotune=True)
-    t_batch = time.perf_counter() - t0
-    plans = [batch.plan(k) for k in range(len(mats))]
+    tb = ctx.batch(dev, [1024] * len(mats), B.Schedule(**LEARNED, learned=model), graph=False, autotune=True)
+    plans = [tb.plan(k) for k in range(len(mats))]
+    tb.close()
+    t_tune = time.perf_counter() - t0
 
-    def step(i, host=False):
-        first = ((rank * 1_000_000 + i) * T) % (1 << 47)
-        if host:  # the one-shot public call from pinned host CSR (e2e)
-            res, _ = ctx.estimate_batch_ex(pinned, nt, args.seed, sched, first_traj=first)
-        else:
-            res, _ = batch.run(first, args.seed)
-        return res
+    def job(i, host=False):
+        first = ((rank * 4096 + i) << 30) % (1 << 47)
+        return ctx.estimate_batch_ex(pinned if host else dev, nt, args.seed, sched, first_traj=first)[0]
 
     for i in range(args.warmup):
-        step(i)
+        job(i)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    runs = [[] for _ in mats]  # per matrix: the result of every timed step
-    tot_traj = 0
-    alg_bytes = 0
-    mlp_rows = 0
-    kern_ms = 0.0
-    prep_ms = 0.0
+    jobs = []
+    kern_ms = prep_ms = 0.0
+    alg_bytes = mlp_rows = 0
     launches = 0
     if dist:
         dist.barrier()
@@ -580,104 +637,104 @@ def main():
     for i in range(args.steps):
         flush.fill_(float(i))  # L2 flush between timed steps (outside the events)
         ev[i][0].record(stream)
-        res = step(args.warmup + i)
+        res = job(args.warmup + i)
         ev[i][1].record(stream)
         info = ctx.last_call_info()
         kern_ms += info["traj_kernel_ms"]
         prep_ms += info["prep_kernel_ms"]
-        launches += 4  # one graph: prepare, trajectories, stats partial, stats merge
-        for k, r in enumerate(res):
-            runs[k].append(r)
-            tot_traj += r["n_traj"]
-            alg_bytes += r["alg_bytes"]
-            mlp_rows += r["mlp_rows"]
+        rounds = max(r["rounds"] for r in res)
+        launches += 1 + 3 * rounds  # prepare; per round: trajectories, statistics partial + merge
+        alg_bytes += sum(r["alg_bytes"] for r in res)
+        mlp_rows += sum(r["mlp_rows"] for r in res)
+        jobs.append(res)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_dev = sum(step_ms) / 1e3
-    # e2e: the same steps through the public API from pinned host buffers
+    step_s = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    t_dev = sum(step_s)
+    summ = [job_summary(res, t) for res, t in zip(jobs, step_s)]
+    tot_ess = sum(js["ess"] for js in summ)
+    tot_traj = sum(js["traj"] for js in summ)
+    # e2e: the same jobs through the public call from pinned host CSR
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    runs_e2e = [[] for _ in mats]
+    e2e_ess = 0.0
     for i in range(args.steps):
-        res = step(10_000 + i, host=True)
-        for k, r in enumerate(res):
-            runs_e2e[k].append(r)
+        e2e_ess += sum(r["ess"] for r in job(10_000 + i, host=True))
     t_e2e = time.perf_counter() - t0
     info = ctx.last_call_info()
     h2d, d2h = info["h2d_bytes"], info["d2h_bytes"]
 
     if dist:
-        # every rank ran disjoint trajectories of the same matrices: pool them
         t = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_dev, t_e2e = float(t[0]), float(t[1])
-        s = torch.tensor([float(tot_traj)], dtype=torch.float64, device="cuda")
+        s = torch.tensor([tot_ess, e2e_ess, float(tot_traj)], dtype=torch.float64, device="cuda")
         dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        tot_traj = int(s[0])
-        for lst in (runs, runs_e2e):
-            got = [None] * world
-            dist.all_gather_object(got, lst)
-            for k in range(len(lst)):
-                lst[k] = [r for g in got for r in g[k]]
+        tot_ess, e2e_ess, tot_traj = float(s[0]), float(s[1]), int(s[2])
 
-    tot_ess, med_rse = pooled_ess(runs)
-    e2e_ess, _ = pooled_ess(runs_e2e)
     value = tot_ess / t_dev
     ess_per_traj = tot_ess / max(1, tot_traj)
+    note = None
     if args.mats != N_MATS or args.nmax != N_HI:
-        line_cfg_note = f"reduced case: first {args.mats} matrices, n<={args.nmax} (not a bench value)"
-    else:
-        line_cfg_note = None
+        note = f"reduced case: first {args.mats} matrices, n<={args.nmax} (not a bench value)"
     peaks = measured_peaks()
-    # roofline of the dominant kernel (the trajectory kernel with the learned
-    # proposal): its dense work is the network on BF16 tensor cores, 9344
-    # multiply-add flops per live candidate; the algorithmic-bytes figure
-    # against HBM is reported beside it
-    tc_peak = peaks["bf16_tflops"] if peaks else 1800.0
     hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0
-    kern_s = kern_ms / args.steps / 1e3
-    achieved_tf = (mlp_rows / args.steps) * 9344.0 / kern_s / 1e12
-    achieved_gb = (alg_bytes / args.steps) / kern_s / 1e9
-    traffic = ncu_traffic_per_launch(T, len(mats))
+    tc_peak = peaks["bf16_tflops"] if peaks else 1800.0
+    kern_s = kern_ms / 1e3
+    achieved_gb = alg_bytes / kern_s / 1e9
+    achieved_tf = mlp_rows * 9344.0 / kern_s / 1e12
+    rounds_per_job = statistics.median(js["rounds"] for js in summ)
+    traffic = ncu_traffic_per_launch(args.eps, len(mats))
+    ess_k = np.concatenate([js["ess_k"] for js in summ])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "traj_per_matrix_per_step": T,
+        "config": {"workload": WORKLOAD, "eps": args.eps, "traj_cap_per_matrix": TRAJ_CAP,
                    "l2": "flushed between timed steps (256 MB write outside the step events)",
-                   "parallelism": f"replicas{world}", "note": line_cfg_note},
+                   "parallelism": f"replicas{world}", "note": note},
         "traj_per_s": tot_traj / t_dev,
         "ess_per_traj": ess_per_traj,
-        "median_rse": med_rse,
-        "ess_definition": "per matrix, Sec. 2 ESS of all its timed trajectories pooled, summed over matrices",
-        "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": tc_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / tc_peak, "traffic": traffic,
+        "job": {"seconds_median": statistics.median(step_s), "rounds_median": rounds_per_job,
+                "matrices_at_target": int(np.mean([js["met"] for js in summ])),
+                "ess_per_matrix_median": float(np.median(ess_k)),
+                "ess_per_matrix_min": float(ess_k.min()),
+                "traj_per_job": tot_traj / args.steps,
+                "ess_definition": "Sec. 2 ESS of each matrix at its stop (RSE <= eps), summed over matrices"},
+        "roofline": {"bound": "hbm", "achieved": achieved_gb, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_gb / hbm_peak, "traffic": traffic,
                      "kernel": "traj_kernel<float, learned>",
-                     "peak_source": "measured bf16 burst" if peaks else "fallback",
-                     "flops": "9344 per live candidate evaluated by the network (useful rows only)",
-                     "alg_hbm_gbs": achieved_gb, "alg_hbm_frac": achieved_gb / hbm_peak,
-                     "kernel_ms_per_step": kern_ms / args.steps,
-                     "prep_ms_per_step": prep_ms / args.steps},
+                     "peak_source": "measured copy (MEASURED_PEAKS.json)" if peaks else "fallback",
+                     "bytes": "algorithmic, counted per trajectory on the device (pm_result.alg_bytes: "
+                              "16 B/vertex init; per step 8 B per adjacency entry of v and u + 16 B pointers, "
+                              "32 B per degree decrement; features 8 B per entry of each candidate's list "
+                              "+ 16 B per candidate); per launch = summed over the step's launches",
+                     "kernel_ms_per_step": kern_ms / args.steps, "prep_ms_per_step": prep_ms / args.steps,
+                     "l2": {"achieved": achieved_gb, "peak": bw["l2_read_gbs"], "unit": "GB/s",
+                            "frac": achieved_gb / bw["l2_read_gbs"], "peak_source": "pm_probe_bandwidth"},
+                     "smem_peak_gbs": bw["smem_read_gbs"],
+                     "tensor": {"achieved": achieved_tf, "peak": tc_peak, "unit": "TFLOP/s",
+                                "frac": achieved_tf / tc_peak,
+                                "flops": "9344 per live candidate evaluated by the network"}},
         "gpu_launches": launches * world,
-        "batch": {"graph": True, "autotune": True, "create_seconds": t_batch,
-                  "layouts": {"staged": sum(p["staged"] for p in plans), "gstate": sum(p["gstate"] for p in plans),
-                              "tuned": sum(p["tuned"] for p in plans),
-                              "groups_per_sm_median": statistics.median(p["groups"] for p in plans)}},
+        "layouts": {"autotune_seconds": t_tune, "staged": sum(p["staged"] for p in plans),
+                    "gstate": sum(p["gstate"] for p in plans), "tuned": sum(p["tuned"] for p in plans),
+                    "groups_per_sm_median": statistics.median(p["groups"] for p in plans)},
         "clocks": clk,
         "e2e": {"value": e2e_ess / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "how": "the same jobs through estimate_permanent_batch from pinned host CSR, host wall clock"},
     }
     line["train"] = {"objective": "per-step centred squared error", "pairs": train_rep["n_pairs"],
                      "loss_first": train_rep["loss_first"],
                      "loss_last": train_rep["loss_last"], "seconds": t_train,
                      "where": "before the timed region"}
     if not args.no_compare:
-        cmp = compare_arms(ctx, B, dev, args, T)
-        cmp["learned_batched_vs_plain_unbatched"] = value / cmp["plain_unbatched_ess_per_s"]
-        cmp["learned_batched_vs_adaptive_sk_batched"] = value / cmp["adaptive_sk_batched_ess_per_s"]
+        cmp = compare_arms(ctx, B, dev, args, summ[0]["t_k"], summ[0]["ess_k"])
+        for name in ("plain_unbatched", "plain_batched", "adaptive_sk_batched"):
+            cmp[f"learned_batched_vs_{name}"] = value / cmp[name]["ess_per_s"]
         line["compare"] = cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mats, bf16_params(model.params()), ess_per_traj)

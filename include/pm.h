@@ -14,7 +14,10 @@
  *  - returns pm_status; PM_OK (0) on success.  No function aborts the process
  *    or traps the device; device-side failures come back through a status
  *    word read after the stream synchronises (PM_EDEVICE).
- *  - outputs are written only when the call returns PM_OK.
+ *  - outputs are written only when the call returns PM_OK, or PM_ETIMEOUT /
+ *    PM_ECANCELLED from a call that stopped early (time budget, cancel):
+ *    then they describe the trajectories that ran (pm_result.stop says why
+ *    a matrix stopped).
  *  - all pointers are caller-owned and not retained after the call returns,
  *    except the handles the library allocates (pm_context, pm_matrix).
  *  - a context serialises its work on one CUDA stream; calls on one context
@@ -36,8 +39,8 @@ typedef enum {
     PM_EINVAL = 1,         /* malformed matrix, size mismatch, bad schedule, NULL argument */
     PM_ENOMEM = 2,         /* device or pinned-host allocation failed */
     PM_ECUDA = 3,          /* a CUDA runtime call failed (the message is kept, see pm_last_error) */
-    PM_ETIMEOUT = 4,       /* a bounded device-side wait ran out */
-    PM_ECANCELLED = 5,
+    PM_ETIMEOUT = 4,       /* the call's time budget (pm_schedule.time_budget_s) ran out first */
+    PM_ECANCELLED = 5,     /* pm_context_cancel stopped the call */
     PM_EUNSUPPORTED = 6,   /* size or option outside what this build supports */
     PM_EDEVICE = 7         /* a kernel reported an internal error through the status word */
 } pm_status;
@@ -88,7 +91,32 @@ typedef struct {
                               precision = PM_PREC_FP32_PROPOSAL.  The correction still
                               uses the realised probability, so the estimate stays
                               unbiased. */
+    /* Run control (Sec. 4: runs stop at a relative-error target or a time
+     * cap).  0 switches each off; both >= 0 and finite.
+     *   rse_target     estimate_permanent(_batch) / pm_estimate_batch_ex run
+     *                  rounds of trajectories until each matrix's RSE is at
+     *                  most rse_target (with at least min(1024, n_traj)
+     *                  trajectories and two alive) or its n_traj ran; the
+     *                  rounds use consecutive trajectory ids, so n_traj is
+     *                  an upper bound.  pm_batch_create rejects it (a
+     *                  resident batch runs fixed counts).
+     *   time_budget_s  the call starts no trajectory once this much time has
+     *                  passed (host clock between rounds, the device clock
+     *                  %globaltimer inside a launch); trajectories already
+     *                  started run to their end.  If matrices are still
+     *                  short of their target or n_traj, the call returns
+     *                  PM_ETIMEOUT with the results of what ran.
+     * pm_trace, training teachers and pm_server (whose requests carry their
+     * own targets) ignore or reject them: the server requires 0. */
+    double rse_target;
+    double time_budget_s;
 } pm_schedule;
+
+/* Why a matrix's run ended (pm_result.stop). */
+enum { PM_STOP_COMPLETE = 0,   /* all n_traj trajectories ran */
+       PM_STOP_TARGET = 1,     /* RSE reached rse_target */
+       PM_STOP_TIME = 2,       /* the time budget ran out */
+       PM_STOP_CANCELLED = 3 };
 
 typedef struct {
     double log_estimate;   /* ln(mean X); -INFINITY if every X = 0 */
@@ -105,17 +133,45 @@ typedef struct {
     uint64_t n_full_sk;    /* full SK iterations over all trajectories */
     uint64_t n_local_sk;   /* Local repairs over all trajectories */
     double seconds;        /* wall time of the call on the host clock */
-    uint64_t alg_bytes;    /* algorithmic bytes the trajectories of this matrix touched:
-                              8 B per adjacency entry of each picked vertex and partner,
-                              16 B per live edge per full SK iteration, 16 B per vertex
-                              of each Local repair, 8 B per vertex at initialisation */
+    uint64_t alg_bytes;    /* algorithmic bytes the trajectories of this matrix touched
+                              (the method's own traffic, whatever the memory level):
+                              16 B per vertex at initialisation; per step 8 B per
+                              adjacency entry of the picked vertex and of its partner
+                              (index + liveness check) and 16 B of list pointers,
+                              32 B per degree decrement (read-modify-write + the
+                              minimum-degree structure), the scale (4 or 8 B) and value
+                              (4 B) per candidate of a scaled / weighted proposal; the
+                              learned proposal's features 8 B per adjacency entry of
+                              each live candidate + 16 B per candidate; 16 B per live
+                              edge per full SK iteration, 16 B per vertex of each Local
+                              repair, 16 B per live edge + 48 B per active row per DM */
     double kernel_ms;      /* device time of the trajectory kernel of the call (CUDA events
                               on the context's stream; shared by all matrices of a batch) */
     uint64_t mlp_rows;     /* learned proposal: network evaluations of live candidates
                               (2 * (8*64 + 64*64 + 64) = 9344 multiply-add flops each) */
+    uint64_t traj_ns;      /* sum over this matrix's trajectories of their device
+                              durations (%globaltimer, start to end); trajectories of a
+                              launch overlap, so a matrix's share of the launch's time
+                              is its traj_ns over the launch's total */
+    uint32_t rounds;       /* trajectory launches the result merges */
+    int32_t stop;          /* PM_STOP_* */
 } pm_result;
 
-/* Bookkeeping of the most recent estimate / trace call of a context. */
+/* Layout of one matrix in a trajectory launch (see pm_batch_create). */
+typedef struct {
+    int32_t g;               /* warps per trajectory */
+    int32_t groups;          /* trajectories in flight per CTA (one CTA per SM) */
+    int32_t staged;          /* matrix adjacency staged in shared memory */
+    int32_t rc_smem;         /* scaling vectors in shared memory */
+    int32_t gstate;          /* trajectory state in global memory (large n) */
+    int32_t dm_smem;         /* inner DM's workspace and edge mask in shared memory */
+    int32_t tuned;           /* 1 if the autotuner chose this layout */
+    int32_t reserved;
+    double probe_traj_per_s;      /* the chosen layout's probe rate (-1: not probed) */
+    double heuristic_traj_per_s;  /* the heuristic layout's probe rate (-1: not probed) */
+} pm_plan_info;
+
+/* Bookkeeping of the most recent estimate / trace / batch call of a context. */
 typedef struct {
     uint64_t h2d_bytes;       /* host -> device bytes the call copied */
     uint64_t d2h_bytes;       /* device -> host bytes the call copied */
@@ -123,6 +179,8 @@ typedef struct {
     double prep_kernel_ms;    /* device time of the preprocessing kernel */
     int32_t grid;             /* CTAs of the trajectory launch */
     int32_t warps_per_cta;    /* warps (trajectory slots) per CTA */
+    pm_plan_info first_plan;  /* layout of the call's first matrix (g = 0: no launch;
+                                 tuned and the probe rates are not filled in) */
 } pm_call_info;
 
 typedef struct pm_context pm_context;
@@ -132,6 +190,24 @@ typedef struct pm_context pm_context;
  * the context).  Device workspaces are allocated lazily and grown as needed. */
 pm_status pm_context_create(pm_context** ctx, int device, void* cuda_stream);
 pm_status pm_context_destroy(pm_context* ctx);
+
+/* Ask the context's running estimate call (or resident-batch run) to stop:
+ * safe to call from any host thread at any time.  It sets a flag in pinned
+ * host memory that the trajectory kernel reads before it starts each chunk
+ * of trajectories; started trajectories run to their end, and the call
+ * returns PM_ECANCELLED with the results of what ran.  Every estimate call
+ * and batch run clears the flag when it starts, so a cancel that arrives
+ * between calls is dropped. */
+pm_status pm_context_cancel(pm_context* ctx);
+
+/* Merge the results of disjoint trajectory sets of one matrix (other ranks,
+ * earlier rounds or resumed runs with other trajectory ids) through their
+ * sufficient statistics: M, #alive, ln sum X and ln sum X^2, from which the
+ * estimate, ESS, p_match (Sec. 2), relative spread and RSE (Sec. 4
+ * "Metrics") follow exactly; operation counts, bytes, times and rounds are
+ * summed, stop is the largest.  Host arithmetic only (no device needed).
+ * parts[count], count >= 1; out may alias no part. */
+pm_status pm_merge_results(const pm_result* parts, int32_t count, pm_result* out);
 
 /* Estimate per(csr) from n_traj trajectories with Philox4x32-10 seed `seed`;
  * trajectory k draws from counter (k, matrix index 0, step, attempt), so any
@@ -160,12 +236,20 @@ pm_status pm_estimate_batch_ex(pm_context* ctx, const pm_csr* mats, int32_t coun
  *   deg_v[count][n]      live degree of v when it was picked, -1 after death
  *   dead_step[count]     step at which the trajectory died, -1 if it completed
  *   log_x[count]         ln X, -INFINITY for a dead trajectory
- *   logits[count][n][32] learned proposal only: network output of the q-th live
- *                        candidate (adjacency order) of step t, q < 32. */
+ *   logits[count][n][logit_stride]
+ *                        learned proposal only: network output of the q-th live
+ *                        candidate (adjacency order) of step t, q < logit_stride
+ *                        (0 where a step has fewer candidates; a stride of the
+ *                        largest row or column length of csr keeps every
+ *                        candidate of every step).  logit_stride is ignored when
+ *                        logits is NULL, else 1 .. 65535 (PM_EINVAL otherwise).
+ * The trajectory kernel runs in the layout the context's autotuner chose for
+ * this matrix's size class and schedule (pm_batch_create with
+ * PM_BATCH_AUTOTUNE), else in the heuristic layout. */
 pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index,
                    uint64_t first_traj, uint32_t count, uint64_t seed,
                    const pm_schedule* schedule, int32_t* chosen, int32_t* deg_v,
-                   int32_t* dead_step, double* log_x, float* logits);
+                   int32_t* dead_step, double* log_x, float* logits, uint32_t logit_stride);
 
 /* Preprocessing only (InitialDM + K0 outer SK): host outputs, any may be NULL:
  * ok (1 if a perfect matching exists), keep[nnz] (1 = edge survives the
@@ -179,6 +263,15 @@ pm_status pm_preprocess(pm_context* ctx, const pm_csr* csr, const pm_schedule* s
  * out[count][4]); for checking the generator against published vectors. */
 pm_status pm_philox_blocks(pm_context* ctx, const uint32_t ctr[4], const uint32_t key[2],
                            uint32_t count, uint32_t* out);
+
+/* Measure the device's on-chip read bandwidth (a diagnostic with no
+ * counterpart in the paper; the roofline denominators of traffic that stays
+ * on chip): *l2_read_gbs from 200 passes of 16-byte L2-cached reads over a
+ * 64 MiB buffer (smaller than L2, so every pass after the first hits L2),
+ * *smem_read_gbs from conflict-free 16-byte reads of 96 KiB of shared memory
+ * per CTA on two CTAs per SM; GB/s = bytes read / CUDA-event time.
+ * Allocates and frees a 64 MiB device buffer. */
+pm_status pm_probe_bandwidth(pm_context* ctx, double* l2_read_gbs, double* smem_read_gbs);
 
 /* Copy the bookkeeping of the context's most recent call into *info. */
 pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info);
@@ -210,19 +303,6 @@ pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info);
  * PM_ECUDA if capture or instantiation fails. */
 typedef struct pm_batch pm_batch;
 enum { PM_BATCH_GRAPH = 1, PM_BATCH_AUTOTUNE = 2 };
-
-typedef struct {
-    int32_t g;               /* warps per trajectory */
-    int32_t groups;          /* trajectories in flight per CTA (one CTA per SM) */
-    int32_t staged;          /* matrix adjacency staged in shared memory */
-    int32_t rc_smem;         /* scaling vectors in shared memory */
-    int32_t gstate;          /* trajectory state in global memory (large n) */
-    int32_t dm_smem;         /* inner DM's workspace and edge mask in shared memory */
-    int32_t tuned;           /* 1 if the autotuner chose this layout */
-    int32_t reserved;
-    double probe_traj_per_s;      /* the chosen layout's probe rate (-1: not probed) */
-    double heuristic_traj_per_s;  /* the heuristic layout's probe rate (-1: not probed) */
-} pm_plan_info;
 
 pm_status pm_batch_create(pm_context* ctx, const pm_csr* mats, int32_t count,
                           const uint64_t* n_traj, const pm_schedule* schedule, uint32_t flags,
@@ -331,6 +411,15 @@ typedef struct {
  * for a seeded random initialisation. */
 pm_status pm_model_create(pm_context* ctx, const float* params, uint64_t seed, pm_model** out);
 pm_status pm_model_destroy(pm_model* model);
+/* Write the FP32 master parameters to `path` (8-byte magic "PMMODEL1",
+ * uint32 version 1, uint32 count 4801, the parameters, a 64-bit FNV-1a
+ * checksum of their bytes; little-endian), through a temporary file renamed
+ * into place.  PM_EINVAL if the file cannot be written. */
+pm_status pm_model_save(pm_context* ctx, const pm_model* model, const char* path);
+/* Create a model on the context's device from a file written by
+ * pm_model_save.  PM_EINVAL for a missing, truncated, foreign or corrupted
+ * file (magic, version, count, length and checksum are all checked). */
+pm_status pm_model_load(pm_context* ctx, const char* path, pm_model** out);
 /* FP32 master parameters (host out, 4801 floats) / replace them. */
 pm_status pm_model_get_params(pm_context* ctx, const pm_model* model, float* params);
 pm_status pm_model_set_params(pm_context* ctx, pm_model* model, const float* params);

@@ -89,7 +89,7 @@ def lib():
         L.or_prep_set_max_steps.argtypes = [P, C.c_int]
         L.or_prep_mask.argtypes = [P, P]
         L.or_forced_run.restype = C.c_int
-        L.or_forced_run.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P]
+        L.or_forced_run.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, C.c_int32]
         L.or_run.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
                              P, P, P, P, P]
         L.or_dm_mask.restype = C.c_int
@@ -104,9 +104,9 @@ def lib():
         L.or_record.restype = C.c_int64
         L.or_record.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int64, P, P, P, P]
         L.or_run_ext_model.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
-                                       P, P, P, P, P, P, P]
+                                       P, P, P, P, P, C.c_int32, P, P]
         L.or_run_ext.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
-                                 P, P, P, P, P, P]
+                                 P, P, P, P, P, P, C.c_int32]
         L.or_run_model.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int64, C.c_int,
                                    P, P, P, P]
         _lib = L
@@ -249,16 +249,17 @@ class Prepared:
     def run_ext(self, seed: int, count: int, logits, first_traj: int = 0, matrix: int = 0,
                 threads: int = 1):
         """Trajectories with the learned proposal's logits supplied:
-        logits[count, n, 32] (candidate q of step t in adjacency order)."""
+        logits[count, n, L] (candidate q < L of step t in adjacency order; a
+        step with more than L live candidates ends its trajectory)."""
         lg = np.ascontiguousarray(logits, dtype=np.float32)
-        assert lg.shape == (count, self.n, 32)
+        assert lg.ndim == 3 and lg.shape[:2] == (count, self.n) and lg.shape[2] >= 1
         lx = np.zeros(count)
         ds = np.zeros(count, dtype=np.int32)
         ch = np.zeros((count, self.n, 2), dtype=np.int32)
         dv = np.zeros((count, self.n), dtype=np.int32)
         oc = np.zeros(3, dtype=np.int64)
         lib().or_run_ext(self.h, seed, matrix, first_traj, count, threads, _ptr(lx), _ptr(ds),
-                         _ptr(ch), _ptr(dv), _ptr(oc), _ptr(lg))
+                         _ptr(ch), _ptr(dv), _ptr(oc), _ptr(lg), lg.shape[2])
         return dict(log_x=lx, dead_step=ds, chosen=ch, deg_v=dv)
 
     def run_model(self, seed: int, count: int, params, first_traj: int = 0, matrix: int = 0,
@@ -287,19 +288,19 @@ class Prepared:
 
     def run_ext_model(self, seed: int, count: int, logits, params, first_traj: int = 0, matrix: int = 0,
                       threads: int = 1):
-        """Paths that follow the supplied logits[count, n, 32] (as run_ext),
+        """Paths that follow the supplied logits[count, n, L] (as run_ext),
         with this side's network evaluated at every visited state: returns
-        run_ext's dict plus model_logits[count, n, 32]."""
+        run_ext's dict plus model_logits[count, n, L]."""
         lg = np.ascontiguousarray(logits, dtype=np.float32)
-        assert lg.shape == (count, self.n, 32)
+        assert lg.ndim == 3 and lg.shape[:2] == (count, self.n) and lg.shape[2] >= 1
         pm = np.ascontiguousarray(params, dtype=np.float64)
         lx = np.zeros(count)
         ds = np.zeros(count, dtype=np.int32)
         ch = np.zeros((count, self.n, 2), dtype=np.int32)
         dv = np.zeros((count, self.n), dtype=np.int32)
-        ml = np.zeros((count, self.n, 32), dtype=np.float32)
+        ml = np.zeros(lg.shape, dtype=np.float32)
         lib().or_run_ext_model(self.h, seed, matrix, first_traj, count, threads, _ptr(lx), _ptr(ds), _ptr(ch),
-                               _ptr(dv), _ptr(lg), _ptr(pm), _ptr(ml))
+                               _ptr(dv), _ptr(lg), lg.shape[2], _ptr(pm), _ptr(ml))
         return dict(log_x=lx, dead_step=ds, chosen=ch, deg_v=dv, model_logits=ml)
 
     def forced(self, choices, logits=None):
@@ -316,8 +317,9 @@ class Prepared:
         chosen = np.zeros((max(1, self.n), 2), dtype=np.int32)
         counts = np.zeros(3, dtype=np.int32)
         lg = None if logits is None else np.ascontiguousarray(logits, dtype=np.float32)
+        stride = 0 if lg is None else int(lg.shape[-1])
         need = lib().or_forced_run(self.h, _ptr(ch), len(ch), _ptr(w), C.byref(W), C.byref(nc),
-                                   C.byref(lx), C.byref(ds), _ptr(chosen), _ptr(counts), _ptr(lg))
+                                   C.byref(lx), C.byref(ds), _ptr(chosen), _ptr(counts), _ptr(lg), stride)
         info = dict(chosen=chosen[: self.n], n_dm=int(counts[0]), n_full_sk=int(counts[1]),
                     n_local_sk=int(counts[2]))
         if need:

@@ -554,18 +554,22 @@ typedef struct {
  * t-th step takes candidate forced[t] instead of a Philox draw; when t reaches
  * n_forced the function stops and reports the candidate weights (need_choice). */
 /* learned-proposal hooks (an extension; the paper has no learned
- * proposal): ext_logits[t * 32 + q] is the logit of the q-th live candidate
- * at step t; record_* collect (features, target) pairs of the SK estimator. */
+ * proposal): ext_logits[t * lstride + q] is the logit of the q-th live
+ * candidate at step t (lstride >= the largest candidate count; a step with
+ * more candidates cannot be replayed and ends the trajectory with
+ * dead_reason 4); record_* collect (features, target) pairs of the SK
+ * estimator. */
 typedef struct {
     const double* model;       /* [4801] network parameters, or NULL */
-    const float* ext_logits;   /* [n][32] or NULL */
+    const float* ext_logits;   /* [n][lstride] or NULL */
+    int32_t lstride;           /* row length of ext_logits and model_logits_out */
     float* rec_feat;           /* [cap][8] or NULL */
     float* rec_target;         /* [cap] */
     uint64_t* rec_key;         /* [cap]: traj << 28 | t << 14 | q */
     uint32_t* rec_group;       /* [cap] or NULL: index within the step's pairs << 16 | their count */
     int64_t rec_cap, rec_n;
     int rec_full;              /* a step's pairs no longer fit: recording has stopped */
-    float* model_logits_out;   /* [n][32] or NULL: the network's own logits along the path */
+    float* model_logits_out;   /* [n][lstride] or NULL: the network's own logits along the path */
 } or_learn;
 
 typedef struct {
@@ -853,7 +857,7 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
                 Ln->rec_n += kept;
             }
         }
-        if (Ln && Ln->ext_logits && nc > 32) {  /* replay supports up to 32 candidates */
+        if (Ln && Ln->ext_logits && nc > Ln->lstride) {  /* more candidates than logits supplied */
             res->log_x = -INFINITY; res->dead_step = t; res->dead_reason = 4; return;
         }
         float* lg_model = NULL;
@@ -872,11 +876,12 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
             }
         }
         if (lg_model && Ln->model_logits_out)
-            for (int q = 0; q < nc && q < 32; ++q) Ln->model_logits_out[(int64_t)t * 32 + q] = lg_model[q];
+            for (int q = 0; q < nc && q < Ln->lstride; ++q)
+                Ln->model_logits_out[(int64_t)t * Ln->lstride + q] = lg_model[q];
         for (int q = 0; q < nc; ++q) {
             double sv;
             if (Ln && Ln->ext_logits) {  /* supplied logits take precedence */
-                const float ex = or_exp_score(Ln->ext_logits[(int64_t)t * 32 + q]);
+                const float ex = or_exp_score(Ln->ext_logits[(int64_t)t * Ln->lstride + q]);
                 sv = P->val ? (double)((float)entry(P, T->cand_e[q]) * ex) : (double)ex;
             } else if (lg_model) {
                 const float ex = or_exp_score(lg_model[q]);
@@ -979,7 +984,7 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
 int or_forced_run(const or_prep* P, const int32_t* forced, int32_t n_forced, uint64_t* w_out,
                   uint64_t* W_out, int32_t* n_cand, double* log_x, int32_t* dead_step,
                   int32_t* chosen /* [n][2] or NULL */, int32_t* counts /* [3] or NULL */,
-                  const float* ext_logits /* [n][32] or NULL */)
+                  const float* ext_logits /* [n][lstride] or NULL */, int32_t lstride)
 {
     or_traj* T = traj_alloc(P);
     or_forced F;
@@ -991,6 +996,7 @@ int or_forced_run(const or_prep* P, const int32_t* forced, int32_t n_forced, uin
     or_learn L;
     memset(&L, 0, sizeof(L));
     L.ext_logits = ext_logits;
+    L.lstride = lstride;
     run_trajectory(T, 0, 0, 0, chosen, NULL, &F, ext_logits ? &L : NULL, &res);
     traj_free(T);
     *W_out = F.W_out;
@@ -1014,9 +1020,10 @@ typedef struct {
     int32_t* dead_step;
     int32_t* chosen;  /* [count][n][2] or NULL */
     int32_t* degv;    /* [count][n] or NULL */
-    const float* ext_logits;  /* [count][n][32] or NULL */
+    const float* ext_logits;  /* [count][n][lstride] or NULL */
+    int32_t lstride;
     const double* model;      /* network parameters or NULL */
-    float* model_logits;      /* [count][n][32] or NULL: the network's logits along the path */
+    float* model_logits;      /* [count][n][lstride] or NULL: the network's logits along the path */
     int64_t counts[3];
 } or_job;
 
@@ -1029,9 +1036,10 @@ static void* job_main(void* arg)
         or_traj_result res;
         or_learn L;
         memset(&L, 0, sizeof(L));
-        if (J->ext_logits) L.ext_logits = J->ext_logits + q * (int64_t)n * 32;
+        L.lstride = J->lstride;
+        if (J->ext_logits) L.ext_logits = J->ext_logits + q * (int64_t)n * J->lstride;
         L.model = J->model;
-        if (J->model_logits) L.model_logits_out = J->model_logits + q * (int64_t)n * 32;
+        if (J->model_logits) L.model_logits_out = J->model_logits + q * (int64_t)n * J->lstride;
         run_trajectory(T, J->seed, J->first + (uint64_t)q, J->matrix,
                        J->chosen ? J->chosen + q * 2 * n : NULL,
                        J->degv ? J->degv + q * n : NULL, NULL,
@@ -1048,13 +1056,13 @@ static void* job_main(void* arg)
 
 void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
                 int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
-                int64_t* op_counts, const float* ext_logits);
+                int64_t* op_counts, const float* ext_logits, int32_t lstride);
 
 void or_run(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
             int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
             int64_t* op_counts /* [3]: DM calls, full SK sweeps, local repairs */)
 {
-    or_run_ext(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, op_counts, NULL);
+    or_run_ext(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, op_counts, NULL, 0);
 }
 
 /* Trajectories lo..hi of one call spread over nthreads host threads: plain,
@@ -1062,7 +1070,8 @@ void or_run(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_tra
  * both (the network's logits then go to model_logits). */
 static void run_jobs(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
                      int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
-                     int64_t* op_counts, const float* ext_logits, const double* model, float* model_logits)
+                     int64_t* op_counts, const float* ext_logits, int32_t lstride, const double* model,
+                     float* model_logits)
 {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > count) nthreads = count > 0 ? (int)count : 1;
@@ -1074,6 +1083,7 @@ static void run_jobs(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t 
         jobs[t].log_x = log_x; jobs[t].dead_step = dead_step; jobs[t].chosen = chosen;
         jobs[t].degv = degv;
         jobs[t].ext_logits = ext_logits;
+        jobs[t].lstride = lstride;
         jobs[t].model = model;
         jobs[t].model_logits = model_logits;
     }
@@ -1090,26 +1100,26 @@ static void run_jobs(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t 
 }
 
 /* or_run with the learned proposal's logits supplied per trajectory and step
- * (ext_logits[count][n][32], candidate q of step t in adjacency order). */
+ * (ext_logits[count][n][lstride], candidate q of step t in adjacency order). */
 void or_run_ext(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
                 int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
-                int64_t* op_counts, const float* ext_logits)
+                int64_t* op_counts, const float* ext_logits, int32_t lstride)
 {
     run_jobs(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, op_counts, ext_logits,
-             NULL, NULL);
+             lstride, NULL, NULL);
 }
 
 /* Paths that follow supplied logits (ext_logits, as or_run_ext) while the
  * network with parameters `model` is evaluated at every step on this side's
- * own features: its logits go to model_logits[count][n][32] (candidate q < 32
- * of step t in adjacency order), so a device network can be compared with
- * this one on exactly the states the device visited. */
+ * own features: its logits go to model_logits[count][n][lstride] (candidate
+ * q < lstride of step t in adjacency order), so a device network can be
+ * compared with this one on exactly the states the device visited. */
 void or_run_ext_model(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
                       int nthreads, double* log_x, int32_t* dead_step, int32_t* chosen, int32_t* degv,
-                      const float* ext_logits, const double* model, float* model_logits)
+                      const float* ext_logits, int32_t lstride, const double* model, float* model_logits)
 {
-    run_jobs(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, NULL, ext_logits, model,
-             model_logits);
+    run_jobs(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, chosen, degv, NULL, ext_logits,
+             lstride, model, model_logits);
 }
 
 /* Trajectories of the learned proposal computed here: features, the FP64
@@ -1119,7 +1129,7 @@ void or_run_ext_model(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t
 void or_run_model(const or_prep* P, uint64_t seed, uint32_t matrix, uint64_t first_traj, int64_t count,
                   int nthreads, double* log_x, int32_t* dead_step, int64_t* op_counts, const double* model)
 {
-    run_jobs(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, NULL, NULL, op_counts, NULL, model,
+    run_jobs(P, seed, matrix, first_traj, count, nthreads, log_x, dead_step, NULL, NULL, op_counts, NULL, 0, model,
              NULL);
 }
 

@@ -47,7 +47,8 @@ class pm_csr(C.Structure):
 class pm_schedule(C.Structure):
     _fields_ = [("vertex_rule", C.c_int32), ("initial_dm", C.c_int32), ("K0", C.c_int32),
                 ("K", C.c_int32), ("sk", C.c_int32), ("dm", C.c_int32), ("precision", C.c_int32),
-                ("reserved", C.c_int32), ("theta", C.c_double), ("learned", C.c_void_p)]
+                ("reserved", C.c_int32), ("theta", C.c_double), ("learned", C.c_void_p),
+                ("rse_target", C.c_double), ("time_budget_s", C.c_double)]
 
 
 class pm_train_cfg(C.Structure):
@@ -87,10 +88,19 @@ class pm_result(C.Structure):
                 ("log_sum_x", C.c_double), ("log_sum_x2", C.c_double), ("n_traj", C.c_uint64),
                 ("n_alive", C.c_uint64), ("n_dm_calls", C.c_uint64), ("n_full_sk", C.c_uint64),
                 ("n_local_sk", C.c_uint64), ("seconds", C.c_double), ("alg_bytes", C.c_uint64),
-                ("kernel_ms", C.c_double), ("mlp_rows", C.c_uint64)]
+                ("kernel_ms", C.c_double), ("mlp_rows", C.c_uint64), ("traj_ns", C.c_uint64), ("rounds", C.c_uint32),
+                ("stop", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "pm_result":
+        r = cls()
+        for f, _ in cls._fields_:
+            if f in d:
+                setattr(r, f, d[f])
+        return r
 
 
 class pm_request_done(C.Structure):
@@ -100,10 +110,13 @@ class pm_request_done(C.Structure):
 
 class pm_call_info(C.Structure):
     _fields_ = [("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64), ("traj_kernel_ms", C.c_double),
-                ("prep_kernel_ms", C.c_double), ("grid", C.c_int32), ("warps_per_cta", C.c_int32)]
+                ("prep_kernel_ms", C.c_double), ("grid", C.c_int32), ("warps_per_cta", C.c_int32),
+                ("first_plan", pm_plan_info)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "first_plan"}
+        d["first_plan"] = self.first_plan.as_dict()
+        return d
 
 
 def _load():
@@ -120,7 +133,15 @@ def _load():
     L.pm_estimate_batch_ex.argtypes = [P, C.POINTER(pm_csr), C.c_int32, P, C.c_uint64, C.c_uint64,
                                        C.POINTER(pm_schedule), C.POINTER(pm_result), P]
     L.pm_trace.argtypes = [P, C.POINTER(pm_csr), C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64,
-                           C.POINTER(pm_schedule), P, P, P, P, P]
+                           C.POINTER(pm_schedule), P, P, P, P, P, C.c_uint32]
+    L.pm_context_cancel.argtypes = [P]
+    L.pm_probe_bandwidth.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.pm_probe_bandwidth.restype = C.c_int
+    L.pm_merge_results.argtypes = [C.POINTER(pm_result), C.c_int32, C.POINTER(pm_result)]
+    L.pm_model_save.argtypes = [P, P, C.c_char_p]
+    L.pm_model_load.argtypes = [P, C.c_char_p, C.POINTER(P)]
+    for name in ("pm_context_cancel", "pm_merge_results", "pm_model_save", "pm_model_load"):
+        getattr(L, name).restype = C.c_int
     L.pm_model_create.argtypes = [P, P, C.c_uint64, C.POINTER(P)]
     L.pm_model_destroy.argtypes = [P]
     L.pm_model_get_params.argtypes = [P, P, P]
@@ -183,7 +204,24 @@ EXPORTED = ["pm_context_create", "pm_context_destroy", "estimate_permanent",
             "pm_model_create", "pm_model_destroy", "pm_model_get_params", "pm_model_set_params",
             "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs",
             "pm_batch_create", "pm_batch_run", "pm_batch_plan_info", "pm_batch_destroy",
-            "pm_server_create", "pm_server_submit", "pm_server_round", "pm_server_clock", "pm_server_destroy"]
+            "pm_server_create", "pm_server_submit", "pm_server_round", "pm_server_clock", "pm_server_destroy",
+            "pm_context_cancel", "pm_merge_results", "pm_model_save", "pm_model_load", "pm_probe_bandwidth"]
+
+STOP_COMPLETE, STOP_TARGET, STOP_TIME, STOP_CANCELLED = 0, 1, 2, 3
+
+
+def merge_results(results: Sequence[dict]) -> dict:
+    """pm_merge_results: merge result dicts of disjoint trajectory sets of
+    one matrix (host arithmetic in the library; no device needed)."""
+    rs = list(results)
+    if not rs:
+        raise ValueError("nothing to merge")
+    arr = (pm_result * len(rs))(*[pm_result.from_dict(r) for r in rs])
+    out = pm_result()
+    st = _lib.pm_merge_results(arr, len(rs), C.byref(out))
+    if st != PM_OK:
+        raise PmError(st, "pm_merge_results")
+    return out.as_dict()
 
 
 @dataclass
@@ -197,11 +235,14 @@ class Schedule:
     precision: int = PREC_FP64
     theta: float = 0.33
     learned: Optional["Model"] = None
+    rse_target: float = 0.0
+    time_budget_s: float = 0.0
 
     def c(self) -> pm_schedule:
         return pm_schedule(self.vertex_rule, self.initial_dm, self.K0, self.K, self.sk, self.dm,
                            self.precision, 0, self.theta,
-                           None if self.learned is None else self.learned.h.value)
+                           None if self.learned is None else self.learned.h.value,
+                           self.rse_target, self.time_budget_s)
 
 
 def preset(name: str, precision: int = PREC_FP32_PROPOSAL) -> Schedule:
@@ -274,14 +315,42 @@ class Context:
             msg = _lib.pm_last_error(self.h).decode() if ctx and self.h else ""
             raise PmError(st, msg)
 
+    def _check_run(self, st: int) -> int:
+        """As _check, but a call that stopped early (time budget, cancel)
+        returns its status: its outputs describe the trajectories that ran."""
+        if st in (PM_ETIMEOUT, PM_ECANCELLED):
+            return st
+        self._check(st)
+        return st
+
+    def probe_bandwidth(self) -> dict:
+        """pm_probe_bandwidth: measured L2 and shared-memory read GB/s."""
+        l2, sm = C.c_double(), C.c_double()
+        self._check(_lib.pm_probe_bandwidth(self.h, C.byref(l2), C.byref(sm)))
+        return {"l2_read_gbs": l2.value, "smem_read_gbs": sm.value}
+
+    def cancel(self):
+        """pm_context_cancel: stop the running call (any thread)."""
+        self._check(_lib.pm_context_cancel(self.h))
+
+    def model_load(self, path: str) -> "Model":
+        """pm_model_load: a model from a file written by Model.save."""
+        m = Model.__new__(Model)
+        m.ctx = self
+        m.h = C.c_void_p()
+        self._check(_lib.pm_model_load(self.h, os.fsencode(path), C.byref(m.h)))
+        return m
+
     # ---- entry points ----
     def estimate_permanent(self, m, n_traj: int, seed: int, schedule: Schedule) -> dict:
         c, keep = make_csr(m)
         out = pm_result()
         s = schedule.c()
-        self._check(_lib.estimate_permanent(self.h, C.byref(c), c.n, n_traj, seed, C.byref(s),
-                                            C.byref(out)))
-        return out.as_dict()
+        st = self._check_run(_lib.estimate_permanent(self.h, C.byref(c), c.n, n_traj, seed, C.byref(s),
+                                                     C.byref(out)))
+        d = out.as_dict()
+        d["status"] = st
+        return d
 
     def estimate_permanent_batch(self, mats: Sequence, n_traj: Sequence[int], seed: int,
                                  schedule: Schedule) -> List[dict]:
@@ -294,9 +363,9 @@ class Context:
         nt = np.ascontiguousarray(n_traj, dtype=np.uint64)
         outs = (pm_result * len(cs))()
         s = schedule.c()
-        self._check(_lib.estimate_permanent_batch(self.h, arr, len(cs), nt.ctypes.data, seed,
-                                                  C.byref(s), outs))
-        return [o.as_dict() for o in outs]
+        st = self._check_run(_lib.estimate_permanent_batch(self.h, arr, len(cs), nt.ctypes.data, seed,
+                                                           C.byref(s), outs))
+        return [dict(o.as_dict(), status=st) for o in outs]
 
     def estimate_batch_ex(self, mats: Sequence, n_traj: Sequence[int], seed: int,
                           schedule: Schedule, first_traj: int = 0, want_log_x: bool = False):
@@ -311,10 +380,10 @@ class Context:
         outs = (pm_result * len(cs))()
         lx = np.zeros(int(nt.sum()), dtype=np.float64) if want_log_x else None
         s = schedule.c()
-        self._check(_lib.pm_estimate_batch_ex(self.h, arr, len(cs), nt.ctypes.data, first_traj, seed,
-                                              C.byref(s), outs,
-                                              None if lx is None else lx.ctypes.data))
-        return [o.as_dict() for o in outs], lx
+        st = self._check_run(_lib.pm_estimate_batch_ex(self.h, arr, len(cs), nt.ctypes.data, first_traj, seed,
+                                                       C.byref(s), outs,
+                                                       None if lx is None else lx.ctypes.data))
+        return [dict(o.as_dict(), status=st) for o in outs], lx
 
     def server(self, schedule: Schedule, seed: int = 1, device_budget_bytes: int = 8 << 30,
                steps_per_round: int = 1 << 20, traj_min: int = 32, traj_max: int = 1 << 16,
@@ -334,19 +403,30 @@ class Context:
         return b
 
     def trace(self, m, count: int, seed: int, schedule: Schedule, first_traj: int = 0,
-              matrix_index: int = 0) -> dict:
+              matrix_index: int = 0, logit_stride: Optional[int] = None) -> dict:
+        """Paths of trajectories first_traj .. first_traj + count - 1
+        (pm_trace).  With the learned proposal, logits[count, n, L] holds the
+        network output of every live candidate of every step; L defaults to
+        the largest row or column length of m, which keeps them all."""
         c, keep = make_csr(m)
         n = c.n
         chosen = np.zeros((count, n, 2), dtype=np.int32)
         degv = np.zeros((count, n), dtype=np.int32)
         dead = np.zeros(count, dtype=np.int32)
         lx = np.zeros(count, dtype=np.float64)
-        lg = np.zeros((count, n, 32), dtype=np.float32) if schedule.learned is not None else None
+        lg = None
+        if schedule.learned is not None:
+            if logit_stride is None:
+                rows = np.diff(np.asarray(m.row_ptr))
+                cols = np.bincount(np.asarray(m.col_idx), minlength=n)
+                logit_stride = int(max(1, rows.max(initial=0), cols.max(initial=0)))
+            lg = np.zeros((count, n, logit_stride), dtype=np.float32)
         s = schedule.c()
         self._check(_lib.pm_trace(self.h, C.byref(c), matrix_index, first_traj, count, seed,
                                   C.byref(s), chosen.ctypes.data, degv.ctypes.data,
                                   dead.ctypes.data, lx.ctypes.data,
-                                  None if lg is None else lg.ctypes.data))
+                                  None if lg is None else lg.ctypes.data,
+                                  0 if lg is None else lg.shape[2]))
         out = dict(chosen=chosen, deg_v=degv, dead_step=dead, log_x=lx)
         if lg is not None:
             out["logits"] = lg
@@ -418,6 +498,10 @@ class Model:
             self.close()
         except Exception:
             pass
+
+    def save(self, path: str):
+        """pm_model_save: write the parameters to a file (Context.model_load reads it)."""
+        self.ctx._check(_lib.pm_model_save(self.ctx.h, self.h, os.fsencode(path)))
 
     def params(self) -> np.ndarray:
         out = np.zeros(N_PARAM, dtype=np.float32)
@@ -491,8 +575,9 @@ class Batch:
         """Returns (results, log_x or None) as Context.estimate_batch_ex."""
         outs = (pm_result * self.count)()
         lx = np.zeros(int(self.n_traj.sum()), dtype=np.float64) if want_log_x else None
-        self.ctx._check(_lib.pm_batch_run(self.h, first_traj, seed, outs, None if lx is None else lx.ctypes.data))
-        return [o.as_dict() for o in outs], lx
+        st = self.ctx._check_run(_lib.pm_batch_run(self.h, first_traj, seed, outs,
+                                                   None if lx is None else lx.ctypes.data))
+        return [dict(o.as_dict(), status=st) for o in outs], lx
 
     def plan(self, k: int) -> dict:
         info = pm_plan_info()

@@ -45,11 +45,15 @@ struct pm_context {
     int sm_count = 0;
     std::string last_error;
     Workspace ws;
+    Workspace ws2;                // the rounds of a call with an RSE target or a time budget
+    int* cancel_host = nullptr;   // cancel flag: pinned host word mapped into the device
+    int* cancel_dev = nullptr;
     std::map<std::string, std::array<int, 5>> tuned;  // autotuned layout policy per size class
     std::vector<pm_batch*> batches;                     // live batches (destroyed with the context)
     double last_traj_ms = 0, last_prep_ms = 0;
     uint64_t last_h2d = 0, last_d2h = 0;
     int last_grid = 0, last_wpc = 0;
+    Plan last_plan{};
 };
 
 namespace {
@@ -123,6 +127,8 @@ pm_status check_schedule(pm_context* ctx, const pm_schedule* s)
     if (s->precision < 0 || s->precision > 1) return fail(ctx, PM_EINVAL, "bad precision");
     if (s->K0 < 0 || s->K < 0 || s->reserved != 0) return fail(ctx, PM_EINVAL, "bad K0/K/reserved");
     if (!(s->theta == s->theta)) return fail(ctx, PM_EINVAL, "theta is NaN");
+    if (!(s->rse_target >= 0 && s->rse_target < INFINITY)) return fail(ctx, PM_EINVAL, "bad rse_target");
+    if (!(s->time_budget_s >= 0 && s->time_budget_s < INFINITY)) return fail(ctx, PM_EINVAL, "bad time_budget_s");
     if (s->learned && (s->sk != 0 || s->precision != 0))
         return fail(ctx, PM_EINVAL, "the learned proposal needs sk = NONE and the FP32 proposal");
     return PM_OK;
@@ -284,6 +290,31 @@ Policy policy_of(const Plan& p)
     return o;
 }
 
+// size class of a matrix for the autotuner: half-octaves of n
+int size_class(int n) { return (int)std::floor(2.0 * std::log2((double)std::max(1, n))); }
+
+std::string class_key(int cls, const Sched& s, bool learned)
+{
+    return std::to_string(cls) + "|" + std::to_string(s.vertex_rule) + std::to_string(s.sk) + std::to_string(s.dm) +
+           std::to_string(s.precision) + std::to_string(s.K) + "|" + (learned ? "L" : "-");
+}
+
+// The layout of a matrix when the caller gives none: the autotuner's choice
+// cached in the context for its size class and schedule, if one fits, else
+// the heuristic.
+Plan default_plan(const pm_context* ctx, int n, int64_t m, int rb, const Sched& s, int smem_max, bool learned)
+{
+    auto it = ctx->tuned.find(class_key(size_class(n), s, learned));
+    if (it != ctx->tuned.end()) {
+        Policy pol;
+        pol.staged = it->second[0]; pol.rc_smem = it->second[1]; pol.gstate = it->second[2];
+        pol.g = it->second[3]; pol.dm_smem = it->second[4];
+        const Plan p = plan_for(n, m, rb, s, smem_max, learned, pol);
+        if (p.groups >= 1) return p;
+    }
+    return make_plan(n, m, rb, s, smem_max, learned);
+}
+
 struct Run {
     // inputs
     const pm_csr* mats = nullptr;
@@ -299,7 +330,8 @@ struct Run {
     pm_result* outs = nullptr;
     int32_t *chosen = nullptr, *deg_v = nullptr, *dead_step = nullptr;
     double* log_x = nullptr;
-    float* logits = nullptr;        // trace: [T][n][32]
+    float* logits = nullptr;        // trace: [T][n][logit_stride]
+    uint32_t logit_stride = 0;
     const void* model = nullptr;    // learned proposal device image
     // recording (device buffers)
     float* rec_feat = nullptr;
@@ -314,6 +346,11 @@ struct Run {
     // matrices already prepared in device memory that outlives the run
     // (host copies of their descriptors; mats then supply n and nnz only)
     const DevMatrix* prepared = nullptr;
+    // per matrix, the local index of its first trajectory (empty: 0)
+    std::vector<uint64_t> first_local;
+    // run control (0: none): device-side time budget of the trajectory launch
+    uint64_t budget_ns = 0;
+    double rse_target = 0, budget_s = 0;
 };
 
 struct MatOff {
@@ -332,7 +369,8 @@ struct Staged {
     std::vector<MatOff> mo;
     size_t o_mats = 0, o_inputs = 0, o_prefix = 0, o_logx = 0, o_counters = 0, o_work = 0, o_status = 0;
     size_t o_parts = 0, o_sout = 0, o_chosen = 0, o_degv = 0, o_dead = 0, o_logits = 0;
-    size_t o_plans = 0, o_chunks = 0, o_cctr = 0, layout_end = 0, chunk_cap = 0;
+    size_t o_plans = 0, o_chunks = 0, o_cctr = 0, o_tstart = 0, layout_end = 0, chunk_cap = 0;
+    uint32_t stop_bits = 0;       // ST_TIMEOUT / ST_CANCELLED seen by collect()
     int chunks_stats = 1;
     std::vector<Plan> plans;
     std::vector<Chunk> chunks;
@@ -400,7 +438,7 @@ pm_status stage_inputs(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, 
     S.o_inputs = L.take(sizeof(DevInput) * count);
     S.o_prefix = L.take(8 * (count + 1));
     S.o_logx = L.take(8 * std::max<uint64_t>(S.total, 1));
-    S.o_counters = L.take(8 * 5 * count);
+    S.o_counters = L.take(8 * kCounters * count);
     S.o_work = L.take(8);
     S.o_status = L.take(4);
     uint64_t max_t = 1;
@@ -412,13 +450,14 @@ pm_status stage_inputs(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, 
         S.o_chosen = L.take(4 * S.total * 2 * (size_t)S.n_max);
         S.o_degv = L.take(4 * S.total * (size_t)S.n_max);
         S.o_dead = L.take(4 * std::max<uint64_t>(S.total, 1));
-        if (R.model) S.o_logits = L.take(4 * S.total * (size_t)S.n_max * 32);
+        if (R.model && R.logit_stride) S.o_logits = L.take(4 * S.total * (size_t)S.n_max * R.logit_stride);
     }
     // the plans and the chunk list (at most one chunk per trajectory)
     S.chunk_cap = std::max<size_t>(S.total + count, min_chunks);
     S.o_plans = L.take(sizeof(Plan) * count);
     S.o_chunks = L.take(sizeof(Chunk) * S.chunk_cap);
     S.o_cctr = L.take(8);
+    S.o_tstart = L.take(8);
     S.layout_end = L.off;
     pm_status st = grow(ctx, &ws.arena, &ws.arena_cap, L.off);
     if (st != PM_OK) return st;
@@ -472,13 +511,13 @@ pm_status stage_inputs(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, 
     S.h2d += sizeof(DevMatrix) * count + sizeof(DevInput) * count + 8 * (count + 1);
 
     // pinned read-back area
-    const size_t pin_need = sizeof(StatsOut) * count + 8 * 5 * count + 8 + sizeof(DevMatrix) * count + 128;
+    const size_t pin_need = sizeof(StatsOut) * count + 8 * kCounters * count + 8 + sizeof(DevMatrix) * count + 128;
     st = grow_pinned(ctx, ws, pin_need);
     if (st != PM_OK) return st;
     S.h_sout = (StatsOut*)ws.pinned;
     S.h_cnt = (unsigned long long*)(S.h_sout + count);
-    S.h_status = (uint32_t*)(S.h_cnt + 5 * count);
-    S.h_mats = (DevMatrix*)(ws.pinned + align_up(sizeof(StatsOut) * count + 8 * 5 * count + 8, 64));
+    S.h_status = (uint32_t*)(S.h_cnt + kCounters * count);
+    S.h_mats = (DevMatrix*)(ws.pinned + align_up(sizeof(StatsOut) * count + 8 * kCounters * count + 8, 64));
     if (!ws.ev0) {
         PM_CUDA(cudaEventCreate(&ws.ev0));
         PM_CUDA(cudaEventCreate(&ws.ev1));
@@ -504,8 +543,8 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
     S.plans.assign(count, Plan{});
     S.smem_need = kCtaMiscBytes;
     for (int k = 0; k < count; ++k) {
-        S.plans[k] = given ? (*given)[k] : make_plan(R.mats[k].n, R.mats[k].nnz, (int)S.rb, R.s, smem_max,
-                                                      R.model != nullptr);
+        S.plans[k] = given ? (*given)[k] : default_plan(ctx, R.mats[k].n, R.mats[k].nnz, (int)S.rb, R.s, smem_max,
+                                                         R.model != nullptr);
         if (S.plans[k].groups < 1)
             return fail(ctx, PM_EUNSUPPORTED, "trajectory state does not fit in shared memory");
         S.smem_need = std::max(S.smem_need, kCtaMiscBytes + learned_smem(R.model != nullptr) + S.plans[k].mat_bytes +
@@ -529,10 +568,12 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
     S.chunks.clear();
     for (int k : order) {
         const uint64_t csz = (uint64_t)S.plans[k].groups * 2;
+        const uint64_t base = R.first_local.empty() ? 0 : R.first_local[k];
         for (uint64_t f = 0; f < R.ntraj[k]; f += csz) {
             Chunk c;
             c.k = k;
-            c.first = f;
+            c.first = base + f;
+            c.slot0 = S.prefix[k] + f;
             c.count = (uint32_t)std::min<uint64_t>(csz, R.ntraj[k] - f);
             S.chunks.push_back(c);
         }
@@ -568,8 +609,14 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
         tp.chosen = (int32_t*)P(S.o_chosen);
         tp.deg_v = (int32_t*)P(S.o_degv);
         tp.dead_step = (int32_t*)P(S.o_dead);
-        if (R.model) tp.trace_logits = (float*)P(S.o_logits);
+        if (R.model && R.logit_stride) {
+            tp.trace_logits = (float*)P(S.o_logits);
+            tp.logit_stride = (int)R.logit_stride;
+        }
     }
+    tp.budget_ns = R.budget_ns;
+    tp.t_start = (unsigned long long*)P(S.o_tstart);
+    tp.cancel = ctx->cancel_dev;
     tp.model = R.model;
     tp.rec_feat = R.rec_feat;
     tp.rec_target = R.rec_target;
@@ -587,7 +634,7 @@ pm_status enqueue_prep(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
 {
     uint8_t* A = ws.arena;
     auto P = [&](size_t off) { return (void*)(A + off); };
-    PM_CUDA(cudaMemsetAsync(P(S.o_counters), 0, 8 * 5 * R.count, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(P(S.o_counters), 0, 8 * kCounters * R.count, ctx->stream));
     PM_CUDA(cudaMemsetAsync(P(S.o_work), 0, 8, ctx->stream));
     PM_CUDA(cudaMemsetAsync(P(S.o_status), 0, 4, ctx->stream));
     if (!R.prepared)
@@ -600,8 +647,12 @@ pm_status enqueue_traj(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
 {
     if (!S.launch_traj) return PM_OK;
     PM_CUDA(cudaMemsetAsync(ws.arena + S.o_cctr, 0, 8, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(ws.arena + S.o_tstart, 0, 8, ctx->stream));
+    // ln X = NaN (all bits set) marks trajectories a stopped launch never started
+    PM_CUDA(cudaMemsetAsync(ws.arena + S.o_logx, 0xFF, 8 * S.total, ctx->stream));
     if (S.tp.trace_logits)
-        PM_CUDA(cudaMemsetAsync(S.tp.trace_logits, 0, 4 * S.total * (size_t)S.n_max * 32, ctx->stream));
+        PM_CUDA(cudaMemsetAsync(S.tp.trace_logits, 0, 4 * S.total * (size_t)S.n_max * R.logit_stride,
+                                ctx->stream));
     PM_CUDA(launch_trajectories(S.tp, S.grid, S.smem_need, R.trace, ctx->stream));
     return PM_OK;
 }
@@ -615,7 +666,7 @@ pm_status enqueue_tail(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
         PM_CUDA(launch_stats((const double*)P(S.o_logx), S.prefix.data(), (const uint64_t*)P(S.o_prefix), count,
                              (StatsPartial*)P(S.o_parts), S.chunks_stats, (StatsOut*)P(S.o_sout), ctx->stream));
         PM_CUDA(cudaMemcpyAsync(S.h_sout, P(S.o_sout), sizeof(StatsOut) * count, cudaMemcpyDeviceToHost, ctx->stream));
-        PM_CUDA(cudaMemcpyAsync(S.h_cnt, P(S.o_counters), 8 * 5 * count, cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(cudaMemcpyAsync(S.h_cnt, P(S.o_counters), 8 * kCounters * count, cudaMemcpyDeviceToHost, ctx->stream));
     }
     PM_CUDA(cudaMemcpyAsync(S.h_status, P(S.o_status), 4, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaMemcpyAsync(S.h_mats, P(S.o_mats), sizeof(DevMatrix) * count, cudaMemcpyDeviceToHost, ctx->stream));
@@ -642,7 +693,7 @@ pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, doubl
     uint8_t* A = ws.arena;
     auto P = [&](size_t off) { return (void*)(A + off); };
     uint64_t d2h = 4 + sizeof(DevMatrix) * count;
-    if (S.launch_traj) d2h += sizeof(StatsOut) * count + 8 * 5 * count;
+    if (S.launch_traj) d2h += sizeof(StatsOut) * count + 8 * kCounters * count;
     {
         float ms = 0;
         ctx->last_prep_ms = (cudaEventElapsedTime(&ms, ws.ev2, ws.ev0) == cudaSuccess) ? ms : -1.0;
@@ -652,7 +703,9 @@ pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, doubl
     }
     ctx->last_grid = S.launch_traj ? S.grid : 0;
     ctx->last_wpc = S.launch_traj ? kCtaWarps : 0;
-    const uint32_t status = *S.h_status;
+    ctx->last_plan = (S.launch_traj && !S.plans.empty()) ? S.plans[0] : Plan{};
+    const uint32_t status = *S.h_status & ~kStatusStopBits;
+    S.stop_bits = *S.h_status & kStatusStopBits;
     if (status & ST_BAD_INPUT) return fail(ctx, PM_EINVAL, "malformed CSR (device validation)");
     if (status & ST_CAPACITY) return fail(ctx, PM_EUNSUPPORTED, "a row or column holds more than 65534 entries");
     if (status) return fail(ctx, PM_EDEVICE, "device status " + std::to_string(status));
@@ -662,7 +715,8 @@ pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, doubl
         if (R.chosen) PM_CUDA(cudaMemcpy(R.chosen, P(S.o_chosen), 4 * T * 2 * n, cudaMemcpyDeviceToHost));
         if (R.deg_v) PM_CUDA(cudaMemcpy(R.deg_v, P(S.o_degv), 4 * T * n, cudaMemcpyDeviceToHost));
         if (R.dead_step) PM_CUDA(cudaMemcpy(R.dead_step, P(S.o_dead), 4 * T, cudaMemcpyDeviceToHost));
-        if (R.logits && R.model) PM_CUDA(cudaMemcpy(R.logits, P(S.o_logits), 4 * T * n * 32, cudaMemcpyDeviceToHost));
+        if (R.logits && R.model && R.logit_stride)
+            PM_CUDA(cudaMemcpy(R.logits, P(S.o_logits), 4 * T * n * R.logit_stride, cudaMemcpyDeviceToHost));
     }
     if (R.log_x && S.total) {
         PM_CUDA(cudaMemcpy(R.log_x, P(S.o_logx), 8 * S.total, cudaMemcpyDeviceToHost));
@@ -703,15 +757,27 @@ pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, doubl
             o.log_sum_x2 = so.log_sum_x2;
             o.n_traj = so.n;
             o.n_alive = so.alive;
-            o.n_dm_calls = S.h_cnt[5 * k + 0];
-            o.n_full_sk = S.h_cnt[5 * k + 1];
-            o.n_local_sk = S.h_cnt[5 * k + 2];
-            o.alg_bytes = S.h_cnt[5 * k + 3];
-            o.mlp_rows = S.h_cnt[5 * k + 4];
+            o.n_dm_calls = S.h_cnt[kCounters * k + 0];
+            o.n_full_sk = S.h_cnt[kCounters * k + 1];
+            o.n_local_sk = S.h_cnt[kCounters * k + 2];
+            o.alg_bytes = S.h_cnt[kCounters * k + 3];
+            o.mlp_rows = S.h_cnt[kCounters * k + 4];
+            o.traj_ns = S.h_cnt[kCounters * k + 5];
             o.kernel_ms = ctx->last_traj_ms;
             o.seconds = secs;
+            o.rounds = 1;
+            o.stop = (S.stop_bits & ST_CANCELLED) ? PM_STOP_CANCELLED
+                     : (S.stop_bits & ST_TIMEOUT) ? PM_STOP_TIME : PM_STOP_COMPLETE;
         }
     }
+    return PM_OK;
+}
+
+// status of a call whose launch may have stopped early: outputs are written
+pm_status stop_status(pm_context* ctx, uint32_t stop_bits)
+{
+    if (stop_bits & ST_CANCELLED) return fail(ctx, PM_ECANCELLED, "cancelled (pm_context_cancel)");
+    if (stop_bits & ST_TIMEOUT) return fail(ctx, PM_ETIMEOUT, "the time budget ran out");
     return PM_OK;
 }
 
@@ -730,10 +796,226 @@ pm_status execute(pm_context* ctx, Run& R)
     if (st != PM_OK) return st;
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return collect(ctx, ctx->ws, R, S, secs);
+    st = collect(ctx, ctx->ws, R, S, secs);
+    if (st != PM_OK) return st;
+    return stop_status(ctx, S.stop_bits);
 }
 
 }  // namespace
+
+// Sufficient statistics of disjoint trajectory sets of one matrix (Sec. 2:
+// the estimate, ESS and p_match; Sec. 4 "Metrics": relative spread and RSE
+// all follow from M, #alive, ln sum X and ln sum X^2), plus the operation
+// counts; merged exactly in any order.
+struct Suff {
+    uint64_t n = 0, alive = 0, n_dm = 0, n_full = 0, n_loc = 0, alg = 0, mlp = 0, traj_ns = 0;
+    double lse1 = -INFINITY, lse2 = -INFINITY, kernel_ms = 0, seconds = 0;
+    uint32_t rounds = 0;
+    static double lse_add(double a, double b)
+    {
+        if (a == -INFINITY) return b;
+        if (b == -INFINITY) return a;
+        const double m = a > b ? a : b;
+        return m + std::log(std::exp(a - m) + std::exp(b - m));
+    }
+    void add(const pm_result& o)
+    {
+        n += o.n_traj;
+        alive += o.n_alive;
+        if (o.n_alive) {
+            lse1 = lse_add(lse1, o.log_sum_x);
+            lse2 = lse_add(lse2, o.log_sum_x2);
+        }
+        n_dm += o.n_dm_calls;
+        n_full += o.n_full_sk;
+        n_loc += o.n_local_sk;
+        alg += o.alg_bytes;
+        mlp += o.mlp_rows;
+        traj_ns += o.traj_ns;
+        kernel_ms += o.kernel_ms > 0 ? o.kernel_ms : 0;
+        seconds += o.seconds > 0 ? o.seconds : 0;
+        rounds += o.rounds;
+    }
+    void fill(pm_result& o) const
+    {
+        std::memset(&o, 0, sizeof(o));
+        o.n_traj = n;
+        o.n_alive = alive;
+        o.log_sum_x = lse1;
+        o.log_sum_x2 = lse2;
+        o.n_dm_calls = n_dm;
+        o.n_full_sk = n_full;
+        o.n_local_sk = n_loc;
+        o.alg_bytes = alg;
+        o.mlp_rows = mlp;
+        o.traj_ns = traj_ns;
+        o.kernel_ms = kernel_ms;
+        o.seconds = seconds;
+        o.rounds = rounds;
+        o.p_match = n ? (double)alive / (double)n : 0.0;
+        if (n == 0 || lse1 == -INFINITY) {
+            o.log_estimate = -INFINITY;
+            o.rel_spread = o.rse = NAN;
+            return;
+        }
+        const double M = (double)n;
+        o.log_estimate = lse1 - std::log(M);
+        o.estimate = std::exp(o.log_estimate);
+        o.ess = std::exp(2 * lse1 - lse2);
+        if (n > 1) {  // s_X^2 / mean^2 = (M sum X^2 / (sum X)^2 - 1) M / (M - 1)
+            const double ratio = M * std::exp(lse2 - 2 * lse1);
+            o.rel_spread = std::sqrt(std::max(0.0, ratio - 1.0) * M / (M - 1.0));
+            o.rse = o.rel_spread / std::sqrt(M);
+        } else {
+            o.rel_spread = o.rse = NAN;
+        }
+    }
+};
+
+namespace {
+
+// Trajectories a matrix must have before its RSE may end its run.
+constexpr uint64_t kMinTrajForTarget = 1024;
+
+// A call with an RSE target or a time budget: preprocessing once, then rounds
+// of trajectories over the matrices still running (consecutive trajectory
+// ids per matrix, so the rounds together are the trajectories one launch
+// would run), statistics merged on the host after each round.  A matrix stops
+// when its RSE (Sec. 4 "Metrics") is at most the target with at least
+// kMinTrajForTarget trajectories (or all of n_traj) and two alive, or when its
+// n_traj ran; the call stops when every matrix has stopped, the budget is
+// spent (PM_ETIMEOUT) or the context is cancelled (PM_ECANCELLED).
+pm_status execute_rounds(pm_context* ctx, Run& R)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    auto elapsed = [&] { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+    PM_CUDA(cudaSetDevice(ctx->device));
+    const int count = R.count;
+    // preprocessing (InitialDM, outer SK, degrees, tree) into the context's workspace
+    Run Pr;
+    Pr.mats = R.mats;
+    Pr.count = count;
+    Pr.ntraj.assign(count, 0);
+    Pr.matrix_index0 = R.matrix_index0;
+    Pr.s = R.s;
+    Pr.prep_only = true;
+    Pr.model = R.model;
+    Staged SP;
+    pm_status st = stage_inputs(ctx, ctx->ws, Pr, SP);
+    if (st == PM_OK) st = stage_plans(ctx, ctx->ws, Pr, SP, nullptr);
+    if (st == PM_OK) st = enqueue(ctx, ctx->ws, Pr, SP);
+    if (st != PM_OK) return st;
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    st = collect(ctx, ctx->ws, Pr, SP, 0.0);
+    if (st != PM_OK) return st;
+    const double prep_ms = ctx->last_prep_ms;
+    uint64_t h2d = ctx->last_h2d, d2h = ctx->last_d2h;
+    std::vector<DevMatrix> dms(SP.h_mats, SP.h_mats + count);
+    // rounds
+    std::vector<uint64_t> req_prefix(count + 1, 0);
+    for (int k = 0; k < count; ++k) req_prefix[k + 1] = req_prefix[k] + R.ntraj[k];
+    if (R.log_x)
+        for (uint64_t i = 0; i < req_prefix[count]; ++i) R.log_x[i] = NAN;
+    std::vector<Suff> acc(count);
+    std::vector<uint64_t> done(count, 0), size(count, 0);
+    std::vector<int32_t> stop(count, -1);
+    const uint64_t slots = (uint64_t)ctx->sm_count * kCtaWarps;
+    for (int k = 0; k < count; ++k) {
+        if (R.ntraj[k] == 0) stop[k] = PM_STOP_COMPLETE;
+        size[k] = R.rse_target > 0 ? std::max<uint64_t>(kMinTrajForTarget, 2 * slots / (uint64_t)count) : R.ntraj[k];
+    }
+    uint32_t stop_bits = 0;
+    double traj_ms = 0;
+    std::vector<double> lx;
+    for (;;) {
+        int running = 0;
+        for (int k = 0; k < count; ++k) running += stop[k] < 0;
+        if (!running) break;
+        Run Q;
+        Q.mats = R.mats;
+        Q.count = count;
+        Q.prepared = dms.data();
+        Q.s = R.s;
+        Q.seed = R.seed;
+        Q.first_traj = R.first_traj;
+        Q.model = R.model;
+        Q.first_local = done;
+        Q.ntraj.assign(count, 0);
+        for (int k = 0; k < count; ++k)
+            if (stop[k] < 0) Q.ntraj[k] = std::min(size[k], R.ntraj[k] - done[k]);
+        if (R.budget_s > 0) {
+            const double rem = R.budget_s - elapsed();
+            if (rem <= 0) { stop_bits |= ST_TIMEOUT; break; }
+            Q.budget_ns = (uint64_t)std::max(1.0, rem * 1e9);
+        }
+        std::vector<pm_result> outs(count);
+        Q.outs = outs.data();
+        uint64_t tot = 0;
+        for (int k = 0; k < count; ++k) tot += Q.ntraj[k];
+        if (R.log_x) {
+            lx.assign(tot, 0.0);
+            Q.log_x = lx.data();
+        }
+        Staged S;
+        st = stage_inputs(ctx, ctx->ws2, Q, S);
+        if (st == PM_OK) st = stage_plans(ctx, ctx->ws2, Q, S, nullptr);
+        if (st == PM_OK) st = enqueue(ctx, ctx->ws2, Q, S);
+        if (st != PM_OK) return st;
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+        st = collect(ctx, ctx->ws2, Q, S, 0.0);
+        if (st != PM_OK) return st;
+        traj_ms += ctx->last_traj_ms > 0 ? ctx->last_traj_ms : 0;
+        h2d += ctx->last_h2d;
+        d2h += ctx->last_d2h;
+        stop_bits |= S.stop_bits;
+        uint64_t off = 0;
+        for (int k = 0; k < count; ++k) {
+            if (!Q.ntraj[k]) continue;
+            outs[k].kernel_ms = 0;  // a launch's time is shared by its matrices: reported once below
+            acc[k].add(outs[k]);
+            if (R.log_x)
+                std::copy(lx.begin() + off, lx.begin() + off + Q.ntraj[k], R.log_x + req_prefix[k] + done[k]);
+            off += Q.ntraj[k];
+            done[k] += Q.ntraj[k];  // ids consumed (a stopped launch leaves some unstarted)
+            const bool ran_all = outs[k].n_traj == Q.ntraj[k];
+            pm_result cur;
+            acc[k].fill(cur);
+            const bool met = R.rse_target > 0 && cur.n_traj >= std::min(kMinTrajForTarget, R.ntraj[k]) &&
+                             cur.n_alive >= 2 && cur.rse <= R.rse_target;
+            if (met) {
+                stop[k] = PM_STOP_TARGET;
+            } else if (!ran_all) {
+                stop[k] = (S.stop_bits & ST_CANCELLED) ? PM_STOP_CANCELLED : PM_STOP_TIME;
+            } else if (done[k] >= R.ntraj[k]) {
+                stop[k] = PM_STOP_COMPLETE;
+            } else if (R.rse_target > 0) {  // next round: toward the trajectories the target needs
+                const double M = (double)cur.n_traj;
+                double need = (cur.rse == cur.rse && cur.n_alive >= 2)
+                                  ? 1.1 * M * (cur.rse / R.rse_target) * (cur.rse / R.rse_target)
+                                  : 4.0 * M;
+                need = std::min(need, 5.0 * (double)done[k]);
+                size[k] = std::max<uint64_t>(size[k], (uint64_t)std::max(0.0, need - (double)done[k]));
+            }
+        }
+        if (stop_bits) break;
+    }
+    const double secs = elapsed();
+    ctx->last_traj_ms = traj_ms;
+    ctx->last_prep_ms = prep_ms;
+    ctx->last_h2d = h2d;
+    ctx->last_d2h = d2h;
+    for (int k = 0; k < count; ++k) {
+        pm_result& o = R.outs[k];
+        acc[k].fill(o);
+        o.kernel_ms = traj_ms;
+        o.seconds = secs;
+        o.stop = stop[k] >= 0 ? stop[k] : (stop_bits & ST_CANCELLED) ? PM_STOP_CANCELLED : PM_STOP_TIME;
+    }
+    return stop_status(ctx, stop_bits);
+}
+
+}  // namespace
+
 
 extern "C" {
 
@@ -754,11 +1036,25 @@ pm_status pm_context_create(pm_context** out, int device, void* cuda_stream)
             ctx->own_stream = (e == cudaSuccess);
         }
     }
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&ctx->cancel_host, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *(volatile int*)ctx->cancel_host = 0;
+        e = cudaHostGetDevicePointer((void**)&ctx->cancel_dev, ctx->cancel_host, 0);
+    }
     if (e != cudaSuccess) {
+        if (ctx->cancel_host) cudaFreeHost(ctx->cancel_host);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
         return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
     }
     *out = ctx;
+    return PM_OK;
+}
+
+pm_status pm_context_cancel(pm_context* ctx)
+{
+    if (!ctx || !ctx->cancel_host) return PM_EINVAL;
+    __atomic_store_n(ctx->cancel_host, 1, __ATOMIC_SEQ_CST);
     return PM_OK;
 }
 
@@ -772,6 +1068,8 @@ pm_status pm_context_destroy(pm_context* ctx)
     for (pm_batch* b : ctx->batches) batch_delete(b);
     ctx->batches.clear();
     ctx->ws.release();
+    ctx->ws2.release();
+    if (ctx->cancel_host) cudaFreeHost(ctx->cancel_host);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return PM_OK;
@@ -809,6 +1107,10 @@ pm_status pm_estimate_batch_ex(pm_context* ctx, const pm_csr* mats, int32_t coun
     R.outs = outs;
     R.log_x = log_x;
     R.model = schedule->learned ? schedule->learned->img : nullptr;
+    R.rse_target = schedule->rse_target;
+    R.budget_s = schedule->time_budget_s;
+    if (ctx->cancel_host) *(volatile int*)ctx->cancel_host = 0;
+    if (R.rse_target > 0 || R.budget_s > 0) return execute_rounds(ctx, R);
     return execute(ctx, R);
 }
 
@@ -828,7 +1130,7 @@ pm_status estimate_permanent(pm_context* ctx, const pm_csr* csr, int32_t n, uint
 
 pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index, uint64_t first_traj, uint32_t count,
                    uint64_t seed, const pm_schedule* schedule, int32_t* chosen, int32_t* deg_v, int32_t* dead_step,
-                   double* log_x, float* logits)
+                   double* log_x, float* logits, uint32_t logit_stride)
 {
     if (!ctx) return PM_EINVAL;
     pm_status st = check_schedule(ctx, schedule);
@@ -837,6 +1139,8 @@ pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index, ui
     if (st != PM_OK) return st;
     if (count < 1 || matrix_index > 0xFFFF || first_traj + count > ((uint64_t)1 << 48))
         return fail(ctx, PM_EINVAL, "bad trace range");
+    if (logits && (logit_stride < 1 || logit_stride > (uint32_t)kMaxDegree + 1))
+        return fail(ctx, PM_EINVAL, "logit_stride must be in 1 .. 65535 when logits is given");
     Run R;
     R.mats = csr;
     R.count = 1;
@@ -851,6 +1155,7 @@ pm_status pm_trace(pm_context* ctx, const pm_csr* csr, uint32_t matrix_index, ui
     R.dead_step = dead_step;
     R.log_x = log_x;
     R.logits = logits;
+    R.logit_stride = logits ? logit_stride : 0;
     R.model = schedule->learned ? schedule->learned->img : nullptr;
     return execute(ctx, R);
 }
@@ -889,6 +1194,47 @@ pm_status pm_philox_blocks(pm_context* ctx, const uint32_t ctr[4], const uint32_
     return PM_OK;
 }
 
+pm_status pm_probe_bandwidth(pm_context* ctx, double* l2_read_gbs, double* smem_read_gbs)
+{
+    if (!ctx || !l2_read_gbs || !smem_read_gbs) return PM_EINVAL;
+    PM_CUDA(cudaSetDevice(ctx->device));
+    const size_t bytes = (size_t)64 << 20;  // half of the 126 MB L2
+    const int iters = 200;
+    DevBuf buf, sink;
+    PM_CUDA(cudaMalloc(&buf.p, bytes));
+    PM_CUDA(cudaMalloc(&sink.p, 8));
+    PM_CUDA(cudaMemsetAsync(buf.p, 1, bytes, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(sink.p, 0, 8, ctx->stream));
+    cudaEvent_t e0, e1;
+    PM_CUDA(cudaEventCreate(&e0));
+    PM_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](auto&& launch) -> double {
+        if (launch() != cudaSuccess) return -1.0;  // warm-up (fills L2)
+        cudaEventRecord(e0, ctx->stream);
+        if (launch() != cudaSuccess) return -1.0;
+        cudaEventRecord(e1, ctx->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    const int grid = ctx->sm_count * 4;
+    const double l2_ms = timed([&] {
+        return launch_l2_probe(buf.p, bytes, iters, grid, (unsigned long long*)sink.p, ctx->stream);
+    });
+    const int sm_bytes = 96 << 10, sm_iters = 2000;
+    const double sm_ms = timed([&] {
+        return launch_smem_probe(sm_bytes, sm_iters, ctx->sm_count * 2, (unsigned long long*)sink.p, ctx->stream);
+    });
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    PM_CUDA(cudaGetLastError());
+    if (l2_ms <= 0 || sm_ms <= 0) return fail(ctx, PM_ECUDA, "bandwidth probe failed");
+    *l2_read_gbs = (double)bytes * iters / (l2_ms * 1e-3) / 1e9;
+    *smem_read_gbs = (double)sm_bytes * sm_iters * ctx->sm_count * 2 / (sm_ms * 1e-3) / 1e9;
+    return PM_OK;
+}
+
 pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info)
 {
     if (!ctx || !info) return PM_EINVAL;
@@ -898,6 +1244,11 @@ pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info)
     info->prep_kernel_ms = ctx->last_prep_ms;
     info->grid = ctx->last_grid;
     info->warps_per_cta = ctx->last_wpc;
+    std::memset(&info->first_plan, 0, sizeof(info->first_plan));
+    const Plan& p = ctx->last_plan;
+    info->first_plan.g = p.g; info->first_plan.groups = p.groups; info->first_plan.staged = p.staged;
+    info->first_plan.rc_smem = p.rc_smem; info->first_plan.gstate = p.gstate; info->first_plan.dm_smem = p.dm_smem;
+    info->first_plan.probe_traj_per_s = info->first_plan.heuristic_traj_per_s = -1.0;
     return PM_OK;
 }
 
@@ -954,15 +1305,6 @@ static void batch_delete(pm_batch* b) { delete b; }
 
 namespace {
 
-// size class of a matrix for the autotuner: half-octaves of n
-int size_class(int n) { return (int)std::floor(2.0 * std::log2((double)std::max(1, n))); }
-
-std::string class_key(int cls, const Sched& s, bool learned)
-{
-    return std::to_string(cls) + "|" + std::to_string(s.vertex_rule) + std::to_string(s.sk) + std::to_string(s.dm) +
-           std::to_string(s.precision) + std::to_string(s.K) + "|" + (learned ? "L" : "-");
-}
-
 // Trajectories per second of matrix k under `plan`: a probe launch on up to
 // 32 SMs, two trajectories per group, ids far from any run's range.
 pm_status probe_plan(pm_context* ctx, pm_batch* b, int k, const Plan& plan, double* rate)
@@ -980,7 +1322,7 @@ pm_status probe_plan(pm_context* ctx, pm_batch* b, int k, const Plan& plan, doub
     // probe buffers: plans, chunks, zero prefix, ln X, counters, chunk counter, slots
     Layout L;
     const size_t o_pl = L.take(sizeof(Plan) * count), o_ch = L.take(sizeof(Chunk) * pgrid),
-                 o_pf = L.take(8 * (count + 1)), o_lx = L.take(8 * ntr), o_ct = L.take(8 * 5 * count),
+                 o_pf = L.take(8 * (count + 1)), o_lx = L.take(8 * ntr), o_ct = L.take(8 * kCounters * count),
                  o_cc = L.take(8), o_sl = L.take(sl.bytes * (size_t)pgrid * kCtaWarps);
     DevBuf buf;
     PM_CUDA(cudaMalloc(&buf.p, L.off));
@@ -992,11 +1334,12 @@ pm_status probe_plan(pm_context* ctx, pm_batch* b, int k, const Plan& plan, doub
         chunks[c].k = k;
         chunks[c].count = per_chunk;
         chunks[c].first = (uint64_t)c * per_chunk;
+        chunks[c].slot0 = (uint64_t)c * per_chunk;
     }
     PM_CUDA(cudaMemcpyAsync(B + o_pl, plans.data(), sizeof(Plan) * count, cudaMemcpyHostToDevice, ctx->stream));
     PM_CUDA(cudaMemcpyAsync(B + o_ch, chunks.data(), sizeof(Chunk) * pgrid, cudaMemcpyHostToDevice, ctx->stream));
     PM_CUDA(cudaMemsetAsync(B + o_pf, 0, 8 * (count + 1), ctx->stream));
-    PM_CUDA(cudaMemsetAsync(B + o_ct, 0, 8 * 5 * count, ctx->stream));
+    PM_CUDA(cudaMemsetAsync(B + o_ct, 0, 8 * kCounters * count, ctx->stream));
     PM_CUDA(cudaMemsetAsync(B + o_cc, 0, 8, ctx->stream));
     TrajParams tp = S.tp;
     tp.plans = (const Plan*)(B + o_pl);
@@ -1010,6 +1353,8 @@ pm_status probe_plan(pm_context* ctx, pm_batch* b, int k, const Plan& plan, doub
     tp.chunk_counter = (int*)(B + o_cc);
     tp.slots = B + o_sl;
     tp.slot = sl;
+    tp.budget_ns = 0;
+    tp.cancel = nullptr;
     const int smem = kCtaMiscBytes + learned_smem(R.model != nullptr) + plan.mat_bytes + plan.groups * plan.state_bytes;
     PM_CUDA(cudaEventRecord(b->ws.ev0, ctx->stream));
     PM_CUDA(launch_trajectories(tp, pgrid, smem, false, ctx->stream));
@@ -1104,6 +1449,7 @@ pm_status pm_batch_create(pm_context* ctx, const pm_csr* mats, int32_t count, co
     *out = nullptr;
     pm_status st = check_schedule(ctx, schedule);
     if (st != PM_OK) return st;
+    if (schedule->rse_target != 0) return fail(ctx, PM_EINVAL, "a resident batch runs fixed trajectory counts: rse_target must be 0");
     for (int k = 0; k < count; ++k) {
         st = check_csr(ctx, &mats[k]);
         if (st != PM_OK) return st;
@@ -1145,6 +1491,7 @@ pm_status pm_batch_create(pm_context* ctx, const pm_csr* mats, int32_t count, co
     R.ntraj.assign(n_traj, n_traj + count);
     R.s = to_sched(schedule);
     R.model = schedule->learned ? schedule->learned->img : nullptr;
+    R.budget_ns = (uint64_t)(schedule->time_budget_s * 1e9);
     b->info.assign(count, pm_plan_info{});
     st = stage_inputs(ctx, b->ws, R, b->S, (size_t)ctx->sm_count + count);
     if (st != PM_OK) return bail(st);
@@ -1221,6 +1568,7 @@ pm_status pm_batch_run(pm_batch* b, uint64_t first_traj, uint64_t seed, pm_resul
     R.log_x = log_x;
     b->S.tp.first_traj = first_traj;
     b->S.tp.seed = seed;
+    if (ctx->cancel_host) *(volatile int*)ctx->cancel_host = 0;
     if (b->exec[0]) {
         if (b->traj_node) {
             void* args[] = {&b->S.tp};
@@ -1245,7 +1593,8 @@ pm_status pm_batch_run(pm_batch* b, uint64_t first_traj, uint64_t seed, pm_resul
     pm_status st = collect(ctx, b->ws, R, b->S, secs);
     R.outs = nullptr;
     R.log_x = nullptr;
-    return st;
+    if (st != PM_OK) return st;
+    return stop_status(ctx, b->S.stop_bits);
 }
 
 pm_status pm_batch_plan_info(const pm_batch* b, int32_t k, pm_plan_info* info)
@@ -1289,9 +1638,7 @@ struct Request {
     DevMatrix dm{};               // prepared descriptor (device pointers into ws)
     size_t bytes = 0;             // device bytes held
     bool prepared = false;
-    // merged statistics (Sec. 2 / Sec. 4: sufficient statistics of all rounds)
-    uint64_t n = 0, alive = 0, n_dm = 0, n_full = 0, n_loc = 0;
-    double lse1 = -INFINITY, lse2 = -INFINITY;
+    Suff st;                      // merged statistics of all rounds
     void release()
     {
         for (void* b : bufs) cudaFree(b);
@@ -1300,42 +1647,13 @@ struct Request {
     }
 };
 
-double lse_add(double a, double b)
-{
-    if (a == -INFINITY) return b;
-    if (b == -INFINITY) return a;
-    const double m = a > b ? a : b;
-    return m + std::log(std::exp(a - m) + std::exp(b - m));
-}
-
-// statistics of merged sufficient statistics (as the statistics kernels)
+// statistics of a request's merged rounds (seconds, kernel_ms, alg_bytes:
+// 0, as documented for pm_request_done)
 void fill_result(const Request& q, pm_result& o)
 {
-    std::memset(&o, 0, sizeof(o));
-    o.n_traj = q.n;
-    o.n_alive = q.alive;
-    o.log_sum_x = q.lse1;
-    o.log_sum_x2 = q.lse2;
-    o.n_dm_calls = q.n_dm;
-    o.n_full_sk = q.n_full;
-    o.n_local_sk = q.n_loc;
-    o.p_match = q.n ? (double)q.alive / (double)q.n : 0.0;
-    if (q.n == 0 || q.lse1 == -INFINITY) {
-        o.log_estimate = -INFINITY;
-        o.rel_spread = o.rse = NAN;
-        return;
-    }
-    const double M = (double)q.n;
-    o.log_estimate = q.lse1 - std::log(M);
-    o.estimate = std::exp(o.log_estimate);
-    o.ess = std::exp(2 * q.lse1 - q.lse2);
-    if (q.n > 1) {
-        const double ratio = M * std::exp(q.lse2 - 2 * q.lse1);
-        o.rel_spread = std::sqrt(std::max(0.0, ratio - 1.0) * M / (M - 1.0));
-        o.rse = o.rel_spread / std::sqrt(M);
-    } else {
-        o.rel_spread = o.rse = NAN;
-    }
+    q.st.fill(o);
+    o.kernel_ms = o.seconds = 0;
+    o.alg_bytes = o.mlp_rows = 0;
 }
 
 }  // namespace
@@ -1411,6 +1729,8 @@ pm_status pm_server_create(pm_context* ctx, const pm_server_cfg* cfg, pm_server*
         return fail(ctx, PM_EINVAL, "bad server configuration");
     pm_status st = check_schedule(ctx, &cfg->schedule);
     if (st != PM_OK) return st;
+    if (cfg->schedule.rse_target != 0 || cfg->schedule.time_budget_s != 0)
+        return fail(ctx, PM_EINVAL, "server requests carry their own targets: rse_target and time_budget_s must be 0");
     pm_server* sv = new (std::nothrow) pm_server();
     if (!sv) return PM_ENOMEM;
     sv->ctx = ctx;
@@ -1551,18 +1871,12 @@ pm_status pm_server_round(pm_server* sv, pm_request_done* done, uint32_t cap, ui
         for (int k = 0; k < count; ++k) {
             Request* q = sv->active[k];
             const pm_result& o = outs[k];
-            q->n += o.n_traj;
-            q->alive += o.n_alive;
-            q->lse1 = lse_add(q->lse1, o.log_sum_x);
-            q->lse2 = lse_add(q->lse2, o.log_sum_x2);
-            q->n_dm += o.n_dm_calls;
-            q->n_full += o.n_full_sk;
-            q->n_loc += o.n_local_sk;
-            q->done_traj += o.n_traj;
+            q->st.add(o);
+            q->done_traj += R.ntraj[k];
             q->rounds += 1;
             pm_result cur;
             fill_result(*q, cur);
-            const bool met = q->n >= sv->cfg.min_traj_done && q->alive >= 2 && cur.rse <= q->target_rse;
+            const bool met = q->st.n >= sv->cfg.min_traj_done && q->st.alive >= 2 && cur.rse <= q->target_rse;
             const bool spent = q->done_traj >= q->max_traj;
             if ((met || spent) && *n_done < cap) {
                 sv->bytes_active -= q->bytes;
@@ -1662,6 +1976,74 @@ pm_status pm_model_set_params(pm_context* ctx, pm_model* m, const float* params)
     PM_CUDA(cudaMemcpyAsync(m->master, params, 4 * model_param_count(), cudaMemcpyHostToDevice, ctx->stream));
     PM_CUDA(launch_model_image(m->master, m->img, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return PM_OK;
+}
+
+// Model file: 8-byte magic, uint32 version, uint32 parameter count, the FP32
+// master parameters (little-endian, the layout of pm_model_get_params), and
+// a 64-bit FNV-1a checksum of the parameter bytes.
+static const char kModelMagic[8] = {'P', 'M', 'M', 'O', 'D', 'E', 'L', '1'};
+
+static uint64_t fnv1a(const uint8_t* p, size_t n)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+    return h;
+}
+
+pm_status pm_model_save(pm_context* ctx, const pm_model* m, const char* path)
+{
+    if (!ctx || !m || !path) return PM_EINVAL;
+    const int np = model_param_count();
+    std::vector<float> h(np);
+    pm_status st = pm_model_get_params(ctx, m, h.data());
+    if (st != PM_OK) return st;
+    const uint32_t ver = 1, cnt = (uint32_t)np;
+    const uint64_t sum = fnv1a((const uint8_t*)h.data(), 4 * (size_t)np);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(ctx, PM_EINVAL, std::string("cannot write ") + tmp);
+    bool ok = std::fwrite(kModelMagic, 1, 8, f) == 8 && std::fwrite(&ver, 4, 1, f) == 1 &&
+              std::fwrite(&cnt, 4, 1, f) == 1 && std::fwrite(h.data(), 4, np, f) == (size_t)np &&
+              std::fwrite(&sum, 8, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return fail(ctx, PM_EINVAL, std::string("cannot write ") + path);
+    }
+    return PM_OK;
+}
+
+pm_status pm_model_load(pm_context* ctx, const char* path, pm_model** out)
+{
+    if (!ctx || !path || !out) return PM_EINVAL;
+    *out = nullptr;
+    const int np = model_param_count();
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, PM_EINVAL, std::string("cannot read ") + path);
+    char magic[8];
+    uint32_t ver = 0, cnt = 0;
+    uint64_t sum = 0;
+    std::vector<float> h(np);
+    char extra;
+    const bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kModelMagic, 8) == 0 &&
+                    std::fread(&ver, 4, 1, f) == 1 && ver == 1 && std::fread(&cnt, 4, 1, f) == 1 &&
+                    cnt == (uint32_t)np && std::fread(h.data(), 4, np, f) == (size_t)np &&
+                    std::fread(&sum, 8, 1, f) == 1 && std::fread(&extra, 1, 1, f) == 0 &&
+                    sum == fnv1a((const uint8_t*)h.data(), 4 * (size_t)np);
+    std::fclose(f);
+    if (!ok) return fail(ctx, PM_EINVAL, std::string("not a model file of this library: ") + path);
+    return pm_model_create(ctx, h.data(), 0, out);
+}
+
+pm_status pm_merge_results(const pm_result* parts, int32_t count, pm_result* out)
+{
+    if (!parts || count < 1 || !out) return PM_EINVAL;
+    Suff s;
+    for (int32_t i = 0; i < count; ++i) s.add(parts[i]);
+    s.fill(*out);
+    out->stop = PM_STOP_COMPLETE;
+    for (int32_t i = 0; i < count; ++i) out->stop = std::max(out->stop, parts[i].stop);
     return PM_OK;
 }
 

@@ -21,7 +21,12 @@ enum : uint32_t {
     ST_BAD_INPUT = 1u << 1,
     ST_INTERNAL = 1u << 2,
     ST_CAPACITY = 1u << 3,
+    // not errors: the launch stopped starting trajectories early (every
+    // trajectory it started ran to its end; the others keep ln X = NaN)
+    ST_TIMEOUT = 1u << 4,     // the launch's time budget ran out
+    ST_CANCELLED = 1u << 5,   // the context's cancel flag was raised
 };
+constexpr uint32_t kStatusStopBits = ST_TIMEOUT | ST_CANCELLED;
 
 // Original input matrix A on the device (int32 offsets, validated).
 struct DevInput {
@@ -156,13 +161,18 @@ struct Plan {
     int mat_bytes;     // shared bytes of the staged matrix (0 if not staged)
 };
 
-// a run of trajectories first .. first + count - 1 (indices inside matrix k)
+// a run of trajectories first .. first + count - 1 (indices inside matrix k);
+// trajectory first + q writes its ln X to log_x[slot0 + q]
 struct Chunk {
     int k;
     uint32_t count;
     uint64_t first;
+    uint64_t slot0;
 };
 
+// per-matrix counters of a launch: DM calls, full SK iterations, Local
+// repairs, algorithmic bytes, network rows, trajectory nanoseconds
+constexpr int kCounters = 6;
 constexpr int kCtaWarps = 16;            // 512 threads, one CTA per SM
 constexpr int kCtaMiscBytes = 64;
 constexpr int kGroupMiscInts = 32;
@@ -179,7 +189,7 @@ struct TrajParams {
     uint64_t seed;
     Sched s;
     double* log_x;            // [prefix[count]]
-    unsigned long long* counters;  // [count][5]: DM calls, full SK, local SK, algorithmic bytes, network rows
+    unsigned long long* counters;  // [count][kCounters], see kCounters
     int* chunk_counter;
     uint32_t* status;
     uint8_t* slots;           // per-group global scratch, kCtaWarps slots per CTA
@@ -188,7 +198,15 @@ struct TrajParams {
     int32_t* chosen;
     int32_t* deg_v;
     int32_t* dead_step;
-    float* trace_logits;      // [T][n][32] logits of the live candidates (learned proposal)
+    float* trace_logits;      // [T][n][logit_stride] logits of the live candidates (learned proposal)
+    int logit_stride;         // candidates kept per step in trace_logits
+    // run control: no trajectory starts once budget_ns (> 0) nanoseconds of
+    // device time (%globaltimer) have passed since the launch's first CTA
+    // began (t_start, zeroed before the launch), or once *cancel != 0
+    // (host-mapped flag, may be nullptr); started trajectories run to the end
+    uint64_t budget_ns;
+    unsigned long long* t_start;
+    const volatile int* cancel;
     // learned proposal: BF16 device image of the network, or nullptr
     const void* model;
     // recording of (features, SK target) pairs, or rec_feat == nullptr
@@ -252,6 +270,10 @@ cudaError_t launch_stats(const double* log_x, const uint64_t* h_prefix, const ui
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t count, uint32_t* out,
                           cudaStream_t st);
 int traj_max_smem_bytes();
+// on-chip bandwidth probes (pm_probe.cu)
+cudaError_t launch_l2_probe(const void* buf, size_t bytes, int iters, int grid, unsigned long long* sink,
+                            cudaStream_t st);
+cudaError_t launch_smem_probe(int smem_bytes, int iters, int grid, unsigned long long* sink, cudaStream_t st);
 // the kernel launch_trajectories would launch for these parameters (to find
 // its node in a captured graph)
 const void* traj_kernel_entry(const TrajParams& p, bool trace);

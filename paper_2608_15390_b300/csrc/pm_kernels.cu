@@ -328,13 +328,17 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(const double* log_x,
     const int k = blockIdx.y, ch = blockIdx.x;
     const uint64_t b0 = prefix[k], b1 = prefix[k + 1], len = b1 - b0;
     const uint64_t lo = b0 + len * ch / chunks, hi = b0 + len * (ch + 1) / chunks;
-    double mx = -INFINITY, alive = 0;
+    // ln X = NaN marks a trajectory that a stopped launch never started: it
+    // is not part of the sample (dead trajectories are -inf and count)
+    double mx = -INFINITY, alive = 0, ran = 0;
     for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const double v = log_x[i];
+        if (v == v) ran += 1;
         if (v > -INFINITY) { mx = fmax(mx, v); alive += 1; }
     }
     mx = block_reduce_max(mx, sh);
     alive = block_reduce_sum(alive, sh);
+    ran = block_reduce_sum(ran, sh);
     double s1 = 0, s2 = 0;
     if (mx > -INFINITY) {
         for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
@@ -346,12 +350,12 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(const double* log_x,
     }
     s1 = block_reduce_sum(s1, sh);
     s2 = block_reduce_sum(s2, sh);
-    const double cnt = (double)(hi - lo);
     double m2 = 0;
     if (mx > -INFINITY) {
-        const double mean = s1 / cnt;
+        const double mean = s1 / ran;
         for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const double v = log_x[i];
+            if (!(v == v)) continue;
             const double y = v > -INFINITY ? exp(v - mx) : 0.0;
             m2 += (y - mean) * (y - mean);
         }
@@ -360,7 +364,7 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(const double* log_x,
     if (threadIdx.x == 0) {
         StatsPartial& p = parts[(size_t)k * chunks + ch];
         p.c = mx; p.s1 = s1; p.s2 = s2; p.m2 = m2;
-        p.cnt = hi - lo;
+        p.cnt = (unsigned long long)ran;
         p.alive = (unsigned long long)alive;
     }
 }

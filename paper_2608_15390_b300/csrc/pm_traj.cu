@@ -392,7 +392,8 @@ __device__ __forceinline__ CandLoads cand_loads(const MV<Idx>& V, const DevMatri
 // Integer sums: identical to neighbour_degree_sum.
 template <typename Idx>
 __device__ __forceinline__ int neighbour_degree_sum_flat(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask,
-                                                         bool vrow, int pp, bool live, int lane, int* acc)
+                                                         bool vrow, int pp, bool live, int lane, int* acc,
+                                                         int& entries)
 {
     const int n = V.n;
     int b = 0, len = 0;
@@ -408,6 +409,7 @@ __device__ __forceinline__ int neighbour_degree_sum_flat(const MV<Idx>& V, const
     }
     const int excl = incl - len;
     const int total = __shfl_sync(kFull, incl, 31);
+    entries = total;
     acc[lane] = 0;
     __syncwarp();
     const unsigned lm = __ballot_sync(kFull, live && len > 0);
@@ -457,6 +459,13 @@ __device__ __forceinline__ void cand_features(const MV<Idx>& V, const uint16_t* 
     f[5] = lsv;
     f[6] = __logf(sl);
     f[7] = vals ? __logf(bv) : 0.0f;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // misc slots of a group (two step buffers so a fast leader never overwrites
@@ -547,7 +556,10 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     unsigned n_dm = 0, n_full = 0, n_loc = 0;
     bool dm_matched = false;  // the DM workspace holds this trajectory's last perfect matching
     int dead_step = -1;
-    uint64_t alg_bytes = (uint64_t)2 * n * 4;
+    // algorithmic bytes of the trajectory: 16 B per vertex for the initial
+    // degrees and minimum-degree structure; then per step the counts below
+    uint64_t alg_bytes = (uint64_t)16 * n;
+    const uint64_t t_begin = (leader && lane == 0) ? global_ns() : 0;
     uint64_t mlp_rows = 0;  // network evaluations of live candidates (learned proposal)
     int m_live = Mp->m;
 
@@ -605,8 +617,12 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     const int li = __popc(lmk & ((1u << lane) - 1u));
                     const CandLoads cl = cand_loads<Idx>(V, Mp, vrow, e, pp, live);
                     // the feature tile doubles as the sums' scratch until the features are written
+                    int entries = 0;
                     const int sum_l = neighbour_degree_sum_flat<Idx>(V, deg, mask, vrow, pp, live, lane,
-                                                                     reinterpret_cast<int*>(feat));
+                                                                     reinterpret_cast<int*>(feat), entries);
+                    // features: each live candidate's list (index + degree, 8 B
+                    // an entry) and pointers, its outer scale and entry value
+                    alg_bytes += (uint64_t)8 * entries + (uint64_t)16 * nl;
                     if (live) {
                         float f[8];
                         cand_features<Idx>(V, deg, t, vrow, pp, sum_v, sum_l, (float)dv, lsv, cl, f);
@@ -640,7 +656,8 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 auto side_outputs = [&](int e, int pp, bool live, float lg, int live_base) {
                     const unsigned lmk = __ballot_sync(kFull, live);
                     const int li = live_base + __popc(lmk & ((1u << lane) - 1u));
-                    if (TRACE && model && live && li < 32) P.trace_logits[(gq * n + t) * 32 + li] = lg;
+                    if (TRACE && model && live && li < P.logit_stride)
+                        P.trace_logits[((size_t)gq * n + t) * P.logit_stride + li] = lg;
                     return __popc(lmk);
                 };
                 // recording of (features, SK target) pairs: a pair is kept
@@ -925,7 +942,13 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 cnt_r = vrow ? cnt_u : cnt_v;
                 cnt_c = vrow ? cnt_v : cnt_u;
                 m_live -= dv + cnt_u;
-                alg_bytes += (uint64_t)8 * (uint64_t)(len + ulen);
+                // both eliminated lists: index + liveness check (8 B an entry)
+                // and the two pointers of each list; 32 B per decrement
+                // (degree read-modify-write + minimum-degree update); the
+                // proposal's scale (and value) per candidate of v
+                alg_bytes += (uint64_t)8 * (uint64_t)(len + ulen) + 16 + (uint64_t)32 * (uint64_t)(cnt_v + cnt_u);
+                if (!uniform && !model) alg_bytes += (uint64_t)sizeof(Real) * (uint64_t)len;
+                if ((vrow ? V.rv : V.cv) != nullptr) alg_bytes += (uint64_t)4 * (uint64_t)len;
                 __syncwarp();
                 if (S.vertex_rule != VR_ROW) tree_fix2(deg, tree, T, R, n + C, lane);
                 track = RA<Real>::mul(track, z);
@@ -953,7 +976,12 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         if (mb[M_DEAD]) break;
         if (t + 1 >= n) continue;
         if (mb[M_DM]) {
-            if (leader) ++n_dm;
+            if (leader) {
+                ++n_dm;
+                // a DM call: the matching repair and the SCC pass read each
+                // live edge about once in each direction, plus per-vertex state
+                alg_bytes += (uint64_t)16 * (uint64_t)m_live + (uint64_t)24 * (uint64_t)(2 * (n - t - 1));
+            }
             if (leader) {
                 const bool okdm =
                     dm_warp(n, V.rp, V.ci, V.cp, V.ri, V.ce, LiveTraj{deg, mask, n}, mask, dmws, lane, dm_matched);
@@ -1017,13 +1045,34 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     if (leader && lane == 0) {
         P.log_x[gq] = (dead_step >= 0) ? -INFINITY : num.log_value() - den.log_value();
         if (TRACE) P.dead_step[gq] = dead_step;
-        if (n_dm) atomicAdd(P.counters + 5 * k + 0, (unsigned long long)n_dm);
-        if (n_full) atomicAdd(P.counters + 5 * k + 1, (unsigned long long)n_full);
-        if (n_loc) atomicAdd(P.counters + 5 * k + 2, (unsigned long long)n_loc);
-        atomicAdd(P.counters + 5 * k + 3, (unsigned long long)alg_bytes);
-        if (mlp_rows) atomicAdd(P.counters + 5 * k + 4, (unsigned long long)mlp_rows);
+        unsigned long long* cnt = P.counters + kCounters * k;
+        if (n_dm) atomicAdd(cnt + 0, (unsigned long long)n_dm);
+        if (n_full) atomicAdd(cnt + 1, (unsigned long long)n_full);
+        if (n_loc) atomicAdd(cnt + 2, (unsigned long long)n_loc);
+        atomicAdd(cnt + 3, (unsigned long long)alg_bytes);
+        if (mlp_rows) atomicAdd(cnt + 4, (unsigned long long)mlp_rows);
+        atomicAdd(cnt + 5, (unsigned long long)(global_ns() - t_begin));
     }
     gsync(G);
+}
+
+// Whether the launch must start no further trajectory: its time budget is
+// spent, or (checked by the CTA at chunk claims, `poll_cancel`) the host
+// raised the context's cancel flag.  Sets the matching status bit.
+__device__ __forceinline__ bool stop_starting(const TrajParams& P, bool poll_cancel)
+{
+    if (P.budget_ns) {
+        const unsigned long long t0 = *reinterpret_cast<volatile unsigned long long*>(P.t_start);
+        if (t0 && global_ns() - t0 > P.budget_ns) {
+            atomicOr(P.status, ST_TIMEOUT);
+            return true;
+        }
+    }
+    if (poll_cancel && P.cancel && *P.cancel) {
+        atomicOr(P.status, ST_CANCELLED);
+        return true;
+    }
+    return false;
 }
 
 template <typename Real, typename Idx, bool TRACE, int MODE>
@@ -1078,17 +1127,19 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
     }
     G.misc = reinterpret_cast<int*>(sbase + off);
     for (;;) {
-        if (G.wig == 0 && lane == 0) G.misc[M_TRAJ] = atomicAdd(ctr_traj, 1);
+        if (G.wig == 0 && lane == 0)
+            G.misc[M_TRAJ] = (P.budget_ns && stop_starting(P, false)) ? (int)ch.count : atomicAdd(ctr_traj, 1);
         gsync(G);
         const int q = G.misc[M_TRAJ];
         gsync(G);
         if (q >= (int)ch.count) break;
         const uint64_t local = ch.first + (uint64_t)q;
+        const uint64_t gq = ch.slot0 + (uint64_t)q;
         if (pl.gstate)
-            run_group<Real, Idx, TRACE, MODE, uint32_t>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm,
+            run_group<Real, Idx, TRACE, MODE, uint32_t>(P, Mp, V, k, gq, local, deg, tree, r_sm,
                                                         reinterpret_cast<uint32_t*>(lists), feat, Ms, slot, dm_sm, mask_sm, G);
         else
-            run_group<Real, Idx, TRACE, MODE, uint16_t>(P, Mp, V, k, P.prefix[k] + local, local, deg, tree, r_sm,
+            run_group<Real, Idx, TRACE, MODE, uint16_t>(P, Mp, V, k, gq, local, deg, tree, r_sm,
                                                         reinterpret_cast<uint16_t*>(lists), feat, Ms, slot, dm_sm, mask_sm, G);
     }
 }
@@ -1099,7 +1150,10 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
     extern __shared__ __align__(16) uint8_t smem[];
     int* cmisc = reinterpret_cast<int*>(smem);  // [0] chunk, [1] trajectory counter, [2] staged matrix
     const int tid = threadIdx.x;
-    if (tid == 0) cmisc[2] = -1;
+    if (tid == 0) {
+        cmisc[2] = -1;
+        if (P.budget_ns) atomicCAS(P.t_start, 0ull, (unsigned long long)global_ns());  // the first CTA starts the clock
+    }
     // the learned proposal's weights, staged once per CTA
     const DevModel* Ms = nullptr;
     int model_bytes = 0;
@@ -1113,7 +1167,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
     for (;;) {
         __syncthreads();
         if (tid == 0) {
-            cmisc[0] = atomicAdd(P.chunk_counter, 1);
+            cmisc[0] = stop_starting(P, true) ? P.n_chunks : atomicAdd(P.chunk_counter, 1);
             cmisc[1] = 0;
         }
         __syncthreads();

@@ -6,7 +6,12 @@ the bench uses.
   trajectory (ln X within 1e-12), the statistics against the oracle's, and the
   estimate against the exact permanent (Ryser) within the reported RSE.
 - The 64-matrix bench batch run as one persistent launch with Adaptive SK:
-  sampled trajectories of several matrices replayed by the oracle."""
+  sampled trajectories of several matrices replayed by the oracle.
+- The bench's own learned schedule on the same batch, as the bench runs it
+  (a resident batch, CUDA graph, autotuned layouts): on the largest matrices
+  the chosen edges of sampled trajectories, traced in the same layout, are
+  replayed bit-exact by the oracle, and the batch run's ln X of those
+  trajectories agrees with the oracle's."""
 import math
 
 import numpy as np
@@ -47,3 +52,32 @@ def test_bench_batch_sampled_against_the_oracle():
     for k in small:
         o = O.Prepared(mats[k], osched).run(seed=1, count=8, first_traj=5000, matrix=int(k), threads=8)
         assert logx_close(lx[T * k:T * k + 8], o["log_x"], 1e-12) <= 1e-12, k
+
+
+def test_bench_learned_batch_largest_matrices():
+    B = binding()
+    rng = np.random.default_rng(21)
+    p = (rng.normal(size=O.N_PARAM) * 0.3).astype(np.float32)
+    model = ctx().model(p)
+    mats = G.batch_er(64, 100, 2000, 4.0, 8.0, seed=2)
+    sched = B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL, learned=model)
+    T, first, seed = 256, 3 << 20, 1
+    bt = ctx().batch(mats, [T] * 64, sched, graph=True, autotune=True)
+    _, lx = bt.run(first, seed, want_log_x=True)
+    osched = O.Schedule(initial_dm=1, K0=100, precision=O.PREC_FP32)
+    largest = [int(k) for k in np.argsort([m.n for m in mats])[-3:]]
+    for k in largest:
+        c = 6
+        g = ctx().trace(mats[k], c, seed, sched, first_traj=first, matrix_index=k)
+        plan = bt.plan(k)
+        used = ctx().last_call_info()["first_plan"]
+        for f in ("g", "groups", "staged", "rc_smem", "gstate", "dm_smem"):
+            assert used[f] == plan[f], (k, f, used, plan)
+        o = O.Prepared(mats[k], osched).run_ext(seed=seed, count=c, logits=g["logits"], first_traj=first,
+                                                matrix=k, threads=8)
+        assert np.array_equal(g["chosen"], o["chosen"]), k
+        assert np.array_equal(g["dead_step"], o["dead_step"]), k
+        assert logx_close(lx[T * k:T * k + c], o["log_x"], 1e-12) <= 1e-12, k
+        assert np.array_equal(g["log_x"], lx[T * k:T * k + c]), k
+    bt.close()
+    model.close()

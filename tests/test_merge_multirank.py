@@ -32,6 +32,18 @@ def test_merge_equals_whole_run():
     assert got["n_traj"] == 3000 and got["n_alive"] == whole["n_alive"]
 
 
+def test_merge_sums_counts_and_keeps_the_largest_stop_reason():
+    a = {"n_traj": 10, "n_alive": 4, "log_sum_x": 1.0, "log_sum_x2": 2.5, "n_dm_calls": 3, "n_full_sk": 7,
+         "n_local_sk": 11, "alg_bytes": 100, "mlp_rows": 9, "rounds": 1, "stop": 0}
+    b = {"n_traj": 6, "n_alive": 0, "log_sum_x": -math.inf, "log_sum_x2": -math.inf, "n_dm_calls": 1,
+         "n_full_sk": 2, "n_local_sk": 3, "alg_bytes": 50, "mlp_rows": 1, "rounds": 2, "stop": 2}
+    r = merge([a, b])
+    assert (r["n_traj"], r["n_alive"], r["n_dm_calls"], r["n_full_sk"], r["n_local_sk"]) == (16, 4, 4, 9, 14)
+    assert (r["alg_bytes"], r["mlp_rows"], r["rounds"], r["stop"]) == (150, 10, 3, 2)
+    assert r["log_estimate"] == pytest.approx(1.0 - math.log(16), rel=1e-15)
+    assert r["ess"] == pytest.approx(math.exp(2 * 1.0 - 2.5), rel=1e-15)
+
+
 def test_merge_all_dead_and_single():
     d = {"n_traj": 5, "n_alive": 0, "log_sum_x": -math.inf, "log_sum_x2": -math.inf}
     r = merge([d, d])

@@ -324,6 +324,29 @@ def test_estimate_converges_to_ryser():
     assert st["ess"] <= st["n_traj"] * st["p_match"] + 1e-9   # Cauchy-Schwarz (Sec. 2)
 
 
+def test_first_pick_frequencies_match_the_weights():
+    """The draw-to-candidate map (the first live candidate whose prefix sum of
+    integer weights exceeds an exact-uniform r in [0, W)) realises q = w / W
+    of Eq. 3: the first step's state is the same for every trajectory, so
+    over 2e5 trajectories the partners of step 0 follow w_u / W (chi-square
+    test at significance 1e-4 on weights that differ by up to 2x)."""
+    from scipy.stats import chi2
+    A = G.random_weighted(12, 0.5, seed=3, lo=1.0, hi=2.0)
+    P = O.Prepared(A, O.Schedule(K0=3, precision=O.PREC_FP64))
+    kind, w, W, _, _ = P.forced([])
+    assert kind == "need" and len(w) >= 4 and sum(w) == W
+    assert max(w) > 1.3 * min(w)
+    partner = [P.forced([k])[-1]["chosen"][0][1] for k in range(len(w))]
+    res = P.run(seed=11, count=200_000, threads=os.cpu_count() or 1, trace=True)
+    ch = res["chosen"][:, 0, :]
+    assert (ch[:, 0] == ch[0, 0]).all()  # the same picked vertex everywhere
+    obs = np.array([(ch[:, 1] == u).sum() for u in partner], dtype=float)
+    assert obs.sum() == 200_000
+    exp = 200_000 * np.array(w, dtype=float) / W
+    stat = float(((obs - exp) ** 2 / exp).sum())
+    assert chi2.sf(stat, len(w) - 1) > 1e-4, (stat, obs, exp)
+
+
 def test_run_is_thread_count_invariant():
     A = G.er_planted(60, 4.0, seed=5)
     P = O.Prepared(A, O.preset("local_threshold", O.PREC_FP32))
