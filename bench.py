@@ -5,29 +5,27 @@ Workload: 64 Erdos-Renyi bipartite matrices with a planted permutation,
 n ~ U{100..2000}, average degree ~ U[4, 8] (generator seed 2).
 
 A step is one whole job at fixed relative error: every matrix of the batch
-estimated until its RSE (Sec. 4 "Metrics") is at most eps (default 0.05;
---eps), through the public call estimate_permanent_batch with
-rse_target = eps: preprocessing once (CSC build, initial DM, outer SK), then
-rounds of one persistent launch over the matrices still short of the target
-(consecutive trajectory ids per matrix, statistics merged after each round).
-Steps use disjoint trajectory ids.
+estimated until its RSE (Sec. 4 "Metrics") is at most eps (default 0.1;
+--eps), through the public call estimate_permanent_batch with rse_target =
+eps and a time budget (default 4 s; --budget): preprocessing once (CSC
+build, initial DM, outer SK), then rounds of one persistent launch over the
+matrices still short of the target (consecutive trajectory ids per matrix,
+statistics merged after each round).  A matrix the budget stops first is
+censored: it keeps the ESS it reached, and the line counts the matrices at
+target.  Steps use disjoint trajectory ids.
 
 value: effective samples per second of the learned proposal run batched
 (the metric's "learned+batched"): the Sec. 2 ESS of every matrix at its stop,
 summed over the matrices and steps, over the device time of the steps (CUDA
-events on the launching stream).  At a fixed RSE each matrix ends with
-ESS ~ 1/eps^2, so no matrix dominates the sum; the job time is set by the
-hardest matrices.  The network is trained before the timed region (time
-reported) on pairs recorded from an SK-scheduled run on 16 training matrices
-of the same family (seed 7).
+events on the launching stream).  At a fixed RSE a matrix ends with
+ESS ~ 1/eps^2, so no matrix dominates the sum.  The network is trained before
+the timed region (time reported) on pairs recorded from an SK-scheduled run
+on 16 training matrices of the same family (seed 7).
 
-compare: the metric's "plain" (outer SK only) run one matrix per call and
-run batched, and SK(100,10)-Adaptive run batched, each as one job at the
-same eps under a time budget; a matrix that the budget stops before its
-target gets its time to target extrapolated from its own rate
-(t_k (rse_k / eps)^2, the RSE of a fixed estimator falling as 1/sqrt(M)),
-and the arm is marked extrapolated.  Per-matrix times come from each
-matrix's share of the device time (pm_result.traj_ns).
+compare: the metric's "plain" (outer SK only) run batched and one matrix per
+call, and SK(100,10)-Adaptive run batched, each as one job at the same eps and
+budget; per matrix, ESS/s over its attributed device time (pm_result.dev_ms),
+and the learned/arm ratios over the matrices that reached the target in both.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--eps E] [--impl ours|reference]
 
@@ -58,14 +56,15 @@ from paper_2608_15390_b300.merge import merge  # noqa: E402
 METRIC = "effective samples/s at fixed rel. error, learned+batched vs plain, 1 B300"
 UNIT = "effective samples/s"
 N_MATS, N_LO, N_HI, D_LO, D_HI, GEN_SEED = 64, 100, 2000, 4.0, 8.0, 2
-EPS = 0.05
-TRAJ_CAP = 1 << 26  # per matrix and job: an upper bound the RSE target ends first
+EPS = 0.1
+STEP_BUDGET_S = 4.0  # device-side time budget of one job (a step)
+TRAJ_CAP = 1 << 26  # per matrix and job: an upper bound the target or the budget ends first
 WORKLOAD_CORE = ("64 ER+planted-permutation matrices, n~U{100..2000}, avg degree~U[4,8] "
                  "(generator seed 2); learned proposal (8-64-64-1 BF16 network) with two-sided MD, "
                  "initial DM, outer SK(100), FP32 proposal, FP64 log-weights")
-WORKLOAD = (WORKLOAD_CORE + "; a step estimates every matrix to RSE <= eps (estimate_permanent_batch with "
-            "rse_target: preprocessing, then rounds of one persistent launch over the unfinished matrices), "
-            "layouts autotuned")
+WORKLOAD = (WORKLOAD_CORE + "; a step estimates every matrix to RSE <= eps within a time budget "
+            "(estimate_permanent_batch with rse_target and time_budget_s: preprocessing, then rounds of one "
+            "persistent launch over the unfinished matrices), layouts autotuned")
 
 
 def parse():
@@ -77,12 +76,13 @@ def parse():
     p.add_argument("--eps", type=float, default=EPS, help="RSE target of every matrix in a job")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the comparison arms")
-    p.add_argument("--compare-budget", type=float, default=40.0,
-                   help="seconds of device time per comparison arm before extrapolating")
+    p.add_argument("--budget", type=float, default=STEP_BUDGET_S,
+                   help="time budget of one job (a step, and each comparison arm), seconds")
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--mats", type=int, default=N_MATS,
                    help="use the first K matrices (profiling of a smaller case)")
-    p.add_argument("--workload", default="batch", choices=["batch", "serving", "large"],
+    p.add_argument("--study-budget", type=float, default=2.0, help="seconds per run of the e4 / theta studies")
+    p.add_argument("--workload", default="batch", choices=["batch", "serving", "large", "e4", "theta", "ablation"],
                    help="batch: the 64-matrix batch (the metric); serving: the Poisson request stream; "
                         "large: one n = 1e5 band matrix (state in global memory)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of each serving load")
@@ -246,77 +246,60 @@ def timed(ctx, stream, fn):
 def job_summary(res, t_job):
     """A job's figures from its per-matrix results and device time t_job:
     effective samples (Sec. 2 ESS at each matrix's stop), trajectories, and
-    per matrix its share of the device time (traj_ns) and its ESS per
-    second of that share."""
-    ess = np.array([r["ess"] for r in res])
-    ns = np.array([float(r["traj_ns"]) for r in res])
-    share = ns / ns.sum() if ns.sum() > 0 else np.full(len(res), 1.0 / len(res))
-    t_k = t_job * share
-    return {"ess": float(ess.sum()), "traj": int(sum(r["n_traj"] for r in res)), "t_k": t_k,
-            "ess_k": ess, "rse_k": np.array([r["rse"] for r in res]),
-            "rounds": int(max(r["rounds"] for r in res)),
-            "met": int(sum(r["stop"] == 1 for r in res))}
+    per matrix its attributed device time (pm_result.dev_ms), ESS and
+    whether it stopped at the RSE target."""
+    return {"ess": float(sum(r["ess"] for r in res)), "traj": int(sum(r["n_traj"] for r in res)),
+            "t_k": np.array([r["dev_ms"] / 1e3 for r in res]), "ess_k": np.array([r["ess"] for r in res]),
+            "rse_k": np.array([r["rse"] for r in res]), "met_k": np.array([r["stop"] == 1 for r in res]),
+            "rounds": int(max(r["rounds"] for r in res)), "met": int(sum(r["stop"] == 1 for r in res)),
+            "t_job": t_job}
 
 
-def arm_at_eps(res, t_job, eps):
-    """An arm's job at eps: measured where every matrix met the target; a
-    matrix stopped by the time budget gets its time to target and its ESS
-    extrapolated from its own rate (RSE ~ 1/sqrt(M) at a fixed estimator):
-    t_k (rse_k / eps)^2 and ess_k (rse_k / eps)^2."""
-    js = job_summary(res, t_job)
-    t_k, ess_k = js["t_k"].copy(), js["ess_k"].copy()
-    extrap = 0
-    for k, r in enumerate(res):
-        if r["stop"] != 1:
-            f = (r["rse"] / eps) ** 2 if r["rse"] == r["rse"] and r["n_alive"] >= 2 else math.inf
-            t_k[k] *= max(1.0, f)
-            ess_k[k] *= max(1.0, f)
-            extrap += 1
-    return {"ess_per_s": float(ess_k.sum() / t_k.sum()), "job_seconds": float(t_k.sum()),
-            "extrapolated_matrices": extrap, "t_k": t_k, "ess_k": ess_k,
-            "traj_per_s": js["traj"] / t_job, "median_rse": float(np.nanmedian(js["rse_k"]))}
+def arm_figures(js):
+    """An arm's job at eps: its ESS/s over the whole job, over the matrices
+    that reached the target, and the count of matrices the budget stopped."""
+    m = js["met_k"]
+    return {"ess_per_s": js["ess"] / js["t_job"], "job_seconds": js["t_job"], "matrices_at_target": int(m.sum()),
+            "ess_per_s_at_target": float(js["ess_k"][m].sum() / js["t_k"][m].sum()) if m.any() else None,
+            "traj_per_s": js["traj"] / js["t_job"], "median_rse": float(np.nanmedian(js["rse_k"]))}
 
 
-def compare_arms(ctx, B, dev, args, learned_tk, learned_essk):
-    """The metric's "plain" (outer SK only) one matrix per call and batched,
-    and SK(100,10)-Adaptive batched, each one job at args.eps with a time
-    budget; the learned arm's per-matrix figures (first timed job) beside
-    them for the per-matrix ratios of ESS/s at eps."""
+def compare_arms(ctx, B, dev, args, learned):
+    """The metric's "plain" (outer SK only) run batched and one matrix per
+    call, and SK(100,10)-Adaptive batched, each one job at the same eps and
+    time budget as a learned step (one matrix per call: 1/64 of the budget
+    each); per-matrix ratios of ESS/s over the matrices that reached the
+    target in both arms."""
     import torch
     stream = torch.cuda.current_stream()
-    out = {}
     first = (1 << 44)
-    arms = {"plain_batched": B.Schedule(**LEARNED, rse_target=args.eps, time_budget_s=args.compare_budget),
-            "adaptive_sk_batched": B.Schedule(**schedule_fields(), rse_target=args.eps,
-                                              time_budget_s=args.compare_budget)}
+    out = {}
+    arms = {"plain_batched": B.Schedule(**LEARNED, rse_target=args.eps, time_budget_s=args.budget),
+            "adaptive_sk_batched": B.Schedule(**schedule_fields(), rse_target=args.eps, time_budget_s=args.budget)}
     for name, sched in arms.items():
         (res, _), dt = timed(ctx, stream, lambda: ctx.estimate_batch_ex(dev, [TRAJ_CAP] * len(dev), args.seed, sched,
                                                                        first_traj=first))
-        out[name] = arm_at_eps(res, dt, args.eps)
-    # plain, one matrix per call, each with its share of the budget
-    res_u, t_u = [], []
-    per = args.compare_budget / len(dev)
-    sched = B.Schedule(**LEARNED, rse_target=args.eps, time_budget_s=per)
+        out[name] = job_summary(res, dt)
+        print(f"compare {name}: {dt:.2f} s, {out[name]['met']} at target", file=sys.stderr, flush=True)
+    sched = B.Schedule(**LEARNED, rse_target=args.eps, time_budget_s=args.budget / len(dev))
+    res_u, t_u = [], 0.0
     for k, m in enumerate(dev):
         (r, _), dt = timed(ctx, stream, lambda: ctx.estimate_batch_ex([m], [TRAJ_CAP], args.seed, sched,
                                                                      first_traj=first + k))
         res_u.append(r[0])
-        t_u.append(dt)
-    a = [arm_at_eps([r], t, args.eps) for r, t in zip(res_u, t_u)]
-    t_k = np.array([x["t_k"][0] for x in a])
-    ess_k = np.array([x["ess_k"][0] for x in a])
-    out["plain_unbatched"] = {"ess_per_s": float(ess_k.sum() / t_k.sum()), "job_seconds": float(t_k.sum()),
-                              "extrapolated_matrices": int(sum(x["extrapolated_matrices"] for x in a)),
-                              "t_k": t_k, "ess_k": ess_k,
-                              "traj_per_s": sum(r["n_traj"] for r in res_u) / sum(t_u),
-                              "median_rse": float(np.nanmedian([r["rse"] for r in res_u]))}
-    lr = learned_essk / learned_tk
+        t_u += dt
+    out["plain_unbatched"] = job_summary(res_u, t_u)
+    print(f"compare plain_unbatched: {t_u:.2f} s", file=sys.stderr, flush=True)
     cmp = {}
-    for name, d in out.items():
-        ratio_k = lr / (d["ess_k"] / d["t_k"])
-        cmp[name] = {k: v for k, v in d.items() if k not in ("t_k", "ess_k")}
-        cmp[name]["learned_vs_this_per_matrix_median"] = float(np.median(ratio_k))
-        cmp[name]["learned_vs_this_per_matrix_geomean"] = float(np.exp(np.mean(np.log(ratio_k))))
+    lr = learned["ess_k"] / learned["t_k"]
+    for name, js in out.items():
+        cmp[name] = arm_figures(js)
+        both = learned["met_k"] & js["met_k"]
+        cmp[name]["matrices_at_target_in_both"] = int(both.sum())
+        if both.any():
+            ratio = lr[both] / (js["ess_k"][both] / js["t_k"][both])
+            cmp[name]["learned_vs_this_per_matrix_median"] = float(np.median(ratio))
+            cmp[name]["learned_vs_this_per_matrix_geomean"] = float(np.exp(np.mean(np.log(ratio))))
     return cmp
 
 
@@ -358,11 +341,12 @@ def oracle_train(seed=5, pairs=40000, steps=300, batch=512, lr=2e-3):
 
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands on the host cores, running
-    the learned proposal (network trained by the oracle itself, untimed) on a
-    bounded sample of the workload (every 8th matrix).  The oracle cannot
-    take a matrix to RSE <= eps within minutes, so each matrix's ESS and CPU
-    time at eps are extrapolated from its pooled sample by the rule the GPU's
-    comparison arms use: both scale with (rse_k / eps)^2."""
+    the learned proposal (network trained by the oracle itself, untimed) as
+    the GPU arm's jobs do, on a bounded sample of the workload (every 8th
+    matrix): a step runs rounds of trajectories over the sampled matrices
+    still short of RSE <= eps (at least 1024 trajectories) until all reach it
+    or the step's time budget ends; value = the sampled matrices' ESS at their
+    stop, summed over the steps, over the CPU time of the steps."""
     if rank != 0:
         return
     import oracle as O
@@ -376,39 +360,46 @@ def run_reference(args, rank, world):
     preps = [O.Prepared(mats[k], sched) for k in sample]
     per = 4 * threads
 
-    def step(i, logs, secs):
-        for q, (k, P) in enumerate(zip(sample, preps)):
-            t = time.perf_counter()
-            lx = P.run_model(seed=args.seed, count=per, params=params, first_traj=i * per, matrix=k,
-                             threads=threads)["log_x"]
-            if secs is not None:
-                secs[q] += time.perf_counter() - t
-                logs[q].append(lx)
+    def job(i):
+        t_start = time.perf_counter()
+        logs = [[] for _ in sample]
+        done = [False] * len(sample)
+        rnd = 0
+        while not all(done) and time.perf_counter() - t_start < args.budget:
+            for q, (k, P) in enumerate(zip(sample, preps)):
+                if done[q]:
+                    continue
+                first = (i << 30) + rnd * per
+                logs[q].append(P.run_model(seed=args.seed, count=per, params=params, first_traj=first, matrix=k,
+                                           threads=threads)["log_x"])
+                st = O.stats(np.concatenate(logs[q]))
+                done[q] = st["n_traj"] >= 1024 and st["n_alive"] >= 2 and st["rse"] <= args.eps
+            rnd += 1
+        sts = [O.stats(np.concatenate(lx)) for lx in logs]
+        return sum(st["ess"] for st in sts), sum(st["n_traj"] for st in sts), sum(done), \
+            time.perf_counter() - t_start
 
     for i in range(args.warmup):
-        step(i, None, None)
-    logs = [[] for _ in sample]
-    secs = [0.0] * len(sample)
-    t0 = time.perf_counter()
+        job(i)
+    tot_ess = tot_traj = 0
+    met = []
+    dt = 0.0
     for i in range(args.steps):
-        step(args.warmup + i, logs, secs)
-    dt = time.perf_counter() - t0
-    ess_eps, t_eps = 0.0, 0.0
-    for q in range(len(sample)):
-        st = O.stats(np.concatenate(logs[q]))
-        f = max(1.0, (st["rse"] / args.eps) ** 2) if st["n_alive"] >= 2 else math.inf
-        ess_eps += st["ess"] * f
-        t_eps += secs[q] * f
-    val = ess_eps / t_eps
-    tot_traj = len(sample) * per * args.steps
+        e, n, d, t = job(args.warmup + i)
+        tot_ess += e
+        tot_traj += n
+        met.append(d)
+        dt += t
+    val = tot_ess / dt
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_CORE + "; the CPU oracle on the host cores", "eps": args.eps,
-                       "sample": f"8 of the 64 matrices (every 8th), {per} trajectories each per step, "
-                                 "preprocessing excluded; ESS and time at eps extrapolated per matrix "
-                                 "as (rse/eps)^2 from the pooled sample",
+                       "step_budget_s": args.budget,
+                       "sample": f"8 of the 64 matrices (every 8th), rounds of {per} trajectories per "
+                                 "unfinished matrix, preprocessing excluded",
+                       "matrices_at_target_mean": float(np.mean(met)),
                        "network": f"trained by the oracle ({t_train:.1f} s, untimed)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{tot_traj} learned-proposal trajectories over {args.steps} steps"},
@@ -569,6 +560,244 @@ def run_large(args, local):
     ctx.close()
 
 
+PRESETS = ("fixed_all", "adaptive_threshold", "local_threshold", "adaptive_tracked", "local_tracked")
+
+
+def e4_matrices():
+    """The E4 study's block-diagonal matrices (Sec. 4 known-permanent family)
+    with their exact ln per(A), stored by tests/golden/make_e4_log_permanents.py."""
+    d = json.load(open(os.path.join(ROOT, "tests", "golden", "e4_log_permanents.json")))
+    out = []
+    for r in d["matrices"]:
+        m = G.block_diagonal(r["n"], r["p"], seed=r["seed"], weighted=r["weighted"])
+        assert m.nnz == r["nnz"]
+        out.append((r, m))
+    return out
+
+
+def budget_run(ctx, B, m, sched, budget, seed, first=0, cap=1 << 22):
+    """One estimate of m on a time budget (the paper's runs stop at a time
+    cap, Sec. 4): the trajectories started within `budget` seconds."""
+    sched.time_budget_s = budget
+    t0 = time.perf_counter()
+    r = ctx.estimate_permanent_batch([m], [cap], seed, sched)[0] if first == 0 else \
+        ctx.estimate_batch_ex([m], [cap], seed, sched, first_traj=first)[0][0]
+    r["wall_s"] = time.perf_counter() - t0
+    return r
+
+
+def run_e4(args, local):
+    """NEXT-1: the five presets of Sec. 4 on the known-permanent block-diagonal
+    family (binary and U[1, 1.5] weights, n in {100, 500, 1000, 2000},
+    deletion probability p in {0.1, 0.5, 0.9}) with equal GPU-time budgets,
+    FP32 proposal.  Per preset: trajectories in the budget, RSE, p_match,
+    the realised relative error against the exact permanent, and the trend
+    of the local_threshold / fixed_all trajectory ratio with p (Table 2 and
+    the discussion of Figs. 4-5)."""
+    import torch
+    from paper_2608_15390_b300 import binding as B
+    torch.cuda.set_device(local)
+    ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
+    mats = e4_matrices()
+    rows = []
+    for name in PRESETS:
+        for info, m in mats:
+            r = budget_run(ctx, B, m, B.preset(name), args.study_budget, args.seed)
+            le = r["log_estimate"]
+            err = abs(math.expm1(le - info["log_per"])) if le > -math.inf else 1.0
+            rows.append({"preset": name, "n": info["n"], "p": info["p"], "weighted": info["weighted"],
+                         "traj": r["n_traj"], "rse": r["rse"], "p_match": r["p_match"], "rel_err": err,
+                         "within_3rse": bool(err <= 3 * r["rse"]) if r["rse"] == r["rse"] else False,
+                         "dm_per_traj": r["n_dm_calls"] / max(1, r["n_traj"]),
+                         "sk_iter_per_traj": r["n_full_sk"] / max(1, r["n_traj"]),
+                         "local_per_traj": r["n_local_sk"] / max(1, r["n_traj"])})
+    summary = {}
+    for name in PRESETS:
+        rs = [x for x in rows if x["preset"] == name]
+        summary[name] = {"median_traj": float(np.median([x["traj"] for x in rs])),
+                         "median_rse": float(np.nanmedian([x["rse"] for x in rs])),
+                         "min_p_match": float(min(x["p_match"] for x in rs)),
+                         "median_rel_err": float(np.median([x["rel_err"] for x in rs])),
+                         "within_3rse": sum(x["within_3rse"] for x in rs), "runs": len(rs)}
+    by_p = {}
+    for p in (0.1, 0.5, 0.9):
+        ratio = [l["traj"] / max(1, f["traj"]) for l in rows if l["preset"] == "local_threshold" and l["p"] == p
+                 for f in rows if f["preset"] == "fixed_all" and f["p"] == p and f["n"] == l["n"]
+                 and f["weighted"] == l["weighted"]]
+        by_p[str(p)] = float(np.median(ratio))
+    out = {"workload": "e4", "metric": "five presets on equal GPU-time budgets, known-permanent family",
+           "config": {"budget_s_per_run": args.study_budget, "matrices": len(mats),
+                      "grid": "n in {100,500,1000,2000} x p in {0.1,0.5,0.9} x {binary, U[1,1.5]} "
+                              "(generator seeds 4000+i)", "precision": "FP32 proposal, FP64 log-weights"},
+           "summary": summary, "local_threshold_over_fixed_all_traj_by_p": by_p, "runs": rows,
+           "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def run_theta(args, local):
+    """NEXT-2: sensitivity of the Thrs and Trck DM policies to theta (the
+    paper leaves Trck's open, Sec. 4): the four adaptive / local presets with
+    theta in {0.1, 0.2, 0.33, 0.5, 0.7, 0.9} on a time budget each, on three
+    E4 matrices (n = 1000, binary, p = 0.1 / 0.5 / 0.9) and two ER+planted
+    matrices (n = 500 / 1000, d = 6).  Figure of merit: the work-normalised
+    relative variance RSE^2 x seconds (lower is better; ESS/s ~ 1/that)."""
+    import torch
+    from paper_2608_15390_b300 import binding as B
+    torch.cuda.set_device(local)
+    ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
+    mats = [(f"e4 n=1000 p={i['p']}", m) for i, m in e4_matrices() if i["n"] == 1000 and not i["weighted"]]
+    mats += [(f"er n={n} d=6", G.er_planted(n, 6.0, seed=3100 + n)) for n in (500, 1000)]
+    thetas = (0.1, 0.2, 0.33, 0.5, 0.7, 0.9)
+    rows = []
+    for name in ("adaptive_threshold", "local_threshold", "adaptive_tracked", "local_tracked"):
+        for label, m in mats:
+            for th in thetas:
+                s = B.preset(name)
+                s.theta = th
+                r = budget_run(ctx, B, m, s, args.study_budget, args.seed)
+                wv = r["rse"] ** 2 * r["wall_s"] if r["rse"] == r["rse"] else math.inf
+                rows.append({"preset": name, "matrix": label, "theta": th, "traj": r["n_traj"], "rse": r["rse"],
+                             "p_match": r["p_match"], "dm_per_traj": r["n_dm_calls"] / max(1, r["n_traj"]),
+                             "work_norm_var": wv})
+    best = {}
+    for name in ("adaptive_threshold", "local_threshold", "adaptive_tracked", "local_tracked"):
+        for label, _ in mats:
+            rs = [x for x in rows if x["preset"] == name and x["matrix"] == label]
+            b = min(rs, key=lambda x: x["work_norm_var"])
+            ref = [x for x in rs if x["theta"] == 0.33][0]
+            best[f"{name} | {label}"] = {"best_theta": b["theta"],
+                                         "gain_vs_0.33": ref["work_norm_var"] / b["work_norm_var"]
+                                         if b["work_norm_var"] > 0 else None}
+    out = {"workload": "theta", "metric": "RSE^2 x seconds per (preset, matrix, theta); lower is better",
+           "config": {"budget_s_per_run": args.study_budget, "thetas": thetas}, "best": best, "runs": rows,
+           "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def first_infeasible_steps(m, chosen):
+    """For each traced path, the first step whose child (the residual after
+    removing the chosen pair) has no perfect matching, or -1 (Sec. 2: a
+    residual without a perfect matching contributes X = 0).  A perfect
+    matching of the residual is kept and repaired after each elimination by
+    one alternating breadth-first search (host code)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import maximum_bipartite_matching
+    n = m.n
+    rp, ci = np.asarray(m.row_ptr), np.asarray(m.col_idx)
+    A = csr_matrix((np.ones(len(ci)), ci, rp), shape=(n, n))
+    base = maximum_bipartite_matching(A, perm_type="column")  # row i -> its column
+    out = []
+    for path in chosen:
+        mr = base.copy()
+        mc = np.full(n, -1)
+        mc[mr] = np.arange(n)
+        arow = np.ones(n, bool)
+        acol = np.ones(n, bool)
+        bad = -1
+        for t, (v, u) in enumerate(path):
+            if v < 0:
+                break
+            R, Cc = (v, u - n) if v < n else (u, v - n)
+            arow[R] = False
+            acol[Cc] = False
+            if mr[R] == Cc:
+                continue
+            c_free, r_free = mr[R], mc[Cc]  # their partners lose them
+            mc[c_free] = -1
+            mr[r_free] = -1
+            par = {}
+            frontier, found = [r_free], False
+            while frontier and not found:
+                nxt = []
+                for i in frontier:
+                    for j in ci[rp[i]:rp[i + 1]]:
+                        if not acol[j] or j in par:
+                            continue
+                        par[j] = i
+                        if j == c_free:
+                            found = True
+                            break
+                        nxt.append(mc[j])
+                    if found:
+                        break
+                frontier = nxt
+            if not found:
+                bad = t
+                break
+            j = c_free
+            while True:  # flip the alternating path
+                i = par[j]
+                nj = mr[i]
+                mr[i] = j
+                mc[j] = i
+                if i == r_free:
+                    break
+                j = nj
+        out.append(bad)
+    return out
+
+
+def run_ablation(args, local):
+    """NEXT-4: the row-order vertex rule of Alg. 1 against the two-sided
+    minimum-degree rule (Sec. 3.2, Fig. 2) on ER+planted matrices and E4
+    matrices, plain (outer SK only) and SK(100,10) Adaptive without inner DM,
+    1000 trajectories each (p_match and relative spread, as the paper's
+    sphere3 / Trefethen comparison); and the z-bucket histogram of the first
+    infeasible child along plain two-sided-MD paths (z = r_v c_u of the
+    chosen edge from the outer scaling)."""
+    import torch
+    from paper_2608_15390_b300 import binding as B
+    torch.cuda.set_device(local)
+    ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
+    mats = [(f"er n={n} d=6", G.er_planted(n, 6.0, seed=3200 + n)) for n in (200, 500, 1000)]
+    mats += [(f"e4 n={i['n']} p={i['p']}", m) for i, m in e4_matrices()
+             if i["n"] == 500 and not i["weighted"]]
+    rows = []
+    for label, m in mats:
+        for sk_name, sk in (("plain", B.SK_NONE), ("adaptive_sk", B.SK_ADAPTIVE)):
+            for vr_name, vr in (("row_order", B.VR_ROW_ORDER), ("two_sided_md", B.VR_MIN_DEGREE_2SIDED)):
+                s = B.Schedule(vertex_rule=vr, initial_dm=1, K0=100, K=10, sk=sk, precision=B.PREC_FP32_PROPOSAL)
+                t0 = time.perf_counter()
+                r = ctx.estimate_permanent(m, 1000, args.seed, s)
+                rows.append({"matrix": label, "schedule": sk_name, "vertex_rule": vr_name,
+                             "p_match": r["p_match"], "rel_spread": r["rel_spread"],
+                             "traj_per_s": 1000 / (time.perf_counter() - t0)})
+    # z-bucket histogram of infeasible children (plain two-sided MD, outer SK)
+    edges = np.linspace(0, 1, 11)
+    steps = np.zeros(11)
+    fails = np.zeros(11)
+    s = B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL)
+    for label, m in mats:
+        if m.n > 500:
+            continue
+        pre = ctx.preprocess(m, s)
+        r0, c0 = pre["r"], pre["c"]
+        tr = ctx.trace(m, 100, args.seed, s)
+        bad = first_infeasible_steps(m, tr["chosen"])
+        for q in range(100):
+            for t in range(m.n):
+                v, u = tr["chosen"][q, t]
+                if v < 0:
+                    break
+                R, Cc = (v, u - m.n) if v < m.n else (u, v - m.n)
+                z = float(np.float32(r0[R]) * np.float32(c0[Cc]))
+                b = min(10, int(z * 10))
+                steps[b] += 1
+                if t == bad[q]:
+                    fails[b] += 1
+                    break
+    hist = [{"z_lo": float(edges[b]) if b < 10 else 1.0, "steps": int(steps[b]), "first_infeasible": int(fails[b]),
+             "rate": float(fails[b] / steps[b]) if steps[b] else None} for b in range(11)]
+    out = {"workload": "ablation", "metric": "p_match and relative spread: row order vs two-sided MD; "
+           "z-bucket rate of first infeasible children", "vertex_rule": rows, "z_histogram": hist,
+           "config": {"trajectories": 1000, "histogram": "100 traced plain two-sided-MD paths per matrix "
+                      "with n <= 500; bucket 10 holds z >= 1"}, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -582,6 +811,10 @@ def main():
     if args.workload == "large":
         if rank == 0:
             run_large(args, local)
+        return
+    if args.workload in ("e4", "theta", "ablation"):
+        if rank == 0:
+            {"e4": run_e4, "theta": run_theta, "ablation": run_ablation}[args.workload](args, local)
         return
     import torch
     torch.cuda.set_device(local)
@@ -604,7 +837,7 @@ def main():
     train_rep = model.train(training_matrices(), B.Schedule(**TEACHER), n_pairs=2_000_000, epochs=4,
                             batch=8192, lr=2e-3, seed=12, objective=B.OBJ_CENTRED)
     t_train = time.perf_counter() - t0
-    sched = B.Schedule(**LEARNED, learned=model, rse_target=args.eps)
+    sched = B.Schedule(**LEARNED, learned=model, rse_target=args.eps, time_budget_s=args.budget)
     nt = [TRAJ_CAP] * len(mats)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -622,6 +855,7 @@ def main():
 
     for i in range(args.warmup):
         job(i)
+        print(f"warm-up {i} done", file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
@@ -647,6 +881,8 @@ def main():
         alg_bytes += sum(r["alg_bytes"] for r in res)
         mlp_rows += sum(r["mlp_rows"] for r in res)
         jobs.append(res)
+        print(f"step {i}: {sum(r['stop'] == 1 for r in res)} of {len(res)} matrices at target, "
+              f"{max(r['rounds'] for r in res)} rounds", file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -692,17 +928,20 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "eps": args.eps, "traj_cap_per_matrix": TRAJ_CAP,
+        "config": {"workload": WORKLOAD, "eps": args.eps, "step_budget_s": args.budget,
+                   "traj_cap_per_matrix": TRAJ_CAP,
                    "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "parallelism": f"replicas{world}", "note": note},
         "traj_per_s": tot_traj / t_dev,
         "ess_per_traj": ess_per_traj,
         "job": {"seconds_median": statistics.median(step_s), "rounds_median": rounds_per_job,
-                "matrices_at_target": int(np.mean([js["met"] for js in summ])),
+                "matrices_at_target_mean": float(np.mean([js["met"] for js in summ])),
+                "ess_per_s_at_target": float(sum(js["ess_k"][js["met_k"]].sum() for js in summ)
+                                             / max(1e-12, sum(js["t_k"][js["met_k"]].sum() for js in summ))),
                 "ess_per_matrix_median": float(np.median(ess_k)),
-                "ess_per_matrix_min": float(ess_k.min()),
                 "traj_per_job": tot_traj / args.steps,
-                "ess_definition": "Sec. 2 ESS of each matrix at its stop (RSE <= eps), summed over matrices"},
+                "ess_definition": "Sec. 2 ESS of each matrix at its stop (RSE <= eps, or the step's time "
+                                  "budget for the matrices it censors), summed over matrices and steps"},
         "roofline": {"bound": "hbm", "achieved": achieved_gb, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved_gb / hbm_peak, "traffic": traffic,
                      "kernel": "traj_kernel<float, learned>",
@@ -732,7 +971,7 @@ def main():
                      "loss_last": train_rep["loss_last"], "seconds": t_train,
                      "where": "before the timed region"}
     if not args.no_compare:
-        cmp = compare_arms(ctx, B, dev, args, summ[0]["t_k"], summ[0]["ess_k"])
+        cmp = compare_arms(ctx, B, dev, args, summ[0])
         for name in ("plain_unbatched", "plain_batched", "adaptive_sk_batched"):
             cmp[f"learned_batched_vs_{name}"] = value / cmp[name]["ess_per_s"]
         line["compare"] = cmp

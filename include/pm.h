@@ -82,7 +82,15 @@ typedef struct {
     int32_t sk;            /* pm_sk_policy */
     int32_t dm;            /* pm_dm_policy */
     int32_t precision;     /* pm_precision */
-    int32_t reserved;      /* must be 0 */
+    int32_t local_cap;     /* 0: the Local repair of Eq. 5.  L > 0: a bounded-work variant
+                              (Sec. 3.3 leaves its design open; no counterpart in the paper's
+                              results): the two-hop expansion skips vertices whose adjacency
+                              list in B^(0) (A after the initial DM) holds more than L entries,
+                              and the normalisation sum of such
+                              a vertex is estimated from a systematic sample of L list positions
+                              ((o + q floor(len / L)) mod len, o from a Philox draw of the step)
+                              scaled by deg / (live samples).  Scales only shape the proposal,
+                              so the estimate stays unbiased. */
     double theta;          /* Thrs / Trck threshold theta_th = theta_tr */
     const struct pm_model* learned;  /* NULL: the scaled proposal of Eq. 3.  Otherwise the
                               learned proposal (no counterpart in the paper): candidate l
@@ -153,6 +161,9 @@ typedef struct {
                               durations (%globaltimer, start to end); trajectories of a
                               launch overlap, so a matrix's share of the launch's time
                               is its traj_ns over the launch's total */
+    double dev_ms;         /* this matrix's share of the trajectory kernels' device time:
+                              per launch, the launch's time x traj_ns of this matrix / the
+                              launch's total traj_ns; summed over the launches merged */
     uint32_t rounds;       /* trajectory launches the result merges */
     int32_t stop;          /* PM_STOP_* */
 } pm_result;

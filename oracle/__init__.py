@@ -55,7 +55,7 @@ def build(force: bool = False) -> str:
 class _Schedule(C.Structure):
     _fields_ = [("vertex_rule", C.c_int32), ("initial_dm", C.c_int32), ("K0", C.c_int32),
                 ("K", C.c_int32), ("sk", C.c_int32), ("dm", C.c_int32),
-                ("precision", C.c_int32), ("pad", C.c_int32), ("theta", C.c_double)]
+                ("precision", C.c_int32), ("local_cap", C.c_int32), ("theta", C.c_double)]
 
 
 class _Stats(C.Structure):
@@ -168,10 +168,11 @@ class Schedule:
     dm: int = DM_NONE
     precision: int = PREC_FP64
     theta: float = 0.33
+    local_cap: int = 0  # 0: Local repair of Eq. 5; L > 0: the bounded-work reading (sampled sums)
 
     def c(self) -> _Schedule:
         return _Schedule(self.vertex_rule, self.initial_dm, self.K0, self.K, self.sk, self.dm,
-                         self.precision, 0, self.theta)
+                         self.precision, self.local_cap, self.theta)
 
 
 PRESETS = {

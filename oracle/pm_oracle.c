@@ -165,7 +165,8 @@ enum { DM_NONE = 0, DM_ALL = 1, DM_THRS = 2, DM_TRCK = 3 };
 enum { PREC_FP32 = 0, PREC_FP64 = 1 };
 
 typedef struct {
-    int32_t vertex_rule, initial_dm, K0, K, sk, dm, precision, pad;
+    int32_t vertex_rule, initial_dm, K0, K, sk, dm, precision;
+    int32_t local_cap;  /* 0: the Local repair of Eq. 5; L > 0: its bounded-work variant */
     double theta;
 } or_schedule;
 
@@ -181,6 +182,10 @@ typedef struct {
     or_schedule s;
     int fp32;
     uint8_t* mask0;     /* edges kept by the initial DM (1) */
+    /* B^(0) = A after the initial DM, every trajectory's starting matrix:
+     * its row lists as A's edge ids (b0re, pointers b0rp) and its column
+     * lists as A's CSC positions (b0ck, pointers b0cp), in A's order */
+    int64_t *b0rp, *b0re, *b0cp, *b0ck;
     double* r0;         /* outer scaling, float-valued in FP32 mode */
     double* c0;
     int ok;             /* initial DM found a perfect matching */
@@ -396,11 +401,73 @@ static void sk_sweep(or_traj* T)
     }
 }
 
+/* ---- Bounded-work Local repair.  Sec. 3.3 leaves it to future work: cap
+ * the incident edges examined and approximate the local normalisation sums
+ * by sampling the neighbourhood.  This build's reading, for a cap L > 0, with
+ * lists taken in B^(0) (A after the initial DM: the matrix every trajectory
+ * starts from, whose later residuals only mark entries dead):
+ *   - the two-hop expansion skips a vertex whose B^(0) list (live and dead
+ *     entries) is longer than L: its neighbours keep their scales;
+ *   - the sum of a vertex whose list is longer than L is estimated from a
+ *     systematic sample of L list positions k_q = (o + q s) mod len,
+ *     q = 0..L-1, s = floor(len / L), o = u mod len, u the step's sampling
+ *     word (Philox draw 2048 of the trajectory's step): the terms of the
+ *     live sampled entries summed in sample order, times deg / (their count);
+ *     no live sample keeps the old scale.
+ * Scales only shape the proposal, and the weight uses the realised q, so the
+ * estimator stays unbiased whatever L. ---- */
+#define OR_LOCAL_DRAW 2048u
+
+static double sampled_row_sum(const or_traj* T, int i, const double* c, uint64_t u, int L, int* cnt)
+{
+    const or_prep* P = T->P;
+    const int64_t b = P->b0rp[i], len = P->b0rp[i + 1] - b, s = len / L, o = (int64_t)(u % (uint64_t)len);
+    double acc = 0;
+    int k = 0;
+    for (int q = 0; q < L; ++q) {
+        const int64_t e = P->b0re[b + (o + (int64_t)q * s) % len];
+        const int j = P->ci[e];
+        if (!edge_live(T, e, i, j)) continue;
+        acc = rnd(P->fp32, acc + rnd(P->fp32, entry(P, e) * c[j]));
+        ++k;
+    }
+    *cnt = k;
+    return acc;
+}
+
+static double sampled_col_sum(const or_traj* T, int j, const double* r, uint64_t u, int L, int* cnt)
+{
+    const or_prep* P = T->P;
+    const int64_t b = P->b0cp[j], len = P->b0cp[j + 1] - b, s = len / L, o = (int64_t)(u % (uint64_t)len);
+    double acc = 0;
+    int k = 0;
+    for (int q = 0; q < L; ++q) {
+        const int64_t kk = P->b0ck[b + (o + (int64_t)q * s) % len];
+        const int i = P->ri[kk];
+        const int64_t e = P->ce[kk];
+        if (!edge_live(T, e, i, j)) continue;
+        acc = rnd(P->fp32, acc + rnd(P->fp32, entry(P, e) * r[i]));
+        ++k;
+    }
+    *cnt = k;
+    return acc;
+}
+
+/* new scale of a vertex from its (possibly sampled) sum: 1 / (sum deg / cnt) */
+static double scale_from_sample(const or_prep* P, double old, double sum, int deg, int cnt)
+{
+    if (cnt == 0) return old;
+    const double est = rnd(P->fp32, rnd(P->fp32, sum * (double)deg) / (double)cnt);
+    return rnd(P->fp32, 1.0 / est);
+}
+
 /* ---- Local repair (Eq. 5).  nR/nC: N_t(C)\{R} (rows) and N_t(R)\{C}
  * (columns), collected before elimination. R_loc = nR U N_{t+1}(nC),
  * C_loc = nC U N_{t+1}(nR); new values use only the old vectors and are
- * committed together. ---- */
-static void local_repair(or_traj* T, const int32_t* nR, int cntR, const int32_t* nC, int cntC)
+ * committed together.  cap L > 0: the bounded-work variant above, u the
+ * step's sampling word. ---- */
+static void local_repair(or_traj* T, const int32_t* nR, int cntR, const int32_t* nC, int cntC, int L,
+                         uint64_t u)
 {
     const or_prep* P = T->P;
     const int n = P->n;
@@ -412,11 +479,13 @@ static void local_repair(or_traj* T, const int32_t* nR, int cntR, const int32_t*
     for (int q = 0; q < cntC; ++q) ADD_C(nC[q]);
     for (int q = 0; q < cntC; ++q) { /* child neighbours of the columns in nC */
         int j = nC[q];
+        if (L > 0 && P->b0cp[j + 1] - P->b0cp[j] > L) continue;
         for (int64_t k = P->cp[j]; k < P->cp[j + 1]; ++k)
             if (edge_live(T, P->ce[k], P->ri[k], j)) ADD_R(P->ri[k]);
     }
     for (int q = 0; q < cntR; ++q) { /* child neighbours of the rows in nR */
         int i = nR[q];
+        if (L > 0 && P->b0rp[i + 1] - P->b0rp[i] > L) continue;
         for (int64_t e = P->rp[i]; e < P->rp[i + 1]; ++e)
             if (edge_live(T, e, i, P->ci[e])) ADD_C(P->ci[e]);
     }
@@ -424,11 +493,27 @@ static void local_repair(or_traj* T, const int32_t* nR, int cntR, const int32_t*
 #undef ADD_C
     for (int q = 0; q < lr; ++q) {
         int i = T->listr[q];
-        T->newr[q] = (T->deg[i] == 0) ? T->r[i] : rnd(P->fp32, 1.0 / row_sum(T, i, T->c));
+        if (T->deg[i] == 0) {
+            T->newr[q] = T->r[i];
+        } else if (L > 0 && P->b0rp[i + 1] - P->b0rp[i] > L) {
+            int cnt;
+            const double sm = sampled_row_sum(T, i, T->c, u, L, &cnt);
+            T->newr[q] = scale_from_sample(P, T->r[i], sm, T->deg[i], cnt);
+        } else {
+            T->newr[q] = rnd(P->fp32, 1.0 / row_sum(T, i, T->c));
+        }
     }
     for (int q = 0; q < lc; ++q) {
         int j = T->listc[q];
-        T->newc[q] = (T->deg[n + j] == 0) ? T->c[j] : rnd(P->fp32, 1.0 / col_sum(T, j, T->r));
+        if (T->deg[n + j] == 0) {
+            T->newc[q] = T->c[j];
+        } else if (L > 0 && P->b0cp[j + 1] - P->b0cp[j] > L) {
+            int cnt;
+            const double sm = sampled_col_sum(T, j, T->r, u, L, &cnt);
+            T->newc[q] = scale_from_sample(P, T->c[j], sm, T->deg[n + j], cnt);
+        } else {
+            T->newc[q] = rnd(P->fp32, 1.0 / col_sum(T, j, T->r));
+        }
     }
     for (int q = 0; q < lr; ++q) T->r[T->listr[q]] = T->newr[q];
     for (int q = 0; q < lc; ++q) T->c[T->listc[q]] = T->newc[q];
@@ -517,6 +602,20 @@ or_prep* or_prepare(int n, int64_t m, const int64_t* rp, const int32_t* ci, cons
     if (P->ok)
         for (int k = 0; k < s->K0; ++k) sk_sweep(T);
     memcpy(P->mask0, T->mask, (size_t)m);
+    P->b0rp = (int64_t*)xcalloc(n + 1, 8);
+    P->b0cp = (int64_t*)xcalloc(n + 1, 8);
+    P->b0re = (int64_t*)xcalloc(m, 8);
+    P->b0ck = (int64_t*)xcalloc(m, 8);
+    for (int i = 0; i < n; ++i) {
+        P->b0rp[i + 1] = P->b0rp[i];
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+            if (P->mask0[e]) P->b0re[P->b0rp[i + 1]++] = e;
+    }
+    for (int j = 0; j < n; ++j) {
+        P->b0cp[j + 1] = P->b0cp[j];
+        for (int64_t k = P->cp[j]; k < P->cp[j + 1]; ++k)
+            if (P->mask0[P->ce[k]]) P->b0ck[P->b0cp[j + 1]++] = k;
+    }
     memcpy(P->r0, T->r, (size_t)n * 8);
     memcpy(P->c0, T->c, (size_t)n * 8);
     traj_free(T);
@@ -527,6 +626,7 @@ void or_prep_free(or_prep* P)
 {
     if (!P) return;
     free(P->cp); free(P->ri); free(P->ce); free(P->mask0); free(P->r0); free(P->c0);
+    free(P->b0rp); free(P->b0re); free(P->b0cp); free(P->b0ck);
     free(P);
 }
 
@@ -971,7 +1071,8 @@ static void run_trajectory(or_traj* T, uint64_t seed, uint64_t traj, uint32_t ma
                 for (int q = 0; q < nit; ++q) sk_sweep(T);
                 res->n_full_sk += nit;
             } else if (s->sk == SK_LOCAL) {
-                local_repair(T, T->nbrR, cntR, T->nbrC, cntC);
+                local_repair(T, T->nbrR, cntR, T->nbrC, cntC, s->local_cap,
+                             s->local_cap > 0 ? or_draw_u64(seed, traj, matrix, (uint32_t)t, OR_LOCAL_DRAW) : 0);
                 res->n_local_sk++;
             }
         }

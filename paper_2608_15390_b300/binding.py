@@ -47,7 +47,7 @@ class pm_csr(C.Structure):
 class pm_schedule(C.Structure):
     _fields_ = [("vertex_rule", C.c_int32), ("initial_dm", C.c_int32), ("K0", C.c_int32),
                 ("K", C.c_int32), ("sk", C.c_int32), ("dm", C.c_int32), ("precision", C.c_int32),
-                ("reserved", C.c_int32), ("theta", C.c_double), ("learned", C.c_void_p),
+                ("local_cap", C.c_int32), ("theta", C.c_double), ("learned", C.c_void_p),
                 ("rse_target", C.c_double), ("time_budget_s", C.c_double)]
 
 
@@ -88,7 +88,7 @@ class pm_result(C.Structure):
                 ("log_sum_x", C.c_double), ("log_sum_x2", C.c_double), ("n_traj", C.c_uint64),
                 ("n_alive", C.c_uint64), ("n_dm_calls", C.c_uint64), ("n_full_sk", C.c_uint64),
                 ("n_local_sk", C.c_uint64), ("seconds", C.c_double), ("alg_bytes", C.c_uint64),
-                ("kernel_ms", C.c_double), ("mlp_rows", C.c_uint64), ("traj_ns", C.c_uint64), ("rounds", C.c_uint32),
+                ("kernel_ms", C.c_double), ("mlp_rows", C.c_uint64), ("traj_ns", C.c_uint64), ("dev_ms", C.c_double), ("rounds", C.c_uint32),
                 ("stop", C.c_int32)]
 
     def as_dict(self) -> dict:
@@ -237,10 +237,11 @@ class Schedule:
     learned: Optional["Model"] = None
     rse_target: float = 0.0
     time_budget_s: float = 0.0
+    local_cap: int = 0
 
     def c(self) -> pm_schedule:
         return pm_schedule(self.vertex_rule, self.initial_dm, self.K0, self.K, self.sk, self.dm,
-                           self.precision, 0, self.theta,
+                           self.precision, self.local_cap, self.theta,
                            None if self.learned is None else self.learned.h.value,
                            self.rse_target, self.time_budget_s)
 

@@ -125,7 +125,7 @@ pm_status check_schedule(pm_context* ctx, const pm_schedule* s)
     if (s->sk < 0 || s->sk > 3) return fail(ctx, PM_EINVAL, "bad sk policy");
     if (s->dm < 0 || s->dm > 3) return fail(ctx, PM_EINVAL, "bad dm policy");
     if (s->precision < 0 || s->precision > 1) return fail(ctx, PM_EINVAL, "bad precision");
-    if (s->K0 < 0 || s->K < 0 || s->reserved != 0) return fail(ctx, PM_EINVAL, "bad K0/K/reserved");
+    if (s->K0 < 0 || s->K < 0 || s->local_cap < 0) return fail(ctx, PM_EINVAL, "bad K0/K/local_cap");
     if (!(s->theta == s->theta)) return fail(ctx, PM_EINVAL, "theta is NaN");
     if (!(s->rse_target >= 0 && s->rse_target < INFINITY)) return fail(ctx, PM_EINVAL, "bad rse_target");
     if (!(s->time_budget_s >= 0 && s->time_budget_s < INFINITY)) return fail(ctx, PM_EINVAL, "bad time_budget_s");
@@ -743,6 +743,8 @@ pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, doubl
     ctx->last_h2d = S.h2d;
     ctx->last_d2h = d2h;
     if (R.outs) {
+        double ns_total = 0;
+        for (int k = 0; k < count; ++k) ns_total += (double)S.h_cnt[kCounters * k + 5];
         for (int k = 0; k < count; ++k) {
             pm_result& o = R.outs[k];
             std::memset(&o, 0, sizeof(o));
@@ -765,6 +767,8 @@ pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, doubl
             o.traj_ns = S.h_cnt[kCounters * k + 5];
             o.kernel_ms = ctx->last_traj_ms;
             o.seconds = secs;
+            o.dev_ms = (ns_total > 0 && ctx->last_traj_ms > 0)
+                           ? ctx->last_traj_ms * (double)o.traj_ns / ns_total : 0.0;
             o.rounds = 1;
             o.stop = (S.stop_bits & ST_CANCELLED) ? PM_STOP_CANCELLED
                      : (S.stop_bits & ST_TIMEOUT) ? PM_STOP_TIME : PM_STOP_COMPLETE;
@@ -809,7 +813,7 @@ pm_status execute(pm_context* ctx, Run& R)
 // counts; merged exactly in any order.
 struct Suff {
     uint64_t n = 0, alive = 0, n_dm = 0, n_full = 0, n_loc = 0, alg = 0, mlp = 0, traj_ns = 0;
-    double lse1 = -INFINITY, lse2 = -INFINITY, kernel_ms = 0, seconds = 0;
+    double lse1 = -INFINITY, lse2 = -INFINITY, kernel_ms = 0, seconds = 0, dev_ms = 0;
     uint32_t rounds = 0;
     static double lse_add(double a, double b)
     {
@@ -832,6 +836,7 @@ struct Suff {
         alg += o.alg_bytes;
         mlp += o.mlp_rows;
         traj_ns += o.traj_ns;
+        dev_ms += o.dev_ms;
         kernel_ms += o.kernel_ms > 0 ? o.kernel_ms : 0;
         seconds += o.seconds > 0 ? o.seconds : 0;
         rounds += o.rounds;
@@ -849,6 +854,7 @@ struct Suff {
         o.alg_bytes = alg;
         o.mlp_rows = mlp;
         o.traj_ns = traj_ns;
+        o.dev_ms = dev_ms;
         o.kernel_ms = kernel_ms;
         o.seconds = seconds;
         o.rounds = rounds;
@@ -1079,7 +1085,7 @@ static Sched to_sched(const pm_schedule* s)
 {
     Sched o;
     o.vertex_rule = s->vertex_rule; o.initial_dm = s->initial_dm; o.K0 = s->K0; o.K = s->K;
-    o.sk = s->sk; o.dm = s->dm; o.precision = s->precision; o.reserved = 0; o.theta = s->theta;
+    o.sk = s->sk; o.dm = s->dm; o.precision = s->precision; o.local_cap = s->local_cap; o.theta = s->theta;
     return o;
 }
 

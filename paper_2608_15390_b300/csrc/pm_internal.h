@@ -14,6 +14,9 @@ constexpr int kMaxN = 1 << 22;
 constexpr int kMaxDegree = 65534;
 constexpr int kMaxTreeLevels = 4;
 constexpr int kMaxRngAttempts = 256;
+// Philox draw index of a step's sampling word for the bounded-work Local
+// repair (beyond every draw the partner sampling can take)
+constexpr uint32_t kLocalDraw = 2048;
 
 // device status word bits
 enum : uint32_t {
@@ -60,7 +63,8 @@ struct DevMatrix {
 };
 
 struct Sched {
-    int vertex_rule, initial_dm, K0, K, sk, dm, precision, reserved;
+    int vertex_rule, initial_dm, K0, K, sk, dm, precision;
+    int local_cap;  // 0: the Local repair of Eq. 5; L > 0: its bounded-work variant
     double theta;
 };
 

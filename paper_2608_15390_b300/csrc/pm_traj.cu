@@ -269,22 +269,61 @@ __device__ void sk_iteration(const MV<Idx>& V, const uint8_t* mask, Real* r, Rea
     gsync(G);
 }
 
+// Bounded-work Local repair (cap L > 0; Sec. 3.3 leaves the design open): the
+// new scale of a vertex whose list in B^(0) (the matrix the trajectories run
+// on, compacted after the initial DM) holds more than L entries, from the L
+// list positions (o + q floor(len / L)) mod len, o = u mod len: the live
+// sampled terms summed in sample order, times deg / (their count); no live
+// sample keeps the old scale.  Explicit liveness tests (the count matters).
+template <typename Real, typename Idx>
+__device__ Real sampled_scale(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, const Real* sc, bool row,
+                              int x, uint64_t u, int L, Real old)
+{
+    const int n = V.n;
+    const int b = row ? V.rp[x] : V.cp[x];
+    const int len = (row ? V.rp[x + 1] : V.cp[x + 1]) - b;
+    const int s = len / L;
+    const int o = (int)(u % (uint64_t)len);
+    Real acc = 0;
+    int cnt = 0;
+    for (int q = 0; q < L; ++q) {
+        const int k = b + (int)(((long long)o + (long long)q * s) % len);
+        int p, e;
+        if (row) { p = n + (int)V.ci[k]; e = k; }
+        else { p = (int)V.ri[k]; e = V.ce[k]; }
+        if (deg[p] == kInact || (mask && !mask[e])) continue;
+        Real t = sc[row ? p - n : p];
+        const float* vals = row ? V.rv : V.cv;
+        if (vals) t = RA<Real>::mul((Real)__ldg(vals + k), t);
+        acc = RA<Real>::add(acc, t);
+        ++cnt;
+    }
+    if (cnt == 0) return old;
+    const Real est = RA<Real>::div(RA<Real>::mul(acc, (Real)deg[row ? x : n + x]), (Real)cnt);
+    return RA<Real>::rcp(est);
+}
+
 // Local repair (Eq. 5) by the leader warp.  lr: N_t(C)\{R} (rows), lc:
 // N_t(R)\{C} (columns).  R_loc = lr U N_{t+1}(lc), C_loc = lc U N_{t+1}(lr).
 // New row scales read the old c and are staged (deduplicated by stamp);
 // column scales read the old r and are written in place; staged rows commit
-// last.  Returns the number of staged rows.
+// last.  With a cap L > 0, lists longer than L are not expanded and their
+// sums are sampled (sampled_scale, u the step's sampling word).  Returns the
+// number of staged rows.
 template <typename Real, typename Idx>
 __device__ int local_repair(const MV<Idx>& V, const uint16_t* deg, const uint8_t* mask, Real* r, Real* c,
                             const int* lr, int nr, const int* lc, int nc, int* stamp, int st, int* tmp_id,
-                            Real* tmp_val, int* tmp_cnt, int lane)
+                            Real* tmp_val, int* tmp_cnt, int lane, int L, uint64_t u)
 {
     const int n = V.n;
     if (lane == 0) *tmp_cnt = 0;
     __syncwarp();
     auto stage_row = [&](int i) {
         if (atomicExch(&stamp[i], st) == st) return;
-        const Real v = (deg[i] == 0) ? r[i] : RA<Real>::rcp(row_sum<Real, Idx>(V, mask, c, i));
+        Real v;
+        if (deg[i] == 0) v = r[i];
+        else if (L > 0 && V.rp[i + 1] - V.rp[i] > L) v = sampled_scale<Real, Idx>(V, deg, mask, c, true, i, u, L, r[i]);
+        else v = RA<Real>::rcp(row_sum<Real, Idx>(V, mask, c, i));
         const int q = atomicAdd(tmp_cnt, 1);
         tmp_id[q] = i;
         tmp_val[q] = v;
@@ -292,6 +331,7 @@ __device__ int local_repair(const MV<Idx>& V, const uint16_t* deg, const uint8_t
     for (int q = lane; q < nr; q += 32) stage_row(lr[q]);
     for (int q = lane; q < nc; q += 32) {
         const int j = lc[q];
+        if (L > 0 && V.cp[j + 1] - V.cp[j] > L) continue;
         for (int k = V.cp[j]; k < V.cp[j + 1]; ++k) {
             const int i = V.ri[k];
             if (deg[i] == kInact || (mask && !mask[V.ce[k]])) continue;
@@ -300,11 +340,14 @@ __device__ int local_repair(const MV<Idx>& V, const uint16_t* deg, const uint8_t
     }
     __syncwarp();
     auto col_new = [&](int j) {
-        c[j] = (deg[n + j] == 0) ? c[j] : RA<Real>::rcp(col_sum<Real, Idx>(V, mask, r, j));
+        if (deg[n + j] == 0) return;
+        if (L > 0 && V.cp[j + 1] - V.cp[j] > L) c[j] = sampled_scale<Real, Idx>(V, deg, mask, r, false, j, u, L, c[j]);
+        else c[j] = RA<Real>::rcp(col_sum<Real, Idx>(V, mask, r, j));
     };
     for (int q = lane; q < nc; q += 32) col_new(lc[q]);
     for (int q = lane; q < nr; q += 32) {
         const int i = lr[q];
+        if (L > 0 && V.rp[i + 1] - V.rp[i] > L) continue;
         for (int k = V.rp[i]; k < V.rp[i + 1]; ++k) {
             const int j = V.ci[k];
             if (deg[n + j] == kInact || (mask && !mask[k])) continue;
@@ -412,15 +455,22 @@ __device__ __forceinline__ int neighbour_degree_sum_flat(const MV<Idx>& V, const
     entries = total;
     acc[lane] = 0;
     __syncwarp();
-    const unsigned lm = __ballot_sync(kFull, live && len > 0);
+    const bool has = live && len > 0;
+    const unsigned lm = __ballot_sync(kFull, has);
     for (int base = 0; base < total; base += 32) {
         const int f = base + lane;
+        // the candidate whose range holds f is the last one starting at or
+        // before f: candidates starting before this chunk, plus the starts
+        // inside it up to f (ranges are contiguous in lane order)
+        const unsigned before = __ballot_sync(kFull, has && excl < base);
+        const unsigned starts =
+            __reduce_or_sync(kFull, (has && excl >= base && excl < base + 32) ? 1u << (excl - base) : 0u);
+        const int rank = __popc(before) + __popc(starts & (0xFFFFFFFFu >> (31 - lane)));
         int owner = -1, pos = 0;
-        for (unsigned mk = lm; mk; mk &= mk - 1u) {  // the candidate whose range holds f
-            const int c = __ffs(mk) - 1;
-            const int ce0 = __shfl_sync(kFull, excl, c), cl = __shfl_sync(kFull, len, c), cb = __shfl_sync(kFull, b, c);
-            if (f >= ce0 && f < ce0 + cl) { owner = c; pos = cb + (f - ce0); }
-        }
+        if (f < total) owner = (int)__fns(lm, 0, rank);  // lane of the rank-th candidate
+        const int src = owner >= 0 ? owner : 0;
+        const int oe = __shfl_sync(kFull, excl, src), ob = __shfl_sync(kFull, b, src);
+        if (owner >= 0) pos = ob + (f - oe);
         if (owner >= 0) {
             unsigned d;
             bool ok;
@@ -1034,8 +1084,9 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         } else if (use_local) {
             if (leader) {
                 const int cr = mb[M_CNTR], cc = mb[M_CNTC];
+                const uint64_t us = S.local_cap > 0 ? draw_u64(P.seed, traj, midx, (uint32_t)t, kLocalDraw) : 0;
                 const int staged = local_repair<Real, Idx>(V, deg, mask, r, c, list_r, cr, list_c, cc, stamp, t + 1,
-                                                           tmp_id, tmp_val, G.misc + M_TMP, lane);
+                                                           tmp_id, tmp_val, G.misc + M_TMP, lane, S.local_cap, us);
                 ++n_loc;
                 alg_bytes += (uint64_t)16 * (uint64_t)(staged + cr + cc);
             }

@@ -26,7 +26,7 @@ def ctx():
 def to_gpu_sched(s: "O.Schedule"):
     b = binding()
     return b.Schedule(vertex_rule=s.vertex_rule, initial_dm=s.initial_dm, K0=s.K0, K=s.K, sk=s.sk,
-                      dm=s.dm, precision=s.precision, theta=s.theta)
+                      dm=s.dm, precision=s.precision, theta=s.theta, local_cap=s.local_cap)
 
 
 def logx_close(a, b, tol):

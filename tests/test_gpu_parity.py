@@ -91,6 +91,19 @@ def test_long_adjacency_lists():
 
 
 @pytest.mark.parametrize("prec", FP)
+@pytest.mark.parametrize("cap", [4, 16, 64])
+def test_bounded_local_repair_power_law_hubs(prec, cap):
+    """The bounded-work Local repair (a reading of the variant Sec. 3.3
+    leaves open): power-law rows with hubs of 60-360 entries, so hubs are
+    neither expanded nor summed exactly but sampled with the step's Philox
+    offset; local_threshold and local_tracked, both precisions."""
+    for name, n, seed in (("local_threshold", 400, 2), ("local_tracked", 800, 1)):
+        s = O.preset(name, prec)
+        s.local_cap = cap
+        compare_trace(G.powerlaw_planted(n, seed=seed), s, 24, seed=5)
+
+
+@pytest.mark.parametrize("prec", FP)
 def test_two_level_degree_tree(prec):
     # 2n > 1024 leaves: the minimum-degree tree has two stored levels
     m = G.er_planted(700, 5.0, seed=17)

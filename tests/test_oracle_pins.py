@@ -168,6 +168,11 @@ SCHEDULES = {
     "local_threshold_fp32": O.preset("local_threshold", precision=O.PREC_FP32),
     "adaptive_threshold_fp32": O.preset("adaptive_threshold", precision=O.PREC_FP32),
     "fixed_none_fp32": O.Schedule(K0=5, K=3, sk=O.SK_FIXED, precision=O.PREC_FP32),
+    # the bounded-work Local repair (cap 2: lists of 3+ entries are sampled
+    # and not expanded); any scaling keeps E[X] = per(A)
+    "local_threshold_cap2": O.Schedule(initial_dm=1, K0=100, K=10, sk=O.SK_LOCAL, dm=O.DM_THRS, local_cap=2),
+    "local_tracked_cap2_fp32": O.Schedule(initial_dm=1, K0=100, K=10, sk=O.SK_LOCAL, dm=O.DM_TRCK,
+                                          local_cap=2, precision=O.PREC_FP32),
 }
 
 
@@ -204,6 +209,23 @@ def test_enumeration_is_unbiased(name, case):
     assert est == pytest.approx(per, rel=1e-12)
     if SCHEDULES[name].dm == O.DM_ALL:
         assert all(ds < 0 for _, _, ds, _ in leaves)  # DM on every child: p_match = 1
+
+
+def test_bounded_local_with_a_cap_above_every_list_is_eq5():
+    """A cap at least as long as every adjacency list samples nothing and
+    expands everything: the Local repair of Eq. 5 itself."""
+    A = G.powerlaw_planted(300, seed=2)
+    longest = int(max(np.diff(A.row_ptr).max(), np.bincount(A.col_idx, minlength=A.n).max()))
+    for prec in (O.PREC_FP64, O.PREC_FP32):
+        exact = O.Prepared(A, O.preset("local_threshold", prec)).run(seed=3, count=32, trace=True)
+        s = O.preset("local_threshold", prec)
+        s.local_cap = longest
+        capped = O.Prepared(A, s).run(seed=3, count=32, trace=True)
+        assert np.array_equal(exact["chosen"], capped["chosen"])
+        assert np.array_equal(exact["log_x"], capped["log_x"])
+        s.local_cap = 8  # hubs are sampled: other scales, other paths
+        small = O.Prepared(A, s).run(seed=3, count=32, trace=True)
+        assert not np.array_equal(exact["chosen"], small["chosen"])
 
 
 def test_enumeration_zero_permanent():
