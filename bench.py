@@ -563,15 +563,27 @@ def run_large(args, local):
 PRESETS = ("fixed_all", "adaptive_threshold", "local_threshold", "adaptive_tracked", "local_tracked")
 
 
-def e4_matrices():
-    """The E4 study's block-diagonal matrices (Sec. 4 known-permanent family)
-    with their exact ln per(A), stored by tests/golden/make_e4_log_permanents.py."""
-    d = json.load(open(os.path.join(ROOT, "tests", "golden", "e4_log_permanents.json")))
+# the E4 study's grid (as tests/golden/make_e4_log_permanents.py): order,
+# deletion probability, weights; generator seed 4000 + index
+E4_GRID = [(n, p, w) for n in (100, 500, 1000, 2000) for p in (0.1, 0.5, 0.9) for w in (False, True)]
+
+
+def e4_matrices(with_permanents=True):
+    """The E4 study's block-diagonal matrices (Sec. 4 known-permanent family),
+    with their exact ln per(A) as stored by
+    tests/golden/make_e4_log_permanents.py when with_permanents."""
+    pers = {}
+    if with_permanents:
+        d = json.load(open(os.path.join(ROOT, "tests", "golden", "e4_log_permanents.json")))
+        pers = {r["index"]: r for r in d["matrices"]}
     out = []
-    for r in d["matrices"]:
-        m = G.block_diagonal(r["n"], r["p"], seed=r["seed"], weighted=r["weighted"])
-        assert m.nnz == r["nnz"]
-        out.append((r, m))
+    for i, (n, p, w) in enumerate(E4_GRID):
+        m = G.block_diagonal(n, p, seed=4000 + i, weighted=w)
+        info = {"index": i, "n": n, "p": p, "weighted": w, "seed": 4000 + i}
+        if with_permanents:
+            assert pers[i]["nnz"] == m.nnz and pers[i]["n"] == n
+            info["log_per"] = pers[i]["log_per"]
+        out.append((info, m))
     return out
 
 
@@ -646,7 +658,7 @@ def run_theta(args, local):
     from paper_2608_15390_b300 import binding as B
     torch.cuda.set_device(local)
     ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
-    mats = [(f"e4 n=1000 p={i['p']}", m) for i, m in e4_matrices() if i["n"] == 1000 and not i["weighted"]]
+    mats = [(f"e4 n=1000 p={i['p']}", m) for i, m in e4_matrices(False) if i["n"] == 1000 and not i["weighted"]]
     mats += [(f"er n={n} d=6", G.er_planted(n, 6.0, seed=3100 + n)) for n in (500, 1000)]
     thetas = (0.1, 0.2, 0.33, 0.5, 0.7, 0.9)
     rows = []
@@ -752,7 +764,7 @@ def run_ablation(args, local):
     torch.cuda.set_device(local)
     ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
     mats = [(f"er n={n} d=6", G.er_planted(n, 6.0, seed=3200 + n)) for n in (200, 500, 1000)]
-    mats += [(f"e4 n={i['n']} p={i['p']}", m) for i, m in e4_matrices()
+    mats += [(f"e4 n={i['n']} p={i['p']}", m) for i, m in e4_matrices(False)
              if i["n"] == 500 and not i["weighted"]]
     rows = []
     for label, m in mats:

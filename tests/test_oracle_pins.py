@@ -488,3 +488,19 @@ def test_prefix_replay_matches_full_run():
     alive = full["dead_step"] < 0
     assert np.array_equal(pre["chosen"][:, :50], full["chosen"][:, :50])
     assert np.all(pre["chosen"][alive, 50:] == -1)
+
+
+def test_e4_golden_log_permanents_reproduce():
+    """The stored exact ln per(A) of the E4 study (tests/golden/
+    make_e4_log_permanents.py) for the binary n = 100 matrices (integer
+    Ryser, fast), recomputed from the block product (Sec. 4 known-permanent
+    family)."""
+    import json
+    d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "e4_log_permanents.json")))
+    for r in d["matrices"]:
+        if r["n"] != 100 or r["weighted"]:
+            continue
+        m = G.block_diagonal(r["n"], r["p"], seed=r["seed"], weighted=r["weighted"])
+        lp = sum(math.log(O.ryser_real(b) if r["weighted"] else O.ryser(b)) for b in m.blocks)
+        assert lp == pytest.approx(r["log_per"], rel=1e-12)
+        assert m.nnz == r["nnz"] and len(m.blocks) == r["blocks"]
