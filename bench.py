@@ -82,10 +82,17 @@ def parse():
     p.add_argument("--mats", type=int, default=N_MATS,
                    help="use the first K matrices (profiling of a smaller case)")
     p.add_argument("--study-budget", type=float, default=2.0, help="seconds per run of the e4 / theta studies")
-    p.add_argument("--workload", default="batch", choices=["batch", "serving", "large", "e4", "theta", "ablation"],
+    p.add_argument("--theta", type=float, default=0.1, help="large workload: Thrs threshold of local_threshold")
+    p.add_argument("--large-budget", type=float, default=60.0, help="large workload: seconds of the filtering run")
+    p.add_argument("--train-mats", type=int, default=100, help="learned workload: training matrices (n = 1e4)")
+    p.add_argument("--train-pairs", type=int, default=10_000_000, help="learned workload: training pairs")
+    p.add_argument("--workload", default="batch",
+                   choices=["batch", "serving", "large", "e4", "theta", "ablation", "learned"],
                    help="batch: the 64-matrix batch (the metric); serving: the Poisson request stream; "
                         "large: one n = 1e5 band matrix (state in global memory)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of each serving load")
+    p.add_argument("--serve-estimator", default="learned", choices=["learned", "local", "local_capped"],
+                   help="estimator of the serving workload")
     p.add_argument("--nmax", type=int, default=N_HI,
                    help="draw n from U{100..nmax} instead (profiling of a smaller case)")
     return p.parse_args()
@@ -437,11 +444,16 @@ def run_serving(args, local):
     from paper_2608_15390_b300 import binding as B
     torch.cuda.set_device(local)
     ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
-    model = ctx.model(seed=21)
-    train = [G.powerlaw_planted(n, seed=900 + k) for k, n in enumerate(np.geomspace(50, 3000, 16).astype(int))]
-    model.train(train, B.Schedule(**TEACHER), n_pairs=1_000_000, epochs=4, batch=8192, lr=2e-3, seed=22,
-                objective=B.OBJ_CENTRED)
-    sched = B.Schedule(**LEARNED, learned=model)
+    model = None
+    if args.serve_estimator == "learned":
+        model = ctx.model(seed=21)
+        train = [G.powerlaw_planted(n, seed=900 + k) for k, n in enumerate(np.geomspace(50, 3000, 16).astype(int))]
+        model.train(train, B.Schedule(**TEACHER), n_pairs=1_000_000, epochs=4, batch=8192, lr=2e-3, seed=22,
+                    objective=B.OBJ_CENTRED)
+        sched = B.Schedule(**LEARNED, learned=model)
+    else:  # Local SK repair after every step (no inner DM), exact or with the bounded-work cap
+        sched = B.Schedule(initial_dm=1, K0=100, K=10, sk=B.SK_LOCAL, dm=B.DM_NONE, precision=B.PREC_FP32_PROPOSAL,
+                           local_cap=32 if args.serve_estimator == "local_capped" else 0)
 
     def make_server():
         return ctx.server(sched, seed=args.seed, device_budget_bytes=32 << 30, steps_per_round=1 << 22,
@@ -496,12 +508,17 @@ def run_serving(args, local):
         line.update({"load": frac, "arrival_rate_req_per_s": rate, "arrivals": len(pending)})
         loads.append(line)
         sv.close()
-    model.close()
+    if model is not None:
+        model.close()
     out = {"metric": "serving: p50 / p99 latency and throughput at RSE <= 1e-2", "workload": "serving",
            "config": {"requests": "n = floor(exp U[ln 50, ln 5e4]), power-law rows (2.5, min 2) + planted "
                                   "permutation, RSE target 1e-2, budget 2^26 trajectory steps each "
                                   "(1024 to 2^16 trajectories)",
-                      "estimator": "learned proposal, two-sided MD, initial DM, outer SK(100)",
+                      "estimator": {"learned": "learned proposal, two-sided MD, initial DM, outer SK(100)",
+                                    "local": "Local SK repair after every step (Eq. 5, exact), initial DM, "
+                                             "outer SK(100), no inner DM",
+                                    "local_capped": "the same with the bounded-work Local repair, cap 32"
+                                    }[args.serve_estimator],
                       "admission": "device bytes of admitted requests <= 32 GiB, first come first served",
                       "arrival_window_s": args.serve_seconds},
            "capacity_req_per_s": capacity, "capacity_run": cap_line, "loads": loads, "data": "synthetic"}
@@ -513,19 +530,28 @@ def run_large(args, local):
     """The large sparse configuration: n = 1e5, width-3 band (|i-j| <= 1) plus a
     planted permutation plus uniform off-band entries up to m = 5e5 (generator
     seed 3).  Each trajectory's degrees and tree live in global memory (the
-    group's slot), so the trajectory kernel is bound by L2/HBM traffic: the
-    line reports trajectories/s and the algorithmic bytes against the HBM
-    copy peak.  The schedules with inner SK or DM are out of reach at this size
-    (every full sweep or DM call touches all 5e5 edges), so the estimator is
-    the plain one (two-sided MD, initial DM, outer SK(100)) on a slice of the
-    configuration's 2^20 trajectories: --steps waves of one trajectory per
-    group slot of the GPU."""
+    group's slot).  Two estimators:
+      plain             two-sided MD, initial DM, outer SK(100): --steps waves
+                        of one trajectory per group slot of the GPU (a resident
+                        batch replayed from a CUDA graph);
+      local_threshold   the filtering schedule of Sec. 3.3 (Local SK repair,
+                        Thrs DM at theta = --theta) on a time budget of
+                        --large-budget seconds, up to 2^20 trajectories: a
+                        16-warp group per trajectory shares each DM call's
+                        component step.
+    Each line reports trajectories, p_match, RSE, ESS and the algorithmic
+    bytes against the measured HBM copy peak."""
     import torch
     from paper_2608_15390_b300 import binding as B
     torch.cuda.set_device(local)
     ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
     m = G.band_random(100_000, 500_000, seed=3)
     dev = G.Csr(m.n, torch.from_numpy(m.row_ptr).cuda(), torch.from_numpy(m.col_idx).cuda())
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0
+    matrix = ("n=1e5, |i-j|<=1 band + planted permutation + uniform off-band entries to m=5e5 (generator seed 3)")
+    out = []
+    # plain
     sched = B.Schedule(**LEARNED)
     props = torch.cuda.get_device_properties(local)
     T = props.multi_processor_count * 16
@@ -535,27 +561,42 @@ def run_large(args, local):
     runs, kern, alg = [], 0.0, 0
     for i in range(args.steps):
         res, _ = bt.run((i + 1) * T, args.seed)
-        info = ctx.last_call_info()
-        kern += info["traj_kernel_ms"]
+        kern += ctx.last_call_info()["traj_kernel_ms"]
         runs.append(res[0])
         alg += res[0]["alg_bytes"]
     plan = bt.plan(0)
     bt.close()
     mrg = merge(runs)
-    peaks = measured_peaks()
-    hbm_peak = peaks["hbm_gbs"] if peaks else 6400.0
     ach = alg / (kern / 1e3) / 1e9
-    line = {"metric": "trajectories/s, n = 1e5 band matrix", "workload": "large", "value": args.steps * T / (kern / 1e3),
-            "unit": "trajectories/s", "steps": args.steps, "traj_per_step": T, "data": "synthetic",
-            "config": {"matrix": "n=1e5, |i-j|<=1 band + planted permutation + uniform off-band entries to m=5e5 "
-                                 "(generator seed 3)", "estimator": "plain: two-sided MD, initial DM, outer SK(100)",
-                       "layout": plan},
-            "ess_per_traj": mrg["ess"] / mrg["n_traj"], "p_match": mrg["p_match"], "rse": mrg["rse"],
-            "prep_ms": prep_ms, "kernel_ms_per_step": kern / args.steps,
-            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                         "peak_source": "measured copy" if peaks else "fallback",
-                         "bytes": "algorithmic: 8 B per trajectory vertex at start, 8 B per scanned adjacency "
-                                  "entry of the picked vertex and its partner"}}
+    out.append({"estimator": "plain: two-sided MD, initial DM, outer SK(100)", "layout": plan,
+                "traj": mrg["n_traj"], "traj_per_s": mrg["n_traj"] / (kern / 1e3), "p_match": mrg["p_match"],
+                "rse": mrg["rse"], "ess": mrg["ess"], "prep_ms": prep_ms, "kernel_s": kern / 1e3,
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak}})
+    print(f"plain: {mrg['n_traj']} trajectories, p_match {mrg['p_match']}", file=sys.stderr, flush=True)
+    # local_threshold on a time budget
+    s = B.preset("local_threshold")
+    s.theta = args.theta
+    s.time_budget_s = args.large_budget
+    t0 = time.perf_counter()
+    r = ctx.estimate_batch_ex([dev], [1 << 20], args.seed, s, first_traj=1 << 30)[0][0]
+    wall = time.perf_counter() - t0
+    info = ctx.last_call_info()
+    ks = info["traj_kernel_ms"] / 1e3
+    ach = r["alg_bytes"] / ks / 1e9 if ks > 0 else 0.0
+    out.append({"estimator": f"local_threshold (Local SK repair, Thrs DM, theta {args.theta}), time budget "
+                             f"{args.large_budget} s", "traj": r["n_traj"], "status": r["status"], "stop": r["stop"],
+                "traj_per_s": r["n_traj"] / ks if ks > 0 else None, "p_match": r["p_match"], "rse": r["rse"],
+                "ess": r["ess"], "log_estimate": r["log_estimate"],
+                "dm_calls_per_traj": r["n_dm_calls"] / max(1, r["n_traj"]),
+                "local_repairs_per_traj": r["n_local_sk"] / max(1, r["n_traj"]), "kernel_s": ks, "wall_s": wall,
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak}})
+    print(f"local_threshold: {r['n_traj']} trajectories, p_match {r['p_match']}", file=sys.stderr, flush=True)
+    line = {"metric": "n = 1e5 band matrix: plain and filtering estimators", "workload": "large", "data": "synthetic",
+            "config": {"matrix": matrix, "peak_source": "measured copy (MEASURED_PEAKS.json)" if peaks else "fallback",
+                       "bytes": "algorithmic, counted per trajectory on the device (pm_result.alg_bytes)"},
+            "runs": out}
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -810,6 +851,61 @@ def run_ablation(args, local):
     ctx.close()
 
 
+def run_learned_scale(args, local):
+    """Configuration 4 at its stated scale: the learned proposal trained on
+    pairs recorded from the SK(100,10) Fixed teacher on 100 ER+planted
+    matrices (n = 1e4, d = 6, generator seeds 1000-1099), evaluated on
+    held-out seeds (2000+) at n = 1e4 and n = 1e5 against the plain estimator
+    (outer SK only, same vertex rule), each matrix run to RSE <= eps within a
+    time budget through estimate_permanent (rse_target, time_budget_s)."""
+    import torch
+    from paper_2608_15390_b300 import binding as B
+    torch.cuda.set_device(local)
+    ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
+    train = [G.er_planted(10_000, 6.0, seed=1000 + k) for k in range(args.train_mats)]
+    model = ctx.model(seed=31)
+    t0 = time.perf_counter()
+    rep = model.train(train, B.Schedule(**TEACHER), n_pairs=args.train_pairs, epochs=2, batch=8192, lr=2e-3,
+                      seed=32, objective=B.OBJ_CENTRED)
+    t_train = time.perf_counter() - t0
+    print(f"trained on {rep['n_pairs']} pairs in {t_train:.1f} s", file=sys.stderr, flush=True)
+    rows = []
+    for n, count in ((10_000, 4), (100_000, 2)):
+        for q in range(count):
+            m = G.er_planted(n, 6.0, seed=2000 + q + (100 if n > 10_000 else 0))
+            for arm, s in (("plain", B.Schedule(**LEARNED)), ("learned", B.Schedule(**LEARNED, learned=model))):
+                s.rse_target = args.eps
+                s.time_budget_s = args.study_budget
+                r = ctx.estimate_batch_ex([m], [TRAJ_CAP], args.seed, s)[0][0]
+                t = r["dev_ms"] / 1e3
+                rows.append({"n": n, "matrix_seed": 2000 + q + (100 if n > 10_000 else 0), "arm": arm,
+                             "traj": r["n_traj"], "p_match": r["p_match"], "rse": r["rse"], "ess": r["ess"],
+                             "device_s": t, "ess_per_s": r["ess"] / t if t > 0 else None,
+                             "at_target": r["stop"] == 1, "traj_per_s": r["n_traj"] / t if t > 0 else None})
+                print(f"n={n} #{q} {arm}: {r['n_traj']} traj, p_match {r['p_match']:.3f}, rse {r['rse']:.3g}",
+                      file=sys.stderr, flush=True)
+    ratios = {}
+    for n in (10_000, 100_000):
+        rs = []
+        for q in range(4):
+            a = [x for x in rows if x["n"] == n and x["matrix_seed"] % 100 == q and x["arm"] == "learned"]
+            b = [x for x in rows if x["n"] == n and x["matrix_seed"] % 100 == q and x["arm"] == "plain"]
+            if a and b and a[0]["ess_per_s"] and b[0]["ess_per_s"]:
+                rs.append(a[0]["ess_per_s"] / b[0]["ess_per_s"])
+        ratios[str(n)] = {"learned_vs_plain_ess_per_s": rs, "median": float(np.median(rs)) if rs else None}
+    out = {"workload": "learned", "metric": "effective samples/s at fixed RSE (budgeted), learned vs plain",
+           "config": {"train": f"{args.train_mats} ER+planted matrices n=1e4 d=6 (seeds 1000+), teacher "
+                               "SK(100,10) Fixed, per-step centred loss, 2 epochs, batch 8192",
+                      "eval": "held-out ER+planted d=6: 4 at n=1e4 (seeds 2000-2003), 2 at n=1e5 (seeds 2100-2101)",
+                      "eps": args.eps, "budget_s_per_run": args.study_budget},
+           "train": {"pairs": rep["n_pairs"], "seconds": t_train, "record_s": rep["seconds_record"],
+                     "train_s": rep["seconds_train"], "loss_first": rep["loss_first"], "loss_last": rep["loss_last"]},
+           "ratios": ratios, "runs": rows, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+    model.close()
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -824,9 +920,10 @@ def main():
         if rank == 0:
             run_large(args, local)
         return
-    if args.workload in ("e4", "theta", "ablation"):
+    if args.workload in ("e4", "theta", "ablation", "learned"):
         if rank == 0:
-            {"e4": run_e4, "theta": run_theta, "ablation": run_ablation}[args.workload](args, local)
+            {"e4": run_e4, "theta": run_theta, "ablation": run_ablation,
+             "learned": run_learned_scale}[args.workload](args, local)
         return
     import torch
     torch.cuda.set_device(local)

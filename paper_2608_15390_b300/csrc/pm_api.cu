@@ -185,7 +185,10 @@ Plan plan_for(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learn
     Plan p{};
     p.lists = full;
     p.g = pol.g;
-    if (pol.g < 1 || pol.g > kCtaWarps || (pol.g & (pol.g - 1)) || (!full && pol.g != 1)) return p;
+    // several warps per trajectory: full-SK schedules, and DM schedules whose
+    // state is in global memory (the group runs the DM's component step)
+    if (pol.g < 1 || pol.g > kCtaWarps || (pol.g & (pol.g - 1)) || (!full && pol.g != 1 && !(dm && pol.gstate)))
+        return p;
     if (pol.gstate) {
         p.gstate = 1;
         p.rc_smem = need_rc;
@@ -216,7 +219,7 @@ std::vector<Policy> candidate_policies(int n, int64_t m, int rb, const Sched& s,
     const bool dm = s.dm != 0;
     std::vector<Policy> out;
     const int combos[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
-    for (int g = 1; g <= (full ? kCtaWarps : 1); g *= 2) {
+    for (int g = 1; g <= ((full || dm) ? kCtaWarps : 1); g *= 2) {
         for (int dms = 0; dms <= (dm ? 1 : 0); ++dms) {
             for (const auto& cb : combos) {
                 Policy pol;
@@ -276,7 +279,10 @@ Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max, bool lear
         Policy gs;
         gs.gstate = 1;
         gs.rc_smem = need_rc;
-        gs.g = full ? 4 : 1;
+        // DM schedules on large matrices: one trajectory per CTA, whose 16 warps
+        // share the DM's component step (a warp-serial step over 2n vertices in
+        // global memory would dominate)
+        gs.g = full ? 4 : (s.dm != 0 && n >= 8192) ? kCtaWarps : 1;
         const Plan p = plan_for(n, m, rb, s, smem_max, learned, gs);
         if (p.groups >= 1) best = p;
     }
@@ -615,6 +621,7 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
         }
     }
     tp.budget_ns = R.budget_ns;
+    tp.hard_ns = R.budget_ns ? 2 * R.budget_ns + 5000000000ull : 0;
     tp.t_start = (unsigned long long*)P(S.o_tstart);
     tp.cancel = ctx->cancel_dev;
     tp.model = R.model;
@@ -1360,6 +1367,7 @@ pm_status probe_plan(pm_context* ctx, pm_batch* b, int k, const Plan& plan, doub
     tp.slots = B + o_sl;
     tp.slot = sl;
     tp.budget_ns = 0;
+    tp.hard_ns = 0;
     tp.cancel = nullptr;
     const int smem = kCtaMiscBytes + learned_smem(R.model != nullptr) + plan.mat_bytes + plan.groups * plan.state_bytes;
     PM_CUDA(cudaEventRecord(b->ws.ev0, ctx->stream));

@@ -12,6 +12,14 @@ namespace pm {
 
 // workspace (19 n + 3 ints): mr[n] mc[n] vis[n] cur[n] stk[n+1] idx[2n] low[2n]
 // comp[2n] it[2n] onst[2n] cstk[2n+1] sstk[2n+1]
+struct DmWs {
+    int *mr, *mc, *vis, *cur, *stk, *idx, *low, *comp, *it, *onst, *cstk, *sstk;
+    __device__ DmWs(int* ws, int n)
+    {
+        mr = ws; mc = mr + n; vis = mc + n; cur = vis + n; stk = cur + n; idx = stk + n + 1; low = idx + 2 * n;
+        comp = low + 2 * n; it = comp + 2 * n; onst = it + 2 * n; cstk = onst + 2 * n; sstk = cstk + 2 * n + 1;
+    }
+};
 
 
 
@@ -29,21 +37,10 @@ namespace pm {
 // few augmenting searches remain.  The supported-edge set does not depend on
 // which perfect matching the SCC step starts from, so the result is the same.
 template <class Live, typename Idx>
-__device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri, const int* ce,
-                        const Live& live, uint8_t* mask, int* ws, int lane, bool repair = false)
+__device__ bool dm_match_warp(int n, const int* rp, const Idx* ci, const Live& live, int* ws, int lane, bool repair)
 {
-    int* mr = ws;
-    int* mc = mr + n;
-    int* vis = mc + n;
-    int* cur = vis + n;
-    int* stk = cur + n;
-    int* idx = stk + n + 1;
-    int* low = idx + 2 * n;
-    int* comp = low + 2 * n;
-    int* it = comp + 2 * n;
-    int* onst = it + 2 * n;
-    int* cstk = onst + 2 * n;
-    int* sstk = cstk + 2 * n + 1;
+    const DmWs W(ws, n);
+    int *mr = W.mr, *mc = W.mc, *vis = W.vis, *cur = W.cur, *stk = W.stk;
 
     if (repair) {
         for (int i = lane; i < n; i += 32) {
@@ -145,17 +142,34 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
         if (!unmatched) break;
         if (!augmented) return false;
     }
+    return true;
+}
 
-    // strongly connected components (Tarjan with explicit stacks); the next
-    // successor of a column is found by a ballot over its adjacency
+// Strongly connected components of the oriented residual (matching edges
+// row -> column, the others column -> row) by Tarjan with explicit stacks,
+// one warp; the next successor of a column is found by a ballot over its
+// adjacency.  presolved: comp[x] in [0, 2n) marks a vertex whose component
+// an earlier pass already found (a whole component of the graph, so the
+// components of the other vertices are those of the graph without it); such
+// vertices are neither visited nor followed, and the new components get ids
+// 2n + k.  Otherwise every active vertex is visited and ids start at 0.
+template <class Live, typename Idx>
+__device__ void dm_tarjan_warp(int n, const int* cp, const Idx* ri, const int* ce, const Live& live, int* ws,
+                               int lane, bool presolved)
+{
+    const DmWs W(ws, n);
+    int *mr = W.mr, *idx = W.idx, *low = W.low, *comp = W.comp, *it = W.it, *onst = W.onst, *cstk = W.cstk,
+        *sstk = W.sstk;
     const int V = 2 * n;
-    int* ib = vis;  // [2n] over vis and cur, which the matching no longer needs
+    auto solved = [&](int x) { return presolved && comp[x] >= 0 && comp[x] < V; };
+    int* ib = W.vis;  // [2n] over vis and cur, which the matching no longer needs
     for (int x = lane; x < V; x += 32) { idx[x] = -1; onst[x] = 0; }
     __syncwarp();
-    int counter = 0, ncomp = 0, sp = 0;
+    int counter = 0, ncomp = presolved ? V : 0, sp = 0;
     for (int s0 = 0; s0 < V; s0 += 32) {
       const int sl = s0 + lane;
-      unsigned todo = __ballot_sync(kFull, sl < V && (sl < n ? live.row(sl) : live.col(sl - n)) && idx[sl] < 0);
+      unsigned todo = __ballot_sync(kFull, sl < V && (sl < n ? live.row(sl) : live.col(sl - n)) && idx[sl] < 0 &&
+                                               !solved(sl));
       while (todo) {
         const int s = s0 + __ffs(todo) - 1;
         todo &= todo - 1u;
@@ -174,6 +188,7 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
                 if (it[x] < 0) {
                     it[x] = 0;
                     w = n + mr[x];
+                    if (solved(w)) w = -1;
                 }
             } else {
                 // the eligible entries of the chunk scanned last stay in ib[x]
@@ -194,7 +209,7 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
                         int i = 0;
                         if (kk < en) {
                             i = ri[kk];
-                            ok = mr[i] != j && live.edge(ce[kk], i, j);
+                            ok = mr[i] != j && live.edge(ce[kk], i, j) && !solved(i);
                         }
                         const unsigned bal = __ballot_sync(kFull, ok);
                         if (bal) {
@@ -246,15 +261,161 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
       }
     }
     __syncwarp();
-    for (int i = lane; i < n; i += 32) {
+}
+
+// Remove the unsupported edges: a live non-matching edge whose ends lie in
+// different components (rows tid, tid + nthr, ...).
+template <class Live, typename Idx>
+__device__ void dm_mask_rows(int n, const int* rp, const Idx* ci, const Live& live, uint8_t* mask, int* ws, int tid,
+                             int nthr)
+{
+    const DmWs W(ws, n);
+    for (int i = tid; i < n; i += nthr) {
         if (!live.row(i)) continue;
         for (int e = rp[i]; e < rp[i + 1]; ++e) {
             const int j = ci[e];
-            if (mr[i] != j && live.edge(e, i, j) && comp[i] != comp[n + j]) mask[e] = 0;
+            if (W.mr[i] != j && live.edge(e, i, j) && W.comp[i] != W.comp[n + j]) mask[e] = 0;
         }
     }
+}
+
+// The whole DM step on one warp: perfect matching, components, mask.
+template <class Live, typename Idx>
+__device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri, const int* ce,
+                        const Live& live, uint8_t* mask, int* ws, int lane, bool repair = false)
+{
+    if (!dm_match_warp<Live, Idx>(n, rp, ci, live, ws, lane, repair)) return false;
+    dm_tarjan_warp<Live, Idx>(n, cp, ri, ce, live, ws, lane, false);
+    dm_mask_rows<Live, Idx>(n, rp, ci, live, mask, ws, lane, 32);
     __syncwarp();
     return true;
+}
+
+// Group-parallel first pass of the component step for large residuals (all
+// nthr threads of a trajectory's group; sync() is the group barrier; sh: 8
+// ints of the group's shared memory).  Leaves comp[x] = -1 for the active
+// vertices it does not settle and, for the ones it does, an id in [0, 2n) of
+// a whole component:
+//   1. trimming: an undone vertex with no undone successor or no undone
+//      predecessor lies on no cycle of the undone vertices, so it is a
+//      component of its own (repeated while it removes vertices, at most 64
+//      passes; the fixed point does not depend on the order);
+//   2. one forward and one backward breadth-first search over the undone
+//      vertices from the smallest undone id p: their intersection is p's
+//      component (in the usual sparse residual, the one giant component).
+// What is left is finished by dm_tarjan_warp(presolved = true).  Every loop
+// is bounded: at most 64 trimming passes, and a search level adds at least
+// one new vertex, so at most 2n levels.
+template <class Live, typename Idx, class Sync>
+__device__ void dm_scc_group_prepass(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri, const int* ce,
+                                     const Live& live, int* ws, int tid, int nthr, int* sh, Sync sync)
+{
+    const DmWs W(ws, n);
+    int *mr = W.mr, *mc = W.mc, *comp = W.comp;
+    int* fw = W.idx;   // reached by the forward search
+    int* bw = W.low;   // reached by the backward search
+    int* qa = W.cstk;  // frontiers (2n + 1 ints each)
+    int* qb = W.sstk;
+    const int V = 2 * n;
+    auto active = [&](int x) { return x < n ? live.row(x) : live.col(x - n); };
+    for (int x = tid; x < V; x += nthr) {
+        comp[x] = active(x) ? -1 : -2;
+        fw[x] = 0;
+        bw[x] = 0;
+    }
+    if (tid == 0) { sh[0] = 0; sh[1] = 0; sh[2] = 0x7FFFFFFF; }
+    sync();
+    // 1. trimming
+    for (int pass = 0; pass < 64; ++pass) {
+        int* flag = sh + (pass & 1);
+        for (int x = tid; x < V; x += nthr) {
+            if (comp[x] != -1) continue;
+            bool has_out = false, has_in = false;
+            if (x < n) {  // row x: out = its matched column; in = its other live columns
+                has_out = comp[n + mr[x]] == -1;
+                for (int e = rp[x]; e < rp[x + 1] && !has_in; ++e) {
+                    const int j = ci[e];
+                    has_in = j != mr[x] && live.edge(e, x, j) && comp[n + j] == -1;
+                }
+            } else {      // column j: in = its matched row; out = its other live rows
+                const int j = x - n;
+                has_in = comp[mc[j]] == -1;
+                for (int k = cp[j]; k < cp[j + 1] && !has_out; ++k) {
+                    const int i = ri[k];
+                    has_out = i != mc[j] && live.edge(ce[k], i, j) && comp[i] == -1;
+                }
+            }
+            if (!has_out || !has_in) {
+                comp[x] = x;
+                *flag = 1;
+            }
+        }
+        sync();
+        const bool changed = *flag != 0;
+        if (tid == 0) sh[(pass + 1) & 1] = 0;  // the next pass's flag (last read two barriers ago)
+        sync();
+        if (!changed) break;
+    }
+    // 2. pivot: the smallest undone id
+    for (int x = tid; x < V; x += nthr)
+        if (comp[x] == -1) atomicMin(sh + 2, x);
+    sync();
+    const int p = sh[2];
+    if (p >= V) return;  // trimming settled everything
+    for (int dir = 0; dir < 2; ++dir) {  // 0: forward (successors), 1: backward (predecessors)
+        int* mark = dir == 0 ? fw : bw;
+        if (tid == 0) {
+            mark[p] = 1;
+            qa[0] = p;
+            sh[4] = 1;  // frontier size
+            sh[5] = 0;
+            sh[6] = 0;
+        }
+        sync();
+        int* cur = qa;
+        int* nxt = qb;
+        for (int level = 0; level < V; ++level) {
+            const int cnt = sh[4 + (level & 1)];
+            int* ncnt = sh + 4 + ((level + 1) & 1);
+            for (int q = tid; q < cnt; q += nthr) {
+                const int x = cur[q];
+                auto visit = [&](int y) {
+                    if (comp[y] == -1 && atomicExch(&mark[y], 1) == 0) nxt[atomicAdd(ncnt, 1)] = y;
+                };
+                if (x < n) {
+                    if (dir == 0) {
+                        visit(n + mr[x]);
+                    } else {
+                        for (int e = rp[x]; e < rp[x + 1]; ++e) {
+                            const int j = ci[e];
+                            if (j != mr[x] && live.edge(e, x, j)) visit(n + j);
+                        }
+                    }
+                } else {
+                    const int j = x - n;
+                    if (dir == 1) {
+                        visit(mc[j]);
+                    } else {
+                        for (int k = cp[j]; k < cp[j + 1]; ++k) {
+                            const int i = ri[k];
+                            if (i != mc[j] && live.edge(ce[k], i, j)) visit(i);
+                        }
+                    }
+                }
+            }
+            sync();
+            const int next = *ncnt;
+            if (tid == 0) sh[4 + (level & 1)] = 0;  // free the slot read at this level
+            int* tq = cur;
+            cur = nxt;
+            nxt = tq;
+            sync();
+            if (next == 0) break;
+        }
+    }
+    for (int x = tid; x < V; x += nthr)
+        if (comp[x] == -1 && fw[x] && bw[x]) comp[x] = p;
+    sync();
 }
 
 }  // namespace pm

@@ -211,6 +211,10 @@ struct TrajParams {
     uint64_t budget_ns;
     unsigned long long* t_start;
     const volatile int* cancel;
+    // hard limit (0: none): a trajectory still running hard_ns after the
+    // launch's start is abandoned and left out of the sample (ln X = NaN),
+    // so no single long trajectory can hold the launch far past its budget
+    uint64_t hard_ns;
     // learned proposal: BF16 device image of the network, or nullptr
     const void* model;
     // recording of (features, SK target) pairs, or rec_feat == nullptr

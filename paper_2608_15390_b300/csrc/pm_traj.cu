@@ -48,6 +48,7 @@ __device__ __forceinline__ size_t a16(size_t x) { return (x + 15) & ~(size_t)15;
 struct Grp {
     int g, nthr, tid, wig, lane, bar;
     int* misc;
+    bool gdm;  // the group shares the DM's component step (state in global memory, g > 1)
 };
 
 __device__ __forceinline__ void gsync(const Grp& G)
@@ -520,7 +521,8 @@ __device__ __forceinline__ uint64_t global_ns()
 
 // misc slots of a group (two step buffers so a fast leader never overwrites
 // values a slower warp of its group is still reading)
-enum { M_DEAD = 0, M_NIT = 1, M_DM = 2, M_CNTR = 3, M_CNTC = 4, M_STRIDE = 8, M_TMP = 16, M_TRAJ = 17, M_DMOK = 18 };
+enum { M_DEAD = 0, M_NIT = 1, M_DM = 2, M_CNTR = 3, M_CNTC = 4, M_STRIDE = 8, M_TMP = 16, M_TRAJ = 17, M_DMOK = 18,
+       M_DMSH = 20 /* 8 ints: the group DM's counters */ };
 
 // MODE: 0 scaled proposal, 1 learned proposal, 2 recording of (features, SK target) pairs
 template <typename Real, typename Idx, bool TRACE, int MODE, typename ListT>
@@ -613,11 +615,24 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     uint64_t mlp_rows = 0;  // network evaluations of live candidates (learned proposal)
     int m_live = Mp->m;
 
+    bool abandoned = false;
     for (int t = 0; t < n; ++t) {
         int* mb = G.misc + (t & 1) * M_STRIDE;
         if (leader) {
             int dead = 0, nit = 0, run_dm = 0, cnt_r = 0, cnt_c = 0;
-            do {  // the sequential part of step t (breaks out on death)
+            if (P.hard_ns && (t & 63) == 0) {  // far past the budget: leave this trajectory out
+                int over = 0;
+                if (lane == 0) {
+                    const unsigned long long t0 = *reinterpret_cast<volatile unsigned long long*>(P.t_start);
+                    over = t0 && global_ns() - t0 > P.hard_ns;
+                }
+                if (__shfl_sync(kFull, over, 0)) {
+                    if (lane == 0) atomicOr(P.status, ST_TIMEOUT);
+                    abandoned = true;
+                    dead = 1;
+                }
+            }
+            if (!dead) do {  // the sequential part of step t (breaks out on death)
                 // draw 0 of this step depends on (seed, trajectory, step) only:
                 // computed first, it overlaps the pick and the candidate scan
                 const uint64_t u0 = draw_u64(P.seed, traj, midx, (uint32_t)t, 0);
@@ -1032,11 +1047,31 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 // live edge about once in each direction, plus per-vertex state
                 alg_bytes += (uint64_t)16 * (uint64_t)m_live + (uint64_t)24 * (uint64_t)(2 * (n - t - 1));
             }
-            if (leader) {
-                const bool okdm =
-                    dm_warp(n, V.rp, V.ci, V.cp, V.ri, V.ce, LiveTraj{deg, mask, n}, mask, dmws, lane, dm_matched);
-                dm_matched = okdm;
-                if (lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
+            const LiveTraj live{deg, mask, n};
+            if (!G.gdm) {
+                if (leader) {
+                    const bool okdm = dm_warp(n, V.rp, V.ci, V.cp, V.ri, V.ce, live, mask, dmws, lane, dm_matched);
+                    dm_matched = okdm;
+                    if (lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
+                }
+            } else {
+                // a group of warps (large n): the matching repair on the leader
+                // warp, the component step's trimming and giant-component
+                // search on the whole group, Tarjan on the leader for the rest,
+                // the mask on the whole group
+                if (leader) {
+                    const bool okdm = dm_match_warp(n, V.rp, V.ci, live, dmws, lane, dm_matched);
+                    dm_matched = okdm;
+                    if (lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
+                }
+                gsync(G);
+                if (G.misc[M_DMOK]) {
+                    dm_scc_group_prepass(n, V.rp, V.ci, V.cp, V.ri, V.ce, live, dmws, G.tid, G.nthr, G.misc + M_DMSH,
+                                         [&] { gsync(G); });
+                    if (leader) dm_tarjan_warp(n, V.cp, V.ri, V.ce, live, dmws, lane, true);
+                    gsync(G);
+                    dm_mask_rows(n, V.rp, V.ci, live, mask, dmws, G.tid, G.nthr);
+                }
             }
             gsync(G);
             if (!G.misc[M_DMOK]) {
@@ -1094,7 +1129,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         }
     }
     if (leader && lane == 0) {
-        P.log_x[gq] = (dead_step >= 0) ? -INFINITY : num.log_value() - den.log_value();
+        if (!abandoned) P.log_x[gq] = (dead_step >= 0) ? -INFINITY : num.log_value() - den.log_value();
         if (TRACE) P.dead_step[gq] = dead_step;
         unsigned long long* cnt = P.counters + kCounters * k;
         if (n_dm) atomicAdd(cnt + 0, (unsigned long long)n_dm);
@@ -1143,6 +1178,7 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
     G.wig = G.tid >> 5;
     G.lane = lane;
     G.bar = 1 + gidx;
+    G.gdm = pl.gstate && pl.g > 1;
     uint8_t* sbase = gstate + (size_t)gidx * pl.state_bytes;
     uint8_t* slot = P.slots + ((size_t)blockIdx.x * kCtaWarps + gidx) * P.slot.bytes;
     const TreeGeom T = tree_geom(n);

@@ -52,3 +52,19 @@ def test_block_diagonal_known_permanent_n5000():
     r = ctx().estimate_permanent(m, 4096, 4, s)
     assert r["p_match"] > 0
     assert abs(r["log_estimate"] - log_per) < 5 * r["rse"] + 0.05, (r["log_estimate"], log_per, r["rse"])
+
+
+@pytest.mark.parametrize("case", [("band", "local_threshold", O.PREC_FP32), ("er", "local_tracked", O.PREC_FP64)])
+def test_group_dm_whole_trajectories(case):
+    """DM schedules at n >= 8192: the trajectory state lives in global memory
+    and a 16-warp group shares the DM's component step (trimming, one
+    forward-backward search from the smallest undone vertex, Tarjan on the
+    leader warp for the rest).  The supported-edge set is unique (Sec. 2), so
+    masks, and with them paths, degrees and death steps, are bit-exact against
+    the oracle's matching + Tarjan."""
+    kind, name, prec = case
+    m = G.band_random(8200, 41000, seed=3) if kind == "band" else G.er_planted(9000, 5.0, seed=78)
+    g, o = compare_trace(m, O.preset(name, prec), count=4, seed=3)
+    plan = ctx().last_call_info()["first_plan"]
+    assert plan["gstate"] == 1 and plan["g"] == 16, plan
+    assert g["deg_v"][g["deg_v"] >= 0].size > 8000
