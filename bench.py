@@ -82,7 +82,10 @@ def parse():
     p.add_argument("--mats", type=int, default=N_MATS,
                    help="use the first K matrices (profiling of a smaller case)")
     p.add_argument("--study-budget", type=float, default=2.0, help="seconds per run of the e4 / theta studies")
-    p.add_argument("--theta", type=float, default=0.1, help="large workload: Thrs threshold of local_threshold")
+    p.add_argument("--theta", type=float, default=0.33, help="large workload: theta of the filtering preset")
+    p.add_argument("--large-preset", default="local_threshold", choices=list(PRESETS),
+                   help="large workload: the filtering preset")
+    p.add_argument("--skip-plain", action="store_true", help="large workload: only the filtering run")
     p.add_argument("--large-budget", type=float, default=60.0, help="large workload: seconds of the filtering run")
     p.add_argument("--train-mats", type=int, default=100, help="learned workload: training matrices (n = 1e4)")
     p.add_argument("--train-pairs", type=int, default=10_000_000, help="learned workload: training pairs")
@@ -553,6 +556,8 @@ def run_large(args, local):
     out = []
     # plain
     sched = B.Schedule(**LEARNED)
+    if args.skip_plain:
+        args.steps = 0
     props = torch.cuda.get_device_properties(local)
     T = props.multi_processor_count * 16
     bt = ctx.batch([dev], [T], sched, graph=True, autotune=False)
@@ -566,16 +571,17 @@ def run_large(args, local):
         alg += res[0]["alg_bytes"]
     plan = bt.plan(0)
     bt.close()
-    mrg = merge(runs)
-    ach = alg / (kern / 1e3) / 1e9
-    out.append({"estimator": "plain: two-sided MD, initial DM, outer SK(100)", "layout": plan,
-                "traj": mrg["n_traj"], "traj_per_s": mrg["n_traj"] / (kern / 1e3), "p_match": mrg["p_match"],
-                "rse": mrg["rse"], "ess": mrg["ess"], "prep_ms": prep_ms, "kernel_s": kern / 1e3,
-                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": ach / hbm_peak}})
-    print(f"plain: {mrg['n_traj']} trajectories, p_match {mrg['p_match']}", file=sys.stderr, flush=True)
-    # local_threshold on a time budget
-    s = B.preset("local_threshold")
+    if runs:
+        mrg = merge(runs)
+        ach = alg / (kern / 1e3) / 1e9
+        out.append({"estimator": "plain: two-sided MD, initial DM, outer SK(100)", "layout": plan,
+                    "traj": mrg["n_traj"], "traj_per_s": mrg["n_traj"] / (kern / 1e3), "p_match": mrg["p_match"],
+                    "rse": mrg["rse"], "ess": mrg["ess"], "prep_ms": prep_ms, "kernel_s": kern / 1e3,
+                    "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": ach / hbm_peak}})
+        print(f"plain: {mrg['n_traj']} trajectories, p_match {mrg['p_match']}", file=sys.stderr, flush=True)
+    # the filtering schedule on a time budget
+    s = B.preset(args.large_preset)
     s.theta = args.theta
     s.time_budget_s = args.large_budget
     t0 = time.perf_counter()
@@ -584,15 +590,15 @@ def run_large(args, local):
     info = ctx.last_call_info()
     ks = info["traj_kernel_ms"] / 1e3
     ach = r["alg_bytes"] / ks / 1e9 if ks > 0 else 0.0
-    out.append({"estimator": f"local_threshold (Local SK repair, Thrs DM, theta {args.theta}), time budget "
-                             f"{args.large_budget} s", "traj": r["n_traj"], "status": r["status"], "stop": r["stop"],
+    out.append({"estimator": f"{args.large_preset} (theta {args.theta}), time budget {args.large_budget} s",
+                "traj": r["n_traj"], "status": r["status"], "stop": r["stop"],
                 "traj_per_s": r["n_traj"] / ks if ks > 0 else None, "p_match": r["p_match"], "rse": r["rse"],
                 "ess": r["ess"], "log_estimate": r["log_estimate"],
                 "dm_calls_per_traj": r["n_dm_calls"] / max(1, r["n_traj"]),
                 "local_repairs_per_traj": r["n_local_sk"] / max(1, r["n_traj"]), "kernel_s": ks, "wall_s": wall,
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                              "frac": ach / hbm_peak}})
-    print(f"local_threshold: {r['n_traj']} trajectories, p_match {r['p_match']}", file=sys.stderr, flush=True)
+    print(f"{args.large_preset}: {r['n_traj']} trajectories, p_match {r['p_match']}", file=sys.stderr, flush=True)
     line = {"metric": "n = 1e5 band matrix: plain and filtering estimators", "workload": "large", "data": "synthetic",
             "config": {"matrix": matrix, "peak_source": "measured copy (MEASURED_PEAKS.json)" if peaks else "fallback",
                        "bytes": "algorithmic, counted per trajectory on the device (pm_result.alg_bytes)"},

@@ -325,6 +325,17 @@ pm_status pm_batch_run(pm_batch* batch, uint64_t first_traj, uint64_t seed, pm_r
                        double* log_x);
 /* The layout matrix k runs with. */
 pm_status pm_batch_plan_info(const pm_batch* batch, int32_t k, pm_plan_info* info);
+
+/* Pin the layout (g, staged, rc_smem, gstate, dm_smem of *layout; the other
+ * fields are ignored) that every later call of this context uses for
+ * matrices of n's size class (half-octave of n) under this schedule, as the
+ * autotuner's cached choice does (no counterpart in the paper: for callers who
+ * tuned offline, and to run a given layout).  A later autotune of the same
+ * class replaces it.  PM_EUNSUPPORTED if the layout does not fit a matrix of
+ * order n with nnz entries under this schedule; a matrix of the class that it
+ * does not fit runs in the heuristic layout. */
+pm_status pm_layout_set(pm_context* ctx, const pm_schedule* schedule, int32_t n, int64_t nnz,
+                        const pm_plan_info* layout);
 pm_status pm_batch_destroy(pm_batch* batch);
 
 /* ---- serving (no counterpart in the paper) --------------------------------

@@ -135,6 +135,8 @@ def _load():
     L.pm_trace.argtypes = [P, C.POINTER(pm_csr), C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64,
                            C.POINTER(pm_schedule), P, P, P, P, P, C.c_uint32]
     L.pm_context_cancel.argtypes = [P]
+    L.pm_layout_set.argtypes = [P, C.POINTER(pm_schedule), C.c_int32, C.c_int64, C.POINTER(pm_plan_info)]
+    L.pm_layout_set.restype = C.c_int
     L.pm_probe_bandwidth.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.pm_probe_bandwidth.restype = C.c_int
     L.pm_merge_results.argtypes = [C.POINTER(pm_result), C.c_int32, C.POINTER(pm_result)]
@@ -205,7 +207,8 @@ EXPORTED = ["pm_context_create", "pm_context_destroy", "estimate_permanent",
             "pm_model_train", "pm_mlp_forward", "pm_mlp_gradient", "pm_record_pairs",
             "pm_batch_create", "pm_batch_run", "pm_batch_plan_info", "pm_batch_destroy",
             "pm_server_create", "pm_server_submit", "pm_server_round", "pm_server_clock", "pm_server_destroy",
-            "pm_context_cancel", "pm_merge_results", "pm_model_save", "pm_model_load", "pm_probe_bandwidth"]
+            "pm_context_cancel", "pm_merge_results", "pm_model_save", "pm_model_load", "pm_probe_bandwidth",
+            "pm_layout_set"]
 
 STOP_COMPLETE, STOP_TARGET, STOP_TIME, STOP_CANCELLED = 0, 1, 2, 3
 
@@ -329,6 +332,13 @@ class Context:
         l2, sm = C.c_double(), C.c_double()
         self._check(_lib.pm_probe_bandwidth(self.h, C.byref(l2), C.byref(sm)))
         return {"l2_read_gbs": l2.value, "smem_read_gbs": sm.value}
+
+    def layout_set(self, schedule: Schedule, n: int, nnz: int, g: int = 1, staged: int = 0, rc_smem: int = 0,
+                   gstate: int = 0, dm_smem: int = 0):
+        """pm_layout_set: pin the layout of n's size class under `schedule`."""
+        lay = pm_plan_info(g, 0, staged, rc_smem, gstate, dm_smem, 0, 0, -1.0, -1.0)
+        s = schedule.c()
+        self._check(_lib.pm_layout_set(self.h, C.byref(s), n, nnz, C.byref(lay)))
 
     def cancel(self):
         """pm_context_cancel: stop the running call (any thread)."""

@@ -1611,6 +1611,25 @@ pm_status pm_batch_run(pm_batch* b, uint64_t first_traj, uint64_t seed, pm_resul
     return stop_status(ctx, b->S.stop_bits);
 }
 
+pm_status pm_layout_set(pm_context* ctx, const pm_schedule* schedule, int32_t n, int64_t nnz,
+                        const pm_plan_info* layout)
+{
+    if (!ctx) return PM_EINVAL;
+    pm_status st = check_schedule(ctx, schedule);
+    if (st != PM_OK) return st;
+    if (!layout || n < 1 || n > kMaxN || nnz < 0) return fail(ctx, PM_EINVAL, "bad layout arguments");
+    const Sched s = to_sched(schedule);
+    const bool learned = schedule->learned != nullptr;
+    Policy pol;
+    pol.staged = layout->staged; pol.rc_smem = layout->rc_smem; pol.gstate = layout->gstate;
+    pol.g = layout->g; pol.dm_smem = layout->dm_smem;
+    const int smem_max = traj_max_smem_bytes();
+    const Plan p = plan_for(n, nnz, s.precision == 1 ? 8 : 4, s, smem_max, learned, pol);
+    if (p.groups < 1) return fail(ctx, PM_EUNSUPPORTED, "the layout does not fit this size and schedule");
+    ctx->tuned[class_key(size_class(n), s, learned)] = {pol.staged, pol.rc_smem, pol.gstate, pol.g, pol.dm_smem};
+    return PM_OK;
+}
+
 pm_status pm_batch_plan_info(const pm_batch* b, int32_t k, pm_plan_info* info)
 {
     if (!b || !info || k < 0 || k >= (int32_t)b->info.size()) return PM_EINVAL;

@@ -10,14 +10,16 @@
 
 namespace pm {
 
-// workspace (19 n + 3 ints): mr[n] mc[n] vis[n] cur[n] stk[n+1] idx[2n] low[2n]
-// comp[2n] it[2n] onst[2n] cstk[2n+1] sstk[2n+1]
+// workspace (20 n + 3 of dm_ws_ints(n) = 21 n + 8 ints): mr[n] mc[n] vis[n]
+// cur[n] stk[n+1] idx[2n] low[2n] comp[2n] it[2n] onst[2n] cstk[2n+1]
+// sstk[2n+1] roots[2n]
 struct DmWs {
-    int *mr, *mc, *vis, *cur, *stk, *idx, *low, *comp, *it, *onst, *cstk, *sstk;
+    int *mr, *mc, *vis, *cur, *stk, *idx, *low, *comp, *it, *onst, *cstk, *sstk, *roots;
     __device__ DmWs(int* ws, int n)
     {
         mr = ws; mc = mr + n; vis = mc + n; cur = vis + n; stk = cur + n; idx = stk + n + 1; low = idx + 2 * n;
         comp = low + 2 * n; it = comp + 2 * n; onst = it + 2 * n; cstk = onst + 2 * n; sstk = cstk + 2 * n + 1;
+        roots = sstk + 2 * n + 1;
     }
 };
 
@@ -151,11 +153,13 @@ __device__ bool dm_match_warp(int n, const int* rp, const Idx* ci, const Live& l
 // adjacency.  presolved: comp[x] in [0, 2n) marks a vertex whose component
 // an earlier pass already found (a whole component of the graph, so the
 // components of the other vertices are those of the graph without it); such
-// vertices are neither visited nor followed, and the new components get ids
-// 2n + k.  Otherwise every active vertex is visited and ids start at 0.
+// vertices are neither visited nor followed, the new components get ids
+// 2n + k, and the searches start from the nroots vertices of W.roots (the
+// unsettled ones, whose idx = -1 and onst = 0 the caller set).  Otherwise
+// every active vertex is visited and ids start at 0.
 template <class Live, typename Idx>
 __device__ void dm_tarjan_warp(int n, const int* cp, const Idx* ri, const int* ce, const Live& live, int* ws,
-                               int lane, bool presolved)
+                               int lane, bool presolved, int nroots = 0)
 {
     const DmWs W(ws, n);
     int *mr = W.mr, *idx = W.idx, *low = W.low, *comp = W.comp, *it = W.it, *onst = W.onst, *cstk = W.cstk,
@@ -163,15 +167,19 @@ __device__ void dm_tarjan_warp(int n, const int* cp, const Idx* ri, const int* c
     const int V = 2 * n;
     auto solved = [&](int x) { return presolved && comp[x] >= 0 && comp[x] < V; };
     int* ib = W.vis;  // [2n] over vis and cur, which the matching no longer needs
-    for (int x = lane; x < V; x += 32) { idx[x] = -1; onst[x] = 0; }
-    __syncwarp();
+    if (!presolved) {
+        for (int x = lane; x < V; x += 32) { idx[x] = -1; onst[x] = 0; }
+        __syncwarp();
+    }
     int counter = 0, ncomp = presolved ? V : 0, sp = 0;
-    for (int s0 = 0; s0 < V; s0 += 32) {
-      const int sl = s0 + lane;
-      unsigned todo = __ballot_sync(kFull, sl < V && (sl < n ? live.row(sl) : live.col(sl - n)) && idx[sl] < 0 &&
+    const int nscan = presolved ? nroots : V;
+    for (int s0 = 0; s0 < nscan; s0 += 32) {
+      const int q = s0 + lane;
+      const int sl = q < nscan ? (presolved ? W.roots[q] : q) : 0;
+      unsigned todo = __ballot_sync(kFull, q < nscan && (sl < n ? live.row(sl) : live.col(sl - n)) && idx[sl] < 0 &&
                                                !solved(sl));
       while (todo) {
-        const int s = s0 + __ffs(todo) - 1;
+        const int s = __shfl_sync(kFull, sl, __ffs(todo) - 1);
         todo &= todo - 1u;
         if (idx[s] >= 0) continue;  // reached by an earlier search of this block
         int ctop = 0;
@@ -298,16 +306,21 @@ __device__ bool dm_warp(int n, const int* rp, const Idx* ci, const int* cp, cons
 // a whole component:
 //   1. trimming: an undone vertex with no undone successor or no undone
 //      predecessor lies on no cycle of the undone vertices, so it is a
-//      component of its own (repeated while it removes vertices, at most 64
-//      passes; the fixed point does not depend on the order);
-//   2. one forward and one backward breadth-first search over the undone
-//      vertices from the smallest undone id p: their intersection is p's
-//      component (in the usual sparse residual, the one giant component).
-// What is left is finished by dm_tarjan_warp(presolved = true).  Every loop
-// is bounded: at most 64 trimming passes, and a search level adds at least
-// one new vertex, so at most 2n levels.
+//      component of its own (two passes: each costs a sweep over the
+//      residual, and chains that would need more passes are left to the
+//      searches and Tarjan, which settle them as well);
+//   2. rounds of one forward and one backward breadth-first search over the
+//      undone vertices from a pivot p, the undone vertex with the longest
+//      adjacency list (ties: the smallest id; a long list makes p likely to
+//      sit in the giant component): their intersection is p's component.
+//      Rounds repeat, with new pivots, while more than max(256, 2n / 64)
+//      vertices are undone, at most 8 times.
+// What is left goes to W.roots (with idx = -1, onst = 0), and its count is
+// returned, for dm_tarjan_warp(presolved = true).  Every loop is bounded: two
+// trimming passes, at most 8 rounds, and a search level adds at least one
+// new vertex, so at most 2n levels per search.
 template <class Live, typename Idx, class Sync>
-__device__ void dm_scc_group_prepass(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri, const int* ce,
+__device__ int dm_scc_group_prepass(int n, const int* rp, const Idx* ci, const int* cp, const Idx* ri, const int* ce,
                                      const Live& live, int* ws, int tid, int nthr, int* sh, Sync sync)
 {
     const DmWs W(ws, n);
@@ -326,7 +339,7 @@ __device__ void dm_scc_group_prepass(int n, const int* rp, const Idx* ci, const 
     if (tid == 0) { sh[0] = 0; sh[1] = 0; sh[2] = 0x7FFFFFFF; }
     sync();
     // 1. trimming
-    for (int pass = 0; pass < 64; ++pass) {
+    for (int pass = 0; pass < 2; ++pass) {
         int* flag = sh + (pass & 1);
         for (int x = tid; x < V; x += nthr) {
             if (comp[x] != -1) continue;
@@ -356,16 +369,27 @@ __device__ void dm_scc_group_prepass(int n, const int* rp, const Idx* ci, const 
         sync();
         if (!changed) break;
     }
-    // 2. pivot: the smallest undone id
-    for (int x = tid; x < V; x += nthr)
-        if (comp[x] == -1) atomicMin(sh + 2, x);
+    // 2. forward-backward rounds; pivot key: list length (capped at 511) over
+    // 23 bits of (2^23 - 1 - id), so the largest key is the longest list with
+    // the smallest id (2n < 2^23)
+    const unsigned kIdMask = (1u << 23) - 1u;
+    for (int round = 1; round <= 8; ++round) {
+    if (tid == 0) { sh[2] = 0; sh[3] = 0; }
     sync();
-    const int p = sh[2];
-    if (p >= V) return;  // trimming settled everything
+    for (int x = tid; x < V; x += nthr) {
+        if (comp[x] != -1) continue;
+        const int len = x < n ? rp[x + 1] - rp[x] : cp[x - n + 1] - cp[x - n];
+        const unsigned key = ((unsigned)min(len, 511) << 23) | (kIdMask - (unsigned)x);
+        atomicMax(reinterpret_cast<unsigned*>(sh + 2), key);
+    }
+    sync();
+    const unsigned pk = (unsigned)sh[2];
+    if (pk == 0) break;  // every vertex settled
+    const int p = (int)(kIdMask - (pk & kIdMask));
     for (int dir = 0; dir < 2; ++dir) {  // 0: forward (successors), 1: backward (predecessors)
         int* mark = dir == 0 ? fw : bw;
         if (tid == 0) {
-            mark[p] = 1;
+            mark[p] = round;
             qa[0] = p;
             sh[4] = 1;  // frontier size
             sh[5] = 0;
@@ -380,7 +404,7 @@ __device__ void dm_scc_group_prepass(int n, const int* rp, const Idx* ci, const 
             for (int q = tid; q < cnt; q += nthr) {
                 const int x = cur[q];
                 auto visit = [&](int y) {
-                    if (comp[y] == -1 && atomicExch(&mark[y], 1) == 0) nxt[atomicAdd(ncnt, 1)] = y;
+                    if (comp[y] == -1 && atomicExch(&mark[y], round) != round) nxt[atomicAdd(ncnt, 1)] = y;
                 };
                 if (x < n) {
                     if (dir == 0) {
@@ -413,9 +437,111 @@ __device__ void dm_scc_group_prepass(int n, const int* rp, const Idx* ci, const 
             if (next == 0) break;
         }
     }
-    for (int x = tid; x < V; x += nthr)
-        if (comp[x] == -1 && fw[x] && bw[x]) comp[x] = p;
+    for (int x = tid; x < V; x += nthr) {
+        if (comp[x] != -1) continue;
+        if (fw[x] == round && bw[x] == round) comp[x] = p;
+        else atomicAdd(sh + 3, 1);  // still undone
+    }
     sync();
+    const int left = sh[3];
+    sync();
+    if (left <= max(256, V / 64)) break;
+    }
+    // the unsettled vertices, for Tarjan
+    if (tid == 0) sh[7] = 0;
+    sync();
+    for (int x = tid; x < V; x += nthr) {
+        if (comp[x] != -1) continue;
+        W.roots[atomicAdd(sh + 7, 1)] = x;
+        W.idx[x] = -1;
+        W.onst[x] = 0;
+    }
+    sync();
+    const int nroots = sh[7];
+    sync();
+    return nroots;
+}
+
+// Group-parallel repair of the kept perfect matching (all nthr threads of
+// the group; sync() is the group barrier; sh: 8 ints of shared memory): pairs
+// whose other end was eliminated are dropped, then every free active row gets
+// an augmenting path by a breadth-first alternating search (rows -> live
+// columns; a matched column leads on to its row) until a free column is
+// reached, and thread 0 flips the path.  Returns false if some free row has
+// no augmenting path (the residual has no perfect matching).  Bounded: each
+// search level claims at least one new column.
+template <class Live, typename Idx, class Sync>
+__device__ bool dm_repair_group(int n, const int* rp, const Idx* ci, const Live& live, int* ws, int tid, int nthr,
+                                int* sh, Sync sync)
+{
+    const DmWs W(ws, n);
+    int *mr = W.mr, *mc = W.mc, *seen = W.vis, *par = W.cur, *freer = W.stk;
+    int* qa = W.idx;  // row frontiers (2n ints each; at most n rows)
+    int* qb = W.low;
+    if (tid == 0) sh[0] = 0;
+    sync();
+    for (int i = tid; i < n; i += nthr) {
+        if (live.row(i) && mr[i] >= 0 && !live.col(mr[i])) mr[i] = -1;
+        if (live.col(i) && mc[i] >= 0 && !live.row(mc[i])) mc[i] = -1;
+        seen[i] = 0;
+    }
+    sync();
+    for (int i = tid; i < n; i += nthr)
+        if (live.row(i) && mr[i] < 0) freer[atomicAdd(sh, 1)] = i;
+    sync();
+    const int nfree = sh[0];
+    sync();
+    for (int f = 0; f < nfree; ++f) {
+        const int s = freer[f];
+        const int stamp = f + 1;
+        if (tid == 0) {
+            qa[0] = s;
+            sh[1] = -1;  // the free column found
+            sh[2] = 1;   // frontier sizes (two slots)
+            sh[3] = 0;
+        }
+        sync();
+        int* cur = qa;
+        int* nxt = qb;
+        int found = -1;
+        for (int level = 0; level < n; ++level) {
+            const int cnt = sh[2 + (level & 1)];
+            int* ncnt = sh + 2 + ((level + 1) & 1);
+            for (int q = tid; q < cnt; q += nthr) {
+                const int x = cur[q];
+                for (int e = rp[x]; e < rp[x + 1]; ++e) {
+                    const int j = ci[e];
+                    if (!live.edge(e, x, j) || atomicExch(&seen[j], stamp) == stamp) continue;
+                    par[j] = x;
+                    if (mc[j] < 0) atomicCAS(sh + 1, -1, j);
+                    else nxt[atomicAdd(ncnt, 1)] = mc[j];
+                }
+            }
+            sync();
+            found = sh[1];
+            const int next = *ncnt;
+            if (tid == 0) sh[2 + (level & 1)] = 0;
+            int* tq = cur;
+            cur = nxt;
+            nxt = tq;
+            sync();
+            if (found >= 0 || next == 0) break;
+        }
+        if (found < 0) return false;
+        if (tid == 0) {  // flip the alternating path ending at the free column
+            int j = found;
+            for (int guard = 0; guard <= n; ++guard) {
+                const int i = par[j];
+                const int nj = mr[i];
+                mr[i] = j;
+                mc[j] = i;
+                if (i == s) break;
+                j = nj;
+            }
+        }
+        sync();
+    }
+    return true;
 }
 
 }  // namespace pm

@@ -47,7 +47,7 @@ struct DevMatrix {
     int ok;              // initial DM found a perfect matching
     int unit_scale;      // binary and r0 = c0 = 1: every proposal is uniform
     int idx;             // matrix index in the Philox counter
-    int pad;
+    int matched;         // dm_ws starts with a perfect matching of B0 (mr[n], mc[n]) from the initial DM
     // A (validated copy with int32 offsets) and its CSC view
     int* a_rp; int* a_ci; float* a_val; int* a_cp; int* a_ri; int* a_ce;
     uint8_t* keep;       // [m_A] edge survives the initial DM
@@ -116,7 +116,7 @@ struct SlotLayout {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline int dm_ws_ints(int n) { return 19 * n + 8; }
+__host__ __device__ inline int dm_ws_ints(int n) { return 21 * n + 8; }
 
 // shared bytes of the initial DM with A's adjacency staged beside its
 // workspace: int32 row/column pointers, uint16 column/row indices

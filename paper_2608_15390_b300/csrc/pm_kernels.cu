@@ -165,6 +165,15 @@ __global__ void __launch_bounds__(1024) prepare_kernel(DevMatrix* mats, const De
     }
     __syncthreads();
     const int ok = ok_s;
+    // keep the initial DM's perfect matching (its edges are supported, so it
+    // is one of B0): a trajectory's first inner DM repairs it instead of
+    // matching from scratch
+    if (s.initial_dm && ok) {
+        const int* src = (s.initial_dm && n < 65536 && prep_stage_bytes(n, m) <= (size_t)dyn_smem) ? dm_smem : dm_ws;
+        if (src != M.dm_ws)
+            for (int q = tid; q < 2 * n; q += nt) M.dm_ws[q] = src[q];
+    }
+    if (tid == 0) M.matched = (s.initial_dm && ok) ? 1 : 0;
 
     // 4. compact to B0 (CSR, then CSC through the CSC view of A)
     for (int i = tid; i < n; i += nt) {

@@ -119,6 +119,26 @@ __device__ void tree_build(const uint16_t* deg, uint32_t* tree, const TreeGeom& 
     }
 }
 
+// the same with the whole group (large n): level by level, one thread per
+// upper entry, a group barrier between levels
+template <class Sync>
+__device__ void tree_build_group(const uint16_t* deg, uint32_t* tree, const TreeGeom& T, int tid, int nthr, Sync sync)
+{
+    for (int l = 1; l <= T.nlev; ++l) {
+        for (int gi = tid; gi < T.size[l]; gi += nthr) {
+            uint32_t best = 0xFFFFFFFFu;
+            for (int q = 0; q < 32; ++q) {
+                const int c = gi * 32 + q;
+                if (c >= T.size[l - 1]) break;
+                const uint32_t key = (l == 1) ? leaf_key(deg, c, T) : tree[T.off[l - 1] + c];
+                best = key < best ? key : best;
+            }
+            tree[T.off[l] + gi] = best;
+        }
+        sync();
+    }
+}
+
 __device__ __forceinline__ int md_pick(const uint16_t* deg, const uint32_t* tree, const TreeGeom& T, int lane)
 {
     uint32_t key = 0xFFFFFFFFu;
@@ -582,11 +602,16 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     }
     uint8_t* mask = nullptr;
     int* dmws = nullptr;
+    bool dm_matched = false;  // the DM workspace holds this trajectory's last perfect matching
     if (use_dm) {
         mask = mask_sm ? mask_sm : slot + P.slot.mask;
         dmws = dm_sm ? dm_sm : reinterpret_cast<int*>(slot + P.slot.dm);
         const int m = Mp->m;
         for (int q = G.tid; q < m; q += G.nthr) mask[q] = 1;
+        if (Mp->matched) {  // start from the initial DM's perfect matching of B0
+            for (int q = G.tid; q < 2 * n; q += G.nthr) dmws[q] = __ldg(Mp->dm_ws + q);
+            dm_matched = true;
+        }
     }
     int *stamp = nullptr, *tmp_id = nullptr, *list_r = nullptr, *list_c = nullptr;
     Real* tmp_val = nullptr;
@@ -606,7 +631,6 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
     Mant64 num, den;
     Real track = 1;
     unsigned n_dm = 0, n_full = 0, n_loc = 0;
-    bool dm_matched = false;  // the DM workspace holds this trajectory's last perfect matching
     int dead_step = -1;
     // algorithmic bytes of the trajectory: 16 B per vertex for the initial
     // degrees and minimum-degree structure; then per step the counts below
@@ -1055,20 +1079,30 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     if (lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
                 }
             } else {
-                // a group of warps (large n): the matching repair on the leader
-                // warp, the component step's trimming and giant-component
-                // search on the whole group, Tarjan on the leader for the rest,
-                // the mask on the whole group
-                if (leader) {
-                    const bool okdm = dm_match_warp(n, V.rp, V.ci, live, dmws, lane, dm_matched);
-                    dm_matched = okdm;
-                    if (lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
+                // a group of warps (large n): the matching repair by group-
+                // parallel augmenting searches (or, with no matching kept, the
+                // leader warp's full matching), the component step's trimming
+                // and giant-component searches on the whole group, Tarjan on
+                // the leader for what is left, the mask on the whole group
+                auto gs = [&] { gsync(G); };
+                bool okdm;
+                if (dm_matched) {
+                    okdm = dm_repair_group(n, V.rp, V.ci, live, dmws, G.tid, G.nthr, G.misc + M_DMSH, gs);
+                } else {
+                    if (leader) {
+                        const bool r = dm_match_warp(n, V.rp, V.ci, live, dmws, lane, false);
+                        if (lane == 0) G.misc[M_DMOK] = r ? 1 : 0;
+                    }
+                    gsync(G);
+                    okdm = G.misc[M_DMOK] != 0;
+                    gsync(G);
                 }
-                gsync(G);
-                if (G.misc[M_DMOK]) {
-                    dm_scc_group_prepass(n, V.rp, V.ci, V.cp, V.ri, V.ce, live, dmws, G.tid, G.nthr, G.misc + M_DMSH,
-                                         [&] { gsync(G); });
-                    if (leader) dm_tarjan_warp(n, V.cp, V.ri, V.ce, live, dmws, lane, true);
+                dm_matched = okdm;
+                if (leader && lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
+                if (okdm) {
+                    const int nroots = dm_scc_group_prepass(n, V.rp, V.ci, V.cp, V.ri, V.ce, live, dmws, G.tid,
+                                                            G.nthr, G.misc + M_DMSH, gs);
+                    if (leader && nroots > 0) dm_tarjan_warp(n, V.cp, V.ri, V.ce, live, dmws, lane, true, nroots);
                     gsync(G);
                     dm_mask_rows(n, V.rp, V.ci, live, mask, dmws, G.tid, G.nthr);
                 }
@@ -1091,7 +1125,19 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 deg[x] = (uint16_t)d;
             }
             gsync(G);
-            if (leader) {
+            if (G.gdm) {  // the whole group rebuilds the tree and counts the live edges
+                tree_build_group(deg, tree, T, G.tid, G.nthr, [&] { gsync(G); });
+                if (G.tid == 0) G.misc[M_DMSH] = 0;
+                gsync(G);
+                int ml = 0;
+                for (int x = G.tid; x < n; x += G.nthr) ml += (deg[x] != kInact) ? deg[x] : 0;
+                atomicAdd(G.misc + M_DMSH, ml);
+                gsync(G);
+                if (leader) {
+                    track = 1;
+                    m_live = G.misc[M_DMSH];
+                }
+            } else if (leader) {
                 tree_build(deg, tree, T, lane);
                 track = 1;
                 int ml = 0;  // live edges of the child = sum of row degrees

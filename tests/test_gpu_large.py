@@ -54,17 +54,48 @@ def test_block_diagonal_known_permanent_n5000():
     assert abs(r["log_estimate"] - log_per) < 5 * r["rse"] + 0.05, (r["log_estimate"], log_per, r["rse"])
 
 
-@pytest.mark.parametrize("case", [("band", "local_threshold", O.PREC_FP32), ("er", "local_tracked", O.PREC_FP64)])
-def test_group_dm_whole_trajectories(case):
-    """DM schedules at n >= 8192: the trajectory state lives in global memory
-    and a 16-warp group shares the DM's component step (trimming, one
-    forward-backward search from the smallest undone vertex, Tarjan on the
-    leader warp for the rest).  The supported-edge set is unique (Sec. 2), so
-    masks, and with them paths, degrees and death steps, are bit-exact against
-    the oracle's matching + Tarjan."""
+def _trace_in_layout(m, sched, count, seed, **layout):
+    """pm_trace of `count` trajectories in a pinned layout (a context of its
+    own, so the pin reaches no other test), against the oracle."""
+    B = binding()
+    c = B.Context(0)
+    gs = to_gpu_sched(sched)
+    c.layout_set(gs, m.n, m.nnz, **layout)
+    g = c.trace(m, count, seed, gs)
+    plan = c.last_call_info()["first_plan"]
+    c.close()
+    o = O.Prepared(m, sched).run(seed=seed, count=count, threads=8, trace=True)
+    assert np.array_equal(g["dead_step"], o["dead_step"])
+    assert np.array_equal(g["deg_v"], o["deg_v"])
+    assert np.array_equal(g["chosen"], o["chosen"])
+    assert logx_close(g["log_x"], o["log_x"], 1e-12) <= 1e-12
+    return g, plan
+
+
+@pytest.mark.parametrize("g", [4, 16])
+@pytest.mark.parametrize("case", [("band", "local_threshold", O.PREC_FP32), ("er", "local_tracked", O.PREC_FP64),
+                                  ("er", "adaptive_threshold", O.PREC_FP32)])
+def test_group_dm_pinned_layout(case, g):
+    """DM schedules with the trajectory state in global memory and a group of
+    g warps sharing the DM's component step (trimming, one forward-backward
+    search from the smallest undone vertex, Tarjan on the leader warp for the
+    rest), pinned with pm_layout_set at n = 3000 where the oracle's DM is
+    fast.  The supported-edge set is unique (Sec. 2), so masks, and with them
+    paths, degrees and death steps, are bit-exact against the oracle's
+    matching + Tarjan; the full-SK schedule also runs its sweeps on the group."""
     kind, name, prec = case
-    m = G.band_random(8200, 41000, seed=3) if kind == "band" else G.er_planted(9000, 5.0, seed=78)
-    g, o = compare_trace(m, O.preset(name, prec), count=4, seed=3)
+    m = G.band_random(3000, 15000, seed=3) if kind == "band" else G.er_planted(3000, 5.0, seed=78)
+    g_out, plan = _trace_in_layout(m, O.preset(name, prec), 6, 3, g=g, gstate=1)
+    assert plan["gstate"] == 1 and plan["g"] == g, plan
+
+
+def test_group_dm_heuristic_layout_n16000():
+    """At n = 16000 four trajectory states no longer fit in shared memory: the
+    heuristic layout of a DM schedule is global state with a 16-warp group
+    (local_threshold at theta = 0.1, FP64; whole trajectories)."""
+    s = O.preset("local_threshold", O.PREC_FP64)
+    s.theta = 0.1
+    m = G.er_planted(16000, 5.0, seed=78)
+    compare_trace(m, s, count=2, seed=3)
     plan = ctx().last_call_info()["first_plan"]
     assert plan["gstate"] == 1 and plan["g"] == 16, plan
-    assert g["deg_v"][g["deg_v"] >= 0].size > 8000
