@@ -969,8 +969,8 @@ def main():
         return ctx.estimate_batch_ex(pinned if host else dev, nt, args.seed, sched, first_traj=first)[0]
 
     for i in range(args.warmup):
-        job(i)
-        print(f"warm-up {i} done", file=sys.stderr, flush=True)
+        res = job(i)
+        print(f"warm-up {i}: {max(r['rounds'] for r in res)} rounds", file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
