@@ -326,6 +326,17 @@ pm_status pm_batch_run(pm_batch* batch, uint64_t first_traj, uint64_t seed, pm_r
 /* The layout matrix k runs with. */
 pm_status pm_batch_plan_info(const pm_batch* batch, int32_t k, pm_plan_info* info);
 
+/* Cost-aware choice of the Thrs / Trck threshold (the paper leaves theta's
+ * tuning open, Sec. 4): for each of thetas[count], one probe estimate of csr
+ * with schedule->theta = thetas[k] on a time budget of probe_s seconds (disjoint
+ * trajectory ids per candidate); its score is the work-normalised relative
+ * variance RSE^2 x device seconds (scores[k], may be NULL; +INFINITY when fewer
+ * than two trajectories stayed alive).  schedule->theta is set to the best
+ * candidate (unchanged if none scored).  schedule->dm must be PM_DM_THRS or
+ * PM_DM_TRCK; its rse_target and time_budget_s are ignored by the probes. */
+pm_status pm_tune_theta(pm_context* ctx, const pm_csr* csr, pm_schedule* schedule, const double* thetas,
+                        int32_t count, double probe_s, uint64_t seed, double* scores);
+
 /* Pin the layout (g, staged, rc_smem, gstate, dm_smem of *layout; the other
  * fields are ignored) that every later call of this context uses for
  * matrices of n's size class (half-octave of n) under this schedule, as the

@@ -137,6 +137,8 @@ def _load():
     L.pm_context_cancel.argtypes = [P]
     L.pm_layout_set.argtypes = [P, C.POINTER(pm_schedule), C.c_int32, C.c_int64, C.POINTER(pm_plan_info)]
     L.pm_layout_set.restype = C.c_int
+    L.pm_tune_theta.argtypes = [P, C.POINTER(pm_csr), C.POINTER(pm_schedule), P, C.c_int32, C.c_double, C.c_uint64, P]
+    L.pm_tune_theta.restype = C.c_int
     L.pm_probe_bandwidth.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.pm_probe_bandwidth.restype = C.c_int
     L.pm_merge_results.argtypes = [C.POINTER(pm_result), C.c_int32, C.POINTER(pm_result)]
@@ -208,7 +210,7 @@ EXPORTED = ["pm_context_create", "pm_context_destroy", "estimate_permanent",
             "pm_batch_create", "pm_batch_run", "pm_batch_plan_info", "pm_batch_destroy",
             "pm_server_create", "pm_server_submit", "pm_server_round", "pm_server_clock", "pm_server_destroy",
             "pm_context_cancel", "pm_merge_results", "pm_model_save", "pm_model_load", "pm_probe_bandwidth",
-            "pm_layout_set"]
+            "pm_layout_set", "pm_tune_theta"]
 
 STOP_COMPLETE, STOP_TARGET, STOP_TIME, STOP_CANCELLED = 0, 1, 2, 3
 
@@ -339,6 +341,16 @@ class Context:
         lay = pm_plan_info(g, 0, staged, rc_smem, gstate, dm_smem, 0, 0, -1.0, -1.0)
         s = schedule.c()
         self._check(_lib.pm_layout_set(self.h, C.byref(s), n, nnz, C.byref(lay)))
+
+    def tune_theta(self, m, schedule: Schedule, thetas, probe_s: float = 0.5, seed: int = 1):
+        """pm_tune_theta: (best theta, scores) by RSE^2 x seconds of probe runs."""
+        c, keep = make_csr(m)
+        th = np.ascontiguousarray(thetas, dtype=np.float64)
+        sc = np.zeros(len(th))
+        s = schedule.c()
+        self._check(_lib.pm_tune_theta(self.h, C.byref(c), C.byref(s), th.ctypes.data, len(th), probe_s, seed,
+                                       sc.ctypes.data))
+        return s.theta, sc
 
     def cancel(self):
         """pm_context_cancel: stop the running call (any thread)."""

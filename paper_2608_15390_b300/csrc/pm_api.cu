@@ -458,8 +458,8 @@ pm_status stage_inputs(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, 
         S.o_dead = L.take(4 * std::max<uint64_t>(S.total, 1));
         if (R.model && R.logit_stride) S.o_logits = L.take(4 * S.total * (size_t)S.n_max * R.logit_stride);
     }
-    // the plans and the chunk list (at most one chunk per trajectory)
-    S.chunk_cap = std::max<size_t>(S.total + count, min_chunks);
+    // the plans and the chunk list (a chunk holds 2 x groups >= 2 trajectories)
+    S.chunk_cap = std::max<size_t>(S.total / 2 + 2 * (size_t)count, min_chunks);
     S.o_plans = L.take(sizeof(Plan) * count);
     S.o_chunks = L.take(sizeof(Chunk) * S.chunk_cap);
     S.o_cctr = L.take(8);
@@ -1609,6 +1609,50 @@ pm_status pm_batch_run(pm_batch* b, uint64_t first_traj, uint64_t seed, pm_resul
     R.log_x = nullptr;
     if (st != PM_OK) return st;
     return stop_status(ctx, b->S.stop_bits);
+}
+
+pm_status pm_tune_theta(pm_context* ctx, const pm_csr* csr, pm_schedule* schedule, const double* thetas,
+                        int32_t count, double probe_s, uint64_t seed, double* scores)
+{
+    if (!ctx) return PM_EINVAL;
+    pm_status st = check_schedule(ctx, schedule);
+    if (st != PM_OK) return st;
+    st = check_csr(ctx, csr);
+    if (st != PM_OK) return st;
+    if (!thetas || count < 1 || !(probe_s > 0 && probe_s < INFINITY))
+        return fail(ctx, PM_EINVAL, "bad tuning arguments");
+    if (schedule->dm != PM_DM_THRS && schedule->dm != PM_DM_TRCK)
+        return fail(ctx, PM_EINVAL, "theta tunes the Thrs / Trck DM policies only");
+    double best = INFINITY;
+    int best_k = -1;
+    for (int k = 0; k < count; ++k) {
+        if (!(thetas[k] == thetas[k])) return fail(ctx, PM_EINVAL, "theta is NaN");
+        pm_schedule s = *schedule;
+        s.theta = thetas[k];
+        s.rse_target = 0;
+        s.time_budget_s = probe_s;
+        pm_result r{};
+        Run R;
+        R.mats = csr;
+        R.count = 1;
+        R.ntraj.assign(1, (uint64_t)1 << 21);  // the budget ends a probe long before
+        R.first_traj = (uint64_t)k << 40;
+        R.seed = seed;
+        R.s = to_sched(&s);
+        R.outs = &r;
+        R.model = s.learned ? s.learned->img : nullptr;
+        R.budget_s = probe_s;
+        st = execute_rounds(ctx, R);
+        if (st != PM_OK && st != PM_ETIMEOUT) return st;
+        // work-normalised relative variance: RSE^2 x device seconds (lower is better)
+        const double score = (r.n_alive >= 2 && r.rse == r.rse && r.dev_ms > 0)
+                                 ? r.rse * r.rse * (r.dev_ms * 1e-3) : INFINITY;
+        if (scores) scores[k] = score;
+        if (score < best) { best = score; best_k = k; }
+    }
+    if (best_k >= 0) schedule->theta = thetas[best_k];
+    ctx->last_error.clear();
+    return PM_OK;
 }
 
 pm_status pm_layout_set(pm_context* ctx, const pm_schedule* schedule, int32_t n, int64_t nnz,

@@ -150,3 +150,18 @@ def test_model_save_load_round_trip(tmp_path):
         ctx().model_load(str(tmp_path / "missing"))
     m1.close()
     m2.close()
+
+
+def test_tune_theta_picks_the_lowest_work_normalised_variance():
+    """pm_tune_theta: one budgeted probe per candidate theta (Thrs / Trck, the
+    threshold Sec. 4 leaves to tuning); the schedule comes back with the
+    candidate of least RSE^2 x device seconds."""
+    B = binding()
+    m = G.er_planted(400, 6.0, seed=91)
+    s = B.preset("local_threshold")
+    thetas = [0.1, 0.33, 0.7]
+    best, scores = ctx().tune_theta(m, s, thetas, probe_s=0.3, seed=4)
+    assert np.isfinite(scores).all(), scores
+    assert best == thetas[int(np.argmin(scores))]
+    with pytest.raises(B.PmError):
+        ctx().tune_theta(m, B.Schedule(initial_dm=1, K0=100, precision=B.PREC_FP32_PROPOSAL), thetas)
