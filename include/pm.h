@@ -177,7 +177,8 @@ typedef struct {
     int32_t gstate;          /* trajectory state in global memory (large n) */
     int32_t dm_smem;         /* inner DM's workspace and edge mask in shared memory */
     int32_t tuned;           /* 1 if the autotuner chose this layout */
-    int32_t reserved;
+    int32_t pair;            /* two trajectories per warp, one per 16-lane half (schedules
+                                without inner SK or DM; `groups` counts trajectories) */
     double probe_traj_per_s;      /* the chosen layout's probe rate (-1: not probed) */
     double heuristic_traj_per_s;  /* the heuristic layout's probe rate (-1: not probed) */
 } pm_plan_info;
@@ -337,7 +338,7 @@ pm_status pm_batch_plan_info(const pm_batch* batch, int32_t k, pm_plan_info* inf
 pm_status pm_tune_theta(pm_context* ctx, const pm_csr* csr, pm_schedule* schedule, const double* thetas,
                         int32_t count, double probe_s, uint64_t seed, double* scores);
 
-/* Pin the layout (g, staged, rc_smem, gstate, dm_smem of *layout; the other
+/* Pin the layout (g, staged, rc_smem, gstate, dm_smem, pair of *layout; the other
  * fields are ignored) that every later call of this context uses for
  * matrices of n's size class (half-octave of n) under this schedule, as the
  * autotuner's cached choice does (no counterpart in the paper: for callers who

@@ -69,11 +69,11 @@ class pm_train_report(C.Structure):
 
 class pm_plan_info(C.Structure):
     _fields_ = [("g", C.c_int32), ("groups", C.c_int32), ("staged", C.c_int32), ("rc_smem", C.c_int32),
-                ("gstate", C.c_int32), ("dm_smem", C.c_int32), ("tuned", C.c_int32), ("reserved", C.c_int32),
+                ("gstate", C.c_int32), ("dm_smem", C.c_int32), ("tuned", C.c_int32), ("pair", C.c_int32),
                 ("probe_traj_per_s", C.c_double), ("heuristic_traj_per_s", C.c_double)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class pm_server_cfg(C.Structure):
@@ -336,9 +336,9 @@ class Context:
         return {"l2_read_gbs": l2.value, "smem_read_gbs": sm.value}
 
     def layout_set(self, schedule: Schedule, n: int, nnz: int, g: int = 1, staged: int = 0, rc_smem: int = 0,
-                   gstate: int = 0, dm_smem: int = 0):
+                   gstate: int = 0, dm_smem: int = 0, pair: int = 0):
         """pm_layout_set: pin the layout of n's size class under `schedule`."""
-        lay = pm_plan_info(g, 0, staged, rc_smem, gstate, dm_smem, 0, 0, -1.0, -1.0)
+        lay = pm_plan_info(g, 0, staged, rc_smem, gstate, dm_smem, 0, pair, -1.0, -1.0)
         s = schedule.c()
         self._check(_lib.pm_layout_set(self.h, C.byref(s), n, nnz, C.byref(lay)))
 

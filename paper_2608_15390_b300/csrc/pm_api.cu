@@ -48,7 +48,7 @@ struct pm_context {
     Workspace ws2;                // the rounds of a call with an RSE target or a time budget
     int* cancel_host = nullptr;   // cancel flag: pinned host word mapped into the device
     int* cancel_dev = nullptr;
-    std::map<std::string, std::array<int, 5>> tuned;  // autotuned layout policy per size class
+    std::map<std::string, std::array<int, 6>> tuned;  // autotuned layout policy per size class
     std::vector<pm_batch*> batches;                     // live batches (destroyed with the context)
     double last_traj_ms = 0, last_prep_ms = 0;
     uint64_t last_h2d = 0, last_d2h = 0;
@@ -166,12 +166,23 @@ namespace {
 // heuristic below and the autotuner (pm_batch_create) both produce a policy;
 // plan_for() turns it into a Plan for a given matrix and shared-memory budget.
 struct Policy {
-    int staged = 0, rc_smem = 0, gstate = 0, g = 1, dm_smem = 0;
+    int staged = 0, rc_smem = 0, gstate = 0, g = 1, dm_smem = 0, pair = 0;
     bool operator==(const Policy& o) const
     {
-        return staged == o.staged && rc_smem == o.rc_smem && gstate == o.gstate && g == o.g && dm_smem == o.dm_smem;
+        return staged == o.staged && rc_smem == o.rc_smem && gstate == o.gstate && g == o.g && dm_smem == o.dm_smem &&
+               pair == o.pair;
+    }
+    std::array<int, 6> key() const { return {staged, rc_smem, gstate, g, dm_smem, pair}; }
+    static Policy of_key(const std::array<int, 6>& k)
+    {
+        Policy p;
+        p.staged = k[0]; p.rc_smem = k[1]; p.gstate = k[2]; p.g = k[3]; p.dm_smem = k[4]; p.pair = k[5];
+        return p;
     }
 };
+
+// schedules a pair plan can run: no inner SK, DM or Local repair
+bool pair_schedule(const Sched& s) { return s.sk == 0 && s.dm == 0; }
 
 int learned_smem(bool learned) { return learned ? (model_infer_bytes() + 15) / 16 * 16 : 0; }
 
@@ -183,6 +194,19 @@ Plan plan_for(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learn
     const bool dm = s.dm != 0;
     const int avail = smem_max - kCtaMiscBytes - learned_smem(learned);
     Plan p{};
+    if (pol.pair) {  // two trajectories per warp, state in shared memory
+        if (!pair_schedule(s) || pol.g != 1 || pol.gstate || pol.rc_smem || pol.dm_smem || (pol.staged && n > 65535))
+            return p;
+        p.g = 1;
+        p.pair = 1;
+        p.staged = pol.staged;
+        p.mat_bytes = pol.staged ? staged_matrix_bytes(n, m, false) : 0;
+        if (p.mat_bytes >= avail) return p;
+        p.state_bytes = pair_state_bytes(n, learned);
+        p.groups = std::min((avail - p.mat_bytes) / p.state_bytes, 2 * kCtaWarps) & ~1;
+        if (p.groups < 0) p.groups = 0;
+        return p;
+    }
     p.lists = full;
     p.g = pol.g;
     // several warps per trajectory: full-SK schedules, and DM schedules whose
@@ -238,10 +262,20 @@ std::vector<Policy> candidate_policies(int n, int64_t m, int rb, const Sched& s,
         gs.g = g;
         if (plan_for(n, m, rb, s, smem_max, learned, gs).groups >= 1) out.push_back(gs);
     }
+    if (pair_schedule(s)) {
+        for (int st = 1; st >= 0; --st) {
+            Policy pp;
+            pp.pair = 1;
+            pp.staged = st;
+            if (plan_for(n, m, rb, s, smem_max, learned, pp).groups >= 4) out.push_back(pp);
+        }
+    }
     return out;
 }
 
-// Heuristic plan: matrix and scaling vectors in shared memory if they fit,
+// Heuristic plan: schedules without inner SK or DM run two trajectories per
+// warp (matrix staged if it fits) when that keeps at least 8 warps busy;
+// otherwise matrix and scaling vectors in shared memory if they fit,
 // then scaling vectors only, then neither; full-SK schedules spread a
 // trajectory over the fewest warps that keep >= 8 warps of the CTA busy,
 // other schedules run one warp per trajectory with as many groups as fit; a
@@ -250,6 +284,15 @@ Plan make_plan(int n, int64_t m, int rb, const Sched& s, int smem_max, bool lear
 {
     const bool full = s.sk == 1 || s.sk == 2;
     const bool need_rc = s.sk != 0;
+    if (pair_schedule(s)) {  // two trajectories per warp while at least 8 warps stay busy
+        for (int st = 1; st >= 0; --st) {
+            Policy pp;
+            pp.pair = 1;
+            pp.staged = st;
+            const Plan p = plan_for(n, m, rb, s, smem_max, learned, pp);
+            if (p.groups >= 16) return p;
+        }
+    }
     Plan best{};
     int best_score = -1;
     const int combos[4][2] = {{1, 1}, {0, 1}, {1, 0}, {0, 0}};
@@ -293,6 +336,7 @@ Policy policy_of(const Plan& p)
 {
     Policy o;
     o.staged = p.staged; o.rc_smem = p.rc_smem; o.gstate = p.gstate; o.g = p.g; o.dm_smem = p.dm_smem;
+    o.pair = p.pair;
     return o;
 }
 
@@ -312,9 +356,7 @@ Plan default_plan(const pm_context* ctx, int n, int64_t m, int rb, const Sched& 
 {
     auto it = ctx->tuned.find(class_key(size_class(n), s, learned));
     if (it != ctx->tuned.end()) {
-        Policy pol;
-        pol.staged = it->second[0]; pol.rc_smem = it->second[1]; pol.gstate = it->second[2];
-        pol.g = it->second[3]; pol.dm_smem = it->second[4];
+        const Policy pol = Policy::of_key(it->second);
         const Plan p = plan_for(n, m, rb, s, smem_max, learned, pol);
         if (p.groups >= 1) return p;
     }
@@ -551,6 +593,11 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
     for (int k = 0; k < count; ++k) {
         S.plans[k] = given ? (*given)[k] : default_plan(ctx, R.mats[k].n, R.mats[k].nnz, (int)S.rb, R.s, smem_max,
                                                          R.model != nullptr);
+        if (S.plans[k].pair && (R.trace || R.rec_feat)) {  // traces and recordings run one trajectory per warp
+            Policy pol = policy_of(S.plans[k]);
+            pol.pair = 0;
+            S.plans[k] = plan_for(R.mats[k].n, R.mats[k].nnz, (int)S.rb, R.s, smem_max, R.model != nullptr, pol);
+        }
         if (S.plans[k].groups < 1)
             return fail(ctx, PM_EUNSUPPORTED, "trajectory state does not fit in shared memory");
         S.smem_need = std::max(S.smem_need, kCtaMiscBytes + learned_smem(R.model != nullptr) + S.plans[k].mat_bytes +
@@ -1261,6 +1308,7 @@ pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info)
     const Plan& p = ctx->last_plan;
     info->first_plan.g = p.g; info->first_plan.groups = p.groups; info->first_plan.staged = p.staged;
     info->first_plan.rc_smem = p.rc_smem; info->first_plan.gstate = p.gstate; info->first_plan.dm_smem = p.dm_smem;
+    info->first_plan.pair = p.pair;
     info->first_plan.probe_traj_per_s = info->first_plan.heuristic_traj_per_s = -1.0;
     return PM_OK;
 }
@@ -1419,8 +1467,7 @@ pm_status autotune(pm_context* ctx, pm_batch* b, std::vector<Plan>& plans)
         double best_rate = -1.0, heur_rate = -1.0;
         auto cached = ctx->tuned.find(key);
         if (cached != ctx->tuned.end()) {
-            best.staged = cached->second[0]; best.rc_smem = cached->second[1];
-            best.gstate = cached->second[2]; best.g = cached->second[3]; best.dm_smem = cached->second[4];
+            best = Policy::of_key(cached->second);
         } else {
             const std::vector<Policy> cands = candidate_policies(n, m, (int)S.rb, R.s, smem_max, learned);
             if (cands.size() > 1) {
@@ -1434,7 +1481,7 @@ pm_status autotune(pm_context* ctx, pm_batch* b, std::vector<Plan>& plans)
                     if (rate > best_rate) { best_rate = rate; best = pol; }
                 }
             }
-            ctx->tuned[key] = {best.staged, best.rc_smem, best.gstate, best.g, best.dm_smem};
+            ctx->tuned[key] = best.key();
         }
         for (int q = 0; q < count; ++q) {
             if (size_class(R.mats[q].n) != cr.first) continue;
@@ -1522,7 +1569,7 @@ pm_status pm_batch_create(pm_context* ctx, const pm_csr* mats, int32_t count, co
         const Plan& p = b->S.plans[k];
         pm_plan_info& I = b->info[k];
         I.g = p.g; I.groups = p.groups; I.staged = p.staged; I.rc_smem = p.rc_smem; I.gstate = p.gstate;
-        I.dm_smem = p.dm_smem;
+        I.dm_smem = p.dm_smem; I.pair = p.pair;
     }
     if (flags & PM_BATCH_GRAPH) {
         PM_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -1666,11 +1713,11 @@ pm_status pm_layout_set(pm_context* ctx, const pm_schedule* schedule, int32_t n,
     const bool learned = schedule->learned != nullptr;
     Policy pol;
     pol.staged = layout->staged; pol.rc_smem = layout->rc_smem; pol.gstate = layout->gstate;
-    pol.g = layout->g; pol.dm_smem = layout->dm_smem;
+    pol.g = layout->g; pol.dm_smem = layout->dm_smem; pol.pair = layout->pair;
     const int smem_max = traj_max_smem_bytes();
     const Plan p = plan_for(n, nnz, s.precision == 1 ? 8 : 4, s, smem_max, learned, pol);
     if (p.groups < 1) return fail(ctx, PM_EUNSUPPORTED, "the layout does not fit this size and schedule");
-    ctx->tuned[class_key(size_class(n), s, learned)] = {pol.staged, pol.rc_smem, pol.gstate, pol.g, pol.dm_smem};
+    ctx->tuned[class_key(size_class(n), s, learned)] = pol.key();
     return PM_OK;
 }
 

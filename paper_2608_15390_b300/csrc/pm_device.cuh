@@ -163,7 +163,18 @@ struct Mant64 {
         mul((uint64_t)sig);
         e += (ef ? (int)ef : 1) - 127 - 23;
     }
-    __device__ __forceinline__ double log_value() const { return log((double)m) + (double)e * 0.6931471805599453; }
+    // ln of the value; explicit roundings (no contraction into an FMA), so
+    // every kernel that inlines it produces the same bits
+    __device__ __forceinline__ double log_value() const
+    {
+        return __dadd_rn(log((double)m), __dmul_rn((double)e, 0.6931471805599453));
+    }
 };
+
+// ln(num / den) of two Mant64 accumulators
+__device__ __forceinline__ double log_ratio(const Mant64& num, const Mant64& den)
+{
+    return __dsub_rn(num.log_value(), den.log_value());
+}
 
 }  // namespace pm

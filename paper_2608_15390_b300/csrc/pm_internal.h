@@ -110,7 +110,7 @@ struct SlotLayout {
     size_t list_r, list_c;// int[n_max] each
     size_t mask;          // uint8[m_max]
     size_t dm;            // int[dm ints]
-    size_t logit;         // float[n_max] logits of long candidate lists (learned proposal)
+    size_t logit;         // float[2][n_max] logits of long candidate lists (learned proposal)
     size_t bytes;
 };
 
@@ -146,7 +146,7 @@ inline SlotLayout slot_layout(int n_max, int m_max, int real_bytes, bool scales,
     L.list_c = local ? take((size_t)n_max * 4) : 0;
     L.mask = dm ? take((size_t)m_max) : 0;
     L.dm = dm ? take((size_t)dm_ws_ints(n_max) * 4) : 0;
-    L.logit = learned ? take((size_t)n_max * 4) : 0;
+    L.logit = learned ? take((size_t)n_max * 8) : 0;  // two lists: one per half-warp trajectory of a pair plan
     L.bytes = align_up(o, 256);
     if (L.bytes == 0) L.bytes = 256;
     return L;
@@ -161,9 +161,21 @@ struct Plan {
     int g, groups, staged, rc_smem, lists;
     int gstate;        // trajectory state in the group's global slot (large n)
     int dm_smem;       // the inner DM's workspace and edge mask in shared memory
-    int state_bytes;   // shared bytes of one group
+    int state_bytes;   // shared bytes of one group (pair plans: of one trajectory)
     int mat_bytes;     // shared bytes of the staged matrix (0 if not staged)
+    int pair;          // two trajectories per warp, one per 16-lane half (`groups`
+                       // trajectory states, even, on groups / 2 warps)
 };
+
+// shared bytes of one trajectory of a pair plan: degrees, tree and (learned
+// proposal) a 16-row feature tile
+inline int pair_state_bytes(int n, bool learned)
+{
+    const TreeGeom G = tree_geom(n);
+    size_t b = align_up((size_t)((2 * n + 7) & ~7) * 2, 16) + align_up((size_t)G.total * 4, 16);
+    if (learned) b += 16 * 24 * 2;
+    return (int)b;
+}
 
 // a run of trajectories first .. first + count - 1 (indices inside matrix k);
 // trajectory first + q writes its ln X to log_x[slot0 + q]

@@ -1175,7 +1175,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
         }
     }
     if (leader && lane == 0) {
-        if (!abandoned) P.log_x[gq] = (dead_step >= 0) ? -INFINITY : num.log_value() - den.log_value();
+        if (!abandoned) P.log_x[gq] = (dead_step >= 0) ? -INFINITY : log_ratio(num, den);
         if (TRACE) P.dead_step[gq] = dead_step;
         unsigned long long* cnt = P.counters + kCounters * k;
         if (n_dm) atomicAdd(cnt + 0, (unsigned long long)n_dm);
@@ -1277,6 +1277,8 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
     }
 }
 
+#include "pm_pair.cuh"
+
 template <typename Real, bool TRACE, int MODE>
 __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
 {
@@ -1333,9 +1335,21 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
             }
             __syncthreads();
             MV<uint16_t> V{n, s_rp, s_cp, s_ci, s_ri, s_ce, Mp->rv, Mp->cv};
+            if constexpr (!TRACE && MODE != 2) {
+                if (pl.pair) {
+                    run_chunk_pair<Real, uint16_t, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
+                    continue;
+                }
+            }
             run_chunk<Real, uint16_t, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
         } else {
             MV<int> V{n, Mp->rp, Mp->cp, Mp->ci, Mp->ri, Mp->ce, Mp->rv, Mp->cv};
+            if constexpr (!TRACE && MODE != 2) {
+                if (pl.pair) {
+                    run_chunk_pair<Real, int, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
+                    continue;
+                }
+            }
             run_chunk<Real, int, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
         }
     }

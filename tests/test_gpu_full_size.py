@@ -71,7 +71,13 @@ def test_bench_learned_batch_largest_matrices():
         g = ctx().trace(mats[k], c, seed, sched, first_traj=first, matrix_index=k)
         plan = bt.plan(k)
         used = ctx().last_call_info()["first_plan"]
-        for f in ("g", "groups", "staged", "rc_smem", "gstate", "dm_smem"):
+        # a trace runs one trajectory per warp: a pair layout's trace takes
+        # its one-per-warp counterpart (same staging), whose ln X bits the
+        # pair layout reproduces (test_gpu_pair)
+        fields = ("staged", "rc_smem", "gstate", "dm_smem") if plan["pair"] else \
+            ("g", "groups", "staged", "rc_smem", "gstate", "dm_smem")
+        assert used["pair"] == 0
+        for f in fields:
             assert used[f] == plan[f], (k, f, used, plan)
         o = O.Prepared(mats[k], osched).run_ext(seed=seed, count=c, logits=g["logits"], first_traj=first,
                                                 matrix=k, threads=8)
