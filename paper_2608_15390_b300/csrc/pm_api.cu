@@ -2226,13 +2226,17 @@ pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, co
     PM_CUDA(cudaMemsetAsync(bl.p, 0, 8, ctx->stream));
     DevBuf bw;
     PM_CUDA(cudaMalloc(&bw.p, mlp_grad_workspace_bytes(ctx->sm_count)));
+    PM_CUDA(cudaMemsetAsync(bw.p, 0, 4, ctx->stream));
     PM_CUDA(launch_mlp_grad(m->img, (const float*)bx.p, (const float*)bt.p, (const int*)bp.p, 0, (int)B,
                             (const uint32_t*)bg.p, (float*)br.p, m->grad, (double*)bl.p, ctx->sm_count, bw.p,
                             ctx->stream));
     PM_CUDA(cudaMemcpyAsync(grad, m->grad, 4 * model_param_count(), cudaMemcpyDeviceToHost, ctx->stream));
     double l = 0;
+    int werr = 0;
     PM_CUDA(cudaMemcpyAsync(&l, bl.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(&werr, bw.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (werr) return fail(ctx, PM_EDEVICE, "a tensor-core completion wait ran out in the gradient kernel");
     if (loss) *loss = l;
     return PM_OK;
 }
@@ -2420,8 +2424,9 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
     PM_CUDA(cudaMalloc(&bp.p, 4 * N));
     PM_CUDA(cudaMemcpy(bp.p, perm.data(), 4 * N, cudaMemcpyHostToDevice));
     if (centred) PM_CUDA(cudaMalloc(&br.p, 4 * max_batch));
-    DevBuf bw;  // partial sums of the gradient reduction
+    DevBuf bw;  // error word and partial sums of the gradient reduction
     PM_CUDA(cudaMalloc(&bw.p, mlp_grad_workspace_bytes(ctx->sm_count)));
+    PM_CUDA(cudaMemsetAsync(bw.p, 0, 4, ctx->stream));
     const uint64_t steps_per_epoch = cuts.size() - 1;
     const uint64_t total_steps = steps_per_epoch * (uint64_t)cfg->epochs;
     PM_CUDA(cudaMalloc(&bl.p, 8 * total_steps));
@@ -2441,8 +2446,11 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
         }
     }
     std::vector<double> losses(total_steps);
+    int werr = 0;
     PM_CUDA(cudaMemcpyAsync(losses.data(), bl.p, 8 * total_steps, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(&werr, bw.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (werr) return fail(ctx, PM_EDEVICE, "a tensor-core completion wait ran out in the gradient kernel");
     const auto t2 = std::chrono::steady_clock::now();
     if (report) {
         std::memset(report, 0, sizeof(*report));

@@ -304,8 +304,10 @@ int model_param_count();
 cudaError_t launch_model_image(const float* master, void* img, cudaStream_t st);
 // group == nullptr: mean squared error; else the per-step centred loss (resid:
 // device scratch of B floats for the batch's residuals)
-// work: device scratch of mlp_grad_workspace_bytes(sm_count) (per-CTA partial
-// sums, reduced in a fixed order so the gradient is reproducible)
+// work: device scratch of mlp_grad_workspace_bytes(sm_count): its first int
+// is the device error flag (the caller zeroes it once and reads it after the
+// last launch; nonzero: a tensor-core completion wait ran out), then per-CTA
+// partial sums, reduced in a fixed order so the gradient is reproducible
 size_t mlp_grad_workspace_bytes(int sm_count);
 cudaError_t launch_mlp_grad(const void* img, const float* feat, const float* target, const int* perm, int64_t row0,
                             int B, const uint32_t* group, float* resid, float* grad, double* loss, int sm_count,

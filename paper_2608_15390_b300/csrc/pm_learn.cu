@@ -1,7 +1,10 @@
 // pm_learn.cu -- training of the learned proposal (an extension:
-// the paper has no learned part).  Forward and backward run on BF16 tensor
-// cores (mma.sync.m16n8k16, FP32 accumulation); Adam keeps FP32 master
-// weights and refreshes the BF16 device image after every step.
+// the paper has no learned part).  The gradient's forward and backward run on
+// the 5th-generation tensor core (tcgen05 MMAs from shared-memory tiles into
+// tensor memory, BF16 operands, FP32 accumulation); the residual pass of the
+// centred loss and the standalone forward use mma.sync tiles of the inference
+// network; Adam keeps FP32 master weights and refreshes the BF16 device image
+// after every step.
 //
 // Losses on the recorded (features, target) pairs, target = the SK scale
 // product ln(r_v c_l): the mean squared error, or the per-step centred squared
@@ -10,14 +13,13 @@
 // invisible to it).  For the latter a forward pass writes the residuals of
 // the batch, and the backward kernel reads its group's mean from them.
 #include <cmath>
+#include <cstddef>
 #include "pm_mlp.cuh"
+#include "pm_umma.cuh"
 
 namespace pm {
 
 namespace {
-
-constexpr int kTrainWarps = 4;
-constexpr int kTrainRows = 32 * kTrainWarps;  // rows per CTA iteration
 
 // offsets of the flat parameter vector: W1[64][8], b1, W2[64][64], b2, W3, b3
 constexpr int oW1 = 0, oB1 = kNH * kNF, oW2 = oB1 + kNH, oB2 = oW2 + kNH * kNH, oW3 = oB2 + kNH, oB3 = oW3 + kNH;
@@ -30,253 +32,307 @@ __device__ __forceinline__ uint16_t bf16_bits(float x)
     return *reinterpret_cast<uint16_t*>(&b);
 }
 
-// sum over the 8 lanes sharing (lane & 3)
-__device__ __forceinline__ float sum_over_g(float v)
-{
-    v += __shfl_xor_sync(kFull, v, 4);
-    v += __shfl_xor_sync(kFull, v, 8);
-    v += __shfl_xor_sync(kFull, v, 16);
-    return v;
-}
+// ---- gradient on the 5th-generation tensor core ----
+//
+// One CTA of 128 threads (a warpgroup: thread r owns row r of a 128-row
+// tile, which is TMEM lane r) runs tiles of the batch.  Per tile, with one
+// thread issuing the MMAs into tensor memory and an mbarrier tracking their
+// completion:
+//   G1  D1 = X W1^T                        (128 x 64, K = 16)
+//       h1 = gelu(D1 + b1)                 -> H tile, bf16
+//   G2  D2 = h1 W2^T                       (128 x 64, K = 64)
+//       z2 = D2 + b2, h2 = gelu(z2), y = h2 . w3 + b3, dy = dL/dy,
+//       dz2 = dy w3 gelu'(z2)              -> A tile [dz2 | h2], H tile [.. | 1, dy]
+//   G3  D3 = dz2 W2                        (dh1; 128 x 64, K = 64)
+//   G4  D4 += [dz2 | h2]^T [h1 | 1 | dy]   (128 x 80, K = the 128 rows)
+//       dz1 = D3 gelu'(D1 + b1)            -> B tile [dz1 | 0]
+//   G5  D5 += [dz1 | 0]^T [X | 1]          (128 x 16, K = the 128 rows)
+// D4 accumulates dW2 (rows 0-63, columns 0-63), db2 (column 64) and dW3
+// (rows 64-127, columns 65 + 66: dy split into two bf16 parts); D5 dW1
+// (rows 0-63, columns 0-7) and db1 (column 8): the bias and output-layer
+// gradients come out of the same MMAs through the constant-one and dy
+// columns.  Operands are bf16 (as the mma.sync path had them: features,
+// activations, dz), accumulation FP32.
+constexpr int kTcRows = 128;
+constexpr int kCX = 16, kCH = 80, kCA = 128, kCB = 128;   // columns of the operand tiles
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kD1 = 0, kD2 = 64, kD4 = 128, kD5 = 208;  // TMEM columns of the accumulators
+constexpr uint32_t kWaitPolls = 1u << 24;
+constexpr uint16_t kBf16One = 0x3F80;
 
-struct TrainSmem {
-    DevModel M;
-    uint16_t dz2t[kNH * kTrainRows];  // [out][row]
-    uint16_t h1t[kNH * kTrainRows];   // [in][row]
-    uint16_t dz1t[kNH * kTrainRows];  // [out][row]
-    uint16_t xt[8 * kTrainRows];      // [feature][row]
+struct TcSmem {
+    uint8_t tX[kTcRows * kCX * 2];   // [X | 1 | 0]
+    uint8_t tH[kTcRows * kCH * 2];   // [h1 | 1, dy_hi, dy_lo, 0 ...]
+    uint8_t tA[kTcRows * kCA * 2];   // [dz2 | h2]
+    uint8_t tB[kTcRows * kCB * 2];   // [dz1 | 0]
+    uint8_t w1[kNH * kCX * 2];       // W1 [hidden][16], inputs 8..15 zero
+    uint8_t w2[kNH * kNH * 2];       // W2 [out][in]
+    uint64_t mbar;
+    uint32_t tmem;
+    float b3;
+    float b1[kNH], b2[kNH], w3[kNH];
+    float red[kTcRows / 32];
+    double lred[kTcRows / 32];
 };
 
-// Gradient of the loss over rows perm[row0 .. row0 + B) of (feat, target),
-// accumulated into grad[kNParam] (FP32 atomics) and loss.  resid == nullptr:
-// mean squared error.  Otherwise the centred loss: resid[r] is the residual
-// of batch row r (from mlp_resid_kernel, the same forward), group[] the group
-// code of a pair (index within its step << 16 | the step's pair count), and
-// the rows of a step are consecutive in the batch.
-__global__ void __launch_bounds__(kTrainWarps * 32) mlp_grad_kernel(const DevModel* Mg, const float* feat,
-                                                                    const float* target, const int* perm,
-                                                                    int64_t row0, int B, float inv_b,
-                                                                    const float* resid, const uint32_t* group,
-                                                                    float* part, double* loss_part)
+__device__ __forceinline__ void st_row16(uint8_t* tile, int r, int c0, int C, const uint32_t (&p)[8])
 {
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane >> 2, t = lane & 3;
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(Mg);
-        uint4* dst = reinterpret_cast<uint4*>(&S.M);
-        for (int q = tid; q < (int)(sizeof(DevModel) / 16); q += blockDim.x) dst[q] = src[q];
-    }
-    __syncthreads();
-    const DevModel* M = &S.M;
-    float acc_w2[8][4], acc_w1[4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        for (int q = 0; q < 4; ++q) acc_w2[j][q] = 0.0f;
-    for (int q = 0; q < 4; ++q) acc_w1[q] = 0.0f;
-    float acc_b1[16], acc_b2[16], acc_w3[16];
-    for (int q = 0; q < 16; ++q) acc_b1[q] = acc_b2[q] = acc_w3[q] = 0.0f;
-    float acc_b3 = 0.0f;
-    double loss = 0.0;
+    *reinterpret_cast<uint4*>(tile + blk_off(r, c0, C)) = make_uint4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<uint4*>(tile + blk_off(r, c0 + 8, C)) = make_uint4(p[4], p[5], p[6], p[7]);
+}
 
-    const int iters = (B + kTrainRows - 1) / kTrainRows;
-    for (int it = blockIdx.x; it < iters; it += gridDim.x) {
-#pragma unroll 1
-        for (int mt = 0; mt < 2; ++mt) {
-            const int lr0 = 32 * w + 16 * mt;              // local row of this tile
-            const int r_g = it * kTrainRows + lr0 + g;     // batch rows g, g + 8
-            const int r_g8 = r_g + 8;
-            const bool v_g = r_g < B, v_g8 = r_g8 < B;
-            float x_g[2] = {0.f, 0.f}, x_g8[2] = {0.f, 0.f};
-            float t_g = 0.f, t_g8 = 0.f;
-            if (v_g) {
-                const int64_t src = perm[row0 + r_g];
-                x_g[0] = feat[src * kNF + 2 * t];
-                x_g[1] = feat[src * kNF + 2 * t + 1];
-                t_g = target[src];
-            }
-            if (v_g8) {
-                const int64_t src = perm[row0 + r_g8];
-                x_g8[0] = feat[src * kNF + 2 * t];
-                x_g8[1] = feat[src * kNF + 2 * t + 1];
-                t_g8 = target[src];
-            }
-            uint32_t a[4] = {pack_bf16(x_g[0], x_g[1]), pack_bf16(x_g8[0], x_g8[1]), 0u, 0u};
-            S.xt[(2 * t) * kTrainRows + lr0 + g] = (uint16_t)(a[0] & 0xFFFFu);
-            S.xt[(2 * t + 1) * kTrainRows + lr0 + g] = (uint16_t)(a[0] >> 16);
-            S.xt[(2 * t) * kTrainRows + lr0 + g + 8] = (uint16_t)(a[1] & 0xFFFFu);
-            S.xt[(2 * t + 1) * kTrainRows + lr0 + g + 8] = (uint16_t)(a[1] >> 16);
-            FwdKeep K;
-            float y_lo, y_hi;
-            mlp_fwd_tile<true>(M, a, lane, y_lo, y_hi, &K);
-            // h1 -> shared [in][row]
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const int c = 16 * kk + 2 * t;
-                S.h1t[c * kTrainRows + lr0 + g] = (uint16_t)(K.h1[kk][0] & 0xFFFFu);
-                S.h1t[(c + 1) * kTrainRows + lr0 + g] = (uint16_t)(K.h1[kk][0] >> 16);
-                S.h1t[c * kTrainRows + lr0 + g + 8] = (uint16_t)(K.h1[kk][1] & 0xFFFFu);
-                S.h1t[(c + 1) * kTrainRows + lr0 + g + 8] = (uint16_t)(K.h1[kk][1] >> 16);
-                S.h1t[(c + 8) * kTrainRows + lr0 + g] = (uint16_t)(K.h1[kk][2] & 0xFFFFu);
-                S.h1t[(c + 9) * kTrainRows + lr0 + g] = (uint16_t)(K.h1[kk][2] >> 16);
-                S.h1t[(c + 8) * kTrainRows + lr0 + g + 8] = (uint16_t)(K.h1[kk][3] & 0xFFFFu);
-                S.h1t[(c + 9) * kTrainRows + lr0 + g + 8] = (uint16_t)(K.h1[kk][3] >> 16);
-            }
-            // output gradient dL/dy = 2 e / B, e the (centred) residual
-            auto centred = [&](int r) -> float {
-                const uint32_t code = group[perm[row0 + r]];
-                const int q = (int)(code >> 16), size = (int)(code & 0xFFFFu);
-                float mean = 0.f;
-                for (int k = 0; k < size; ++k) mean += resid[r - q + k];
-                return resid[r] - mean / (float)size;
-            };
-            float dy_lo = 0.f, dy_hi = 0.f;
-            if (t == 0) {
-                if (v_g) {
-                    const float e = resid ? centred(r_g) : y_lo - t_g;
-                    dy_lo = 2.f * e * inv_b;
-                    loss += (double)e * e * inv_b;
-                }
-                if (v_g8) {
-                    const float e = resid ? centred(r_g8) : y_hi - t_g8;
-                    dy_hi = 2.f * e * inv_b;
-                    loss += (double)e * e * inv_b;
-                }
-                acc_b3 += dy_lo + dy_hi;
-            }
-            dy_lo = __shfl_sync(kFull, dy_lo, g * 4);
-            dy_hi = __shfl_sync(kFull, dy_hi, g * 4);
-            // dW3 and dz2 = dy W3 gelu'(z2)
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const float p0 = dy_lo * bf16lo(K.h2[kk][0]) + dy_hi * bf16lo(K.h2[kk][1]);
-                const float p1 = dy_lo * bf16hi(K.h2[kk][0]) + dy_hi * bf16hi(K.h2[kk][1]);
-                const float p2 = dy_lo * bf16lo(K.h2[kk][2]) + dy_hi * bf16lo(K.h2[kk][3]);
-                const float p3 = dy_lo * bf16hi(K.h2[kk][2]) + dy_hi * bf16hi(K.h2[kk][3]);
-                acc_w3[4 * kk + 0] += sum_over_g(p0);
-                acc_w3[4 * kk + 1] += sum_over_g(p1);
-                acc_w3[4 * kk + 2] += sum_over_g(p2);
-                acc_w3[4 * kk + 3] += sum_over_g(p3);
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = 8 * j + 2 * t;
-                const uint32_t w3pair = ld32(M->w3p + c);  // row 0 of w3p holds W3
-                const float w3a = bf16lo(w3pair), w3b = bf16hi(w3pair);
-                K.z2[j][0] = dy_lo * w3a * gelu_d(K.z2[j][0]);
-                K.z2[j][1] = dy_lo * w3b * gelu_d(K.z2[j][1]);
-                K.z2[j][2] = dy_hi * w3a * gelu_d(K.z2[j][2]);
-                K.z2[j][3] = dy_hi * w3b * gelu_d(K.z2[j][3]);
-                acc_b2[2 * j] += sum_over_g(K.z2[j][0] + K.z2[j][2]);
-                acc_b2[2 * j + 1] += sum_over_g(K.z2[j][1] + K.z2[j][3]);
-                S.dz2t[c * kTrainRows + lr0 + g] = bf16_bits(K.z2[j][0]);
-                S.dz2t[(c + 1) * kTrainRows + lr0 + g] = bf16_bits(K.z2[j][1]);
-                S.dz2t[c * kTrainRows + lr0 + g + 8] = bf16_bits(K.z2[j][2]);
-                S.dz2t[(c + 1) * kTrainRows + lr0 + g + 8] = bf16_bits(K.z2[j][3]);
-            }
-            // dh1 = dz2 W2 (tensor cores), dz1 = dh1 gelu'(z1)
-            uint32_t da[4][4];
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                da[kk][0] = pack_bf16(K.z2[2 * kk][0], K.z2[2 * kk][1]);
-                da[kk][1] = pack_bf16(K.z2[2 * kk][2], K.z2[2 * kk][3]);
-                da[kk][2] = pack_bf16(K.z2[2 * kk + 1][0], K.z2[2 * kk + 1][1]);
-                da[kk][3] = pack_bf16(K.z2[2 * kk + 1][2], K.z2[2 * kk + 1][3]);
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    mma16816(d, da[kk], ld32(M->w2t + (8 * j + g) * kWS + 16 * kk + 2 * t),
-                             ld32(M->w2t + (8 * j + g) * kWS + 16 * kk + 2 * t + 8));
-                const int c = 8 * j + 2 * t;
-                const float z0 = d[0] * gelu_d(K.z1[j][0]), z1 = d[1] * gelu_d(K.z1[j][1]);
-                const float z2 = d[2] * gelu_d(K.z1[j][2]), z3 = d[3] * gelu_d(K.z1[j][3]);
-                acc_b1[2 * j] += sum_over_g(z0 + z2);
-                acc_b1[2 * j + 1] += sum_over_g(z1 + z3);
-                S.dz1t[c * kTrainRows + lr0 + g] = bf16_bits(z0);
-                S.dz1t[(c + 1) * kTrainRows + lr0 + g] = bf16_bits(z1);
-                S.dz1t[c * kTrainRows + lr0 + g + 8] = bf16_bits(z2);
-                S.dz1t[(c + 1) * kTrainRows + lr0 + g + 8] = bf16_bits(z3);
-            }
-        }
-        __syncthreads();
-        // weight gradients over the CTA's 128 rows: warp w owns output rows 16w..16w+15
-#pragma unroll 1
-        for (int kt = 0; kt < kTrainRows / 16; ++kt) {
-            const uint16_t* A2 = S.dz2t + (16 * w + g) * kTrainRows + 16 * kt + 2 * t;
-            uint32_t a2[4] = {ld32(A2), ld32(A2 + 8 * kTrainRows), ld32(A2 + 8), ld32(A2 + 8 * kTrainRows + 8)};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint16_t* Bp = S.h1t + (8 * j + g) * kTrainRows + 16 * kt + 2 * t;
-                mma16816(acc_w2[j], a2, ld32(Bp), ld32(Bp + 8));
-            }
-            const uint16_t* A1 = S.dz1t + (16 * w + g) * kTrainRows + 16 * kt + 2 * t;
-            uint32_t a1[4] = {ld32(A1), ld32(A1 + 8 * kTrainRows), ld32(A1 + 8), ld32(A1 + 8 * kTrainRows + 8)};
-            const uint16_t* Bx = S.xt + g * kTrainRows + 16 * kt + 2 * t;
-            mma16816(acc_w1, a1, ld32(Bx), ld32(Bx + 8));
-        }
-        __syncthreads();
-    }
-    // flush into this CTA's row of partial sums (a fixed-order reduction over
-    // the CTAs follows, so the gradient does not depend on scheduling): the
-    // weight entries belong to one lane each, the bias and W3 entries of the
-    // four warps are added in warp order through shared memory
-    float* prow = part + (size_t)blockIdx.x * kNParam;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int row = 16 * w + g, col = 8 * j + 2 * t;
-        prow[oW2 + row * kNH + col] = acc_w2[j][0];
-        prow[oW2 + row * kNH + col + 1] = acc_w2[j][1];
-        prow[oW2 + (row + 8) * kNH + col] = acc_w2[j][2];
-        prow[oW2 + (row + 8) * kNH + col + 1] = acc_w2[j][3];
-    }
+// Gradient of the loss over rows perm[row0 .. row0 + B) of (feat, target)
+// into this CTA's row of partial sums (part[blockIdx.x][kNParam],
+// loss_part[blockIdx.x]).  resid == nullptr: mean squared error.  Otherwise
+// the centred loss: resid[r] is the residual of batch row r (from
+// mlp_resid_kernel), group[] the group code of a pair (index within its step
+// << 16 | the step's pair count), and the rows of a step are consecutive in
+// the batch.  *err is set if an MMA completion wait runs out.
+__global__ void __launch_bounds__(kTcRows) mlp_grad_kernel(const DevModel* Mg, const float* feat,
+                                                           const float* target, const int* perm, int64_t row0,
+                                                           int B, float inv_b, const float* resid,
+                                                           const uint32_t* group, float* part, double* loss_part,
+                                                           int* err)
+{
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = tid;  // tile row and TMEM lane
     {
-        const int row = 16 * w + g, col = 2 * t;
-        prow[oW1 + row * kNF + col] = acc_w1[0];
-        prow[oW1 + row * kNF + col + 1] = acc_w1[1];
-        prow[oW1 + (row + 8) * kNF + col] = acc_w1[2];
-        prow[oW1 + (row + 8) * kNF + col + 1] = acc_w1[3];
+        uint4* p = reinterpret_cast<uint4*>(smem_raw);
+        constexpr int n16 = (int)(offsetof(TcSmem, w1) / 16);
+        for (int q = tid; q < n16; q += kTcRows) p[q] = make_uint4(0u, 0u, 0u, 0u);
     }
-    float* red = reinterpret_cast<float*>(S.dz2t);  // [kTrainWarps][3 * kNH + 1], free after the last iteration
-    double* lred = reinterpret_cast<double*>(S.h1t);
-    constexpr int kRed = 3 * kNH + 1;
-    if (g == 0) {
-        for (int j = 0; j < 8; ++j) {
-            red[w * kRed + 8 * j + 2 * t] = acc_b1[2 * j];
-            red[w * kRed + 8 * j + 2 * t + 1] = acc_b1[2 * j + 1];
-            red[w * kRed + kNH + 8 * j + 2 * t] = acc_b2[2 * j];
-            red[w * kRed + kNH + 8 * j + 2 * t + 1] = acc_b2[2 * j + 1];
-        }
-        for (int kk = 0; kk < 4; ++kk) {
-            red[w * kRed + 2 * kNH + 16 * kk + 2 * t] = acc_w3[4 * kk + 0];
-            red[w * kRed + 2 * kNH + 16 * kk + 2 * t + 1] = acc_w3[4 * kk + 1];
-            red[w * kRed + 2 * kNH + 16 * kk + 8 + 2 * t] = acc_w3[4 * kk + 2];
-            red[w * kRed + 2 * kNH + 16 * kk + 8 + 2 * t + 1] = acc_w3[4 * kk + 3];
-        }
-    }
-    if (t == 0) {
-        float b3 = acc_b3;
-        b3 += __shfl_xor_sync(0x11111111u, b3, 4);
-        b3 += __shfl_xor_sync(0x11111111u, b3, 8);
-        b3 += __shfl_xor_sync(0x11111111u, b3, 16);
-        if (g == 0) red[w * kRed + 3 * kNH] = b3;
-    }
-    for (int o = 16; o; o >>= 1) loss += __shfl_xor_sync(kFull, loss, o);
-    if (lane == 0) lred[w] = loss;
     __syncthreads();
-    for (int i = tid; i < kRed; i += blockDim.x) {
-        float v = 0.f;
-        for (int q = 0; q < kTrainWarps; ++q) v += red[q * kRed + i];
-        const int dst = i < kNH ? oB1 + i : i < 2 * kNH ? oB2 + (i - kNH) : i < 3 * kNH ? oW3 + (i - 2 * kNH) : oB3;
-        prow[dst] = v;
+    for (int q = tid; q < kNH * kCX; q += kTcRows) {
+        const int h = q / kCX, i = q % kCX;
+        *reinterpret_cast<uint16_t*>(S.w1 + blk_off(h, i, kCX)) = i < kNF ? Mg->w1p[h * kW1S + i] : (uint16_t)0;
     }
+    for (int q = tid; q < kNH * kNH; q += kTcRows) {
+        const int o = q / kNH, i = q % kNH;
+        *reinterpret_cast<uint16_t*>(S.w2 + blk_off(o, i, kNH)) = Mg->w2[o * kWS + i];
+    }
+    for (int q = tid; q < kNH; q += kTcRows) {
+        S.b1[q] = Mg->b1[q];
+        S.b2[q] = Mg->b2[q];
+        S.w3[q] = __uint_as_float((uint32_t)Mg->w3p[q] << 16);
+    }
+    *reinterpret_cast<uint16_t*>(S.tX + blk_off(r, kNF, kCX)) = kBf16One;
+    *reinterpret_cast<uint16_t*>(S.tH + blk_off(r, kNH, kCH)) = kBf16One;
     if (tid == 0) {
-        double l = 0.0;
-        for (int q = 0; q < kTrainWarps; ++q) l += lred[q];
-        loss_part[blockIdx.x] = l;
+        S.b3 = Mg->b3[0];
+        mbar_init(&S.mbar, 1);
     }
+    if (warp == 0) tmem_alloc(&S.tmem, kTmemCols);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's TMEM lanes
+    const uint32_t aX = smem_addr(S.tX), aH = smem_addr(S.tH), aA = smem_addr(S.tA), aB = smem_addr(S.tB),
+                   aW1 = smem_addr(S.w1), aW2 = smem_addr(S.w2);
+    const uint32_t id64 = umma_idesc_bf16(128, 64, 0, 0), id3 = umma_idesc_bf16(128, 64, 0, 1),
+                   id4 = umma_idesc_bf16(128, 80, 1, 1), id5 = umma_idesc_bf16(128, 16, 1, 1);
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    float acc_b3 = 0.f;
+    double loss = 0.0;
+    // the operand tiles written by every thread go to the tensor core
+    auto publish = [&]() {
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+    };
+    // every thread waits for the MMAs committed last; false (for all) if the wait ran out
+    auto complete = [&]() -> bool {
+        const bool done = mbar_wait(&S.mbar, phase, kWaitPolls);
+        phase ^= 1u;
+        tc_fence_after();
+        return __syncthreads_and(done) != 0;
+    };
+    auto centred = [&](int br) -> float {
+        const uint32_t code = group[perm[row0 + br]];
+        const int q = (int)(code >> 16), size = (int)(code & 0xFFFFu);
+        float mean = 0.f;
+        for (int k = 0; k < size; ++k) mean += resid[br - q + k];
+        return resid[br] - mean / (float)size;
+    };
+    const int iters = (B + kTcRows - 1) / kTcRows;
+    for (int it = blockIdx.x; it < iters; it += gridDim.x) {
+        const int br = it * kTcRows + r;
+        const bool valid = br < B;
+        float x[kNF] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, tg = 0.f;
+        if (valid) {
+            const int64_t src = perm[row0 + br];
+            const float4 lo = *reinterpret_cast<const float4*>(feat + src * kNF);
+            const float4 hi = *reinterpret_cast<const float4*>(feat + src * kNF + 4);
+            x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+            x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+            tg = target[src];
+        }
+        *reinterpret_cast<uint4*>(S.tX + blk_off(r, 0, kCX)) =
+            make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+        publish();
+        if (tid == 0) {  // G1
+            tc_fence_after();
+            umma_bf16(tmem + kD1, desc_kmajor(aX, kCX, 0), desc_kmajor(aW1, kCX, 0), id64, false);
+            umma_commit(&S.mbar);
+        }
+        if (!(ok = complete())) break;
+        // h1 = gelu(D1 + b1)
+#pragma unroll 1
+        for (int c0 = 0; c0 < kNH; c0 += 16) {
+            float d[16];
+            tmem_ld16(tl + kD1 + c0, d);
+            uint32_t p[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                p[q] = pack_bf16(gelu_f(d[2 * q] + S.b1[c0 + 2 * q]), gelu_f(d[2 * q + 1] + S.b1[c0 + 2 * q + 1]));
+            st_row16(S.tH, r, c0, kCH, p);
+        }
+        publish();
+        if (tid == 0) {  // G2
+            tc_fence_after();
+#pragma unroll
+            for (int k0 = 0; k0 < kNH; k0 += 16)
+                umma_bf16(tmem + kD2, desc_kmajor(aH, kCH, k0), desc_kmajor(aW2, kNH, k0), id64, k0 > 0);
+            umma_commit(&S.mbar);
+        }
+        if (!(ok = complete())) break;
+        // h2 = gelu(D2 + b2) and the output y (bf16 h2, as the network's inference has it)
+        float y = S.b3;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kNH; c0 += 16) {
+            float d[16];
+            tmem_ld16(tl + kD2 + c0, d);
+            uint32_t p[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                p[q] = pack_bf16(gelu_f(d[2 * q] + S.b2[c0 + 2 * q]), gelu_f(d[2 * q + 1] + S.b2[c0 + 2 * q + 1]));
+                y = fmaf(bf16lo(p[q]), S.w3[c0 + 2 * q], y);
+                y = fmaf(bf16hi(p[q]), S.w3[c0 + 2 * q + 1], y);
+            }
+            st_row16(S.tA, r, kNH + c0, kCA, p);
+        }
+        // dL/dy = 2 e / B, e the (centred) residual
+        float dy = 0.f;
+        if (valid) {
+            const float e = resid ? centred(br) : y - tg;
+            dy = 2.f * e * inv_b;
+            loss += (double)e * e * inv_b;
+        }
+        acc_b3 += dy;
+        // dz2 = dy w3 gelu'(z2)
+#pragma unroll 1
+        for (int c0 = 0; c0 < kNH; c0 += 16) {
+            float d[16];
+            tmem_ld16(tl + kD2 + c0, d);
+            uint32_t p[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = c0 + 2 * q;
+                p[q] = pack_bf16(dy * S.w3[c] * gelu_d(d[2 * q] + S.b2[c]),
+                                 dy * S.w3[c + 1] * gelu_d(d[2 * q + 1] + S.b2[c + 1]));
+            }
+            st_row16(S.tA, r, c0, kCA, p);
+        }
+        {  // [1, dy_hi, dy_lo, 0 ...] beside h1
+            const float dy_hi = __bfloat162float(__float2bfloat16_rn(dy));
+            *reinterpret_cast<uint4*>(S.tH + blk_off(r, kNH, kCH)) =
+                make_uint4(pack_bf16(1.f, dy_hi), pack_bf16(dy - dy_hi, 0.f), 0u, 0u);
+        }
+        publish();
+        if (tid == 0) {  // G3 (into D2's columns, consumed) and G4
+            tc_fence_after();
+#pragma unroll
+            for (int k0 = 0; k0 < kNH; k0 += 16)
+                umma_bf16(tmem + kD2, desc_kmajor(aA, kCA, k0), desc_mnmajor(aW2, kNH, k0, 0), id3, k0 > 0);
+#pragma unroll
+            for (int k0 = 0; k0 < kTcRows; k0 += 16)
+                umma_bf16(tmem + kD4, desc_mnmajor(aA, kCA, k0, 0), desc_mnmajor(aH, kCH, k0, 0), id4,
+                          !first || k0 > 0);
+            umma_commit(&S.mbar);
+        }
+        if (!(ok = complete())) break;
+        // dz1 = dh1 gelu'(z1)
+#pragma unroll 1
+        for (int c0 = 0; c0 < kNH; c0 += 16) {
+            float d[16], z[16];
+            tmem_ld16(tl + kD2 + c0, d);
+            tmem_ld16(tl + kD1 + c0, z);
+            uint32_t p[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = c0 + 2 * q;
+                p[q] = pack_bf16(d[2 * q] * gelu_d(z[2 * q] + S.b1[c]), d[2 * q + 1] * gelu_d(z[2 * q + 1] + S.b1[c + 1]));
+            }
+            st_row16(S.tB, r, c0, kCB, p);
+        }
+        publish();
+        if (tid == 0) {  // G5
+            tc_fence_after();
+#pragma unroll
+            for (int k0 = 0; k0 < kTcRows; k0 += 16)
+                umma_bf16(tmem + kD5, desc_mnmajor(aB, kCB, k0, 0), desc_mnmajor(aX, kCX, k0, 0), id5,
+                          !first || k0 > 0);
+            umma_commit(&S.mbar);
+        }
+        // the tiles are rewritten by the next iteration: wait for G5
+        if (!(ok = complete())) break;
+        first = false;
+    }
+    // this CTA's partial sums: the weight and bias entries from TMEM (one
+    // row per thread), b3 and the loss added in warp order
+    float* prow = part + (size_t)blockIdx.x * kNParam;
+    if (ok && !first) {
+        float w3s = 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 80; c0 += 16) {
+            float d[16];
+            tmem_ld16(tl + kD4 + c0, d);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int c = c0 + q;
+                if (r < kNH) {
+                    if (c < kNH) prow[oW2 + r * kNH + c] = d[q];
+                    else if (c == kNH) prow[oB2 + r] = d[q];
+                } else if (c == kNH + 1 || c == kNH + 2) {
+                    w3s += d[q];
+                }
+            }
+        }
+        if (r >= kNH) prow[oW3 + r - kNH] = w3s;
+        float d[16];
+        tmem_ld16(tl + kD5, d);
+        if (r < kNH) {
+#pragma unroll
+            for (int f = 0; f < kNF; ++f) prow[oW1 + r * kNF + f] = d[f];
+            prow[oB1 + r] = d[kNF];
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        acc_b3 += __shfl_xor_sync(kFull, acc_b3, o);
+        loss += __shfl_xor_sync(kFull, loss, o);
+    }
+    if (lane == 0) {
+        S.red[warp] = acc_b3;
+        S.lred[warp] = loss;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        float b3 = 0.f;
+        double l = 0.0;
+        for (int q = 0; q < kTcRows / 32; ++q) {
+            b3 += S.red[q];
+            l += S.lred[q];
+        }
+        prow[oB3] = b3;
+        loss_part[blockIdx.x] = l;
+        if (!ok) atomicExch(err, 1);
+    }
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // grad[i] = sum over the CTAs (in CTA order) of their partial sums; loss alike
@@ -423,9 +479,11 @@ cudaError_t launch_model_image(const float* master, void* img, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// workspace: [0, 256) the device error word (int, zeroed by the caller), then
+// the per-CTA partial sums and losses
 size_t mlp_grad_workspace_bytes(int sm_count)
 {
-    return (size_t)2 * sm_count * (kNParam * sizeof(float) + sizeof(double)) + 256;
+    return 256 + (size_t)2 * sm_count * (kNParam * sizeof(float) + sizeof(double)) + 256;
 }
 
 cudaError_t launch_mlp_grad(const void* img, const float* feat, const float* target, const int* perm, int64_t row0,
@@ -439,16 +497,17 @@ cudaError_t launch_mlp_grad(const void* img, const float* feat, const float* tar
         if (rg > 4 * sm_count) rg = 4 * sm_count;
         mlp_resid_kernel<<<rg, 128, 0, st>>>(M, feat, target, perm, row0, B, resid);
     }
-    const int smem = (int)sizeof(TrainSmem);
+    const int smem = (int)sizeof(TcSmem);
     cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int iters = (B + kTrainRows - 1) / kTrainRows;
-    const int grid = iters < 2 * sm_count ? iters : 2 * sm_count;
-    float* part = reinterpret_cast<float*>(work);
+    const int iters = (B + kTcRows - 1) / kTcRows;
+    const int grid = iters < 2 * sm_count ? iters : 2 * sm_count;  // two CTAs per SM (TMEM 2 x 256 columns)
+    int* err = reinterpret_cast<int*>(work);
+    float* part = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(work) + 256);
     double* loss_part = reinterpret_cast<double*>(
-        reinterpret_cast<uint8_t*>(work) + ((size_t)2 * sm_count * kNParam * sizeof(float) + 255) / 256 * 256);
-    mlp_grad_kernel<<<grid, kTrainWarps * 32, smem, st>>>(M, feat, target, perm, row0, B, 1.0f / (float)B,
-                                                           group ? resid : nullptr, group, part, loss_part);
+        reinterpret_cast<uint8_t*>(work) + 256 + ((size_t)2 * sm_count * kNParam * sizeof(float) + 255) / 256 * 256);
+    mlp_grad_kernel<<<grid, kTcRows, smem, st>>>(M, feat, target, perm, row0, B, 1.0f / (float)B,
+                                                 group ? resid : nullptr, group, part, loss_part, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     grad_reduce_kernel<<<(kNParam + 255) / 256, 256, 0, st>>>(part, loss_part, grid, grad, loss);

@@ -102,6 +102,34 @@ def test_mlp_gradient_matches_oracle(centred):
     m.close()
 
 
+@pytest.mark.parametrize("centred", [False, True])
+def test_mlp_gradient_many_tiles_per_cta(centred):
+    """50,003 rows: 391 row tiles of 128 over at most two CTAs per SM, so most
+    CTAs accumulate several tiles in tensor memory before their partial sums
+    are read out, and the last tile is ragged; the result is reproducible
+    (fixed-order reduction over the CTAs)."""
+    rng = np.random.default_rng(14)
+    p = rand_params(rng, 0.3)
+    m = ctx().model(p)
+    n = 50_003
+    X = rng.normal(size=(n, 8)).astype(np.float32)
+    T = rng.normal(size=n).astype(np.float32)
+    grp = step_groups(rng, n) if centred else None
+    loss, g = m.gradient(X, T, grp)
+    loss2, g2 = m.gradient(X, T, grp)
+    assert loss == loss2 and np.array_equal(g, g2)
+    ref_loss, ref = O.mlp_grad(oracle_params(p), bf16(X).astype(np.float64), T.astype(np.float64), grp)
+    assert loss == pytest.approx(ref_loss, rel=2e-2)
+    for name, (a, b) in BLOCKS.items():
+        if name == "b3":
+            continue
+        u, v = g[a:b].astype(np.float64), ref[a:b]
+        cos = float(u @ v / (np.linalg.norm(u) * np.linalg.norm(v)))
+        rel = float(np.linalg.norm(u - v) / np.linalg.norm(v))
+        assert cos > 0.999 and rel < 5e-2, (name, cos, rel)
+    m.close()
+
+
 def test_mlp_gradient_rejects_torn_groups():
     rng = np.random.default_rng(5)
     m = ctx().model(rand_params(rng))
