@@ -90,7 +90,7 @@ def parse():
     p.add_argument("--train-mats", type=int, default=100, help="learned workload: training matrices (n = 1e4)")
     p.add_argument("--train-pairs", type=int, default=10_000_000, help="learned workload: training pairs")
     p.add_argument("--workload", default="batch",
-                   choices=["batch", "serving", "large", "e4", "theta", "ablation", "learned"],
+                   choices=["batch", "serving", "large", "e4", "theta", "ablation", "learned", "grad"],
                    help="batch: the 64-matrix batch (the metric); serving: the Poisson request stream; "
                         "large: one n = 1e5 band matrix (state in global memory)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of each serving load")
@@ -912,6 +912,44 @@ def run_learned_scale(args, local):
     ctx.close()
 
 
+def run_grad(args, local):
+    """The learned proposal's training gradient (the tcgen05 kernel, with the
+    residual pass and the fixed-order reduction) on synthetic rows: standard-
+    normal features and targets, mean squared error, B = 8,192 (one training
+    batch), 2^20 and 2^22 rows.  Device time of the kernels per call
+    (pm_call_info.grad_kernel_ms, median of the calls) against the bf16 tensor
+    peak, at 3 x 9,344 flop per row (the 8-64-64-1 network's forward and the
+    two backward products)."""
+    import torch
+    from paper_2608_15390_b300 import binding as B
+    torch.cuda.set_device(local)
+    ctx = B.Context(local, torch.cuda.current_stream().cuda_stream)
+    model = ctx.model(seed=1)
+    peaks = measured_peaks()
+    tc_peak = peaks["bf16_tflops"] if peaks else 1800.0
+    rng = np.random.default_rng(0)
+    out = []
+    for n in (8192, 1 << 20, 1 << 22):
+        X = rng.normal(size=(n, 8)).astype(np.float32)
+        T = rng.normal(size=n).astype(np.float32)
+        model.gradient(X, T)
+        ms = []
+        for _ in range(max(3, args.steps)):
+            model.gradient(X, T)
+            ms.append(ctx.last_call_info()["grad_kernel_ms"])
+        med = float(np.median(ms))
+        tflops = 3 * 9344 * n / (med * 1e-3) / 1e12
+        out.append({"rows": n, "kernel_ms": med, "rows_per_s": n / (med * 1e-3), "tflops": tflops,
+                    "frac_of_bf16_peak": tflops / tc_peak})
+        print(f"rows {n}: {med:.3f} ms, {tflops:.1f} TFLOP/s", file=sys.stderr, flush=True)
+    print(json.dumps({"workload": "grad", "metric": "training-gradient rows/s (device time)", "runs": out,
+                      "peak": {"bf16_tflops": tc_peak,
+                               "source": "measured (MEASURED_PEAKS.json)" if peaks else "fallback"},
+                      "data": "synthetic"}), flush=True)
+    model.close()
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -926,10 +964,10 @@ def main():
         if rank == 0:
             run_large(args, local)
         return
-    if args.workload in ("e4", "theta", "ablation", "learned"):
+    if args.workload in ("e4", "theta", "ablation", "learned", "grad"):
         if rank == 0:
             {"e4": run_e4, "theta": run_theta, "ablation": run_ablation,
-             "learned": run_learned_scale}[args.workload](args, local)
+             "learned": run_learned_scale, "grad": run_grad}[args.workload](args, local)
         return
     import torch
     torch.cuda.set_device(local)

@@ -193,6 +193,8 @@ typedef struct {
     int32_t warps_per_cta;    /* warps (trajectory slots) per CTA */
     pm_plan_info first_plan;  /* layout of the call's first matrix (g = 0: no launch;
                                  tuned and the probe rates are not filled in) */
+    double grad_kernel_ms;    /* device time of the most recent pm_mlp_gradient's kernels
+                                 (residual pass, tensor-core gradient, reduction; 0: none) */
 } pm_call_info;
 
 typedef struct pm_context pm_context;

@@ -111,7 +111,7 @@ class pm_request_done(C.Structure):
 class pm_call_info(C.Structure):
     _fields_ = [("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64), ("traj_kernel_ms", C.c_double),
                 ("prep_kernel_ms", C.c_double), ("grid", C.c_int32), ("warps_per_cta", C.c_int32),
-                ("first_plan", pm_plan_info)]
+                ("first_plan", pm_plan_info), ("grad_kernel_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "first_plan"}

@@ -50,7 +50,7 @@ struct pm_context {
     int* cancel_dev = nullptr;
     std::map<std::string, std::array<int, 6>> tuned;  // autotuned layout policy per size class
     std::vector<pm_batch*> batches;                     // live batches (destroyed with the context)
-    double last_traj_ms = 0, last_prep_ms = 0;
+    double last_traj_ms = 0, last_prep_ms = 0, last_grad_ms = 0;
     uint64_t last_h2d = 0, last_d2h = 0;
     int last_grid = 0, last_wpc = 0;
     Plan last_plan{};
@@ -1310,6 +1310,7 @@ pm_status pm_last_call_info(const pm_context* ctx, pm_call_info* info)
     info->first_plan.rc_smem = p.rc_smem; info->first_plan.gstate = p.gstate; info->first_plan.dm_smem = p.dm_smem;
     info->first_plan.pair = p.pair;
     info->first_plan.probe_traj_per_s = info->first_plan.heuristic_traj_per_s = -1.0;
+    info->grad_kernel_ms = ctx->last_grad_ms;
     return PM_OK;
 }
 
@@ -2227,9 +2228,21 @@ pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, co
     DevBuf bw;
     PM_CUDA(cudaMalloc(&bw.p, mlp_grad_workspace_bytes(ctx->sm_count)));
     PM_CUDA(cudaMemsetAsync(bw.p, 0, 4, ctx->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PM_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, PM_ECUDA, "cudaEventCreate");
+    }
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } evg{e0, e1};
+    PM_CUDA(cudaEventRecord(e0, ctx->stream));
     PM_CUDA(launch_mlp_grad(m->img, (const float*)bx.p, (const float*)bt.p, (const int*)bp.p, 0, (int)B,
                             (const uint32_t*)bg.p, (float*)br.p, m->grad, (double*)bl.p, ctx->sm_count, bw.p,
                             ctx->stream));
+    PM_CUDA(cudaEventRecord(e1, ctx->stream));
     PM_CUDA(cudaMemcpyAsync(grad, m->grad, 4 * model_param_count(), cudaMemcpyDeviceToHost, ctx->stream));
     double l = 0;
     int werr = 0;
@@ -2237,6 +2250,8 @@ pm_status pm_mlp_gradient(pm_context* ctx, const pm_model* m, const float* X, co
     PM_CUDA(cudaMemcpyAsync(&werr, bw.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
     if (werr) return fail(ctx, PM_EDEVICE, "a tensor-core completion wait ran out in the gradient kernel");
+    float gms = 0.f;
+    ctx->last_grad_ms = cudaEventElapsedTime(&gms, e0, e1) == cudaSuccess ? gms : -1.0;
     if (loss) *loss = l;
     return PM_OK;
 }

@@ -61,7 +61,7 @@ constexpr uint32_t kWaitPolls = 1u << 24;
 constexpr uint16_t kBf16One = 0x3F80;
 
 struct TcSmem {
-    uint8_t tX[kTcRows * kCX * 2];   // [X | 1 | 0]
+    uint8_t tX[2][kTcRows * kCX * 2];  // [X | 1 | 0], two tiles (the next tile's G1 overlaps this one's G5)
     uint8_t tH[kTcRows * kCH * 2];   // [h1 | 1, dy_hi, dy_lo, 0 ...]
     uint8_t tA[kTcRows * kCA * 2];   // [dz2 | h2]
     uint8_t tB[kTcRows * kCB * 2];   // [dz1 | 0]
@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(kTcRows) mlp_grad_kernel(const DevModel* Mg, c
         S.b2[q] = Mg->b2[q];
         S.w3[q] = __uint_as_float((uint32_t)Mg->w3p[q] << 16);
     }
-    *reinterpret_cast<uint16_t*>(S.tX + blk_off(r, kNF, kCX)) = kBf16One;
+    *reinterpret_cast<uint16_t*>(S.tX[0] + blk_off(r, kNF, kCX)) = kBf16One;
+    *reinterpret_cast<uint16_t*>(S.tX[1] + blk_off(r, kNF, kCX)) = kBf16One;
     *reinterpret_cast<uint16_t*>(S.tH + blk_off(r, kNH, kCH)) = kBf16One;
     if (tid == 0) {
         S.b3 = Mg->b3[0];
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(kTcRows) mlp_grad_kernel(const DevModel* Mg, c
     tc_fence_after();
     const uint32_t tmem = S.tmem;
     const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's TMEM lanes
-    const uint32_t aX = smem_addr(S.tX), aH = smem_addr(S.tH), aA = smem_addr(S.tA), aB = smem_addr(S.tB),
+    const uint32_t aX0 = smem_addr(S.tX[0]), aH = smem_addr(S.tH), aA = smem_addr(S.tA), aB = smem_addr(S.tB),
                    aW1 = smem_addr(S.w1), aW2 = smem_addr(S.w2);
     const uint32_t id64 = umma_idesc_bf16(128, 64, 0, 0), id3 = umma_idesc_bf16(128, 64, 0, 1),
                    id4 = umma_idesc_bf16(128, 80, 1, 1), id5 = umma_idesc_bf16(128, 16, 1, 1);
@@ -158,12 +159,13 @@ __global__ void __launch_bounds__(kTcRows) mlp_grad_kernel(const DevModel* Mg, c
         for (int k = 0; k < size; ++k) mean += resid[br - q + k];
         return resid[br] - mean / (float)size;
     };
-    const int iters = (B + kTcRows - 1) / kTcRows;
-    for (int it = blockIdx.x; it < iters; it += gridDim.x) {
-        const int br = it * kTcRows + r;
-        const bool valid = br < B;
-        float x[kNF] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, tg = 0.f;
-        if (valid) {
+    // features and target of row r of tile `tile` (zero past the batch)
+    auto load_x = [&](int tile, float (&x)[kNF], float& tg) {
+        const int br = tile * kTcRows + r;
+#pragma unroll
+        for (int f = 0; f < kNF; ++f) x[f] = 0.f;
+        tg = 0.f;
+        if (br < B) {
             const int64_t src = perm[row0 + br];
             const float4 lo = *reinterpret_cast<const float4*>(feat + src * kNF);
             const float4 hi = *reinterpret_cast<const float4*>(feat + src * kNF + 4);
@@ -171,24 +173,48 @@ __global__ void __launch_bounds__(kTcRows) mlp_grad_kernel(const DevModel* Mg, c
             x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
             tg = target[src];
         }
-        *reinterpret_cast<uint4*>(S.tX + blk_off(r, 0, kCX)) =
+    };
+    auto store_x = [&](int buf, const float (&x)[kNF]) {
+        *reinterpret_cast<uint4*>(S.tX[buf] + blk_off(r, 0, kCX)) =
             make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
-        publish();
-        if (tid == 0) {  // G1
-            tc_fence_after();
-            umma_bf16(tmem + kD1, desc_kmajor(aX, kCX, 0), desc_kmajor(aW1, kCX, 0), id64, false);
-            umma_commit(&S.mbar);
-        }
-        if (!(ok = complete())) break;
-        // h1 = gelu(D1 + b1)
-#pragma unroll 1
+    };
+    auto issue_g1 = [&](int buf) {
+        umma_bf16(tmem + kD1, desc_kmajor(aX0 + (uint32_t)buf * (uint32_t)sizeof(S.tX[0]), kCX, 0),
+                  desc_kmajor(aW1, kCX, 0), id64, false);
+    };
+    const int iters = (B + kTcRows - 1) / kTcRows;
+    int it = blockIdx.x, buf = 0;
+    float x[kNF], tg;
+    load_x(it, x, tg);
+    store_x(0, x);
+    publish();
+    if (tid == 0) {  // G1 of the first tile
+        tc_fence_after();
+        issue_g1(0);
+        umma_commit(&S.mbar);
+    }
+    float gd1[kNH];  // gelu'(z1) of row r, from epilogue 1 to epilogue 3
+    for (; it < iters; it += gridDim.x, buf ^= 1) {
+        const int br = it * kTcRows + r;
+        const bool valid = br < B;
+        const int nxt = it + (int)gridDim.x;
+        const bool has_next = nxt < iters;
+        float xn[kNF], tgn;
+        load_x(nxt, xn, tgn);  // in flight during this tile (zero if none)
+        if (!(ok = complete())) break;  // G1 of this tile (and G5 of the previous one)
+        // h1 = gelu(D1 + b1), and gelu'(z1) for the backward pass
+#pragma unroll
         for (int c0 = 0; c0 < kNH; c0 += 16) {
             float d[16];
             tmem_ld16(tl + kD1 + c0, d);
             uint32_t p[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                p[q] = pack_bf16(gelu_f(d[2 * q] + S.b1[c0 + 2 * q]), gelu_f(d[2 * q + 1] + S.b1[c0 + 2 * q + 1]));
+            for (int q = 0; q < 8; ++q) {
+                float h0, h1v;
+                gelu_fd(d[2 * q] + S.b1[c0 + 2 * q], h0, gd1[c0 + 2 * q]);
+                gelu_fd(d[2 * q + 1] + S.b1[c0 + 2 * q + 1], h1v, gd1[c0 + 2 * q + 1]);
+                p[q] = pack_bf16(h0, h1v);
+            }
             st_row16(S.tH, r, c0, kCH, p);
         }
         publish();
@@ -201,15 +227,18 @@ __global__ void __launch_bounds__(kTcRows) mlp_grad_kernel(const DevModel* Mg, c
         }
         if (!(ok = complete())) break;
         // h2 = gelu(D2 + b2) and the output y (bf16 h2, as the network's inference has it)
-        float y = S.b3;
-#pragma unroll 1
+        float y = S.b3, gd2[kNH];
+#pragma unroll
         for (int c0 = 0; c0 < kNH; c0 += 16) {
             float d[16];
             tmem_ld16(tl + kD2 + c0, d);
             uint32_t p[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                p[q] = pack_bf16(gelu_f(d[2 * q] + S.b2[c0 + 2 * q]), gelu_f(d[2 * q + 1] + S.b2[c0 + 2 * q + 1]));
+                float h0, h1v;
+                gelu_fd(d[2 * q] + S.b2[c0 + 2 * q], h0, gd2[c0 + 2 * q]);
+                gelu_fd(d[2 * q + 1] + S.b2[c0 + 2 * q + 1], h1v, gd2[c0 + 2 * q + 1]);
+                p[q] = pack_bf16(h0, h1v);
                 y = fmaf(bf16lo(p[q]), S.w3[c0 + 2 * q], y);
                 y = fmaf(bf16hi(p[q]), S.w3[c0 + 2 * q + 1], y);
             }
@@ -224,16 +253,13 @@ __global__ void __launch_bounds__(kTcRows) mlp_grad_kernel(const DevModel* Mg, c
         }
         acc_b3 += dy;
         // dz2 = dy w3 gelu'(z2)
-#pragma unroll 1
+#pragma unroll
         for (int c0 = 0; c0 < kNH; c0 += 16) {
-            float d[16];
-            tmem_ld16(tl + kD2 + c0, d);
             uint32_t p[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int c = c0 + 2 * q;
-                p[q] = pack_bf16(dy * S.w3[c] * gelu_d(d[2 * q] + S.b2[c]),
-                                 dy * S.w3[c + 1] * gelu_d(d[2 * q + 1] + S.b2[c + 1]));
+                p[q] = pack_bf16(dy * S.w3[c] * gd2[c], dy * S.w3[c + 1] * gd2[c + 1]);
             }
             st_row16(S.tA, r, c0, kCA, p);
         }
@@ -256,32 +282,36 @@ __global__ void __launch_bounds__(kTcRows) mlp_grad_kernel(const DevModel* Mg, c
         }
         if (!(ok = complete())) break;
         // dz1 = dh1 gelu'(z1)
-#pragma unroll 1
+#pragma unroll
         for (int c0 = 0; c0 < kNH; c0 += 16) {
-            float d[16], z[16];
+            float d[16];
             tmem_ld16(tl + kD2 + c0, d);
-            tmem_ld16(tl + kD1 + c0, z);
             uint32_t p[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int c = c0 + 2 * q;
-                p[q] = pack_bf16(d[2 * q] * gelu_d(z[2 * q] + S.b1[c]), d[2 * q + 1] * gelu_d(z[2 * q + 1] + S.b1[c + 1]));
+                p[q] = pack_bf16(d[2 * q] * gd1[c], d[2 * q + 1] * gd1[c + 1]);
             }
             st_row16(S.tB, r, c0, kCB, p);
         }
+        if (has_next) store_x(buf ^ 1, xn);
         publish();
-        if (tid == 0) {  // G5
+        if (tid == 0) {  // G5 of this tile, G1 of the next
             tc_fence_after();
+            const uint32_t aX = aX0 + (uint32_t)buf * (uint32_t)sizeof(S.tX[0]);
 #pragma unroll
             for (int k0 = 0; k0 < kTcRows; k0 += 16)
                 umma_bf16(tmem + kD5, desc_mnmajor(aB, kCB, k0, 0), desc_mnmajor(aX, kCX, k0, 0), id5,
                           !first || k0 > 0);
+            if (has_next) issue_g1(buf ^ 1);
             umma_commit(&S.mbar);
         }
-        // the tiles are rewritten by the next iteration: wait for G5
-        if (!(ok = complete())) break;
         first = false;
+#pragma unroll
+        for (int f = 0; f < kNF; ++f) x[f] = xn[f];
+        tg = tgn;
     }
+    if (ok && !first) ok = complete();  // the last G5
     // this CTA's partial sums: the weight and bias entries from TMEM (one
     // row per thread), b3 and the loss added in warp order
     float* prow = part + (size_t)blockIdx.x * kNParam;

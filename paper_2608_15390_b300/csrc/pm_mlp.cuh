@@ -66,6 +66,14 @@ __device__ __forceinline__ float gelu_f(float x)
     const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
     return 0.5f * x * (1.0f + tanh_hw(u));
 }
+// both at once, from one tanh
+__device__ __forceinline__ void gelu_fd(float x, float& g, float& gd)
+{
+    const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
+    const float th = tanh_hw(u);
+    g = 0.5f * x * (1.0f + th);
+    gd = 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * 0.7978845608028654f * (1.0f + 0.134145f * x * x);
+}
 __device__ __forceinline__ float gelu_d(float x)
 {
     const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
