@@ -396,6 +396,8 @@ struct Run {
     const DevMatrix* prepared = nullptr;
     // per matrix, the local index of its first trajectory (empty: 0)
     std::vector<uint64_t> first_local;
+    // order of the matrices' chunks in the launch (empty: most expensive first)
+    std::vector<int> order;
     // run control (0: none): device-side time budget of the trajectory launch
     uint64_t budget_ns = 0;
     double rse_target = 0, budget_s = 0;
@@ -609,15 +611,20 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
             gstate_bytes = std::max(gstate_bytes, global_state_bytes(R.mats[k].n, (int)S.rb, S.plans[k].lists != 0));
     const SlotLayout sl =
         slot_layout(S.n_max, (int)S.m_max, (int)S.rb, scales, local, dm, gstate_bytes, R.model != nullptr);
-    // chunks: most expensive matrices first, a few trajectories per group
+    // chunks: the caller's order, else the most expensive matrices first; a
+    // few trajectories per group
     std::vector<int> order(count);
     for (int k = 0; k < count; ++k) order[k] = k;
     const bool full_sk = R.s.sk == 1 || R.s.sk == 2;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const double ca = (double)R.mats[a].nnz * (full_sk ? R.mats[a].n : 1);
-        const double cb = (double)R.mats[b].nnz * (full_sk ? R.mats[b].n : 1);
-        return ca > cb;
-    });
+    if ((int)R.order.size() == count) {
+        order = R.order;
+    } else {
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const double ca = (double)R.mats[a].nnz * (full_sk ? R.mats[a].n : 1);
+            const double cb = (double)R.mats[b].nnz * (full_sk ? R.mats[b].n : 1);
+            return ca > cb;
+        });
+    }
     S.chunks.clear();
     for (int k : order) {
         const uint64_t csz = (uint64_t)S.plans[k].groups * 2;
@@ -936,6 +943,11 @@ namespace {
 
 // Trajectories a matrix must have before its RSE may end its run.
 constexpr uint64_t kMinTrajForTarget = 1024;
+// Budgeted rounds: the share of the remaining budget one round may plan for
+// (the rest is kept for the rounds that follow it, with fresher estimates),
+// and the smallest allocation worth a matrix's chunks in a round.
+constexpr double kRoundShare = 0.6;
+constexpr uint64_t kMinRoundTraj = 256;
 
 // A call with an RSE target or a time budget: preprocessing once, then rounds
 // of trajectories over the matrices still running (consecutive trajectory
@@ -945,6 +957,16 @@ constexpr uint64_t kMinTrajForTarget = 1024;
 // kMinTrajForTarget trajectories (or all of n_traj) and two alive, or when its
 // n_traj ran; the call stops when every matrix has stopped, the budget is
 // spent (PM_ETIMEOUT) or the context is cancelled (PM_ECANCELLED).
+//
+// With an RSE target, a time budget and several matrices, the rounds after
+// the first are planned cheapest-to-finish first: each running matrix's trajectories still
+// needed for the target (1.1 M (RSE / target)^2 - M) are priced at its
+// measured launch time per trajectory in the previous rounds, and the
+// matrices are served in increasing order of that price (each round's
+// allocation capped at 5x what the matrix has), until the round's plan fills
+// kRoundShare of the remaining budget (all of it once little is left).  So
+// the budget goes first to the matrices it can bring to the target, and what
+// is left to the rest; their chunks run in the same order.
 pm_status execute_rounds(pm_context* ctx, Run& R)
 {
     const auto t0 = std::chrono::steady_clock::now();
@@ -977,8 +999,10 @@ pm_status execute_rounds(pm_context* ctx, Run& R)
     if (R.log_x)
         for (uint64_t i = 0; i < req_prefix[count]; ++i) R.log_x[i] = NAN;
     std::vector<Suff> acc(count);
-    std::vector<uint64_t> done(count, 0), size(count, 0);
+    std::vector<uint64_t> done(count, 0), size(count, 0), still(count, 0);
+    std::vector<double> ms_per_traj(count, -1.0);  // launch ms per trajectory, last measured
     std::vector<int32_t> stop(count, -1);
+    int round = 0;
     const uint64_t slots = (uint64_t)ctx->sm_count * kCtaWarps;
     for (int k = 0; k < count; ++k) {
         if (R.ntraj[k] == 0) stop[k] = PM_STOP_COMPLETE;
@@ -1007,6 +1031,35 @@ pm_status execute_rounds(pm_context* ctx, Run& R)
             const double rem = R.budget_s - elapsed();
             if (rem <= 0) { stop_bits |= ST_TIMEOUT; break; }
             Q.budget_ns = (uint64_t)std::max(1.0, rem * 1e9);
+            if (R.rse_target > 0 && round > 0 && count > 1) {  // cheapest to finish first
+                double known = 0;
+                int nk = 0;
+                for (int k = 0; k < count; ++k)
+                    if (ms_per_traj[k] > 0) { known += ms_per_traj[k]; ++nk; }
+                const double fallback = nk ? known / nk : 1e-3;
+                auto price = [&](int k) { return ms_per_traj[k] > 0 ? ms_per_traj[k] : fallback; };
+                std::vector<int> cand;
+                for (int k = 0; k < count; ++k)
+                    if (stop[k] < 0) cand.push_back(k);
+                std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+                    return (double)still[a] * price(a) < (double)still[b] * price(b);
+                });
+                const double rem_ms = rem * 1e3;
+                double left = (rem_ms > 400.0 ? kRoundShare : 0.95) * rem_ms;
+                uint64_t planned = 0;
+                for (int k : cand) {
+                    uint64_t a = Q.ntraj[k];
+                    a = std::min<uint64_t>(a, (uint64_t)std::max(0.0, left / price(k)));
+                    if (planned > 0 && a < std::min<uint64_t>(kMinRoundTraj, Q.ntraj[k])) a = 0;
+                    Q.ntraj[k] = a;
+                    left -= (double)a * price(k);
+                    planned += a;
+                }
+                if (!planned) { stop_bits |= ST_TIMEOUT; break; }  // no room left for a useful launch
+                Q.order = cand;
+                for (int k = 0; k < count; ++k)
+                    if (stop[k] >= 0) Q.order.push_back(k);
+            }
         }
         std::vector<pm_result> outs(count);
         Q.outs = outs.data();
@@ -1032,6 +1085,7 @@ pm_status execute_rounds(pm_context* ctx, Run& R)
         for (int k = 0; k < count; ++k) {
             if (!Q.ntraj[k]) continue;
             outs[k].kernel_ms = 0;  // a launch's time is shared by its matrices: reported once below
+            if (outs[k].n_traj > 0 && outs[k].dev_ms > 0) ms_per_traj[k] = outs[k].dev_ms / (double)outs[k].n_traj;
             acc[k].add(outs[k]);
             if (R.log_x)
                 std::copy(lx.begin() + off, lx.begin() + off + Q.ntraj[k], R.log_x + req_prefix[k] + done[k]);
@@ -1053,11 +1107,13 @@ pm_status execute_rounds(pm_context* ctx, Run& R)
                 double need = (cur.rse == cur.rse && cur.n_alive >= 2)
                                   ? 1.1 * M * (cur.rse / R.rse_target) * (cur.rse / R.rse_target)
                                   : 4.0 * M;
+                still[k] = (uint64_t)std::max(0.0, need - (double)done[k]);
                 need = std::min(need, 5.0 * (double)done[k]);
                 size[k] = std::max<uint64_t>(size[k], (uint64_t)std::max(0.0, need - (double)done[k]));
             }
         }
         if (stop_bits) break;
+        ++round;
     }
     const double secs = elapsed();
     ctx->last_traj_ms = traj_ms;

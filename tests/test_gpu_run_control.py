@@ -56,6 +56,40 @@ def test_rse_target_stops_each_matrix_in_rounds():
     assert one[0]["ess"] == pytest.approx(res[0]["ess"], rel=1e-10)
 
 
+def test_budgeted_target_serves_cheapest_to_finish_first():
+    """An RSE target with a time budget over matrices of very different cost:
+    after the first round the budget goes to the matrices it can bring to the
+    target first (priced by their measured launch time per trajectory), the
+    rest get what is left.  The small matrices reach the target (their
+    samples are ids 0 .. M_k - 1), the large ones stop on the budget (a cut
+    round leaves some of its ids unstarted, NaN); every trajectory that ran is
+    bit-identical to the same id of one plain launch."""
+    B = binding()
+    easy = [G.planted_bernoulli(20, 0.3, seed=1), G.er_planted(40, 4.0, seed=60), G.er_planted(40, 4.0, seed=61)]
+    hard = [G.er_planted(1500, 6.0, seed=71), G.er_planted(1400, 6.0, seed=72)]
+    mats = [hard[0], easy[0], easy[1], hard[1], easy[2]]
+    cap = 1 << 22
+    res, lx = ctx().estimate_batch_ex(mats, [cap] * len(mats), 5, plain(rse_target=0.05, time_budget_s=1.5),
+                                      want_log_x=True)
+    for k in (1, 2, 4):
+        assert res[k]["stop"] == B.STOP_TARGET and res[k]["rse"] <= 0.05, (k, res[k])
+    for k in (0, 3):
+        assert res[k]["stop"] == B.STOP_TIME and res[k]["n_traj"] > 0, (k, res[k])
+    assert res[0]["status"] == B.PM_ETIMEOUT
+    for k in range(len(mats)):
+        M = res[k]["n_traj"]
+        seg = lx[cap * k:cap * (k + 1)]
+        assert int((~np.isnan(seg)).sum()) == M, k
+        if res[k]["stop"] == B.STOP_TARGET:  # every round of it ran whole: ids 0 .. M - 1
+            assert not np.isnan(seg[:M]).any(), k
+    # matrix 3's first ids (its index in the batch keys its draws) in one plain launch
+    M = 4096
+    ref, lxr = ctx().estimate_batch_ex(mats, [0, 0, 0, M, 0], 5, plain(), want_log_x=True)
+    seg = lx[cap * 3:cap * 3 + M]
+    ran = ~np.isnan(seg)
+    assert ran.sum() > 0 and np.array_equal(lxr[ran], seg[ran])
+
+
 def _long_plain_workload(seconds=1.5):
     """A plain single-matrix run that takes about `seconds` on this device."""
     m = G.er_planted(1500, 6.0, seed=71)
