@@ -40,16 +40,30 @@ DM_NONE, DM_ALL, DM_THRS, DM_TRCK = 0, 1, 2, 3
 PREC_FP32, PREC_FP64 = 0, 1
 
 
+_LIB_SAN = os.path.join(_HERE, "_build", "liboracle_san.so")
+
+
+def sanitized() -> bool:
+    """ORACLE_SANITIZE=1: load the AddressSanitizer + UndefinedBehaviorSanitizer
+    build (the process must preload libasan; any report aborts it)."""
+    return os.environ.get("ORACLE_SANITIZE") == "1"
+
+
 def build(force: bool = False) -> str:
     """Compile pm_oracle.c into _build/liboracle.so (gcc, no fast-math, no
-    FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+    FMA contraction), or with ORACLE_SANITIZE=1 into _build/liboracle_san.so
+    with -fsanitize=address,undefined (same floating-point flags)."""
+    san = sanitized()
+    out = _LIB_SAN if san else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        tmp = out + f".{os.getpid()}.tmp"
+        flags = ["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+                 "-fno-sanitize-recover=undefined"] if san else ["-O2"]
+        subprocess.check_call(["gcc", *flags, "-std=c11", "-ffp-contract=off", "-fno-fast-math",
                                "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 class _Schedule(C.Structure):
