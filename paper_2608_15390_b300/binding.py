@@ -21,7 +21,10 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libpm_b300.so")
+# PM_LIB=debug selects the PM_DEBUG build (bounds-checked matrix views in the
+# trajectory kernels; an out-of-range access fails the call with PM_EDEVICE)
+DEBUG_BUILD = os.environ.get("PM_LIB") == "debug"
+LIB_PATH = os.path.join(_HERE, "_lib", "libpm_b300_debug.so" if DEBUG_BUILD else "libpm_b300.so")
 
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_ECANCELLED, PM_EUNSUPPORTED, PM_EDEVICE = range(8)
 VR_MIN_DEGREE_2SIDED, VR_ROW_ORDER = 0, 1
@@ -121,7 +124,8 @@ class pm_call_info(C.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"CUDA library not built: {LIB_PATH} (run python -m paper_2608_15390_b300.build)")
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run python -m paper_2608_15390_b300.build"
+                          f"{' --debug' if DEBUG_BUILD else ''})")
     L = C.CDLL(LIB_PATH)
     P = C.c_void_p
     L.pm_context_create.argtypes = [C.POINTER(P), C.c_int, P]

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pm.h"
 #include "pm_internal.h"
 
@@ -691,8 +693,18 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
 // Phase 3: the launch sequence of one run on the stream, in three segments
 // (each capturable: its host sources and destinations live in the workspace):
 // preprocessing, the trajectory kernel, statistics and read-back.
+// NVTX range over a scope (named phases for profilers: `ncu --nvtx
+// --nvtx-include "pm trajectories/"` selects the trajectory launches)
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
 pm_status enqueue_prep(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
 {
+    NvtxScope nv("pm preprocess");
     uint8_t* A = ws.arena;
     auto P = [&](size_t off) { return (void*)(A + off); };
     PM_CUDA(cudaMemsetAsync(P(S.o_counters), 0, 8 * kCounters * R.count, ctx->stream));
@@ -707,6 +719,7 @@ pm_status enqueue_prep(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
 pm_status enqueue_traj(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
 {
     if (!S.launch_traj) return PM_OK;
+    NvtxScope nv("pm trajectories");
     PM_CUDA(cudaMemsetAsync(ws.arena + S.o_cctr, 0, 8, ctx->stream));
     PM_CUDA(cudaMemsetAsync(ws.arena + S.o_tstart, 0, 8, ctx->stream));
     // ln X = NaN (all bits set) marks trajectories a stopped launch never started
@@ -720,6 +733,7 @@ pm_status enqueue_traj(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
 
 pm_status enqueue_tail(pm_context* ctx, Workspace& ws, const Run& R, Staged& S)
 {
+    NvtxScope nv("pm statistics");
     const int count = R.count;
     uint8_t* A = ws.arena;
     auto P = [&](size_t off) { return (void*)(A + off); };
@@ -770,6 +784,8 @@ pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, doubl
     if (status & ST_BAD_INPUT) return fail(ctx, PM_EINVAL, "malformed CSR (device validation)");
     if (status & ST_CAPACITY) return fail(ctx, PM_EUNSUPPORTED, "a row or column holds more than 65534 entries");
     if (status) return fail(ctx, PM_EDEVICE, "device status " + std::to_string(status));
+    if (const unsigned int hits = traj_bounds_hits())  // PM_DEBUG builds only
+        return fail(ctx, PM_EDEVICE, "device bounds check: " + std::to_string(hits) + " out-of-range accesses");
 
     if (R.trace) {
         const size_t T = S.total, n = R.mats[0].n;
@@ -2503,6 +2519,7 @@ pm_status pm_model_train(pm_context* ctx, pm_model* m, const pm_csr* mats, int32
     PM_CUDA(cudaMalloc(&bl.p, 8 * total_steps));
     PM_CUDA(cudaMemsetAsync(bl.p, 0, 8 * total_steps, ctx->stream));
     uint64_t sidx = 0;
+    NvtxScope nv("pm train");
     for (int ep = 0; ep < cfg->epochs; ++ep) {
         for (uint64_t b = 0; b < steps_per_epoch; ++b, ++sidx) {
             const uint64_t row0 = cuts[b];

@@ -11,6 +11,57 @@ namespace pm {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint16_t kInact = 0xFFFFu;
 
+// ---- bounds checks of the PM_DEBUG build ----
+// A checked array view (Chk) tests every index against the array's length and
+// every value it returns against the values the array may hold (an adjacency
+// index below n, a pointer at most m).  A violation is counted in this
+// translation unit's bounds word and the access is replaced by element 0 and
+// value 0, so it stays inside the array; the host reads the word after the
+// call and fails it with PM_EDEVICE.  Release builds use plain pointers;
+// raw() hands an array to code that takes plain pointers (unchecked).
+#ifdef PM_DEBUG
+static __device__ unsigned int g_pm_bounds;
+__device__ __forceinline__ void pm_bounds_hit() { atomicAdd(&g_pm_bounds, 1u); }
+template <typename T>
+struct Chk {
+    const T* p;
+    uint32_t len;   // valid indices [0, len)
+    uint32_t vmax;  // valid values [0, vmax)
+    __device__ __forceinline__ T operator[](long long i) const
+    {
+        if ((unsigned long long)i >= (unsigned long long)len) {
+            pm_bounds_hit();
+            i = 0;
+        }
+        T v = p[i];
+        if ((unsigned long long)(long long)v >= (unsigned long long)vmax) {
+            pm_bounds_hit();
+            v = 0;
+        }
+        return v;
+    }
+};
+template <typename T>
+using ChkPtr = Chk<T>;
+template <typename T>
+__device__ __forceinline__ const T* raw(const Chk<T>& c) { return c.p; }
+#define PM_CLAMP(x, lim)                                                               \
+    do {                                                                               \
+        if ((unsigned long long)(long long)(x) >= (unsigned long long)(lim)) {         \
+            pm_bounds_hit();                                                           \
+            (x) = 0;                                                                   \
+        }                                                                              \
+    } while (0)
+#else
+template <typename T>
+using ChkPtr = const T*;
+template <typename T>
+__device__ __forceinline__ const T* raw(const T* p) { return p; }
+#define PM_CLAMP(x, lim) \
+    do {                 \
+    } while (0)
+#endif
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
 // multiply-xor bijection, key bumped by the Weyl constants between rounds.
 __device__ __forceinline__ void philox10(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,

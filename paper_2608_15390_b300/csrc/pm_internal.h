@@ -290,6 +290,10 @@ cudaError_t launch_stats(const double* log_x, const uint64_t* h_prefix, const ui
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t count, uint32_t* out,
                           cudaStream_t st);
 int traj_max_smem_bytes();
+// PM_DEBUG build: out-of-range accesses the trajectory kernels' checked
+// matrix views counted since the last call (the count is cleared); 0 in
+// release builds
+unsigned int traj_bounds_hits();
 // on-chip bandwidth probes (pm_probe.cu)
 cudaError_t launch_l2_probe(const void* buf, size_t bytes, int iters, int grid, unsigned long long* sink,
                             cudaStream_t st);

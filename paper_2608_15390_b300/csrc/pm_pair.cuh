@@ -366,14 +366,15 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
         const uint64_t u0 = draw_u64(P.seed, traj, midx, (uint32_t)t, 0);
         const bool vr_row = P.s.vertex_rule == VR_ROW;
         const int vm = vr_row ? 0 : md_pick_seg(deg, tree, T, S, has && !abandoned);
-        const int v = (vr_row && has && !abandoned) ? t : vm;
+        int v = (vr_row && has && !abandoned) ? t : vm;
+        PM_CLAMP(v, 2 * n);
         const int dv = (has && !abandoned) ? (int)deg[v] : 0;
         const bool alive = has && !abandoned && dv > 0;  // a step is taken
         const bool vrow = v < n;
         const int vi = vrow ? v : v - n;
         const int beg = alive ? (vrow ? V.rp : V.cp)[vi] : 0;
         const int end = alive ? (vrow ? V.rp : V.cp)[vi + 1] : 0;
-        const Idx* adj = vrow ? V.ci : V.ri;
+        const auto adj = vrow ? V.ci : V.ri;
         const int poff = vrow ? n : 0;
         const int kq = 40 - bitlen((uint32_t)(dv > 0 ? dv : 1));
         const int len = end - beg;
@@ -556,7 +557,7 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
         const bool urow = !vrow;
         const int ub = stepping ? (urow ? V.rp : V.cp)[sel_p] : 0;
         const int ue = stepping ? (urow ? V.rp : V.cp)[sel_p + 1] : 0;
-        const Idx* uadj = urow ? V.ci : V.ri;
+        const auto uadj = urow ? V.ci : V.ri;
         const int uoff = urow ? n : 0;
         const int NU = both_max((ue - ub + 15) >> 4);
         for (int cc = 0; cc < NU; ++cc) {

@@ -34,14 +34,28 @@ enum { DMP_NONE = 0, DMP_ALL = 1, DMP_THRS = 2, DMP_TRCK = 3 };
 template <typename Idx>
 struct MV {
     int n;
-    const int* rp;    // row pointers
-    const int* cp;    // column pointers
-    const Idx* ci;    // column index of each row entry
-    const Idx* ri;    // row index of each column entry
-    const int* ce;    // row-entry id of each column entry (DM masks)
+    ChkPtr<int> rp;   // row pointers
+    ChkPtr<int> cp;   // column pointers
+    ChkPtr<Idx> ci;   // column index of each row entry
+    ChkPtr<Idx> ri;   // row index of each column entry
+    ChkPtr<int> ce;   // row-entry id of each column entry (DM masks)
     const float* rv;  // values in row order or nullptr
     const float* cv;  // values in column order or nullptr
 };
+
+// the view of B0 a trajectory reads (checked arrays in the PM_DEBUG build)
+template <typename Idx>
+__device__ __forceinline__ MV<Idx> make_mv(int n, int m, const int* rp, const int* cp, const Idx* ci, const Idx* ri,
+                                           const int* ce, const float* rv, const float* cv)
+{
+#ifdef PM_DEBUG
+    const uint32_t n1 = (uint32_t)n + 1u, m0 = (uint32_t)m, m1 = (uint32_t)m + 1u;
+    return MV<Idx>{n, {rp, n1, m1}, {cp, n1, m1}, {ci, m0, (uint32_t)n}, {ri, m0, (uint32_t)n}, {ce, m0, m0}, rv, cv};
+#else
+    (void)m;
+    return MV<Idx>{n, rp, cp, ci, ri, ce, rv, cv};
+#endif
+}
 
 __device__ __forceinline__ size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -660,7 +674,8 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 // draw 0 of this step depends on (seed, trajectory, step) only:
                 // computed first, it overlaps the pick and the candidate scan
                 const uint64_t u0 = draw_u64(P.seed, traj, midx, (uint32_t)t, 0);
-                const int v = (S.vertex_rule == VR_ROW) ? t : md_pick(deg, tree, T, lane);
+                int v = (S.vertex_rule == VR_ROW) ? t : md_pick(deg, tree, T, lane);
+                PM_CLAMP(v, 2 * n);
                 const int dv = deg[v];
                 if (TRACE && lane == 0) P.deg_v[gq * n + t] = dv;
                 if (dv == 0) { dead = 1; break; }
@@ -668,7 +683,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 const int vi = vrow ? v : v - n;
                 const int beg = (vrow ? V.rp : V.cp)[vi];
                 const int end = (vrow ? V.rp : V.cp)[vi + 1];
-                const Idx* adj = vrow ? V.ci : V.ri;
+                const auto adj = vrow ? V.ci : V.ri;
                 const int poff = vrow ? n : 0;
                 const int kq = 40 - bitlen((uint32_t)dv);
                 const int len = end - beg;
@@ -1007,7 +1022,7 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                     const bool urow = !vrow;
                     const int ub = (urow ? V.rp : V.cp)[sel_p];
                     const int ue = (urow ? V.rp : V.cp)[sel_p + 1];
-                    const Idx* uadj = urow ? V.ci : V.ri;
+                    const auto uadj = urow ? V.ci : V.ri;
                     const int uoff = urow ? n : 0;
                     ulen = ue - ub;
                     for (int base = ub; base < ue; base += 32) {
@@ -1074,7 +1089,8 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
             const LiveTraj live{deg, mask, n};
             if (!G.gdm) {
                 if (leader) {
-                    const bool okdm = dm_warp(n, V.rp, V.ci, V.cp, V.ri, V.ce, live, mask, dmws, lane, dm_matched);
+                    const bool okdm = dm_warp(n, raw(V.rp), raw(V.ci), raw(V.cp), raw(V.ri), raw(V.ce), live, mask,
+                                              dmws, lane, dm_matched);
                     dm_matched = okdm;
                     if (lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
                 }
@@ -1087,10 +1103,10 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 auto gs = [&] { gsync(G); };
                 bool okdm;
                 if (dm_matched) {
-                    okdm = dm_repair_group(n, V.rp, V.ci, live, dmws, G.tid, G.nthr, G.misc + M_DMSH, gs);
+                    okdm = dm_repair_group(n, raw(V.rp), raw(V.ci), live, dmws, G.tid, G.nthr, G.misc + M_DMSH, gs);
                 } else {
                     if (leader) {
-                        const bool r = dm_match_warp(n, V.rp, V.ci, live, dmws, lane, false);
+                        const bool r = dm_match_warp(n, raw(V.rp), raw(V.ci), live, dmws, lane, false);
                         if (lane == 0) G.misc[M_DMOK] = r ? 1 : 0;
                     }
                     gsync(G);
@@ -1100,11 +1116,12 @@ __device__ void run_group(const TrajParams& P, const DevMatrix* Mp, const MV<Idx
                 dm_matched = okdm;
                 if (leader && lane == 0) G.misc[M_DMOK] = okdm ? 1 : 0;
                 if (okdm) {
-                    const int nroots = dm_scc_group_prepass(n, V.rp, V.ci, V.cp, V.ri, V.ce, live, dmws, G.tid,
+                    const int nroots = dm_scc_group_prepass(n, raw(V.rp), raw(V.ci), raw(V.cp), raw(V.ri), raw(V.ce),
+                                                            live, dmws, G.tid,
                                                             G.nthr, G.misc + M_DMSH, gs);
-                    if (leader && nroots > 0) dm_tarjan_warp(n, V.cp, V.ri, V.ce, live, dmws, lane, true, nroots);
+                    if (leader && nroots > 0) dm_tarjan_warp(n, raw(V.cp), raw(V.ri), raw(V.ce), live, dmws, lane, true, nroots);
                     gsync(G);
-                    dm_mask_rows(n, V.rp, V.ci, live, mask, dmws, G.tid, G.nthr);
+                    dm_mask_rows(n, raw(V.rp), raw(V.ci), live, mask, dmws, G.tid, G.nthr);
                 }
             }
             gsync(G);
@@ -1334,7 +1351,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
                 if (tid == 0) cmisc[2] = ch.k;
             }
             __syncthreads();
-            MV<uint16_t> V{n, s_rp, s_cp, s_ci, s_ri, s_ce, Mp->rv, Mp->cv};
+            const MV<uint16_t> V = make_mv<uint16_t>(n, m, s_rp, s_cp, s_ci, s_ri, s_ce, Mp->rv, Mp->cv);
             if constexpr (!TRACE && MODE != 2) {
                 if (pl.pair) {
                     run_chunk_pair<Real, uint16_t, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
@@ -1343,7 +1360,7 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
             }
             run_chunk<Real, uint16_t, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
         } else {
-            MV<int> V{n, Mp->rp, Mp->cp, Mp->ci, Mp->ri, Mp->ce, Mp->rv, Mp->cv};
+            const MV<int> V = make_mv<int>(n, Mp->m, Mp->rp, Mp->cp, Mp->ci, Mp->ri, Mp->ce, Mp->rv, Mp->cv);
             if constexpr (!TRACE && MODE != 2) {
                 if (pl.pair) {
                     run_chunk_pair<Real, int, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
@@ -1382,6 +1399,19 @@ cudaError_t launch_t(const TrajParams& p, int grid, int smem, cudaStream_t st)
 }
 
 }  // namespace
+
+unsigned int traj_bounds_hits()
+{
+#ifdef PM_DEBUG
+    unsigned int h = 0;
+    const unsigned int z = 0;
+    if (cudaMemcpyFromSymbol(&h, g_pm_bounds, sizeof(h)) != cudaSuccess) return ~0u;
+    if (h && cudaMemcpyToSymbol(g_pm_bounds, &z, sizeof(z)) != cudaSuccess) return ~0u;
+    return h;
+#else
+    return 0;
+#endif
+}
 
 int traj_max_smem_bytes()
 {

@@ -29,6 +29,16 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_debug_library_exports_every_declared_symbol():
+    """The PM_DEBUG variant (bounds-checked trajectory kernels) has the same ABI."""
+    from paper_2608_15390_b300 import build
+    path = build.build(debug=True)
+    assert path.endswith("libpm_b300_debug.so")
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
 def test_binding_loads_and_names_match():
     from paper_2608_15390_b300 import binding
     assert set(declared_functions()) <= set(binding.EXPORTED) | {"pm_status_string", "pm_last_error"}
