@@ -205,7 +205,7 @@ Plan plan_for(int n, int64_t m, int rb, const Sched& s, int smem_max, bool learn
         p.mat_bytes = pol.staged ? staged_matrix_bytes(n, m, false) : 0;
         if (p.mat_bytes >= avail) return p;
         p.state_bytes = pair_state_bytes(n, learned);
-        p.groups = std::min((avail - p.mat_bytes) / p.state_bytes, 2 * kCtaWarps) & ~1;
+        p.groups = std::min((avail - p.mat_bytes) / p.state_bytes, 2 * pair_cta_warps(learned)) & ~1;
         if (p.groups < 0) p.groups = 0;
         return p;
     }
@@ -424,6 +424,7 @@ struct Staged {
     size_t o_plans = 0, o_chunks = 0, o_cctr = 0, o_tstart = 0, layout_end = 0, chunk_cap = 0;
     uint32_t stop_bits = 0;       // ST_TIMEOUT / ST_CANCELLED seen by collect()
     int chunks_stats = 1;
+    int cta_warps = kCtaWarps;    // warps per CTA of the trajectory launch
     std::vector<Plan> plans;
     std::vector<Chunk> chunks;
     int smem_need = kCtaMiscBytes;
@@ -646,7 +647,12 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
     PM_CUDA(cudaMemcpyAsync(P(S.o_chunks), S.chunks.data(), sizeof(Chunk) * S.chunks.size(), cudaMemcpyHostToDevice,
                             ctx->stream));
     S.h2d += sizeof(Plan) * count + sizeof(Chunk) * S.chunks.size();
-    const size_t need_slots = sl.bytes * (size_t)S.grid * kCtaWarps;
+    // every plan with trajectories a pair plan: the 768-thread pair-only kernel
+    bool all_pair = true;
+    for (int k = 0; k < count; ++k)
+        if (R.ntraj[k] > 0 && !S.plans[k].pair) all_pair = false;
+    S.cta_warps = all_pair ? pair_cta_warps(R.model != nullptr) : kCtaWarps;
+    const size_t need_slots = sl.bytes * (size_t)S.grid * S.cta_warps;
     pm_status st = grow(ctx, &ws.slots, &ws.slots_cap, need_slots);
     if (st != PM_OK) return st;
     TrajParams& tp = S.tp;
@@ -667,6 +673,8 @@ pm_status stage_plans(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, c
     tp.status = (uint32_t*)P(S.o_status);
     tp.slots = ws.slots;
     tp.slot = sl;
+    tp.cta_warps = S.cta_warps;
+    tp.pair_kernel = (all_pair && R.model == nullptr) ? 1 : 0;
     if (R.trace) {
         tp.chosen = (int32_t*)P(S.o_chosen);
         tp.deg_v = (int32_t*)P(S.o_degv);
@@ -777,7 +785,7 @@ pm_status collect(pm_context* ctx, Workspace& ws, const Run& R, Staged& S, doubl
         cudaGetLastError();  // a timing that could not be taken is reported as -1
     }
     ctx->last_grid = S.launch_traj ? S.grid : 0;
-    ctx->last_wpc = S.launch_traj ? kCtaWarps : 0;
+    ctx->last_wpc = S.launch_traj ? S.cta_warps : 0;
     ctx->last_plan = (S.launch_traj && !S.plans.empty()) ? S.plans[0] : Plan{};
     const uint32_t status = *S.h_status & ~kStatusStopBits;
     S.stop_bits = *S.h_status & kStatusStopBits;
@@ -1457,7 +1465,8 @@ pm_status probe_plan(pm_context* ctx, pm_batch* b, int k, const Plan& plan, doub
     Layout L;
     const size_t o_pl = L.take(sizeof(Plan) * count), o_ch = L.take(sizeof(Chunk) * pgrid),
                  o_pf = L.take(8 * (count + 1)), o_lx = L.take(8 * ntr), o_ct = L.take(8 * kCounters * count),
-                 o_cc = L.take(8), o_sl = L.take(sl.bytes * (size_t)pgrid * kCtaWarps);
+                 o_cc = L.take(8),
+                 o_sl = L.take(sl.bytes * (size_t)pgrid * (plan.pair ? pair_cta_warps(R.model != nullptr) : kCtaWarps));
     DevBuf buf;
     PM_CUDA(cudaMalloc(&buf.p, L.off));
     uint8_t* B = (uint8_t*)buf.p;
@@ -1487,6 +1496,8 @@ pm_status probe_plan(pm_context* ctx, pm_batch* b, int k, const Plan& plan, doub
     tp.chunk_counter = (int*)(B + o_cc);
     tp.slots = B + o_sl;
     tp.slot = sl;
+    tp.cta_warps = plan.pair ? pair_cta_warps(R.model != nullptr) : kCtaWarps;
+    tp.pair_kernel = (plan.pair && R.model == nullptr) ? 1 : 0;
     tp.budget_ns = 0;
     tp.hard_ns = 0;
     tp.cancel = nullptr;

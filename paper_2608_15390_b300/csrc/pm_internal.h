@@ -190,6 +190,14 @@ struct Chunk {
 // repairs, algorithmic bytes, network rows, trajectory nanoseconds
 constexpr int kCounters = 6;
 constexpr int kCtaWarps = 16;            // 512 threads, one CTA per SM
+// The pair-only kernel of the scaled and uniform proposals (every plan of
+// the launch a pair plan): 24 warps, as their pair path fits in 80 registers
+// a thread.  The learned proposal's pair path runs in the general kernel
+// (16 warps of 128 registers): with fewer registers its two-tile network
+// spills, which cost more than the extra warps gained (they help only where
+// shared memory holds more than 32 trajectory states).
+constexpr int kPairCtaWarps = 24;
+__host__ __device__ constexpr int pair_cta_warps(bool learned) { return learned ? kCtaWarps : kPairCtaWarps; }
 constexpr int kCtaMiscBytes = 64;
 constexpr int kGroupMiscInts = 32;
 
@@ -208,7 +216,9 @@ struct TrajParams {
     unsigned long long* counters;  // [count][kCounters], see kCounters
     int* chunk_counter;
     uint32_t* status;
-    uint8_t* slots;           // per-group global scratch, kCtaWarps slots per CTA
+    uint8_t* slots;           // per-group global scratch, cta_warps slots per CTA
+    int cta_warps;            // warps of a CTA: kCtaWarps, or kPairCtaWarps for the pair-only kernel
+    int pair_kernel;          // launch the pair-only kernel (scaled / uniform proposal, every plan a pair plan)
     SlotLayout slot;
     // trace outputs (nullptr when not tracing)
     int32_t* chosen;

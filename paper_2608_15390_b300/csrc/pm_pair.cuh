@@ -605,7 +605,7 @@ __device__ void run_chunk_pair(const TrajParams& P, const Chunk& ch, const Plan&
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (2 * warp + 1 >= pl.groups) return;
     uint8_t* sbase = gstate + (size_t)(2 * warp) * pl.state_bytes;
-    uint8_t* slot = P.slots + ((size_t)blockIdx.x * kCtaWarps + warp) * P.slot.bytes;
+    uint8_t* slot = P.slots + ((size_t)blockIdx.x * P.cta_warps + warp) * P.slot.bytes;
     run_pair<Real, Idx, MODE>(P, P.mats + ch.k, V, ch.k, ch, pl, sbase, slot, ctr_traj, Ms, warp, lane);
 }
 

@@ -1243,7 +1243,7 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
     G.bar = 1 + gidx;
     G.gdm = pl.gstate && pl.g > 1;
     uint8_t* sbase = gstate + (size_t)gidx * pl.state_bytes;
-    uint8_t* slot = P.slots + ((size_t)blockIdx.x * kCtaWarps + gidx) * P.slot.bytes;
+    uint8_t* slot = P.slots + ((size_t)blockIdx.x * P.cta_warps + gidx) * P.slot.bytes;
     const TreeGeom T = tree_geom(n);
     // trajectory state: in shared memory, or (large n) in the group's slot
     uint8_t* base = pl.gstate ? slot + P.slot.state : sbase;
@@ -1296,8 +1296,11 @@ __device__ void run_chunk(const TrajParams& P, const Chunk& ch, const Plan& pl, 
 
 #include "pm_pair.cuh"
 
-template <typename Real, bool TRACE, int MODE>
-__global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
+// The persistent loop of a trajectory launch: CTAs claim chunks, stage the
+// matrix when its plan says so, and run the chunk's trajectories.  PAIR_ONLY:
+// every plan is a pair plan (the 768-thread kernel).
+template <typename Real, bool TRACE, int MODE, bool PAIR_ONLY>
+__device__ __forceinline__ void traj_body(const TrajParams& P)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     int* cmisc = reinterpret_cast<int*>(smem);  // [0] chunk, [1] trajectory counter, [2] staged matrix
@@ -1352,24 +1355,44 @@ __global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
             }
             __syncthreads();
             const MV<uint16_t> V = make_mv<uint16_t>(n, m, s_rp, s_cp, s_ci, s_ri, s_ce, Mp->rv, Mp->cv);
-            if constexpr (!TRACE && MODE != 2) {
-                if (pl.pair) {
-                    run_chunk_pair<Real, uint16_t, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
-                    continue;
+            if constexpr (PAIR_ONLY) {
+                run_chunk_pair<Real, uint16_t, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
+            } else {
+                if constexpr (!TRACE && MODE != 2) {
+                    if (pl.pair) {
+                        run_chunk_pair<Real, uint16_t, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
+                        continue;
+                    }
                 }
+                run_chunk<Real, uint16_t, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
             }
-            run_chunk<Real, uint16_t, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
         } else {
             const MV<int> V = make_mv<int>(n, Mp->m, Mp->rp, Mp->cp, Mp->ci, Mp->ri, Mp->ce, Mp->rv, Mp->cv);
-            if constexpr (!TRACE && MODE != 2) {
-                if (pl.pair) {
-                    run_chunk_pair<Real, int, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
-                    continue;
+            if constexpr (PAIR_ONLY) {
+                run_chunk_pair<Real, int, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
+            } else {
+                if constexpr (!TRACE && MODE != 2) {
+                    if (pl.pair) {
+                        run_chunk_pair<Real, int, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
+                        continue;
+                    }
                 }
+                run_chunk<Real, int, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
             }
-            run_chunk<Real, int, TRACE, MODE>(P, ch, pl, V, gstate, cmisc + 1, Ms);
         }
     }
+}
+
+template <typename Real, bool TRACE, int MODE>
+__global__ void __launch_bounds__(kCtaWarps * 32, 1) traj_kernel(TrajParams P)
+{
+    traj_body<Real, TRACE, MODE, false>(P);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kPairCtaWarps * 32, 1) traj_pair_kernel(TrajParams P)
+{
+    traj_body<Real, false, 0, true>(P);
 }
 
 // largest dynamic shared memory a launch of fn may request: the device's
@@ -1387,6 +1410,16 @@ int dyn_smem_cap(const void* fn)
 template <typename Real, bool TRACE, int MODE>
 cudaError_t launch_t(const TrajParams& p, int grid, int smem, cudaStream_t st)
 {
+    if constexpr (!TRACE && MODE == 0) {
+        if (p.pair_kernel) {
+            const int cap = dyn_smem_cap((const void*)traj_pair_kernel<Real>);
+            cudaError_t e = cudaFuncSetAttribute(traj_pair_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 smem > cap ? smem : cap);
+            if (e != cudaSuccess) return e;
+            traj_pair_kernel<Real><<<grid, kPairCtaWarps * 32, smem, st>>>(p);
+            return cudaGetLastError();
+        }
+    }
     // the attribute is a per-function cap shared by every launch and by the
     // kernel nodes of captured graphs: keep it at the device maximum so a
     // later, smaller launch never lowers it below a captured node's size
@@ -1423,6 +1456,8 @@ int traj_max_smem_bytes()
 
 const void* traj_kernel_entry(const TrajParams& p, bool trace)
 {
+    if (p.pair_kernel && !trace && !p.rec_feat && !p.model)
+        return p.s.precision == 1 ? (const void*)traj_pair_kernel<double> : (const void*)traj_pair_kernel<float>;
     if (p.s.precision == 1)
         return trace ? (const void*)traj_kernel<double, true, 0> : (const void*)traj_kernel<double, false, 0>;
     if (p.model) return trace ? (const void*)traj_kernel<float, true, 1> : (const void*)traj_kernel<float, false, 1>;
