@@ -186,6 +186,13 @@ struct Policy {
 // schedules a pair plan can run: no inner SK, DM or Local repair
 bool pair_schedule(const Sched& s) { return s.sk == 0 && s.dm == 0; }
 
+// trajectories the GPU runs at once in the usual layouts: one per warp of
+// every SM, two per warp for the schedules the pair layout serves
+uint64_t traj_slots(const pm_context* ctx, const Sched& s)
+{
+    return (uint64_t)ctx->sm_count * kCtaWarps * (pair_schedule(s) ? 2u : 1u);
+}
+
 int learned_smem(bool learned) { return learned ? (model_infer_bytes() + 15) / 16 * 16 : 0; }
 
 // Plan of one matrix under a policy, or groups = 0 if it does not fit.
@@ -1027,7 +1034,7 @@ pm_status execute_rounds(pm_context* ctx, Run& R)
     std::vector<double> ms_per_traj(count, -1.0);  // launch ms per trajectory, last measured
     std::vector<int32_t> stop(count, -1);
     int round = 0;
-    const uint64_t slots = (uint64_t)ctx->sm_count * kCtaWarps;
+    const uint64_t slots = traj_slots(ctx, R.s);
     for (int k = 0; k < count; ++k) {
         if (R.ntraj[k] == 0) stop[k] = PM_STOP_COMPLETE;
         size[k] = R.rse_target > 0 ? std::max<uint64_t>(kMinTrajForTarget, 2 * slots / (uint64_t)count) : R.ntraj[k];
@@ -2045,7 +2052,7 @@ pm_status pm_server_round(pm_server* sv, pm_request_done* done, uint32_t cap, ui
         R.ntraj.resize(count);
         // a round lasts about as long as its longest trajectory, so every
         // request gets at least its share of the GPU's trajectory slots
-        const uint64_t share = (uint64_t)ctx->sm_count * kCtaWarps / (uint64_t)count;
+        const uint64_t share = traj_slots(ctx, sv->s) / (uint64_t)count;
         for (int k = 0; k < count; ++k) {
             Request* q = sv->active[k];
             dims[k] = q->host;
