@@ -454,66 +454,100 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
             if (!net) return 0.f;
             return cc == 0 ? lg_reg : lgbuf[e - beg];
         };
-        // the largest score, the total integer weight W and the draw
+        // the largest score, the total integer weight W, the draw and the
+        // partner (the first live candidate whose prefix weight exceeds it)
         Real smax = 0;
-        uint64_t W = 0;
-        if (uniform) {
-            W = alive ? ((uint64_t)dv << kq) : 0;
-        } else {
-            for (int cc = 0; cc < NCH; ++cc) {
-                const int e = beg + 16 * cc + S.sl;
-                Real sv = 0;
-                if (alive && e < end) {
-                    const int pp = adj[e];
-                    if (entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp + poff)) sv = score(e, pp, logit_at(cc, e));
-                }
-                const Real cm = seg_max_nonneg(sv);
-                smax = cm > smax ? cm : smax;
-            }
-            for (int cc = 0; cc < NCH; ++cc) {
-                const int e = beg + 16 * cc + S.sl;
-                uint64_t w = 0;
-                if (alive && e < end) {
-                    const int pp = adj[e];
-                    if (entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp + poff))
-                        w = quant_weight<Real>(score(e, pp, logit_at(cc, e)), smax, kq);
-                }
-                W += seg_sum_u64(w);
-            }
-        }
-        uint64_t rr = 0;
-        bool rng_fail = false;
-        if (alive) {
-            rr = uniform_below(W, u0, P.seed, traj, midx, (uint32_t)t);
-            rng_fail = rr == ~0ull;
-        }
-        __syncwarp();
-        // the partner: the first live candidate whose prefix weight exceeds rr
+        uint64_t W = 0, rr = 0, w_sel = 0;
         int sel_e = -1, sel_p = -1;
-        uint64_t w_sel = 0, carry = 0;
-        bool found = false;
-        for (int cc = 0; cc < NCH; ++cc) {
-            const int e = beg + 16 * cc + S.sl;
-            int pp = 0;
-            bool live = false;
+        bool rng_fail = false;
+        bool live1 = false;  // one chunk: this lane's candidate is live (kept for the elimination)
+        int pp1 = 0;
+        if (NCH == 1) {  // both lists fit one chunk: each candidate's weight is computed once
+            const int e = beg + S.sl;
+            const bool in = alive && e < end;
+            pp1 = in ? (int)adj[e] : 0;
+            live1 = in && entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp1 + poff);
             uint64_t w = 0;
-            if (alive && !rng_fail && e < end) {
-                pp = adj[e];
-                live = entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp + poff);
-                if (live) w = uniform ? (1ull << kq) : quant_weight<Real>(score(e, pp, logit_at(cc, e)), smax, kq);
+            if (uniform) {
+                w = live1 ? (1ull << kq) : 0ull;
+                W = alive ? ((uint64_t)dv << kq) : 0;
+            } else {
+                const Real sv = live1 ? score(e, pp1, logit_at(0, e)) : (Real)0;
+                smax = seg_max_nonneg(sv);
+                w = live1 ? quant_weight<Real>(sv, smax, kq) : 0ull;
             }
-            const uint64_t pre = seg_incl_scan_u64(w, S.sl) + carry;
-            const unsigned hit = seg_ballot(S, live && !found && pre > rr);
+            const uint64_t pre = seg_incl_scan_u64(w, S.sl);
+            if (!uniform) W = seg_shfl(S, pre, 15);
+            if (alive) {
+                rr = uniform_below(W, u0, P.seed, traj, midx, (uint32_t)t);
+                rng_fail = rr == ~0ull;
+            }
+            __syncwarp();
+            const unsigned hit = seg_ballot(S, live1 && !rng_fail && pre > rr);
             const int sl_hit = hit ? __ffs(hit) - 1 : 0;
-            const int se = seg_shfl(S, e, sl_hit), sp = seg_shfl(S, pp, sl_hit);
+            const int se = seg_shfl(S, e, sl_hit), sp = seg_shfl(S, pp1, sl_hit);
             const uint64_t sw = seg_shfl(S, w, sl_hit);
-            if (hit && !found) {
+            if (hit) {
                 sel_e = se;
                 sel_p = sp;
                 w_sel = sw;
-                found = true;
             }
-            carry = seg_shfl(S, pre, 15);
+        } else {
+            if (uniform) {
+                W = alive ? ((uint64_t)dv << kq) : 0;
+            } else {
+                for (int cc = 0; cc < NCH; ++cc) {
+                    const int e = beg + 16 * cc + S.sl;
+                    Real sv = 0;
+                    if (alive && e < end) {
+                        const int pp = adj[e];
+                        if (entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp + poff))
+                            sv = score(e, pp, logit_at(cc, e));
+                    }
+                    const Real cm = seg_max_nonneg(sv);
+                    smax = cm > smax ? cm : smax;
+                }
+                for (int cc = 0; cc < NCH; ++cc) {
+                    const int e = beg + 16 * cc + S.sl;
+                    uint64_t w = 0;
+                    if (alive && e < end) {
+                        const int pp = adj[e];
+                        if (entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp + poff))
+                            w = quant_weight<Real>(score(e, pp, logit_at(cc, e)), smax, kq);
+                    }
+                    W += seg_sum_u64(w);
+                }
+            }
+            if (alive) {
+                rr = uniform_below(W, u0, P.seed, traj, midx, (uint32_t)t);
+                rng_fail = rr == ~0ull;
+            }
+            __syncwarp();
+            uint64_t carry = 0;
+            bool found = false;
+            for (int cc = 0; cc < NCH; ++cc) {
+                const int e = beg + 16 * cc + S.sl;
+                int pp = 0;
+                bool live = false;
+                uint64_t w = 0;
+                if (alive && !rng_fail && e < end) {
+                    pp = adj[e];
+                    live = entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp + poff);
+                    if (live) w = uniform ? (1ull << kq) : quant_weight<Real>(score(e, pp, logit_at(cc, e)), smax, kq);
+                }
+                const uint64_t pre = seg_incl_scan_u64(w, S.sl) + carry;
+                const unsigned hit = seg_ballot(S, live && !found && pre > rr);
+                const int sl_hit = hit ? __ffs(hit) - 1 : 0;
+                const int se = seg_shfl(S, e, sl_hit), sp = seg_shfl(S, pp, sl_hit);
+                const uint64_t sw = seg_shfl(S, w, sl_hit);
+                if (hit && !found) {
+                    sel_e = se;
+                    sel_p = sp;
+                    w_sel = sw;
+                    found = true;
+                }
+                carry = seg_shfl(S, pre, 15);
+            }
         }
         bool dead = has && !abandoned && (dv == 0 || rng_fail);
         if (rng_fail && S.sl == 0) atomicOr(P.status, ST_RNG_EXHAUSTED);
@@ -539,20 +573,31 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
         __syncwarp();
         // eliminate: the live neighbours of v, then of the partner, lose a degree
         int cnt = 0;
-        for (int cc = 0; cc < NCH; ++cc) {
-            const int e = beg + 16 * cc + S.sl;
-            bool live = false;
-            int pid = 0;
-            if (stepping && e < end) {
-                pid = (int)adj[e] + poff;
-                live = entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pid);
-            }
-            if (live) {
+        if (NCH == 1) {  // the candidates live before the pick, less the partner
+            const bool keep = stepping && live1 && pp1 != sel_p;
+            if (keep) {
+                const int pid = pp1 + poff;
                 const uint32_t d = deg[pid] - 1u;
                 deg[pid] = (uint16_t)d;
                 tree_lower(tree, T, pid, d);
             }
-            cnt += __popc(seg_ballot(S, live));
+            cnt += __popc(seg_ballot(S, keep));
+        } else {
+            for (int cc = 0; cc < NCH; ++cc) {
+                const int e = beg + 16 * cc + S.sl;
+                bool live = false;
+                int pid = 0;
+                if (stepping && e < end) {
+                    pid = (int)adj[e] + poff;
+                    live = entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pid);
+                }
+                if (live) {
+                    const uint32_t d = deg[pid] - 1u;
+                    deg[pid] = (uint16_t)d;
+                    tree_lower(tree, T, pid, d);
+                }
+                cnt += __popc(seg_ballot(S, live));
+            }
         }
         const bool urow = !vrow;
         const int ub = stepping ? (urow ? V.rp : V.cp)[sel_p] : 0;
