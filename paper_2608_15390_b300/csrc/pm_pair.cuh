@@ -380,6 +380,17 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
         const int len = end - beg;
         const int NCH = both_max((len + 15) >> 4);
         const bool net = model && alive && dv >= 2;  // a single live candidate needs no network
+        // both lists fit one 16-lane chunk: this lane's candidate is read once, for the
+        // network, the sampling and the elimination
+        const bool one = NCH == 1;
+        int pp1 = 0;
+        bool live1 = false;
+        if (one) {
+            const int e = beg + S.sl;
+            const bool in = alive && e < end;
+            pp1 = in ? (int)adj[e] : 0;
+            live1 = in && entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp1 + poff);
+        }
 
         // learned proposal: the network's logit of every live candidate
         float lg_reg = 0.f;
@@ -387,11 +398,15 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
             float sum_v = 0.f, lsv = 0.f;
             {
                 int sv_i = 0;
-                for (int cc = 0; cc < NCH; ++cc) {
-                    const int e = beg + 16 * cc + S.sl;
-                    if (net && e < end) {
-                        const int pid = (int)adj[e] + poff;
-                        if (entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pid)) sv_i += deg[pid];
+                if (one) {
+                    if (net && live1) sv_i = deg[pp1 + poff];
+                } else {
+                    for (int cc = 0; cc < NCH; ++cc) {
+                        const int e = beg + 16 * cc + S.sl;
+                        if (net && e < end) {
+                            const int pid = (int)adj[e] + poff;
+                            if (entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pid)) sv_i += deg[pid];
+                        }
                     }
                 }
                 sv_i = seg_sum_int(sv_i);
@@ -404,8 +419,15 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
             for (int cc = 0; cc < NCH; ++cc) {
                 const int e = beg + 16 * cc + S.sl;
                 const bool in = net && e < end;
-                const int pp = in ? (int)adj[e] : 0;
-                const bool live = in && entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp + poff);
+                int pp;
+                bool live;
+                if (one) {
+                    pp = in ? pp1 : 0;
+                    live = net && live1;
+                } else {
+                    pp = in ? (int)adj[e] : 0;
+                    live = in && entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp + poff);
+                }
                 const unsigned lmk = seg_ballot(S, live);
                 const int nl = __popc(lmk);
                 const int li = __popc(lmk & ((1u << S.sl) - 1u));
@@ -460,13 +482,8 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
         uint64_t W = 0, rr = 0, w_sel = 0;
         int sel_e = -1, sel_p = -1;
         bool rng_fail = false;
-        bool live1 = false;  // one chunk: this lane's candidate is live (kept for the elimination)
-        int pp1 = 0;
-        if (NCH == 1) {  // both lists fit one chunk: each candidate's weight is computed once
+        if (one) {  // each candidate's weight is computed once
             const int e = beg + S.sl;
-            const bool in = alive && e < end;
-            pp1 = in ? (int)adj[e] : 0;
-            live1 = in && entry_live(deg, (const uint8_t*)nullptr, V, vrow, e, pp1 + poff);
             uint64_t w = 0;
             if (uniform) {
                 w = live1 ? (1ull << kq) : 0ull;
@@ -573,7 +590,7 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
         __syncwarp();
         // eliminate: the live neighbours of v, then of the partner, lose a degree
         int cnt = 0;
-        if (NCH == 1) {  // the candidates live before the pick, less the partner
+        if (one) {  // the candidates live before the pick, less the partner
             const bool keep = stepping && live1 && pp1 != sel_p;
             if (keep) {
                 const int pid = pp1 + poff;
