@@ -13,8 +13,11 @@
 // network logits -- so every trajectory's ln X is bit-identical to the
 // one-trajectory-per-warp kernel's.  The network evaluates both segments'
 // candidate tiles in one interleaved pass that shares the weight fragments.
-// The file is included inside pm_traj.cu's anonymous namespace, after the
-// step helpers it shares with run_group.
+// When both candidate lists fit one 16-lane chunk (the common case), each
+// candidate is read, scored and weighted once for the whole step.  The file
+// is included inside pm_traj.cu's anonymous namespace, after the step
+// helpers it shares with run_group; the scaled and uniform proposals also
+// run it in the 24-warp pair-only kernel.
 
 struct Seg {
     int h;         // segment (0: lanes 0-15, 1: lanes 16-31)
@@ -288,8 +291,7 @@ __device__ __forceinline__ void mlp_infer8x2(const DevModel* M, const uint16_t* 
 // warp's global scratch (two long-list logit buffers of n_max floats).
 template <typename Real, typename Idx, int MODE>
 __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>& V, int k, const Chunk& ch,
-                         const Plan& pl, uint8_t* sbase, uint8_t* slot, int* ctr_traj, const DevModel* Ms, int warp,
-                         int lane)
+                         const Plan& pl, uint8_t* sbase, uint8_t* slot, int* ctr_traj, const DevModel* Ms, int lane)
 {
     constexpr bool model = MODE == 1;
     const int n = V.n;
@@ -668,6 +670,6 @@ __device__ void run_chunk_pair(const TrajParams& P, const Chunk& ch, const Plan&
     if (2 * warp + 1 >= pl.groups) return;
     uint8_t* sbase = gstate + (size_t)(2 * warp) * pl.state_bytes;
     uint8_t* slot = P.slots + ((size_t)blockIdx.x * P.cta_warps + warp) * P.slot.bytes;
-    run_pair<Real, Idx, MODE>(P, P.mats + ch.k, V, ch.k, ch, pl, sbase, slot, ctr_traj, Ms, warp, lane);
+    run_pair<Real, Idx, MODE>(P, P.mats + ch.k, V, ch.k, ch, pl, sbase, slot, ctr_traj, Ms, lane);
 }
 

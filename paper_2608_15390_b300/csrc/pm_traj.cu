@@ -17,7 +17,10 @@
 //
 // A persistent CTA takes chunks of trajectories of one matrix at a time and,
 // when the plan says so, stages that matrix's adjacency (uint16 indices) in
-// shared memory for all its groups.
+// shared memory for all its groups.  Plans without inner SK or DM may run
+// two trajectories per warp instead (pm_pair.cuh); a launch of such plans
+// only, for the scaled or uniform proposal, uses the 24-warp pair-only
+// kernel.  In the PM_DEBUG build the matrix is read through checked views.
 #include <cmath>
 #include "pm_device.cuh"
 #include "pm_dm.cuh"
