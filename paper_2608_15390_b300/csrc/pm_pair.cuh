@@ -64,6 +64,17 @@ __device__ __forceinline__ int seg_sum_int(int v)
     for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
+__device__ __forceinline__ int seg_max_int(int v)
+{
+#pragma unroll
+    for (int o = 8; o; o >>= 1) {
+        const int t = __shfl_xor_sync(kFull, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+// lists at most this long are summed by their own lane (nbr_degree_sum_seg)
+constexpr int kSerialList = 24;
 __device__ __forceinline__ uint64_t seg_sum_u64(uint64_t v)
 {
 #pragma unroll
@@ -183,7 +194,8 @@ __device__ void tree_fix2_seg(const uint16_t* deg, uint32_t* tree, const TreeGeo
 
 // neighbour_degree_sum_flat for a segment: the degree sums over the live
 // neighbours of each live candidate of the chunk (lane sl holds candidate
-// sl), one pass over the concatenated lists of both segments' candidates;
+// sl).  Short lists are summed by their own lane; otherwise one pass over the
+// concatenated lists of both segments' candidates, lane f taking entry f;
 // acc: 16 ints of the segment's shared scratch.  Integer sums: identical to
 // neighbour_degree_sum.
 template <typename Idx>
@@ -195,6 +207,29 @@ __device__ __forceinline__ int nbr_degree_sum_seg(const MV<Idx>& V, const uint16
     if (live) {
         b = vrow ? V.cp[pp] : V.rp[pp];
         len = (vrow ? V.cp[pp + 1] : V.rp[pp + 1]) - b;
+    }
+    // short lists (every list of both segments at most kSerialList entries):
+    // each lane sums its own candidate's list, no cross-lane traffic
+    const int maxlen = both_max(seg_max_int(len));
+    if (maxlen <= kSerialList) {
+        entries = seg_sum_int(len);
+        int mine = 0;
+        for (int q = 0; q < len; ++q) {
+            const int pos = b + q;
+            unsigned d;
+            bool ok;
+            if (vrow) {  // the candidate is a column: its live rows
+                const int i = V.ri[pos];
+                d = deg[i];
+                ok = d != kInact && (!mask || mask[V.ce[pos]]);
+            } else {     // the candidate is a row: its live columns
+                const int j = V.ci[pos];
+                d = deg[n + j];
+                ok = d != kInact && (!mask || mask[pos]);
+            }
+            if (ok) mine += (int)d;
+        }
+        return mine;
     }
     const int incl = seg_incl_scan_int(len, S.sl);
     const int excl = incl - len;
