@@ -473,6 +473,13 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
                 const int sum_l = nbr_degree_sum_seg<Idx>(V, deg, nullptr, vrow, pp, live, S,
                                                           reinterpret_cast<int*>(feat), entries);
                 if (net && S.sl == 0) alg_bytes += (uint64_t)8 * entries + (uint64_t)16 * nl;
+                uint16_t* f0 = reinterpret_cast<uint16_t*>(sbase + 0 * (size_t)pl.state_bytes + off);
+                const uint16_t* f1 = reinterpret_cast<const uint16_t*>(sbase + 1 * (size_t)pl.state_bytes + off);
+                // at most 4 live candidates in each half (the usual minimum-degree
+                // pick): both halves share one 8-candidate tile of half 0, half 1
+                // in rows 4-7 (each candidate's network output depends on its
+                // own row of features only)
+                const bool packed = both_max(nl) <= 4;
                 if (live) {
                     float f[8];
                     cand_features<Idx>(V, deg, t, vrow, pp, sum_v, sum_l, (float)dv, lsv, cl, f);
@@ -481,18 +488,23 @@ __device__ void run_pair(const TrajParams& P, const DevMatrix* Mp, const MV<Idx>
                     lo.y = pack_bf16(f[2], f[3]);
                     lo.z = pack_bf16(f[4], f[5]);
                     lo.w = pack_bf16(f[6], f[7]);
-                    *reinterpret_cast<uint4*>(feat + li * kFS) = lo;
+                    uint16_t* row = packed ? f0 + (li + 4 * S.h) * kFS : feat + li * kFS;
+                    *reinterpret_cast<uint4*>(row) = lo;
                 }
                 __syncwarp();
                 float lg = 0.f;
-                const int NT = both_max((nl + 7) >> 3);
-                const uint16_t* f0 = reinterpret_cast<const uint16_t*>(sbase + 0 * (size_t)pl.state_bytes + off);
-                const uint16_t* f1 = reinterpret_cast<const uint16_t*>(sbase + 1 * (size_t)pl.state_bytes + off);
-                for (int tile = 0; tile < NT; ++tile) {
-                    float ya, yb;
-                    mlp_infer8x2(Ms, f0 + 8 * tile * kFS, f1 + 8 * tile * kFS, lane, ya, yb);
-                    const float va = __shfl_sync(kFull, ya, 4 * (li & 7)), vb = __shfl_sync(kFull, yb, 4 * (li & 7));
-                    if (live && (li >> 3) == tile) lg = S.h == 0 ? va : vb;
+                if (packed) {
+                    const float y = mlp_infer8(Ms, f0, lane);
+                    const float v = __shfl_sync(kFull, y, 4 * ((li & 3) + 4 * S.h));
+                    if (live) lg = v;
+                } else {
+                    const int NT = both_max((nl + 7) >> 3);
+                    for (int tile = 0; tile < NT; ++tile) {
+                        float ya, yb;
+                        mlp_infer8x2(Ms, f0 + 8 * tile * kFS, f1 + 8 * tile * kFS, lane, ya, yb);
+                        const float va = __shfl_sync(kFull, ya, 4 * (li & 7)), vb = __shfl_sync(kFull, yb, 4 * (li & 7));
+                        if (live && (li >> 3) == tile) lg = S.h == 0 ? va : vb;
+                    }
                 }
                 __syncwarp();
                 mlp_rows += nl;
